@@ -1,0 +1,150 @@
+/*
+ * sg.h -- C ABI of the GB300 stochastic Galerkin (SG) solver for the diffusion equation with a
+ * lognormal coefficient (arXiv 1910.11505).
+ *
+ * The problem (Sec. 2, Eq. Strong_PS): -div(a grad u) = f on [0,1]^2, u = 0 on the boundary,
+ * a = a_min + exp(gamma), gamma a Gaussian field with the separable exponential covariance of
+ * Eq. standard_deviation, truncated to M Karhunen-Loeve terms (Eq. aKL).  The SG discretisation
+ * (Eqs. u_discrete, dataProjection, A_q, stochastic_matrix) on a uniform n x n mesh of bilinear
+ * (Q1) elements gives K u = F with K = sum_k G_k (x) A_k.
+ *
+ * Layout shared by every entry point:
+ *   - a nodal field over the chaos basis is an N x P array, row-major, chaos index fastest:
+ *     X[j*P + b] = coefficient of psi_b at node j.  N = (n+1)^2 nodes including the Dirichlet
+ *     boundary (boundary rows are identity rows, their values are 0 in every solution);
+ *     node id j = i1 + (n+1)*i2 for the grid point (i1/n, i2/n).
+ *   - P = |J(p)| = (M+p)!/(M! p!) chaos terms of the solution, L = |J(q)| terms of the
+ *     coefficient (q = 2p by default), multi-indices in lexicographic order, last index fastest.
+ *   - Every device pointer is owned by the caller and must stay valid until the work queued on
+ *     the given stream has finished.  ``stream`` is a cudaStream_t (NULL = legacy default stream).
+ *
+ * Errors: every int-returning call gives SG_OK (0) or a negative SG_ERR_* code; sg_last_error()
+ * then returns a message (per host thread).  No call aborts the process.
+ */
+#ifndef SG_GB300_H
+#define SG_GB300_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define SG_OK 0
+#define SG_ERR_ARG (-1)            /* invalid argument or unsupported size                     */
+#define SG_ERR_CUDA (-2)           /* a CUDA runtime call failed                               */
+#define SG_ERR_OOM (-3)            /* device allocation failed                                 */
+#define SG_ERR_NAN (-4)            /* NaN or Inf met in a residual norm                        */
+#define SG_ERR_NOT_CONVERGED (-5)  /* GMRES stopped at max_iters above tolerance               */
+
+#define SG_PC_NONE 0       /* identity                                                          */
+#define SG_PC_MEAN 1       /* mean-based block diagonal I (x) ILU0(A_0) (Sec. 1, cited there)   */
+#define SG_PC_FS_GS 2      /* field split, block lower triangular P of Eq. P_preconditioner     */
+#define SG_PC_FS_JACOBI 3  /* field split, block diagonal of K                                  */
+
+#define SG_FP64 0          /* every step in FP64                                                */
+#define SG_MIXED_FP32 1    /* FP32 operator / preconditioner inside FP64 flexible GMRES + IR    */
+#define SG_MIXED_BF16 2    /* BF16-stored operator, FP32 arithmetic, inside FP64 FGMRES + IR    */
+
+typedef struct sg_handle sg_handle;
+
+/* Parameters of one SG system.  a = a_min + exp(mu + sum_n sqrt(lambda_n) b_n(x) y_n). */
+typedef struct {
+  int n;             /* cells per side of the uniform Q1 mesh of [0,1]^2, 2 <= n <= 1024      */
+  int M;             /* KL terms kept, 1 <= M <= 8                                             */
+  int p;             /* total degree of the solution chaos, 0 <= p <= 6                        */
+  int q;             /* total degree of the coefficient chaos; <= 0 selects 2p                 */
+  double sigma;      /* standard deviation of gamma (Eq. standard_deviation), >= 0             */
+  double ell;        /* correlation length L_c, > 0                                            */
+  double a_min;      /* lower bound of a (Assumption 1), >= 0                                  */
+  double mu;         /* mean of gamma                                                          */
+  double f;          /* constant forcing                                                       */
+  int precond;       /* SG_PC_*                                                                 */
+  int inner_iters;   /* ILU(0)-Richardson steps per diagonal block, >= 1                       */
+  int outer_sweeps;  /* steps of the level solver, Eq. level_solver (i_max), >= 1              */
+  int restart;       /* GMRES restart length m, 1 <= m <= 64                                   */
+  int max_iters;     /* cap on GMRES iterations (inner iterations summed over restarts)       */
+  double rtol;       /* stop when ||F - K x||_2 <= max(rtol ||F||_2, atol)                     */
+  double atol;
+  int precision;     /* SG_FP64 | SG_MIXED_FP32 | SG_MIXED_BF16                                */
+  double inner_rtol; /* mixed precision: each inner FGMRES cycle stops once its residual       */
+                     /* estimate drops below inner_rtol times the current true residual        */
+} sg_params;
+
+typedef struct {
+  int iters;         /* GMRES iterations (all cycles; inner FGMRES iterations in mixed mode)  */
+  int restarts;      /* GMRES cycles (mixed mode: refinement steps, one inner cycle each)      */
+  int status;        /* SG_OK, SG_ERR_NOT_CONVERGED or SG_ERR_NAN                              */
+  double rel_resid;  /* final true FP64 residual ||F - K x|| / ||F||                           */
+  double seconds;    /* wall time of the solve of this batch                                   */
+} sg_solve_info;
+
+/* Fill ``prm`` with defaults: n=16, M=2, p=2, q=2p, sigma=0.5, ell=1, a_min=0, mu=0, f=1,
+ * mean preconditioner, 1 inner / 1 outer step, restart 30, max_iters 2000, rtol 1e-10,
+ * atol 0, FP64, inner_rtol 1e-4. */
+void sg_default_params(sg_params* prm);
+
+/* Build ``nsys`` independent SG systems (Sec. 2: KL modes of Eq. gen_eigen in closed form,
+ * chaos coefficients of Eq. dataProjection, stiffness stack of Eq. A_q on the shared 9-point
+ * pattern, triple products G_k of Sec. 2.2, Dirichlet rows, ILU(0) factors for the chosen
+ * preconditioner) on the current CUDA device.  ``prm`` points to nsys parameter sets (host).
+ * All device memory of the systems is owned by the handle.  Work is queued on ``stream`` and
+ * the call synchronises it before returning.  On error *out is NULL. */
+int sg_setup(const sg_params* prm, int nsys, void* stream, sg_handle** out);
+
+/* Sizes of system ``sys``: N nodes, P solution chaos terms, L coefficient chaos terms. */
+int sg_dims(const sg_handle* h, int sys, int* N, int* P, int* L);
+
+/* Number of stored nonzeros of the 9-point pattern and of the triple-product tensor G. */
+int sg_nnz(const sg_handle* h, int sys, long long* nnz_A, long long* nnz_G);
+
+/* Y = K X = sum_k A_k X G_k^T (Eqs. stochastic_matrix, K_matrix); X, Y device, N x P FP64,
+ * must not overlap.  Asynchronous on ``stream``. */
+int sg_matvec(sg_handle* h, int sys, const double* X, double* Y, void* stream);
+
+/* Same operator with the FP32 (precision SG_MIXED_FP32) or BF16 (SG_MIXED_BF16) copy of the
+ * stiffness stack and FP32 arithmetic; X, Y device N x P FP32.  SG_ERR_ARG for an FP64 system. */
+int sg_matvec_lowp(sg_handle* h, int sys, const float* X, float* Y, void* stream);
+
+/* Z = P^{-1} R for the system's preconditioner, with ``outer_sweeps`` steps of Eq. level_solver
+ * from zero and ``inner_iters`` ILU(0)-Richardson steps per diagonal block; mean-based
+ * (I (x) ILU0(A_0)), field-split Gauss-Seidel (Eq. P_preconditioner) or block Jacobi.
+ * R, Z device N x P FP64, must not overlap.  Asynchronous on ``stream``. */
+int sg_precond_apply(sg_handle* h, int sys, const double* R, double* Z, void* stream);
+
+/* F of Eq. stochastic_matrix: F[j*P + 0] = int f phi_j, other chaos terms 0, boundary rows 0.
+ * F device N x P FP64.  Asynchronous on ``stream``. */
+int sg_rhs(sg_handle* h, int sys, double* F, void* stream);
+
+/* Solve K x = F for every system of the handle with restarted right-preconditioned GMRES
+ * (Sec. 3), CGS2 Arnoldi and Givens rotations on the device.  F[s], X[s] are device N x P FP64
+ * arrays; X[s] holds the initial guess on entry (zeros for a cold start) and the solution on
+ * return.  In mixed precision (SG_MIXED_*) the solve is FP64 iterative refinement around an
+ * inner flexible GMRES whose operator and preconditioner run in FP32 arithmetic; the FP64 true
+ * residual decides convergence.  ``info`` (host, nsys entries) is filled; the call returns
+ * SG_OK if every system converged, else the first failing status.  Synchronises ``stream``. */
+int sg_gmres_solve(sg_handle* h, const double* const* F, double* const* X, sg_solve_info* info,
+                   void* stream);
+
+/* Copy an internal array of system ``sys`` to host memory ``dst`` of ``bytes`` bytes, for
+ * tests: what = 0 stack values (nnz_A x L doubles, entry e and chaos k at e*L + k),
+ * 1 CSR row pointers (N+1 ints), 2 CSR columns (nnz_A ints), 3 KL eigenvalues (M doubles),
+ * 4 ILU(0) factor values of the mean block (nnz_A doubles, L strictly below the diagonal with
+ * unit diagonal implied, U on and above), 5 triple products as (k, a, b, value) records sorted by
+ * k then a then b (nnz_G x 4 doubles).  Synchronous.  SG_ERR_ARG if ``bytes`` is too small. */
+int sg_export(const sg_handle* h, int sys, int what, void* dst, size_t bytes);
+
+/* Count of kernel launches this library has queued since load (all handles, all threads). */
+long long sg_launch_count(void);
+
+/* Free every device array of the handle (after synchronising its streams).  NULL is a no-op. */
+void sg_free(sg_handle* h);
+
+/* Message of the last failing call on this host thread ("" if none). */
+const char* sg_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SG_GB300_H */

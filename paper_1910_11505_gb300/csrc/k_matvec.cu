@@ -1,0 +1,147 @@
+// The SG operator Y = sum_k A_k X G_k^T (Eqs. stochastic_matrix and K_matrix): a shared-pattern
+// CSR SpMM over the stacked stiffness values fused with the sparse contraction over the
+// triple-product tensor, row by row, so the N x L x P intermediate never exists in memory.
+//
+// For node row i with stencil entries e (column j_e):
+//   T[k,b] = sum_e A[e,k] X[j_e, b]       for the (k,b) pairs that meet a nonzero G_k[a,b]
+//   Y[i,a] = sum_{(k,b)} G_k[a,b] T[k,b]
+// which costs 9 U + nnz_G fused multiply-adds per row (U = number of such pairs), the fewest of
+// the orderings: building the dense L x P product first costs 9 L P, building K_ab first 9 nnz_G.
+//
+// One CTA works on one row at a time (persistent over rows).  The row's stencil values of a k
+// range and the 9 neighbour rows of X are staged in shared memory; T lives in shared memory for
+// one chunk of pairs; each warp owns output columns a and reduces its entries with shuffles, so
+// the result does not depend on scheduling.
+#include "sg_internal.h"
+
+namespace sg {
+
+namespace {
+
+template <typename T> __device__ __forceinline__ T load_val(const T* p) { return *p; }
+__device__ __forceinline__ float load_as_f32(const float* p) { return *p; }
+__device__ __forceinline__ float load_as_f32(const __nv_bfloat16* p) { return __bfloat162float(*p); }
+__device__ __forceinline__ double load_as_f64(const double* p) { return *p; }
+
+template <typename TA, typename TV>
+__device__ __forceinline__ TA cvt(const TV* p);
+template <> __device__ __forceinline__ double cvt<double, double>(const double* p) { return *p; }
+template <> __device__ __forceinline__ float cvt<float, float>(const float* p) { return *p; }
+template <> __device__ __forceinline__ float cvt<float, __nv_bfloat16>(const __nv_bfloat16* p) {
+  return __bfloat162float(*p);
+}
+
+template <typename TA>
+__device__ __forceinline__ TA warp_sum(TA v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+template <typename TA, typename TV>
+__global__ void __launch_bounds__(256) sg_apply_kernel(
+    int N, int P, int L, const int* __restrict__ rowptr, const int* __restrict__ col,
+    const TV* __restrict__ stack, const int* __restrict__ pair_kb, const int2* __restrict__ chunks,
+    const int2* __restrict__ chunks_k, int nchunks, const int* __restrict__ ent_ptr,
+    const int* __restrict__ ent_u, const TA* __restrict__ ent_g, const TA* __restrict__ X,
+    TA* __restrict__ Y, TA alpha, const TA* __restrict__ B, TA beta, const int* __restrict__ done) {
+  if (done != nullptr && *done) return;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  TA* As = reinterpret_cast<TA*>(smem_raw);   // 9 x kChunkK
+  TA* Xs = As + 9 * kChunkK;                  // 9 x P
+  TA* Ts = Xs + 9 * P;                        // kChunkPairs
+  TA* Ys = Ts + kChunkPairs;                  // P
+  const int tid = threadIdx.x, nth = blockDim.x;
+  const int warp = tid >> 5, lane = tid & 31, nwarp = nth >> 5;
+
+  for (int row = blockIdx.x; row < N; row += gridDim.x) {
+    const int e0 = rowptr[row];
+    const int ne = rowptr[row + 1] - e0;
+    for (int t = tid; t < ne * P; t += nth) {
+      int e = t / P, b = t - e * P;
+      Xs[t] = X[(size_t)col[e0 + e] * P + b];
+    }
+    for (int a = tid; a < P; a += nth) Ys[a] = TA(0);
+    for (int c = 0; c < nchunks; ++c) {
+      const int2 uu = chunks[c];
+      const int2 kr = chunks_k[c];
+      const int kw = kr.y - kr.x;
+      for (int t = tid; t < ne * kw; t += nth) {
+        int e = t / kw, kk = t - e * kw;
+        As[e * kChunkK + kk] = cvt<TA, TV>(stack + (size_t)(e0 + e) * L + kr.x + kk);
+      }
+      __syncthreads();
+      for (int u = uu.x + tid; u < uu.y; u += nth) {
+        int kb = pair_kb[u];
+        int kk = (kb >> 16) - kr.x, b = kb & 0xffff;
+        TA s = TA(0);
+        for (int e = 0; e < ne; ++e) s = fma(As[e * kChunkK + kk], Xs[e * P + b], s);
+        Ts[u - uu.x] = s;
+      }
+      __syncthreads();
+      const int* ep = ent_ptr + (size_t)c * (P + 1);
+      for (int a = warp; a < P; a += nwarp) {
+        TA s = TA(0);
+        for (int t = ep[a] + lane; t < ep[a + 1]; t += 32) s = fma(ent_g[t], Ts[ent_u[t]], s);
+        s = warp_sum(s);
+        if (lane == 0) Ys[a] += s;
+      }
+      __syncthreads();
+    }
+    for (int a = tid; a < P; a += nth) {
+      size_t o = (size_t)row * P + a;
+      TA v = alpha * Ys[a];
+      if (B != nullptr) v = fma(beta, B[o], v);
+      Y[o] = v;
+    }
+    __syncthreads();
+  }
+}
+
+template <typename TA>
+size_t apply_smem(int P) {
+  return sizeof(TA) * (9 * kChunkK + 9 * (size_t)P + kChunkPairs + P);
+}
+
+int num_sms() {
+  static int sms = 0;
+  if (sms == 0) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (sms <= 0) sms = 152;
+  }
+  return sms;
+}
+
+template <typename TA, typename TV>
+int launch_apply(const System& s, const TV* stack, const TA* eg, const TA* X, TA* Y, TA alpha,
+                 const TA* B, TA beta, cudaStream_t st, const int* done) {
+  size_t smem = apply_smem<TA>(s.P);
+  auto kern = sg_apply_kernel<TA, TV>;
+  SG_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  int per_sm = (int)std::max<size_t>(1, std::min<size_t>(8, (200 * 1024) / smem));
+  int grid = std::min(s.N, num_sms() * per_sm);
+  kern<<<grid, 256, smem, st>>>(s.N, s.P, s.L, s.rowptr.p, s.col.p, stack, s.pair_kb.p, s.chunks.p,
+                                s.chunks_k.p, s.op.nchunks, s.ent_ptr.p, s.ent_u.p, eg, X, Y, alpha,
+                                B, beta, done);
+  return check_launch("sg_apply");
+}
+
+}  // namespace
+
+int launch_matvec_f64(const System& s, const double* X, double* Y, double alpha, const double* B,
+                      double beta, cudaStream_t st, const int* done) {
+  return launch_apply<double, double>(s, s.stack.p, s.ent_g.p, X, Y, alpha, B, beta, st, done);
+}
+
+int launch_matvec_f32(const System& s, const float* X, float* Y, float alpha, const float* B,
+                      float beta, cudaStream_t st, const int* done) {
+  if (s.prm.precision == SG_MIXED_BF16)
+    return launch_apply<float, __nv_bfloat16>(s, s.stack_bf16.p, s.ent_g_f32.p, X, Y, alpha, B,
+                                              beta, st, done);
+  return launch_apply<float, float>(s, s.stack_f32.p, s.ent_g_f32.p, X, Y, alpha, B, beta, st,
+                                    done);
+}
+
+}  // namespace sg

@@ -1,0 +1,658 @@
+// C ABI of the SG solver (include/sg.h): setup of the systems, the operator, preconditioner and
+// right-hand-side entry points, and the restarted GMRES driver (Sec. 3) that queues whole Arnoldi
+// cycles per system on the system's own stream and synchronises once per cycle.
+#include <algorithm>
+#include <atomic>
+#include <chrono>
+#include <cmath>
+#include <cstring>
+#include <map>
+#include <mutex>
+
+#include "sg_internal.h"
+
+namespace sg {
+
+// ------------------------------------------------------------------ errors and launch counting
+
+static thread_local std::string g_last_error;
+static std::atomic<long long> g_launches{0};
+
+void set_error(const std::string& msg) { g_last_error = msg; }
+int fail(int code, const std::string& msg) {
+  set_error(msg);
+  return code;
+}
+void count_launch(int n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+int check_launch(const char* what) {
+  count_launch();
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return fail(SG_ERR_CUDA, std::string("launch of ") + what + ": " + cudaGetErrorString(e));
+  return SG_OK;
+}
+
+template <typename T>
+int DBuf<T>::alloc(size_t count) {
+  release();
+  if (count == 0) count = 1;
+  cudaError_t e = cudaMalloc((void**)&p, sizeof(T) * count);
+  if (e != cudaSuccess) {
+    p = nullptr;
+    cudaGetLastError();
+    return fail(SG_ERR_OOM, "cudaMalloc of " + std::to_string(sizeof(T) * count) + " bytes: " + cudaGetErrorString(e));
+  }
+  n = count;
+  return SG_OK;
+}
+template <typename T>
+int DBuf<T>::upload(const std::vector<T>& h, cudaStream_t s) {
+  if (h.empty()) return SG_OK;
+  if (h.size() > n) return fail(SG_ERR_ARG, "upload larger than buffer");
+  SG_CUDA(cudaMemcpyAsync(p, h.data(), sizeof(T) * h.size(), cudaMemcpyHostToDevice, s));
+  SG_CUDA(cudaStreamSynchronize(s));
+  return SG_OK;
+}
+template <typename T>
+void DBuf<T>::release() {
+  if (p) cudaFree(p);
+  p = nullptr;
+  n = 0;
+}
+template struct DBuf<double>;
+template struct DBuf<float>;
+template struct DBuf<int>;
+template struct DBuf<int2>;
+template struct DBuf<unsigned int>;
+template struct DBuf<__nv_bfloat16>;
+
+// ------------------------------------------------------------------ host tables
+
+static int validate(const sg_params& p) {
+  if (p.n < 2 || p.n > 1024) return fail(SG_ERR_ARG, "n must be in [2, 1024]");
+  if (p.M < 1 || p.M > 8) return fail(SG_ERR_ARG, "M must be in [1, 8]");
+  if (p.p < 0 || p.p > 6) return fail(SG_ERR_ARG, "p must be in [0, 6]");
+  if (p.q > 12) return fail(SG_ERR_ARG, "q must be <= 12");
+  if (!(p.sigma >= 0.0) || !(p.ell > 0.0) || !(p.a_min >= 0.0))
+    return fail(SG_ERR_ARG, "need sigma >= 0, ell > 0, a_min >= 0");
+  if (!std::isfinite(p.mu) || !std::isfinite(p.f)) return fail(SG_ERR_ARG, "mu and f must be finite");
+  if (p.precond < SG_PC_NONE || p.precond > SG_PC_FS_JACOBI) return fail(SG_ERR_ARG, "unknown preconditioner");
+  if (p.inner_iters < 1 || p.outer_sweeps < 1) return fail(SG_ERR_ARG, "inner_iters and outer_sweeps must be >= 1");
+  if (p.restart < 1 || p.restart > 64) return fail(SG_ERR_ARG, "restart must be in [1, 64]");
+  if (p.max_iters < 1) return fail(SG_ERR_ARG, "max_iters must be >= 1");
+  if (!(p.rtol >= 0.0) || !(p.atol >= 0.0)) return fail(SG_ERR_ARG, "rtol, atol must be >= 0");
+  if (p.precision < SG_FP64 || p.precision > SG_MIXED_BF16) return fail(SG_ERR_ARG, "unknown precision");
+  if (p.precision != SG_FP64 && !(p.inner_rtol > 0.0 && p.inner_rtol < 1.0))
+    return fail(SG_ERR_ARG, "inner_rtol must be in (0, 1)");
+  return SG_OK;
+}
+
+static int build_tables(System& s) {
+  const sg_params& p = s.prm;
+  std::vector<int> Jp = total_degree_set(p.M, p.p), Jq = total_degree_set(p.M, p.q);
+  s.P = (int)Jp.size() / p.M;
+  s.L = (int)Jq.size() / p.M;
+  if (s.P > 4096 || s.L > 32767) return fail(SG_ERR_ARG, "chaos basis too large");
+  // 1-D triple products e(i, j, k) for i <= q, j, k <= p
+  const int Q1 = p.q + 1, P1 = p.p + 1;
+  std::vector<double> e1((size_t)Q1 * P1 * P1);
+  for (int i = 0; i < Q1; ++i)
+    for (int j = 0; j < P1; ++j)
+      for (int k = 0; k < P1; ++k) e1[((size_t)i * P1 + j) * P1 + k] = hermite_triple(i, j, k);
+  s.triples.clear();
+  for (int k = 0; k < s.L; ++k)
+    for (int a = 0; a < s.P; ++a)
+      for (int b = 0; b < s.P; ++b) {
+        double g = 1.0;
+        for (int d = 0; d < p.M && g != 0.0; ++d)
+          g *= e1[((size_t)Jq[k * p.M + d] * P1 + Jp[a * p.M + d]) * P1 + Jp[b * p.M + d]];
+        if (g != 0.0) s.triples.push_back({k, a, b, g});
+      }
+  s.nnzG = (long long)s.triples.size();
+  // (k, b) pairs in (k, b) order and their chunks
+  std::map<std::pair<int, int>, int> pid;
+  for (auto& t : s.triples) pid[{t.k, t.b}] = 0;
+  OpTables& op = s.op;
+  op.pair_kb.clear();
+  op.chunks.clear();
+  int u = 0;
+  for (auto& kv : pid) {
+    kv.second = u++;
+    op.pair_kb.push_back((kv.first.first << 16) | kv.first.second);
+  }
+  op.npairs = u;
+  std::vector<int> chunk_of(u);
+  for (int v = 0; v < u; ++v) {
+    int k = op.pair_kb[v] >> 16;
+    if (op.chunks.empty() || op.chunks.back().u1 - op.chunks.back().u0 >= kChunkPairs ||
+        k - op.chunks.back().k0 >= kChunkK) {
+      op.chunks.push_back({v, v, k, k});
+    }
+    op.chunks.back().u1 = v + 1;
+    op.chunks.back().k1 = k + 1;
+    chunk_of[v] = (int)op.chunks.size() - 1;
+  }
+  op.nchunks = (int)op.chunks.size();
+  // entries per (chunk, a), sorted by pair
+  std::vector<std::vector<std::pair<int, double>>> bucket((size_t)op.nchunks * s.P);
+  for (auto& t : s.triples) {
+    int v = pid[{t.k, t.b}];
+    int c = chunk_of[v];
+    bucket[(size_t)c * s.P + t.a].push_back({v - op.chunks[c].u0, t.g});
+  }
+  op.ent_ptr.assign((size_t)op.nchunks * (s.P + 1), 0);
+  op.ent_u.clear();
+  op.ent_g.clear();
+  for (int c = 0; c < op.nchunks; ++c) {
+    for (int a = 0; a < s.P; ++a) {
+      auto& bk = bucket[(size_t)c * s.P + a];
+      std::sort(bk.begin(), bk.end());
+      op.ent_ptr[(size_t)c * (s.P + 1) + a] = (int)op.ent_u.size();
+      for (auto& pr : bk) {
+        op.ent_u.push_back(pr.first);
+        op.ent_g.push_back(pr.second);
+      }
+    }
+    op.ent_ptr[(size_t)c * (s.P + 1) + s.P] = (int)op.ent_u.size();
+  }
+  op.nent = (int)op.ent_u.size();
+  return SG_OK;
+}
+
+static int upload_i(DBuf<int>& d, const std::vector<int>& h, cudaStream_t st) {
+  SG_TRY(d.alloc(h.size()));
+  return d.upload(h, st);
+}
+static int upload_d(DBuf<double>& d, const std::vector<double>& h, cudaStream_t st) {
+  SG_TRY(d.alloc(h.size()));
+  return d.upload(h, st);
+}
+static int upload_f(DBuf<float>& d, const std::vector<double>& h, cudaStream_t st) {
+  std::vector<float> f(h.begin(), h.end());
+  SG_TRY(d.alloc(f.size()));
+  return d.upload(f, st);
+}
+
+// Field-split Gauss-Seidel tables: for source block b, the k that couple b to some a > b and,
+// per a > b, the (k index, G_k[a,b]) entries.
+static int build_gs_tables(System& s, cudaStream_t st) {
+  std::vector<int> kptr(s.P + 1, 0), klist, eptr((size_t)s.P * (s.P + 1), 0), ea;
+  std::vector<double> eg;
+  s.gs_max_klen = 0;
+  for (int b = 0; b < s.P; ++b) {
+    std::vector<int> ks;
+    for (auto& t : s.triples)
+      if (t.b == b && t.a > b) ks.push_back(t.k);
+    std::sort(ks.begin(), ks.end());
+    ks.erase(std::unique(ks.begin(), ks.end()), ks.end());
+    kptr[b] = (int)klist.size();
+    klist.insert(klist.end(), ks.begin(), ks.end());
+    s.gs_max_klen = std::max(s.gs_max_klen, (int)ks.size());
+    std::vector<std::vector<std::pair<int, double>>> per_a(s.P);
+    for (auto& t : s.triples)
+      if (t.b == b && t.a > b) {
+        int kl = (int)(std::lower_bound(ks.begin(), ks.end(), t.k) - ks.begin());
+        per_a[t.a].push_back({kl, t.g});
+      }
+    for (int a = 0; a < s.P; ++a) {
+      eptr[(size_t)b * (s.P + 1) + a] = (int)ea.size();
+      std::sort(per_a[a].begin(), per_a[a].end());
+      for (auto& pr : per_a[a]) {
+        ea.push_back(pr.first);
+        eg.push_back(pr.second);
+      }
+    }
+    eptr[(size_t)b * (s.P + 1) + s.P] = (int)ea.size();
+  }
+  kptr[s.P] = (int)klist.size();
+  SG_TRY(upload_i(s.gs_kptr, kptr, st));
+  SG_TRY(upload_i(s.gs_k, klist, st));
+  SG_TRY(upload_i(s.gs_eptr, eptr, st));
+  SG_TRY(upload_i(s.gs_ea, ea, st));
+  SG_TRY(upload_d(s.gs_eg, eg, st));
+  if (s.prm.precision != SG_FP64) SG_TRY(upload_f(s.gs_eg_f32, eg, st));
+  return SG_OK;
+}
+
+static void free_system(System* s) {
+  if (!s) return;
+  if (s->stream) cudaStreamSynchronize(s->stream);
+  DBuf<int>* ib[] = {&s->rowptr, &s->col, &s->diag, &s->lev_f_ptr, &s->lev_f_rows, &s->lev_b_ptr,
+                     &s->lev_b_rows, &s->pair_kb, &s->ent_ptr, &s->ent_u, &s->gs_kptr, &s->gs_k,
+                     &s->gs_eptr, &s->gs_ea, &s->flags};
+  for (auto* b : ib) b->release();
+  DBuf<double>* db[] = {&s->stack, &s->ent_g, &s->blk, &s->fac, &s->gs_eg, &s->acc, &s->tmp,
+                        &s->tmp2, &s->tri_w, &s->V, &s->Z, &s->Hs, &s->cs, &s->sn, &s->g, &s->y,
+                        &s->scal, &s->red, &s->rvec};
+  for (auto* b : db) b->release();
+  DBuf<float>* fb[] = {&s->stack_f32, &s->ent_g_f32, &s->fac_f32, &s->blk_f32, &s->gs_eg_f32,
+                       &s->acc32, &s->tmp32, &s->tmp232, &s->tri_w32, &s->V32, &s->Z32,
+                       &s->mv32a, &s->mv32b};
+  for (auto* b : fb) b->release();
+  s->stack_bf16.release();
+  s->chunks.release();
+  s->chunks_k.release();
+  s->ticket.release();
+  if (s->hpin) cudaFreeHost(s->hpin);
+  if (s->ev) cudaEventDestroy(s->ev);
+  if (s->stream) cudaStreamDestroy(s->stream);
+  delete s;
+}
+
+static int setup_system(System& s, cudaStream_t st) {
+  sg_params& p = s.prm;
+  if (p.q <= 0) p.q = 2 * p.p;
+  s.n = p.n;
+  s.M = p.M;
+  s.pat = make_pattern(p.n);
+  s.N = s.pat.N;
+  s.kl = kl_terms_2d(p.sigma, p.ell, p.M);
+  SG_TRY(build_tables(s));
+  const bool lowp = p.precision != SG_FP64;
+  // smem budgets of the kernels
+  size_t apply_smem = sizeof(double) * (9 * kChunkK + 9 * (size_t)s.P + kChunkPairs + s.P);
+  if (apply_smem > 200 * 1024) return fail(SG_ERR_ARG, "P too large for the operator kernel");
+  s.tri_smem = (size_t)s.N * sizeof(double) <= 200 * 1024;
+  s.tri_smem32 = (size_t)s.N * sizeof(float) <= 200 * 1024;
+
+  SG_CUDA(cudaStreamCreateWithFlags(&s.stream, cudaStreamNonBlocking));
+  SG_CUDA(cudaEventCreateWithFlags(&s.ev, cudaEventDisableTiming));
+  SG_CUDA(cudaMallocHost((void**)&s.hpin, 16 * sizeof(double)));
+
+  SG_TRY(upload_i(s.rowptr, s.pat.rowptr, st));
+  SG_TRY(upload_i(s.col, s.pat.col, st));
+  SG_TRY(upload_i(s.diag, s.pat.diag, st));
+  SG_TRY(upload_i(s.lev_f_ptr, s.pat.lev_f_ptr, st));
+  SG_TRY(upload_i(s.lev_f_rows, s.pat.lev_f_rows, st));
+  SG_TRY(upload_i(s.lev_b_ptr, s.pat.lev_b_ptr, st));
+  SG_TRY(upload_i(s.lev_b_rows, s.pat.lev_b_rows, st));
+
+  // operator tables
+  SG_TRY(upload_i(s.pair_kb, s.op.pair_kb, st));
+  SG_TRY(upload_i(s.ent_ptr, s.op.ent_ptr, st));
+  SG_TRY(upload_i(s.ent_u, s.op.ent_u, st));
+  SG_TRY(upload_d(s.ent_g, s.op.ent_g, st));
+  if (lowp) SG_TRY(upload_f(s.ent_g_f32, s.op.ent_g, st));
+  {
+    std::vector<int2> cu(s.op.nchunks), ck(s.op.nchunks);
+    for (int c = 0; c < s.op.nchunks; ++c) {
+      cu[c] = make_int2(s.op.chunks[c].u0, s.op.chunks[c].u1);
+      ck[c] = make_int2(s.op.chunks[c].k0, s.op.chunks[c].k1);
+    }
+    SG_TRY(s.chunks.alloc(cu.size()));
+    SG_TRY(s.chunks.upload(cu, st));
+    SG_TRY(s.chunks_k.alloc(ck.size()));
+    SG_TRY(s.chunks_k.upload(ck, st));
+  }
+
+  // stiffness stack
+  const size_t nnzL = (size_t)s.pat.nnz * s.L;
+  SG_TRY(s.stack.alloc(nnzL));
+  {
+    DBuf<double> qp;
+    SG_TRY(qp.alloc((size_t)p.n * p.n * 9 * (p.M + 1)));
+    SG_TRY(launch_qp_table(s, qp.p, st));
+    SG_TRY(launch_assemble(s, qp.p, st));
+    SG_CUDA(cudaStreamSynchronize(st));
+    qp.release();
+  }
+  if (p.precision == SG_MIXED_FP32) {
+    SG_TRY(s.stack_f32.alloc(nnzL));
+    SG_TRY(launch_cast_f32(s.stack.p, s.stack_f32.p, nnzL, st));
+  } else if (p.precision == SG_MIXED_BF16) {
+    SG_TRY(s.stack_bf16.alloc(nnzL));
+    SG_TRY(launch_cast_bf16(s.stack.p, s.stack_bf16.p, nnzL, st));
+  }
+
+  // preconditioner blocks and factors
+  const size_t NP = (size_t)s.N * s.P;
+  if (p.precond == SG_PC_MEAN || p.precond == SG_PC_FS_GS || p.precond == SG_PC_FS_JACOBI) {
+    s.nfac = p.precond == SG_PC_MEAN ? 1 : s.P;
+    SG_TRY(s.blk.alloc((size_t)s.nfac * s.pat.nnz));
+    SG_TRY(s.fac.alloc((size_t)s.nfac * s.pat.nnz));
+    SG_TRY(launch_block_values(s, st));
+    SG_TRY(launch_ilu0(s, st));
+    if (lowp) {
+      SG_TRY(s.fac_f32.alloc(s.fac.n));
+      SG_TRY(s.blk_f32.alloc(s.blk.n));
+      SG_TRY(launch_cast_f32(s.fac.p, s.fac_f32.p, s.fac.n, st));
+      SG_TRY(launch_cast_f32(s.blk.p, s.blk_f32.p, s.blk.n, st));
+    }
+    if (p.precond == SG_PC_FS_GS) {
+      SG_TRY(build_gs_tables(s, st));
+      SG_TRY(s.acc.alloc(NP));
+      if (lowp) SG_TRY(s.acc32.alloc(NP));
+    }
+    if (!s.tri_smem) SG_TRY(s.tri_w.alloc(NP));
+    if (lowp && !s.tri_smem32) SG_TRY(s.tri_w32.alloc(NP));
+  }
+  if (p.outer_sweeps > 1) {
+    SG_TRY(s.tmp.alloc(NP));
+    SG_TRY(s.tmp2.alloc(NP));
+    if (lowp) {
+      SG_TRY(s.tmp32.alloc(NP));
+      SG_TRY(s.tmp232.alloc(NP));
+    }
+  }
+
+  // GMRES workspace
+  s.m = p.restart;
+  const int mb = krylov_max_basis();
+  SG_TRY(s.V.alloc((size_t)(s.m + 1) * NP));
+  if (lowp) {
+    SG_TRY(s.Z32.alloc((size_t)s.m * NP));
+    SG_TRY(s.mv32a.alloc(NP));
+    SG_TRY(s.mv32b.alloc(NP));
+  } else {
+    SG_TRY(s.Z.alloc((size_t)s.m * NP));
+  }
+  SG_TRY(s.rvec.alloc(NP));
+  SG_TRY(s.Hs.alloc((size_t)(s.m + 1) * (s.m + 1)));
+  SG_TRY(s.cs.alloc(mb));
+  SG_TRY(s.sn.alloc(mb));
+  SG_TRY(s.g.alloc(mb + 1));
+  SG_TRY(s.y.alloc(3 * mb));
+  SG_TRY(s.scal.alloc(8));
+  SG_TRY(s.red.alloc((size_t)krylov_red_blocks() * mb));
+  SG_TRY(s.flags.alloc(4));
+  SG_TRY(s.ticket.alloc(4));
+  SG_CUDA(cudaMemsetAsync(s.ticket.p, 0, 4 * sizeof(unsigned int), st));
+  SG_CUDA(cudaMemsetAsync(s.flags.p, 0, 4 * sizeof(int), st));
+  SG_CUDA(cudaMemsetAsync(s.scal.p, 0, 8 * sizeof(double), st));
+  SG_CUDA(cudaStreamSynchronize(st));
+  return SG_OK;
+}
+
+static System* get_sys(const sg_handle* h, int sys) {
+  if (!h || sys < 0 || sys >= (int)h->sys.size()) return nullptr;
+  return h->sys[sys];
+}
+
+// ------------------------------------------------------------------ GMRES driver
+
+struct SolveState {
+  System* s;
+  const double* F;
+  double* X;
+  double target = 0, bnorm = 0, beta = 0, prev_beta = 0;
+  int iters = 0, restarts = 0, status = SG_OK;
+  bool active = true;
+  int jmax = 0;
+};
+
+static int iteration(System& s, int j, int last_col) {
+  const size_t n = (size_t)s.N * s.P;
+  cudaStream_t st = s.stream;
+  const int* done = s.flags.p;
+  double* vj = s.V.p + (size_t)j * n;
+  double* w = s.V.p + (size_t)(j + 1) * n;
+  if (s.prm.precision == SG_FP64) {
+    double* zj = s.Z.p + (size_t)j * n;
+    SG_TRY(precond_apply_f64(s, vj, zj, st, done));
+    SG_TRY(launch_matvec_f64(s, zj, w, 1.0, nullptr, 0.0, st, done));
+  } else {
+    float* z32 = s.Z32.p + (size_t)j * n;
+    SG_TRY(k_to_f32(n, vj, s.mv32a.p, done, st));
+    SG_TRY(precond_apply_f32(s, s.mv32a.p, z32, st, done));
+    SG_TRY(launch_matvec_f32(s, z32, s.mv32b.p, 1.0f, nullptr, 0.0f, st, done));
+    SG_TRY(k_to_f64(n, s.mv32b.p, w, done, st));
+  }
+  return k_arnoldi(s, n, j, last_col, st);
+}
+
+// r = F - K x, beta = ||r||, mirrored to host with the cycle flags.
+static int residual(SolveState& ss) {
+  System& s = *ss.s;
+  const size_t n = (size_t)s.N * s.P;
+  SG_TRY(launch_matvec_f64(s, ss.X, s.rvec.p, -1.0, ss.F, 1.0, s.stream));
+  SG_TRY(k_norm(s, n, s.rvec.p, s.scal.p + 1, s.stream));
+  SG_CUDA(cudaMemcpyAsync(s.hpin, s.scal.p, 4 * sizeof(double), cudaMemcpyDeviceToHost, s.stream));
+  SG_CUDA(cudaMemcpyAsync(s.hpin + 4, s.flags.p, 4 * sizeof(int), cudaMemcpyDeviceToHost, s.stream));
+  return SG_OK;
+}
+
+int gmres_solve_all(sg_handle* h, const double* const* F, double* const* X, sg_solve_info* info,
+                    cudaStream_t user) {
+  auto t0 = std::chrono::steady_clock::now();
+  const int ns = (int)h->sys.size();
+  std::vector<SolveState> st(ns);
+  cudaEvent_t start;
+  SG_CUDA(cudaEventCreateWithFlags(&start, cudaEventDisableTiming));
+  SG_CUDA(cudaEventRecord(start, user));
+  for (int i = 0; i < ns; ++i) {
+    System& s = *h->sys[i];
+    st[i].s = &s;
+    st[i].F = F[i];
+    st[i].X = X[i];
+    SG_CUDA(cudaStreamWaitEvent(s.stream, start, 0));
+    SG_TRY(k_norm(s, (size_t)s.N * s.P, F[i], s.scal.p + 2, s.stream));
+    SG_TRY(residual(st[i]));
+  }
+  cudaEventDestroy(start);
+  for (int i = 0; i < ns; ++i) {
+    System& s = *st[i].s;
+    SG_CUDA(cudaStreamSynchronize(s.stream));
+    st[i].bnorm = s.hpin[2];
+    st[i].beta = s.hpin[1];
+    st[i].target = std::max(s.prm.rtol * st[i].bnorm, s.prm.atol);
+    st[i].prev_beta = st[i].beta;
+    if (!std::isfinite(st[i].beta) || !std::isfinite(st[i].bnorm)) st[i].status = SG_ERR_NAN;
+    if (st[i].bnorm == 0.0 && st[i].status == SG_OK) {  // K x = 0 has the solution x = 0
+      SG_CUDA(cudaMemsetAsync(st[i].X, 0, sizeof(double) * (size_t)s.N * s.P, s.stream));
+      st[i].beta = 0.0;
+    }
+  }
+  while (true) {
+    int maxj = 0;
+    for (auto& q : st) {
+      System& s = *q.s;
+      q.active = q.status == SG_OK && q.beta > q.target && q.iters < s.prm.max_iters;
+      if (!q.active) continue;
+      double cyc = q.target;
+      if (s.prm.precision != SG_FP64) cyc = std::max(q.target, s.prm.inner_rtol * q.beta);
+      s.hpin[0] = cyc;
+      SG_CUDA(cudaMemcpyAsync(s.scal.p, s.hpin, sizeof(double), cudaMemcpyHostToDevice, s.stream));
+      SG_TRY(k_init_cycle(s, (size_t)s.N * s.P, s.rvec.p, s.stream));
+      q.jmax = std::min(s.m, s.prm.max_iters - q.iters);
+      maxj = std::max(maxj, q.jmax);
+    }
+    if (maxj == 0) break;
+    for (int j = 0; j < maxj; ++j)
+      for (auto& q : st)
+        if (q.active && j < q.jmax) SG_TRY(iteration(*q.s, j, q.jmax - 1));
+    for (auto& q : st) {
+      if (!q.active) continue;
+      System& s = *q.s;
+      SG_TRY(k_finish_cycle(s, (size_t)s.N * s.P, q.X, s.prm.precision != SG_FP64, s.stream));
+      SG_TRY(residual(q));
+    }
+    for (auto& q : st) {
+      if (!q.active) continue;
+      System& s = *q.s;
+      SG_CUDA(cudaStreamSynchronize(s.stream));
+      const int* fl = reinterpret_cast<const int*>(s.hpin + 4);
+      q.iters += fl[1];
+      q.restarts += 1;
+      q.prev_beta = q.beta;
+      q.beta = s.hpin[1];
+      if (fl[2] != SG_OK || !std::isfinite(q.beta)) q.status = SG_ERR_NAN;
+      // a refinement step that does not reduce the true residual cannot make progress
+      if (s.prm.precision != SG_FP64 && q.beta > q.target && q.beta >= q.prev_beta)
+        q.status = SG_ERR_NOT_CONVERGED;
+      if (fl[1] == 0 && q.beta > q.target && q.status == SG_OK) q.status = SG_ERR_NOT_CONVERGED;
+    }
+  }
+  int rc = SG_OK;
+  double secs = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+  for (int i = 0; i < ns; ++i) {
+    auto& q = st[i];
+    if (q.status == SG_OK && q.beta > q.target) q.status = SG_ERR_NOT_CONVERGED;
+    info[i].iters = q.iters;
+    info[i].restarts = q.restarts;
+    info[i].status = q.status;
+    info[i].rel_resid = q.bnorm > 0 ? q.beta / q.bnorm : 0.0;
+    info[i].seconds = secs;
+    if (q.status != SG_OK && rc == SG_OK) rc = q.status;
+    SG_CUDA(cudaEventRecord(q.s->ev, q.s->stream));
+    SG_CUDA(cudaStreamWaitEvent(user, q.s->ev, 0));
+  }
+  SG_CUDA(cudaStreamSynchronize(user));
+  if (rc != SG_OK) set_error(rc == SG_ERR_NAN ? "NaN or Inf in a residual" : "GMRES did not reach the tolerance");
+  return rc;
+}
+
+}  // namespace sg
+
+using namespace sg;
+
+// ------------------------------------------------------------------ C ABI
+
+extern "C" {
+
+void sg_default_params(sg_params* p) {
+  if (!p) return;
+  std::memset(p, 0, sizeof(*p));
+  p->n = 16;
+  p->M = 2;
+  p->p = 2;
+  p->q = 0;
+  p->sigma = 0.5;
+  p->ell = 1.0;
+  p->a_min = 0.0;
+  p->mu = 0.0;
+  p->f = 1.0;
+  p->precond = SG_PC_MEAN;
+  p->inner_iters = 1;
+  p->outer_sweeps = 1;
+  p->restart = 30;
+  p->max_iters = 2000;
+  p->rtol = 1e-10;
+  p->atol = 0.0;
+  p->precision = SG_FP64;
+  p->inner_rtol = 1e-4;
+}
+
+int sg_setup(const sg_params* prm, int nsys, void* stream, sg_handle** out) {
+  if (!out) return fail(SG_ERR_ARG, "out is NULL");
+  *out = nullptr;
+  if (!prm || nsys < 1) return fail(SG_ERR_ARG, "need nsys >= 1 parameter sets");
+  for (int i = 0; i < nsys; ++i) SG_TRY(validate(prm[i]));
+  cudaStream_t st = (cudaStream_t)stream;
+  sg_handle* h = new sg_handle();
+  cudaGetDevice(&h->device);
+  for (int i = 0; i < nsys; ++i) {
+    System* s = new System();
+    s->prm = prm[i];
+    h->sys.push_back(s);
+    int rc = setup_system(*s, st);
+    if (rc != SG_OK) {
+      std::string msg = g_last_error;
+      sg_free(h);
+      return fail(rc, "system " + std::to_string(i) + ": " + msg);
+    }
+  }
+  return SG_OK;
+}
+
+int sg_dims(const sg_handle* h, int sys, int* N, int* P, int* L) {
+  System* s = get_sys(h, sys);
+  if (!s) return fail(SG_ERR_ARG, "bad handle or system index");
+  if (N) *N = s->N;
+  if (P) *P = s->P;
+  if (L) *L = s->L;
+  return SG_OK;
+}
+
+int sg_nnz(const sg_handle* h, int sys, long long* nnz_A, long long* nnz_G) {
+  System* s = get_sys(h, sys);
+  if (!s) return fail(SG_ERR_ARG, "bad handle or system index");
+  if (nnz_A) *nnz_A = s->pat.nnz;
+  if (nnz_G) *nnz_G = s->nnzG;
+  return SG_OK;
+}
+
+int sg_matvec(sg_handle* h, int sys, const double* X, double* Y, void* stream) {
+  System* s = get_sys(h, sys);
+  if (!s || !X || !Y) return fail(SG_ERR_ARG, "bad handle, system index or pointer");
+  return launch_matvec_f64(*s, X, Y, 1.0, nullptr, 0.0, (cudaStream_t)stream);
+}
+
+int sg_matvec_lowp(sg_handle* h, int sys, const float* X, float* Y, void* stream) {
+  System* s = get_sys(h, sys);
+  if (!s || !X || !Y) return fail(SG_ERR_ARG, "bad handle, system index or pointer");
+  if (s->prm.precision == SG_FP64) return fail(SG_ERR_ARG, "system has no low-precision stack");
+  return launch_matvec_f32(*s, X, Y, 1.0f, nullptr, 0.0f, (cudaStream_t)stream);
+}
+
+int sg_precond_apply(sg_handle* h, int sys, const double* R, double* Z, void* stream) {
+  System* s = get_sys(h, sys);
+  if (!s || !R || !Z) return fail(SG_ERR_ARG, "bad handle, system index or pointer");
+  return precond_apply_f64(*s, R, Z, (cudaStream_t)stream);
+}
+
+int sg_rhs(sg_handle* h, int sys, double* F, void* stream) {
+  System* s = get_sys(h, sys);
+  if (!s || !F) return fail(SG_ERR_ARG, "bad handle, system index or pointer");
+  return launch_rhs(*s, F, (cudaStream_t)stream);
+}
+
+int sg_gmres_solve(sg_handle* h, const double* const* F, double* const* X, sg_solve_info* info,
+                   void* stream) {
+  if (!h || !F || !X || !info) return fail(SG_ERR_ARG, "NULL argument");
+  for (size_t i = 0; i < h->sys.size(); ++i)
+    if (!F[i] || !X[i]) return fail(SG_ERR_ARG, "NULL F or X for system " + std::to_string(i));
+  return gmres_solve_all(h, F, X, info, (cudaStream_t)stream);
+}
+
+int sg_export(const sg_handle* h, int sys, int what, void* dst, size_t bytes) {
+  System* s = get_sys(h, sys);
+  if (!s || !dst) return fail(SG_ERR_ARG, "bad handle, system index or pointer");
+  const void* src = nullptr;
+  size_t need = 0;
+  std::vector<double> tmp;
+  switch (what) {
+    case 0: src = s->stack.p; need = sizeof(double) * (size_t)s->pat.nnz * s->L; break;
+    case 1: src = s->pat.rowptr.data(); need = sizeof(int) * (s->N + 1); break;
+    case 2: src = s->pat.col.data(); need = sizeof(int) * s->pat.nnz; break;
+    case 3:
+      for (auto& t : s->kl) tmp.push_back(t.lam);
+      src = tmp.data();
+      need = sizeof(double) * tmp.size();
+      break;
+    case 4:
+      if (!s->fac.p || s->prm.precond != SG_PC_MEAN) return fail(SG_ERR_ARG, "no mean-block ILU factors");
+      src = s->fac.p;
+      need = sizeof(double) * s->pat.nnz;
+      break;
+    case 5:
+      for (auto& t : s->triples) {
+        tmp.push_back(t.k);
+        tmp.push_back(t.a);
+        tmp.push_back(t.b);
+        tmp.push_back(t.g);
+      }
+      src = tmp.data();
+      need = sizeof(double) * tmp.size();
+      break;
+    default: return fail(SG_ERR_ARG, "unknown export selector");
+  }
+  if (bytes < need) return fail(SG_ERR_ARG, "destination too small: need " + std::to_string(need));
+  if (what == 0 || what == 4) {
+    SG_CUDA(cudaDeviceSynchronize());
+    SG_CUDA(cudaMemcpy(dst, src, need, cudaMemcpyDeviceToHost));
+  } else {
+    std::memcpy(dst, src, need);
+  }
+  return SG_OK;
+}
+
+long long sg_launch_count(void) { return g_launches.load(); }
+
+void sg_free(sg_handle* h) {
+  if (!h) return;
+  for (auto* s : h->sys) free_system(s);
+  delete h;
+}
+
+const char* sg_last_error(void) { return g_last_error.c_str(); }
+
+}  // extern "C"

@@ -1,0 +1,203 @@
+// Internal declarations shared by the translation units of the SG solver library.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/sg.h"
+
+namespace sg {
+
+// ------------------------------------------------------------------ errors
+
+void set_error(const std::string& msg);
+int fail(int code, const std::string& msg);
+
+struct Status {
+  int code = SG_OK;
+  std::string msg;
+};
+
+#define SG_CUDA(call)                                                                  \
+  do {                                                                                 \
+    cudaError_t e_ = (call);                                                           \
+    if (e_ != cudaSuccess)                                                             \
+      return ::sg::fail(SG_ERR_CUDA, std::string(#call " failed: ") + cudaGetErrorString(e_) + \
+                                         " at " __FILE__ ":" + std::to_string(__LINE__)); \
+  } while (0)
+
+#define SG_TRY(call)            \
+  do {                          \
+    int rc_ = (call);           \
+    if (rc_ != SG_OK) return rc_; \
+  } while (0)
+
+void count_launch(int n = 1);
+int check_launch(const char* what);
+
+// ------------------------------------------------------------------ device buffers
+
+template <typename T>
+struct DBuf {
+  T* p = nullptr;
+  size_t n = 0;
+  int alloc(size_t count);
+  int upload(const std::vector<T>& h, cudaStream_t s);
+  void release();
+};
+
+// ------------------------------------------------------------------ host-side setup math
+
+// One 1-D Karhunen-Loeve mode of the kernel exp(-|s-t|/ell) on [0,1], t = x - 1/2:
+// even: cos(w t)/nrm, odd: sin(w t)/nrm, eigenvalue mu = 2c/(w^2+c^2), c = 1/ell.
+struct KL1 {
+  double w, nrm, mu;
+  int odd;
+};
+
+struct KLTerm {  // one 2-D term: sqrt(lambda) f_i(x1) f_j(x2)
+  KL1 fx, fy;
+  double sqrt_lam;
+  double lam;
+  int i, j;
+};
+
+std::vector<KL1> kl_modes_1d(double ell, int count);
+std::vector<KLTerm> kl_terms_2d(double sigma, double ell, int M);
+std::vector<int> total_degree_set(int M, int p);  // |J| x M, lexicographic, last index fastest
+double hermite_triple(int i, int j, int k);
+
+struct Pattern {  // 9-point Q1 pattern, CSR with sorted columns
+  int n = 0, m = 0, N = 0, nnz = 0;
+  std::vector<int> rowptr, col, diag;
+  std::vector<int> lev_f_ptr, lev_f_rows, lev_b_ptr, lev_b_rows;  // wavefront levels
+  int max_width = 0;
+};
+Pattern make_pattern(int n);
+
+// ------------------------------------------------------------------ matvec work tables
+
+// The SG operator per node row i: T[k,b] = sum_e A[e,k] X[col_e, b] for every (k,b) pair that
+// meets a nonzero G_k[a,b]; then Y[i,a] = sum G_k[a,b] T[k,b].  Pairs are sorted by (k, b) and cut
+// into chunks of at most kChunkPairs pairs spanning at most kChunkK consecutive k.
+constexpr int kChunkPairs = 2048;
+constexpr int kChunkK = 256;
+
+struct ChunkDesc {
+  int u0, u1;  // pair range
+  int k0, k1;  // k range (inclusive k0, exclusive k1)
+};
+
+struct OpTables {
+  int npairs = 0, nent = 0, nchunks = 0;
+  std::vector<int> pair_kb;    // k << 16 | b
+  std::vector<ChunkDesc> chunks;
+  std::vector<int> ent_ptr;    // nchunks x (P + 1), offsets into ent_u / ent_g
+  std::vector<int> ent_u;      // pair index local to the chunk
+  std::vector<double> ent_g;   // G_k[a,b]
+};
+
+struct Triple {
+  int k, a, b;
+  double g;
+};
+
+// ------------------------------------------------------------------ per-system state
+
+struct System {
+  sg_params prm;
+  int N = 0, P = 0, L = 0, M = 0, n = 0;
+  long long nnzG = 0;
+  Pattern pat;
+  std::vector<KLTerm> kl;
+  std::vector<Triple> triples;  // sorted by k, a, b
+  OpTables op;
+
+  // device: pattern
+  DBuf<int> rowptr, col, diag, lev_f_ptr, lev_f_rows, lev_b_ptr, lev_b_rows;
+  // device: operator
+  DBuf<double> stack;          // nnz x L
+  DBuf<float> stack_f32;       // nnz x L (SG_MIXED_FP32)
+  DBuf<__nv_bfloat16> stack_bf16;  // nnz x L (SG_MIXED_BF16)
+  DBuf<int> pair_kb, ent_ptr, ent_u;
+  DBuf<int2> chunks;           // (u0 | u1 packed as two ints), k range in chunks_k
+  DBuf<int2> chunks_k;
+  DBuf<double> ent_g;
+  DBuf<float> ent_g_f32;
+  // device: preconditioner
+  int nfac = 0;                // number of factor sets (1 for mean, P for field split)
+  DBuf<double> blk;            // nfac x nnz block matrices (A_0 or K_aa) before factorisation
+  DBuf<double> fac;            // nfac x nnz ILU(0) factors
+  DBuf<float> fac_f32;         // FP32 copy for the mixed inner solver
+  DBuf<float> blk_f32;
+  // field-split Gauss-Seidel scatter tables, per source block b: k list and (a, g) entries
+  DBuf<int> gs_kptr, gs_k, gs_eptr, gs_ea;
+  DBuf<double> gs_eg;
+  DBuf<float> gs_eg_f32;
+  int gs_max_klen = 0;
+  // device scratch
+  DBuf<double> acc;            // N x P  field-split off-diagonal accumulator
+  DBuf<double> tmp, tmp2;      // N x P
+  DBuf<double> tri_w;          // N x P  triangular-solve work (global variant)
+  DBuf<float> acc32, tmp32, tmp232, tri_w32;
+  bool tri_smem = true;        // whether one column fits in shared memory
+  bool tri_smem32 = true;
+  // GMRES workspace
+  int m = 0;
+  DBuf<double> V, Z, Hs, cs, sn, g, y, scal, red;  // see krylov.cu
+  DBuf<int> flags;
+  DBuf<unsigned int> ticket;
+  DBuf<float> V32, Z32;        // inner FGMRES basis for mixed precision (FP32 vectors)
+  DBuf<double> rvec;           // FP64 residual r = F - K x
+  DBuf<float> mv32a, mv32b;    // FP32 operand / result of the inner operator
+  double* hpin = nullptr;      // pinned host mirror of state[0..3] and flags[0..2]
+  cudaStream_t stream = nullptr;
+  cudaEvent_t ev = nullptr;
+};
+
+}  // namespace sg
+
+struct sg_handle {
+  std::vector<sg::System*> sys;
+  int device = 0;
+};
+
+namespace sg {
+
+// ------------------------------------------------------------------ kernels (launchers)
+
+int launch_qp_table(System& s, double* qp, cudaStream_t st);
+int launch_assemble(System& s, const double* qp, cudaStream_t st);
+int launch_rhs(System& s, double* F, cudaStream_t st);
+int launch_block_values(System& s, cudaStream_t st);
+int launch_ilu0(System& s, cudaStream_t st);
+int launch_cast_f32(const double* src, float* dst, size_t n, cudaStream_t st);
+int launch_cast_bf16(const double* src, __nv_bfloat16* dst, size_t n, cudaStream_t st);
+int launch_cast_f64(const float* src, double* dst, size_t n, cudaStream_t st);
+
+// Y = alpha * K X + beta * B  (B may be null when beta == 0)
+int launch_matvec_f64(const System& s, const double* X, double* Y, double alpha, const double* B,
+                      double beta, cudaStream_t st, const int* done = nullptr);
+int launch_matvec_f32(const System& s, const float* X, float* Y, float alpha, const float* B,
+                      float beta, cudaStream_t st, const int* done = nullptr);
+
+int precond_apply_f64(System& s, const double* R, double* Z, cudaStream_t st,
+                      const int* done = nullptr);
+int precond_apply_f32(System& s, const float* R, float* Z, cudaStream_t st,
+                      const int* done = nullptr);
+
+// Krylov launchers (k_krylov.cu)
+int k_norm(System& s, size_t n, const double* r, double* out, cudaStream_t st);
+int k_init_cycle(System& s, size_t n, const double* r, cudaStream_t st);
+int k_arnoldi(System& s, size_t n, int j, int last_col, cudaStream_t st);
+int k_finish_cycle(System& s, size_t n, double* x, bool z32, cudaStream_t st);
+int k_to_f32(size_t n, const double* src, float* dst, const int* flags, cudaStream_t st);
+int k_to_f64(size_t n, const float* src, double* dst, const int* flags, cudaStream_t st);
+int krylov_red_blocks();
+int krylov_max_basis();
+
+}  // namespace sg

@@ -1,0 +1,230 @@
+"""Thin ctypes binding of the C ABI in ``include/sg.h`` (argument marshalling only).
+
+Every computation runs in ``libsg_gb300.so``; this module only converts torch tensors to device
+pointers and CUDA streams to handles.  There is no CPU fallback: if the library is missing or no
+CUDA device is present, the calls raise.
+"""
+
+from __future__ import annotations
+
+import ctypes
+import os
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "_build", "libsg_gb300.so")
+
+SG_OK = 0
+SG_ERR_ARG = -1
+SG_ERR_CUDA = -2
+SG_ERR_OOM = -3
+SG_ERR_NAN = -4
+SG_ERR_NOT_CONVERGED = -5
+
+SG_PC_NONE, SG_PC_MEAN, SG_PC_FS_GS, SG_PC_FS_JACOBI = 0, 1, 2, 3
+SG_FP64, SG_MIXED_FP32, SG_MIXED_BF16 = 0, 1, 2
+
+PRECONDS = {"none": SG_PC_NONE, "mean": SG_PC_MEAN, "fs_gs": SG_PC_FS_GS,
+            "fs_jacobi": SG_PC_FS_JACOBI}
+PRECISIONS = {"fp64": SG_FP64, "fp32": SG_MIXED_FP32, "bf16": SG_MIXED_BF16}
+
+EXPORTED = ["sg_default_params", "sg_setup", "sg_dims", "sg_nnz", "sg_matvec", "sg_matvec_lowp",
+            "sg_precond_apply", "sg_rhs", "sg_gmres_solve", "sg_export", "sg_launch_count",
+            "sg_free", "sg_last_error"]
+
+
+class SGError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"SG error {code}: {msg}")
+        self.code = code
+
+
+class sg_params(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int), ("M", ctypes.c_int), ("p", ctypes.c_int), ("q", ctypes.c_int),
+                ("sigma", ctypes.c_double), ("ell", ctypes.c_double), ("a_min", ctypes.c_double),
+                ("mu", ctypes.c_double), ("f", ctypes.c_double), ("precond", ctypes.c_int),
+                ("inner_iters", ctypes.c_int), ("outer_sweeps", ctypes.c_int),
+                ("restart", ctypes.c_int), ("max_iters", ctypes.c_int), ("rtol", ctypes.c_double),
+                ("atol", ctypes.c_double), ("precision", ctypes.c_int),
+                ("inner_rtol", ctypes.c_double)]
+
+
+class sg_solve_info(ctypes.Structure):
+    _fields_ = [("iters", ctypes.c_int), ("restarts", ctypes.c_int), ("status", ctypes.c_int),
+                ("rel_resid", ctypes.c_double), ("seconds", ctypes.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+_lib = None
+
+
+def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
+    """Load the compiled library (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError(f"{path} is missing: run __graft_entry__.build() (or "
+                           "python paper_1910_11505_gb300/build.py) first")
+    lib = ctypes.CDLL(path)
+    vp, ip, c_int, c_dbl = ctypes.c_void_p, ctypes.POINTER(ctypes.c_int), ctypes.c_int, ctypes.c_double
+    lib.sg_default_params.argtypes = [ctypes.POINTER(sg_params)]
+    lib.sg_default_params.restype = None
+    lib.sg_setup.argtypes = [ctypes.POINTER(sg_params), c_int, vp, ctypes.POINTER(vp)]
+    lib.sg_dims.argtypes = [vp, c_int, ip, ip, ip]
+    lib.sg_nnz.argtypes = [vp, c_int, ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(ctypes.c_longlong)]
+    lib.sg_matvec.argtypes = [vp, c_int, vp, vp, vp]
+    lib.sg_matvec_lowp.argtypes = [vp, c_int, vp, vp, vp]
+    lib.sg_precond_apply.argtypes = [vp, c_int, vp, vp, vp]
+    lib.sg_rhs.argtypes = [vp, c_int, vp, vp]
+    lib.sg_gmres_solve.argtypes = [vp, ctypes.POINTER(vp), ctypes.POINTER(vp),
+                                   ctypes.POINTER(sg_solve_info), vp]
+    lib.sg_export.argtypes = [vp, c_int, c_int, vp, ctypes.c_size_t]
+    lib.sg_launch_count.argtypes = []
+    lib.sg_launch_count.restype = ctypes.c_longlong
+    lib.sg_free.argtypes = [vp]
+    lib.sg_free.restype = None
+    lib.sg_last_error.argtypes = []
+    lib.sg_last_error.restype = ctypes.c_char_p
+    for name in ("sg_setup", "sg_dims", "sg_nnz", "sg_matvec", "sg_matvec_lowp", "sg_precond_apply",
+                 "sg_rhs", "sg_gmres_solve", "sg_export"):
+        getattr(lib, name).restype = c_int
+    _ = c_dbl
+    _lib = lib
+    return lib
+
+
+def _check(rc, allow=()):
+    if rc != SG_OK and rc not in allow:
+        raise SGError(rc, load_library().sg_last_error().decode())
+    return rc
+
+
+def _stream_ptr(stream):
+    if stream is None:
+        import torch
+        return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    if isinstance(stream, int):
+        return ctypes.c_void_p(stream)
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def _ptr(t, dtype_name):
+    import torch
+    if not t.is_cuda:
+        raise ValueError("expected a CUDA tensor")
+    if not t.is_contiguous():
+        raise ValueError("expected a contiguous tensor")
+    want = {"f64": torch.float64, "f32": torch.float32}[dtype_name]
+    if t.dtype != want:
+        raise ValueError(f"expected {want}, got {t.dtype}")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def sg_default_params(**overrides) -> sg_params:
+    p = sg_params()
+    load_library().sg_default_params(ctypes.byref(p))
+    for k, v in overrides.items():
+        if k == "precond" and isinstance(v, str):
+            v = PRECONDS[v]
+        if k == "precision" and isinstance(v, str):
+            v = PRECISIONS[v]
+        setattr(p, k, v)
+    return p
+
+
+class SGHandle:
+    """Owns an ``sg_handle*``; frees it on close() or garbage collection."""
+
+    def __init__(self, raw, params):
+        self.raw = raw
+        self.params = list(params)
+
+    def close(self):
+        if self.raw:
+            load_library().sg_free(self.raw)
+            self.raw = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def nsys(self):
+        return len(self.params)
+
+
+def sg_setup(params, stream=None) -> SGHandle:
+    if isinstance(params, sg_params):
+        params = [params]
+    arr = (sg_params * len(params))(*params)
+    out = ctypes.c_void_p()
+    _check(load_library().sg_setup(arr, len(params), _stream_ptr(stream), ctypes.byref(out)))
+    return SGHandle(out, params)
+
+
+def sg_dims(h: SGHandle, sys: int = 0):
+    N, P, L = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+    _check(load_library().sg_dims(h.raw, sys, ctypes.byref(N), ctypes.byref(P), ctypes.byref(L)))
+    return N.value, P.value, L.value
+
+
+def sg_nnz(h: SGHandle, sys: int = 0):
+    a, g = ctypes.c_longlong(), ctypes.c_longlong()
+    _check(load_library().sg_nnz(h.raw, sys, ctypes.byref(a), ctypes.byref(g)))
+    return a.value, g.value
+
+
+def sg_matvec(h: SGHandle, sys: int, X, Y, stream=None):
+    _check(load_library().sg_matvec(h.raw, sys, _ptr(X, "f64"), _ptr(Y, "f64"), _stream_ptr(stream)))
+
+
+def sg_matvec_lowp(h: SGHandle, sys: int, X, Y, stream=None):
+    _check(load_library().sg_matvec_lowp(h.raw, sys, _ptr(X, "f32"), _ptr(Y, "f32"),
+                                         _stream_ptr(stream)))
+
+
+def sg_precond_apply(h: SGHandle, sys: int, R, Z, stream=None):
+    _check(load_library().sg_precond_apply(h.raw, sys, _ptr(R, "f64"), _ptr(Z, "f64"),
+                                           _stream_ptr(stream)))
+
+
+def sg_rhs(h: SGHandle, sys: int, F, stream=None):
+    _check(load_library().sg_rhs(h.raw, sys, _ptr(F, "f64"), _stream_ptr(stream)))
+
+
+def sg_gmres_solve(h: SGHandle, F, X, stream=None, raise_on_error=True):
+    """F, X: lists (one per system) of device N x P float64 tensors; X holds x0, receives x."""
+    ns = h.nsys
+    Fa = (ctypes.c_void_p * ns)(*[_ptr(f, "f64").value for f in F])
+    Xa = (ctypes.c_void_p * ns)(*[_ptr(x, "f64").value for x in X])
+    info = (sg_solve_info * ns)()
+    rc = load_library().sg_gmres_solve(h.raw, Fa, Xa, info, _stream_ptr(stream))
+    if raise_on_error:
+        _check(rc, allow=(SG_ERR_NOT_CONVERGED,))
+    return rc, [i.as_dict() for i in info]
+
+
+def sg_export(h: SGHandle, sys: int, what: int):
+    """Copy an internal array to host numpy (see sg_export in include/sg.h)."""
+    import numpy as np
+    N, P, L = sg_dims(h, sys)
+    nnzA, nnzG = sg_nnz(h, sys)
+    spec = {0: (np.float64, nnzA * L), 1: (np.int32, N + 1), 2: (np.int32, nnzA),
+            3: (np.float64, h.params[sys].M), 4: (np.float64, nnzA), 5: (np.float64, nnzG * 4)}
+    dt, count = spec[what]
+    out = np.empty(count, dtype=dt)
+    _check(load_library().sg_export(h.raw, sys, what, out.ctypes.data_as(ctypes.c_void_p),
+                                    out.nbytes))
+    return out
+
+
+def sg_launch_count() -> int:
+    return int(load_library().sg_launch_count())
+
+
+def sg_free(h: SGHandle):
+    h.close()

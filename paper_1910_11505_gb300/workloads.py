@@ -1,0 +1,91 @@
+"""Seeded synthetic workloads (parameters and random inputs) shared by tests and the bench.
+
+This module holds no arithmetic of the method: only parameter sets of the configurations and
+seeded random numbers.  The problem itself is synthetic (f = 1 on the unit square), so nothing
+stands in for a dataset.
+
+Configurations (sizes N nodes, P and L chaos terms):
+  c1  n=16,  M=2, p=2 (P=6,  L=15),  sigma=0.5, ell=1,   mean-based preconditioner, rtol 1e-10
+  c2  n=128, M=4, p=3 (P=35, L=210), sigma in {0.25, 0.5, 1, 1.5}, ell=0.5, field-split
+      Gauss-Seidel, rtol 1e-10 (four independent systems, one per sigma)
+  c3  n=256, M=6, p=3 (P=84, L=924), sigma=1, ell=0.5, mixed precision vs FP64, rtol 1e-8
+  c4  64 systems, n in {32, 64, 128, 256}, M in {2..6}, p in {2, 3, 4}, sigma ~ U[0.1, 1.5],
+      ell ~ U[0.25, 2], drawn with splitmix64 from the seed in the order (n, M, p, sigma, ell)
+  c5  n=64, M=4, p=3, sigma ~ U[0.1, 1.5], ell ~ U[0.25, 2] (learned warm start)
+"""
+
+from __future__ import annotations
+
+import numpy as np
+
+DEFAULT_SEED = 1910115050
+MASK64 = (1 << 64) - 1
+
+
+def splitmix64(state: int):
+    """One step of the splitmix64 generator (Steele, Lea, Flood 2014): returns (value, state)."""
+    state = (state + 0x9E3779B97F4A7C15) & MASK64
+    z = state
+    z = ((z ^ (z >> 30)) * 0xBF58476D1CE4E5B9) & MASK64
+    z = ((z ^ (z >> 27)) * 0x94D049BB133111EB) & MASK64
+    return z ^ (z >> 31), state
+
+
+class SplitMix:
+    def __init__(self, seed: int = DEFAULT_SEED):
+        self.state = seed & MASK64
+
+    def next_u64(self) -> int:
+        v, self.state = splitmix64(self.state)
+        return v
+
+    def uniform(self, lo: float = 0.0, hi: float = 1.0) -> float:
+        return lo + (hi - lo) * ((self.next_u64() >> 11) * (1.0 / (1 << 53)))
+
+    def choice(self, seq):
+        return seq[self.next_u64() % len(seq)]
+
+
+def c1_params():
+    return dict(n=16, M=2, p=2, sigma=0.5, ell=1.0, precond="mean", rtol=1e-10)
+
+
+C2_SIGMAS = (0.25, 0.5, 1.0, 1.5)
+
+
+def c2_params(sigma=None):
+    sig = C2_SIGMAS if sigma is None else (sigma,)
+    return [dict(n=128, M=4, p=3, sigma=s, ell=0.5, precond="fs_gs", rtol=1e-10) for s in sig]
+
+
+def c3_params(precision="fp64"):
+    return dict(n=256, M=6, p=3, sigma=1.0, ell=0.5, precond="mean", rtol=1e-8,
+                precision=precision)
+
+
+def c4_params(nsys: int = 64, seed: int = DEFAULT_SEED, precision="fp32"):
+    rng = SplitMix(seed)
+    out = []
+    for _ in range(nsys):
+        n = rng.choice((32, 64, 128, 256))
+        M = rng.choice((2, 3, 4, 5, 6))
+        p = rng.choice((2, 3, 4))
+        sigma = rng.uniform(0.1, 1.5)
+        ell = rng.uniform(0.25, 2.0)
+        out.append(dict(n=n, M=M, p=p, sigma=sigma, ell=ell, precond="mean", rtol=1e-8,
+                        precision=precision))
+    return out
+
+
+def c5_draws(count: int, seed: int = DEFAULT_SEED + 5):
+    rng = SplitMix(seed)
+    return [(rng.uniform(0.1, 1.5), rng.uniform(0.25, 2.0)) for _ in range(count)]
+
+
+def c5_params(sigma, ell):
+    return dict(n=64, M=4, p=3, sigma=sigma, ell=ell, precond="mean", rtol=1e-8)
+
+
+def random_field(N: int, P: int, seed: int = DEFAULT_SEED, scale: float = 1.0) -> np.ndarray:
+    """Seeded N x P float64 test vector with independent N(0, scale^2) entries."""
+    return scale * np.random.default_rng(seed).standard_normal((N, P))

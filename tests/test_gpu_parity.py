@@ -1,0 +1,262 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 oracle on the same seeded inputs.
+
+Tolerances (FP64): relative 1e-12 per operator or preconditioner application, measured as
+max |gpu - oracle| / max |oracle|; 1e-10 on solutions solved to a true relative residual of 1e-13
+(the forward error is bounded by cond(K) times the residual, and cond(K) stays below 1e3 on these
+meshes).
+"""
+
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_1910_11505_gb300 import sg, workloads as W
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+CASES = [
+    dict(n=4, M=2, p=2, sigma=0.7, ell=0.8),
+    dict(n=6, M=3, p=2, sigma=0.5, ell=1.0, a_min=0.01, mu=0.1),
+    dict(n=5, M=1, p=4, sigma=1.0, ell=0.5),
+    dict(n=9, M=4, p=1, sigma=0.3, ell=2.0, f=2.5),
+    dict(n=3, M=2, p=0, sigma=0.4, ell=1.0),
+]
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    from paper_1910_11505_gb300 import build as B
+    B.build()
+    assert torch.cuda.is_available()
+
+
+def _oracle(case):
+    kw = {k: case[k] for k in ("sigma", "ell", "a_min", "mu", "f") if k in case}
+    return O.build_problem(case["n"], case["M"], case["p"], **kw)
+
+
+def _params(case, **extra):
+    d = dict(case)
+    d.update(extra)
+    return sg.sg_default_params(**d)
+
+
+def _relerr(a, b):
+    return float(np.abs(a - b).max() / max(np.abs(b).max(), 1e-300))
+
+
+def _dev(x):
+    return torch.from_numpy(np.ascontiguousarray(x)).cuda()
+
+
+@pytest.mark.parametrize("case", CASES)
+def test_setup_arrays_match_oracle(case):
+    h = sg.sg_setup(_params(case))
+    prob = _oracle(case)
+    N, P, L = sg.sg_dims(h)
+    assert (N, P, L) == (prob.N, prob.P, prob.L)
+    lam = sg.sg_export(h, 0, 3)
+    assert np.allclose(lam, prob.kl.lam, rtol=1e-13, atol=0)
+    rowptr, col = sg.sg_export(h, 0, 1), sg.sg_export(h, 0, 2)
+    vals = sg.sg_export(h, 0, 0).reshape(-1, L)
+    scale = max(abs(A).max() for A in prob.A)
+    for k in range(L):
+        Ak = prob.A[k].toarray()
+        dense = np.zeros_like(Ak)
+        for r in range(N):
+            dense[r, col[rowptr[r]:rowptr[r + 1]]] = vals[rowptr[r]:rowptr[r + 1], k]
+        assert np.abs(dense - Ak).max() <= 1e-13 * scale, k
+    trip = sg.sg_export(h, 0, 5).reshape(-1, 4)
+    G = np.zeros_like(prob.G)
+    G[trip[:, 0].astype(int), trip[:, 1].astype(int), trip[:, 2].astype(int)] = trip[:, 3]
+    assert np.allclose(G, prob.G, rtol=1e-14, atol=1e-15)
+    F = torch.empty(N, P, dtype=torch.float64, device="cuda")
+    sg.sg_rhs(h, 0, F)
+    torch.cuda.synchronize()
+    assert _relerr(F.cpu().numpy(), prob.F) <= 1e-14
+    h.close()
+
+
+@pytest.mark.parametrize("case", CASES)
+def test_matvec_parity(case):
+    h = sg.sg_setup(_params(case))
+    prob = _oracle(case)
+    X = W.random_field(prob.N, prob.P, seed=11)
+    Xd = _dev(X)
+    Y = torch.empty_like(Xd)
+    sg.sg_matvec(h, 0, Xd, Y)
+    torch.cuda.synchronize()
+    ref = O.sg_matvec(prob, X)
+    assert _relerr(Y.cpu().numpy(), ref) <= 1e-12
+    h.close()
+
+
+PC_CASES = [
+    ("mean", 1, 1), ("mean", 3, 1), ("mean", 1, 3),
+    ("fs_gs", 1, 1), ("fs_gs", 2, 1), ("fs_gs", 1, 3),
+    ("fs_jacobi", 1, 1), ("fs_jacobi", 2, 2),
+]
+
+
+@pytest.mark.parametrize("pc,inner,outer", PC_CASES)
+def test_precond_parity(pc, inner, outer):
+    case = CASES[1]
+    h = sg.sg_setup(_params(case, precond=pc, inner_iters=inner, outer_sweeps=outer))
+    prob = _oracle(case)
+    R = W.random_field(prob.N, prob.P, seed=5)
+    Rd = _dev(R)
+    Z = torch.empty_like(Rd)
+    sg.sg_precond_apply(h, 0, Rd, Z)
+    torch.cuda.synchronize()
+    if pc == "mean":
+        if outer == 1:
+            ref = O.mean_precond(prob, R, inner_iters=inner)
+        else:
+            # Eq. level_solver around the mean-based block preconditioner
+            ref = np.zeros_like(R)
+            for _ in range(outer):
+                ref = ref + O.mean_precond(prob, R - O.sg_matvec(prob, ref), inner_iters=inner)
+    else:
+        ref = O.fs_precond(prob, R, mode="gs" if pc == "fs_gs" else "jacobi", inner_iters=inner,
+                           outer_sweeps=outer)
+    assert _relerr(Z.cpu().numpy(), ref) <= 1e-12
+    h.close()
+
+
+@pytest.mark.parametrize("pc", ["none", "mean", "fs_gs", "fs_jacobi"])
+def test_gmres_solution_parity(pc):
+    case = dict(n=8, M=2, p=2, sigma=0.6, ell=1.0)
+    prob = _oracle(case)
+    h = sg.sg_setup(_params(case, precond=pc, rtol=1e-13, restart=10, max_iters=2000))
+    F = _dev(prob.F)
+    X = torch.zeros_like(F)
+    rc, info = sg.sg_gmres_solve(h, [F], [X])
+    assert rc == sg.SG_OK, info
+    K = sum(np.kron(prob.G[k], prob.A[k].toarray()) for k in range(prob.L))
+    ref = np.linalg.solve(K, prob.F.T.ravel()).reshape(prob.P, prob.N).T
+    x = X.cpu().numpy()
+    assert np.linalg.norm(x - ref) <= 1e-10 * np.linalg.norm(ref)
+    assert info[0]["rel_resid"] <= 1e-13
+    true_res = np.linalg.norm(prob.F - O.sg_matvec(prob, x)) / np.linalg.norm(prob.F)
+    assert true_res <= 1.5e-13
+    h.close()
+
+
+def test_gmres_iteration_count_matches_oracle():
+    case = dict(W.c1_params())
+    prob = _oracle(case)
+    h = sg.sg_setup(_params(case))
+    F = _dev(prob.F)
+    X = torch.zeros_like(F)
+    rc, info = sg.sg_gmres_solve(h, [F], [X])
+    assert rc == sg.SG_OK
+    LU = O.ilu0(prob.A[0])
+    N, P = prob.N, prob.P
+    xo, oinfo = O.gmres(lambda v: O.sg_matvec(prob, v.reshape(N, P)).ravel(),
+                        lambda v: O.mean_precond(prob, v.reshape(N, P), LU=LU).ravel(),
+                        prob.F.ravel(), rtol=1e-10, restart=30)
+    assert abs(info[0]["iters"] - oinfo["iters"]) <= 1
+    x = X.cpu().numpy()
+    assert np.linalg.norm(x - xo.reshape(N, P)) <= 1e-8 * np.linalg.norm(x)
+
+
+def test_batch_of_uneven_systems_equals_single_solves():
+    cases = [dict(n=6, M=2, p=2, sigma=0.5, ell=1.0), dict(n=10, M=3, p=1, sigma=0.9, ell=0.6),
+             dict(n=5, M=2, p=3, sigma=0.2, ell=1.5, precond="fs_gs")]
+    params = [_params(c, rtol=1e-12) for c in cases]
+    h = sg.sg_setup(params)
+    Fs, Xs = [], []
+    for i in range(len(cases)):
+        N, P, _ = sg.sg_dims(h, i)
+        F = torch.empty(N, P, dtype=torch.float64, device="cuda")
+        sg.sg_rhs(h, i, F)
+        Fs.append(F)
+        Xs.append(torch.zeros_like(F))
+    rc, info = sg.sg_gmres_solve(h, Fs, Xs)
+    assert rc == sg.SG_OK
+    for i, c in enumerate(cases):
+        hs = sg.sg_setup(params[i])
+        X1 = torch.zeros_like(Fs[i])
+        rc1, info1 = sg.sg_gmres_solve(hs, [Fs[i]], [X1])
+        assert rc1 == sg.SG_OK
+        assert torch.equal(X1, Xs[i])
+        assert info1[0]["iters"] == info[i]["iters"]
+        hs.close()
+    h.close()
+
+
+def test_warm_start_and_zero_rhs():
+    case = dict(n=6, M=2, p=2, sigma=0.5, ell=1.0, rtol=1e-12)
+    prob = _oracle(case)
+    h = sg.sg_setup(_params(case))
+    F = _dev(prob.F)
+    X = torch.zeros_like(F)
+    rc, info = sg.sg_gmres_solve(h, [F], [X])
+    rc2, info2 = sg.sg_gmres_solve(h, [F], [X])  # start from the solution
+    assert rc2 == sg.SG_OK and info2[0]["iters"] <= 1
+    Z = torch.zeros_like(F)
+    X0 = torch.ones_like(F)
+    rc3, info3 = sg.sg_gmres_solve(h, [Z], [X0])
+    assert rc3 == sg.SG_OK
+    assert float(X0.abs().max()) <= 1e-12  # zero right-hand side: x = 0
+    h.close()
+
+
+def test_not_converged_status():
+    case = dict(n=16, M=2, p=2, sigma=0.5, ell=1.0)
+    h = sg.sg_setup(_params(case, precond="none", max_iters=3, rtol=1e-12))
+    N, P, _ = sg.sg_dims(h)
+    F = torch.empty(N, P, dtype=torch.float64, device="cuda")
+    sg.sg_rhs(h, 0, F)
+    X = torch.zeros_like(F)
+    rc, info = sg.sg_gmres_solve(h, [F], [X])
+    assert rc == sg.SG_ERR_NOT_CONVERGED
+    assert info[0]["iters"] == 3 and info[0]["status"] == sg.SG_ERR_NOT_CONVERGED
+    assert 0 < info[0]["rel_resid"] < 1
+    h.close()
+
+
+def test_nan_input_reports_nan():
+    case = dict(n=4, M=2, p=1, sigma=0.5, ell=1.0)
+    h = sg.sg_setup(_params(case))
+    N, P, _ = sg.sg_dims(h)
+    F = torch.ones(N, P, dtype=torch.float64, device="cuda")
+    F[3, 0] = float("nan")
+    X = torch.zeros_like(F)
+    rc, info = sg.sg_gmres_solve(h, [F], [X], raise_on_error=False)
+    assert rc == sg.SG_ERR_NAN and info[0]["status"] == sg.SG_ERR_NAN
+    h.close()
+
+
+@pytest.mark.parametrize("precision", ["fp32", "bf16"])
+def test_lowp_matvec_close_to_fp64(precision):
+    case = CASES[1]
+    h = sg.sg_setup(_params(case, precision=precision))
+    prob = _oracle(case)
+    X = W.random_field(prob.N, prob.P, seed=2)
+    Xd = _dev(X).float()
+    Y = torch.empty_like(Xd)
+    sg.sg_matvec_lowp(h, 0, Xd, Y)
+    torch.cuda.synchronize()
+    ref = O.sg_matvec(prob, X)
+    # FP32 arithmetic on FP32 (BF16) stored values: relative error bound ~ 9 * u * (sum |terms|)
+    tol = 2e-5 if precision == "fp32" else 4e-2
+    assert _relerr(Y.double().cpu().numpy(), ref) <= tol
+    h.close()
+
+
+def test_mixed_fp32_reaches_fp64_residual():
+    case = dict(n=16, M=2, p=2, sigma=0.5, ell=1.0)
+    prob = _oracle(case)
+    h = sg.sg_setup(_params(case, precision="fp32", rtol=1e-10))
+    F = _dev(prob.F)
+    X = torch.zeros_like(F)
+    rc, info = sg.sg_gmres_solve(h, [F], [X])
+    assert rc == sg.SG_OK, info
+    x = X.cpu().numpy()
+    true_res = np.linalg.norm(prob.F - O.sg_matvec(prob, x)) / np.linalg.norm(prob.F)
+    assert true_res <= 1.2e-10
+    assert info[0]["restarts"] >= 2  # at least one refinement step after the first inner solve
+    h.close()
