@@ -137,6 +137,23 @@ int sg_export(const sg_handle* h, int sys, int what, void* dst, size_t bytes);
 /* Count of kernel launches this library has queued since load (all handles, all threads). */
 long long sg_launch_count(void);
 
+/* Live kernel timing.  Kernel classes: */
+#define SG_K_APPLY_F64 0   /* SG operator, FP64                                             */
+#define SG_K_APPLY_LOWP 1  /* SG operator, FP32 arithmetic on the FP32 / BF16 stack          */
+#define SG_K_ILU_SOLVE 2   /* ILU(0) block solves of the preconditioners                    */
+#define SG_K_GS_SCATTER 3  /* field-split Gauss-Seidel off-diagonal push                   */
+#define SG_K_ARNOLDI 4     /* CGS2 dot products, updates, Givens step, normalisation        */
+#define SG_K_OTHER 5       /* norms, cycle start and end, casts                             */
+#define SG_K_NCLASS 6
+/* Start timing: from now on every ``stride``-th launch of each class queued through handle h is
+ * bracketed by CUDA events recorded on the stream it is launched on (up to 2^15 timed launches).
+ * Allocates the events; call it outside a timed region.  Resets previous counts. */
+int sg_timing_start(sg_handle* h, int stride);
+/* Stop timing, wait for the recorded events and report per class (host arrays of SG_K_NCLASS):
+ * ms = summed duration of the timed launches, timed = how many were timed, launches = how many
+ * were queued.  Any pointer may be NULL. */
+int sg_timing_stop(sg_handle* h, double* ms, long long* timed, long long* launches);
+
 /* Free every device array of the handle (after synchronising its streams).  NULL is a no-op. */
 void sg_free(sg_handle* h);
 

@@ -264,11 +264,13 @@ __global__ void to_f64_kernel(size_t n, const float* __restrict__ src, double* _
 // ------------------------------------------------------------------ launchers used by the driver
 
 int k_norm(System& s, size_t n, const double* r, double* out, cudaStream_t st) {
+  TimeScope ts(s.timer, K_OTHER, st);
   norm_kernel<<<kRedBlocks, kRedThreads, 0, st>>>(n, r, s.red.p, s.ticket.p, out);
   return check_launch("norm");
 }
 
 int k_init_cycle(System& s, size_t n, const double* r, cudaStream_t st) {
+  TimeScope ts(s.timer, K_OTHER, st);
   init_cycle_kernel<<<kRedBlocks, kRedThreads, 0, st>>>(n, r, s.V.p, s.scal.p, s.g.p, s.m + 1,
                                                         s.flags.p);
   return check_launch("init_cycle");
@@ -280,21 +282,34 @@ int k_arnoldi(System& s, size_t n, int j, int last_col, cudaStream_t st) {
   double* w = s.V.p + (size_t)(j + 1) * n;
   double* h1 = s.y.p + kMaxBasis;       // scratch: two h vectors after y
   double* h2 = s.y.p + 2 * kMaxBasis;
-  cgs_dots_kernel<<<kRedBlocks, kRedThreads, 0, st>>>(n, s.V.p, nv, w, s.red.p, s.ticket.p, h1,
-                                                      s.flags.p);
+  {
+    TimeScope ts(s.timer, K_ARNOLDI, st);
+    cgs_dots_kernel<<<kRedBlocks, kRedThreads, 0, st>>>(n, s.V.p, nv, w, s.red.p, s.ticket.p, h1,
+                                                        s.flags.p);
+  }
   SG_TRY(check_launch("cgs_dots"));
+  {
+  TimeScope ts(s.timer, K_ARNOLDI, st);
   cgs_update_dots_kernel<<<kRedBlocks, kRedThreads, 0, st>>>(n, s.V.p, nv, w, h1, s.red.p,
                                                              s.ticket.p, h2, s.flags.p);
+  }
   SG_TRY(check_launch("cgs_update_dots"));
-  cgs_update_norm_kernel<<<kRedBlocks, kRedThreads, 0, st>>>(
-      n, s.V.p, nv, w, h1, h2, s.red.p, s.ticket.p, s.Hs.p, s.m + 1, s.cs.p, s.sn.p, s.g.p,
-      s.scal.p, s.flags.p, last_col);
+  {
+    TimeScope ts(s.timer, K_ARNOLDI, st);
+    cgs_update_norm_kernel<<<kRedBlocks, kRedThreads, 0, st>>>(
+        n, s.V.p, nv, w, h1, h2, s.red.p, s.ticket.p, s.Hs.p, s.m + 1, s.cs.p, s.sn.p, s.g.p,
+        s.scal.p, s.flags.p, last_col);
+  }
   SG_TRY(check_launch("cgs_update_norm"));
-  scale_kernel<<<kRedBlocks, kRedThreads, 0, st>>>(n, w, s.scal.p, s.flags.p);
+  {
+    TimeScope ts(s.timer, K_ARNOLDI, st);
+    scale_kernel<<<kRedBlocks, kRedThreads, 0, st>>>(n, w, s.scal.p, s.flags.p);
+  }
   return check_launch("scale");
 }
 
 int k_finish_cycle(System& s, size_t n, double* x, bool z32, cudaStream_t st) {
+  TimeScope ts(s.timer, K_OTHER, st);
   backsolve_kernel<<<1, 32, 0, st>>>(s.Hs.p, s.m + 1, s.g.p, s.y.p, s.flags.p);
   SG_TRY(check_launch("backsolve"));
   if (z32)

@@ -18,11 +18,6 @@ namespace sg {
 
 namespace {
 
-template <typename T> __device__ __forceinline__ T load_val(const T* p) { return *p; }
-__device__ __forceinline__ float load_as_f32(const float* p) { return *p; }
-__device__ __forceinline__ float load_as_f32(const __nv_bfloat16* p) { return __bfloat162float(*p); }
-__device__ __forceinline__ double load_as_f64(const double* p) { return *p; }
-
 template <typename TA, typename TV>
 __device__ __forceinline__ TA cvt(const TV* p);
 template <> __device__ __forceinline__ double cvt<double, double>(const double* p) { return *p; }
@@ -122,6 +117,7 @@ int launch_apply(const System& s, const TV* stack, const TA* eg, const TA* X, TA
   SG_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   int per_sm = (int)std::max<size_t>(1, std::min<size_t>(8, (200 * 1024) / smem));
   int grid = std::min(s.N, num_sms() * per_sm);
+  TimeScope ts(s.timer, sizeof(TA) == 8 ? K_APPLY_F64 : K_APPLY_LOWP, st);
   kern<<<grid, 256, smem, st>>>(s.N, s.P, s.L, s.rowptr.p, s.col.p, stack, s.pair_kb.p, s.chunks.p,
                                 s.chunks_k.p, s.op.nchunks, s.ent_ptr.p, s.ent_u.p, eg, X, Y, alpha,
                                 B, beta, done);

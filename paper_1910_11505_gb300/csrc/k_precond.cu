@@ -164,6 +164,7 @@ int launch_block_solve(System& s, int a0, int ncols, int fac_per_col, const T* R
   using B = PcBufs<T>;
   int nlf = (int)s.pat.lev_f_ptr.size() - 1, nlb = (int)s.pat.lev_b_ptr.size() - 1;
   int inner = std::max(1, s.prm.inner_iters);
+  TimeScope ts(s.timer, K_ILU_SOLVE, st);
   if (B::smem(s)) {
     size_t smem = sizeof(T) * (size_t)s.N;
     auto kern = ilu_block_solve_kernel<T, true>;
@@ -190,6 +191,7 @@ int launch_scatter<double>(System& s, int b, const double* Z, double* acc, cudaS
   auto kern = fs_scatter_kernel<double, double>;
   SG_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   int grid = (s.N + kScatterRows - 1) / kScatterRows;
+  TimeScope ts(s.timer, K_GS_SCATTER, st);
   kern<<<grid, 128, smem, st>>>(s.N, s.P, s.L, b, s.rowptr.p, s.col.p, s.stack.p, s.gs_kptr.p,
                                 s.gs_k.p, s.gs_eptr.p, s.gs_ea.p, s.gs_eg.p, Z, acc, done);
   return check_launch("fs_scatter");
@@ -199,6 +201,7 @@ int launch_scatter<float>(System& s, int b, const float* Z, float* acc, cudaStre
                           const int* done) {
   size_t smem = sizeof(float) * kScatterRows * std::max(1, s.gs_max_klen);
   int grid = (s.N + kScatterRows - 1) / kScatterRows;
+  TimeScope ts(s.timer, K_GS_SCATTER, st);
   if (s.prm.precision == SG_MIXED_BF16) {
     auto kern = fs_scatter_kernel<float, __nv_bfloat16>;
     SG_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
@@ -227,7 +230,6 @@ int apply_once(System& s, const T* R, T* D, cudaStream_t st, const int* done) {
     case SG_PC_FS_GS: {
       T* acc = B::acc(s);
       SG_CUDA(cudaMemsetAsync(acc, 0, sizeof(T) * (size_t)s.N * s.P, st));
-      count_launch();
       for (int a = 0; a < s.P; ++a) {
         SG_TRY(launch_block_solve<T>(s, a, 1, 1, R, a > 0 ? acc : nullptr, D, st, done));
         if (a + 1 < s.P) SG_TRY(launch_scatter<T>(s, a, D, acc, st, done));
@@ -264,6 +266,7 @@ int precond_apply_t(System& s, const T* R, T* Z, cudaStream_t st, const int* don
   for (int sw = 1; sw < s.prm.outer_sweeps; ++sw) {
     SG_TRY(matvec_t<T>(s, Z, B::tmp(s), T(-1), R, T(1), st, done));
     SG_TRY(apply_once<T>(s, B::tmp(s), B::tmp2(s), st, done));
+    TimeScope ts(s.timer, K_OTHER, st);
     axpy_kernel<T><<<1216, 256, 0, st>>>(n, B::tmp2(s), Z, done);
     SG_TRY(check_launch("axpy"));
   }

@@ -31,6 +31,20 @@ int check_launch(const char* what) {
   return SG_OK;
 }
 
+TimeScope::TimeScope(Timer* t_, int cls_, cudaStream_t st_) : t(t_), cls(cls_), st(st_) {
+  if (!t || !t->on) return;
+  long long c = t->count[cls]++;
+  if (c % t->stride != 0 || t->used + 2 > t->ev.size()) return;
+  idx = (long long)t->used;
+  t->used += 2;
+  cudaEventRecord(t->ev[idx], st);
+}
+TimeScope::~TimeScope() {
+  if (idx < 0) return;
+  cudaEventRecord(t->ev[idx + 1], st);
+  t->recs.push_back({cls, (size_t)idx});
+}
+
 template <typename T>
 int DBuf<T>::alloc(size_t count) {
   release();
@@ -542,6 +556,7 @@ int sg_setup(const sg_params* prm, int nsys, void* stream, sg_handle** out) {
   for (int i = 0; i < nsys; ++i) {
     System* s = new System();
     s->prm = prm[i];
+    s->timer = &h->timer;
     h->sys.push_back(s);
     int rc = setup_system(*s, st);
     if (rc != SG_OK) {
@@ -550,6 +565,7 @@ int sg_setup(const sg_params* prm, int nsys, void* stream, sg_handle** out) {
       return fail(rc, "system " + std::to_string(i) + ": " + msg);
     }
   }
+  *out = h;
   return SG_OK;
 }
 
@@ -647,9 +663,48 @@ int sg_export(const sg_handle* h, int sys, int what, void* dst, size_t bytes) {
 
 long long sg_launch_count(void) { return g_launches.load(); }
 
+int sg_timing_start(sg_handle* h, int stride) {
+  if (!h || stride < 1) return fail(SG_ERR_ARG, "bad handle or stride");
+  Timer& t = h->timer;
+  if (t.ev.empty()) {
+    t.ev.resize(1 << 16);
+    for (auto& e : t.ev) SG_CUDA(cudaEventCreate(&e));
+  }
+  t.used = 0;
+  t.recs.clear();
+  for (auto& c : t.count) c = 0;
+  t.stride = stride;
+  t.on = true;
+  return SG_OK;
+}
+
+int sg_timing_stop(sg_handle* h, double* ms, long long* timed, long long* launches) {
+  if (!h) return fail(SG_ERR_ARG, "bad handle");
+  Timer& t = h->timer;
+  t.on = false;
+  double acc[K_NCLASS] = {};
+  long long nt[K_NCLASS] = {};
+  for (auto& r : t.recs) {
+    SG_CUDA(cudaEventSynchronize(t.ev[r.second + 1]));
+    float e = 0.f;
+    SG_CUDA(cudaEventElapsedTime(&e, t.ev[r.second], t.ev[r.second + 1]));
+    acc[r.first] += e;
+    nt[r.first] += 1;
+  }
+  for (int c = 0; c < K_NCLASS; ++c) {
+    if (ms) ms[c] = acc[c];
+    if (timed) timed[c] = nt[c];
+    if (launches) launches[c] = t.count[c];
+  }
+  t.recs.clear();
+  t.used = 0;
+  return SG_OK;
+}
+
 void sg_free(sg_handle* h) {
   if (!h) return;
   for (auto* s : h->sys) free_system(s);
+  for (auto& e : h->timer.ev) cudaEventDestroy(e);
   delete h;
 }
 

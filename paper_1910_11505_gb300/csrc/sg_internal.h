@@ -39,6 +39,32 @@ struct Status {
 void count_launch(int n = 1);
 int check_launch(const char* what);
 
+// ------------------------------------------------------------------ live kernel timing
+
+// Kernel classes timed by sg_timing_start / sg_timing_stop (values match SG_K_* in sg.h).
+enum KClass { K_APPLY_F64 = 0, K_APPLY_LOWP = 1, K_ILU_SOLVE = 2, K_GS_SCATTER = 3,
+              K_ARNOLDI = 4, K_OTHER = 5, K_NCLASS = 6 };
+
+struct Timer {
+  bool on = false;
+  int stride = 1;
+  std::vector<cudaEvent_t> ev;          // start / end pairs
+  size_t used = 0;
+  long long count[K_NCLASS] = {};
+  std::vector<std::pair<int, size_t>> recs;
+};
+
+// Brackets one launch with events on its stream when the handle's timer is on and the launch
+// falls on the sampling stride.
+struct TimeScope {
+  Timer* t;
+  int cls;
+  cudaStream_t st;
+  long long idx = -1;
+  TimeScope(Timer* t_, int cls_, cudaStream_t st_);
+  ~TimeScope();
+};
+
 // ------------------------------------------------------------------ device buffers
 
 template <typename T>
@@ -155,6 +181,7 @@ struct System {
   DBuf<double> rvec;           // FP64 residual r = F - K x
   DBuf<float> mv32a, mv32b;    // FP32 operand / result of the inner operator
   double* hpin = nullptr;      // pinned host mirror of state[0..3] and flags[0..2]
+  Timer* timer = nullptr;      // the handle's timer
   cudaStream_t stream = nullptr;
   cudaEvent_t ev = nullptr;
 };
@@ -164,6 +191,7 @@ struct System {
 struct sg_handle {
   std::vector<sg::System*> sys;
   int device = 0;
+  sg::Timer timer;
 };
 
 namespace sg {

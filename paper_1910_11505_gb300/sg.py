@@ -29,7 +29,9 @@ PRECISIONS = {"fp64": SG_FP64, "fp32": SG_MIXED_FP32, "bf16": SG_MIXED_BF16}
 
 EXPORTED = ["sg_default_params", "sg_setup", "sg_dims", "sg_nnz", "sg_matvec", "sg_matvec_lowp",
             "sg_precond_apply", "sg_rhs", "sg_gmres_solve", "sg_export", "sg_launch_count",
-            "sg_free", "sg_last_error"]
+            "sg_timing_start", "sg_timing_stop", "sg_free", "sg_last_error"]
+
+K_CLASSES = ["apply_f64", "apply_lowp", "ilu_solve", "gs_scatter", "arnoldi", "other"]
 
 
 class SGError(RuntimeError):
@@ -83,12 +85,15 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.sg_export.argtypes = [vp, c_int, c_int, vp, ctypes.c_size_t]
     lib.sg_launch_count.argtypes = []
     lib.sg_launch_count.restype = ctypes.c_longlong
+    lib.sg_timing_start.argtypes = [vp, c_int]
+    lib.sg_timing_stop.argtypes = [vp, ctypes.POINTER(ctypes.c_double),
+                                   ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(ctypes.c_longlong)]
     lib.sg_free.argtypes = [vp]
     lib.sg_free.restype = None
     lib.sg_last_error.argtypes = []
     lib.sg_last_error.restype = ctypes.c_char_p
     for name in ("sg_setup", "sg_dims", "sg_nnz", "sg_matvec", "sg_matvec_lowp", "sg_precond_apply",
-                 "sg_rhs", "sg_gmres_solve", "sg_export"):
+                 "sg_rhs", "sg_gmres_solve", "sg_export", "sg_timing_start", "sg_timing_stop"):
         getattr(lib, name).restype = c_int
     _ = c_dbl
     _lib = lib
@@ -224,6 +229,18 @@ def sg_export(h: SGHandle, sys: int, what: int):
 
 def sg_launch_count() -> int:
     return int(load_library().sg_launch_count())
+
+
+def sg_timing_start(h: SGHandle, stride: int = 1):
+    _check(load_library().sg_timing_start(h.raw, stride))
+
+
+def sg_timing_stop(h: SGHandle):
+    """Returns {class: (ms of timed launches, timed launches, queued launches)}."""
+    n = len(K_CLASSES)
+    ms, tm, la = (ctypes.c_double * n)(), (ctypes.c_longlong * n)(), (ctypes.c_longlong * n)()
+    _check(load_library().sg_timing_stop(h.raw, ms, tm, la))
+    return {c: (ms[i], tm[i], la[i]) for i, c in enumerate(K_CLASSES)}
 
 
 def sg_free(h: SGHandle):
