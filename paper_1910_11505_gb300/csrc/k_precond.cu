@@ -19,60 +19,124 @@ namespace sg {
 
 namespace {
 
-template <typename T>
-__device__ __forceinline__ void ilu_sweeps(T* w, const T* __restrict__ fac,
-                                           const int* __restrict__ rowptr,
-                                           const int* __restrict__ col,
-                                           const int* __restrict__ diag,
-                                           const int* __restrict__ lf_ptr,
-                                           const int* __restrict__ lf_rows, int nlf,
-                                           const int* __restrict__ lb_ptr,
-                                           const int* __restrict__ lb_rows, int nlb) {
-  for (int l = 0; l < nlf; ++l) {
-    for (int t = lf_ptr[l] + threadIdx.x; t < lf_ptr[l + 1]; t += blockDim.x) {
-      int i = lf_rows[t];
-      T s = w[i];
-      for (int e = rowptr[i]; e < diag[i]; ++e) s -= fac[e] * w[col[e]];
-      w[i] = s;
-    }
-    __syncthreads();
-  }
-  for (int l = 0; l < nlb; ++l) {
-    for (int t = lb_ptr[l] + threadIdx.x; t < lb_ptr[l + 1]; t += blockDim.x) {
-      int i = lb_rows[t];
-      int d = diag[i];
-      T s = w[i];
-      for (int e = d + 1; e < rowptr[i + 1]; ++e) s -= fac[e] * w[col[e]];
-      w[i] = s / fac[d];
-    }
-    __syncthreads();
-  }
+// Wavefront schedule of the 9-point Q1 pattern in natural order: row (x, y) of the lower factor
+// depends on (x-1, y-1), (x, y-1), (x+1, y-1), (x-1, y), so the rows with x + 2y = l form level l
+// (3m - 2 levels); the upper factor uses the same levels in reverse.  Factors are stored per
+// factor set as 9 slot arrays in level-major row order (slot (dy+1)*3 + (dx+1); slot 4 holds
+// 1/u_ii; absent neighbours hold 0), so a level needs no index loads and its factors can be
+// fetched one level ahead.
+__device__ __forceinline__ void level_range(int l, int m, int& ylo, int& cnt) {
+  ylo = max(0, (l - (m - 1) + 1) >> 1);
+  int yhi = min(m - 1, l >> 1);
+  cnt = yhi - ylo + 1;
 }
 
-// CTA c solves column a = a0 + c with factor set fsel = (fac_stride ? a : 0):
+// Factors of the next kAhead levels are copied into a shared-memory ring with cp.async while the
+// current level is computed.  Ordinary loads cannot run ahead like this: the level barrier waits
+// for every load the thread has in flight, so each level would pay a full L2 round trip.  Each
+// thread copies and later reads only its own rows' factors, so the ring needs no barrier of its
+// own; cp.async.wait_group orders the copy before the read.
+constexpr int kAhead = 8;
+
+template <typename T>
+__device__ __forceinline__ void cp_async_elem(T* dst, const T* src) {
+  unsigned sa = (unsigned)__cvta_generic_to_shared(dst);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], %2;\n" ::"r"(sa), "l"(src), "n"(sizeof(T)));
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N)); }
+
+// Copy the factors of level l (4 off-diagonal slots, plus 1/u_ii for the upper sweep) of the rows
+// this thread owns into ring slot ``slot``; always commits one group (possibly empty).
+template <typename T, int RPT, bool UPPER>
+__device__ __forceinline__ void stage_level(T* ring, int slot, int W, int l, int nlev, int m,
+                                            int N, const T* __restrict__ lu, const int* lev_off_s) {
+  if (l >= 0 && l < nlev) {
+    int ylo, cnt;
+    level_range(l, m, ylo, cnt);
+    const int base = lev_off_s[l];
+    const int s0 = UPPER ? 5 : 0;
+#pragma unroll
+    for (int r = 0; r < RPT; ++r) {
+      int t = threadIdx.x + r * blockDim.x;
+      if (t < cnt) {
+        T* d = ring + (size_t)slot * 5 * W + t;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) cp_async_elem(d + q * W, lu + (size_t)(s0 + q) * N + base + t);
+        if (UPPER) cp_async_elem(d + 4 * W, lu + (size_t)4 * N + base + t);
+      }
+    }
+  }
+  cp_async_commit();
+}
+
+template <typename T, int RPT, bool UPPER>
+__device__ __forceinline__ void ilu9_sweep(T* w, T* ring, int W, const T* __restrict__ lu, int m,
+                                           int N, const int* lev_off_s, int nlev) {
+  const int o0 = UPPER ? 1 : -m - 1, o1 = UPPER ? m - 1 : -m, o2 = UPPER ? m : -m + 1,
+            o3 = UPPER ? m + 1 : -1;
+  auto lev = [&](int it) { return UPPER ? nlev - 1 - it : it; };
+#pragma unroll
+  for (int d = 0; d < kAhead - 1; ++d)
+    stage_level<T, RPT, UPPER>(ring, d, W, d < nlev ? lev(d) : -1, nlev, m, N, lu, lev_off_s);
+  for (int it = 0; it < nlev; ++it) {
+    int ahead = it + kAhead - 1;
+    stage_level<T, RPT, UPPER>(ring, ahead % kAhead, W, ahead < nlev ? lev(ahead) : -1, nlev, m,
+                               N, lu, lev_off_s);
+    cp_async_wait<kAhead - 1>();
+    const int l = lev(it);
+    int ylo, cnt;
+    level_range(l, m, ylo, cnt);
+    const T* f = ring + (size_t)(it % kAhead) * 5 * W;
+#pragma unroll
+    for (int r = 0; r < RPT; ++r) {
+      int t = threadIdx.x + r * blockDim.x;
+      if (t < cnt) {
+        int y = ylo + t, x = l - 2 * y;
+        int i = x + m * y;
+        T s = w[i];
+        s -= f[t] * w[min(max(i + o0, 0), N - 1)];
+        s -= f[W + t] * w[min(max(i + o1, 0), N - 1)];
+        s -= f[2 * W + t] * w[min(max(i + o2, 0), N - 1)];
+        s -= f[3 * W + t] * w[min(max(i + o3, 0), N - 1)];
+        w[i] = UPPER ? s * f[4 * W + t] : s;
+      }
+    }
+    __syncthreads();
+  }
+  cp_async_wait<0>();
+}
+
+// CTA c solves column a = a0 + c with factor set (fac_per_col ? a : 0):
 //   z = ILU^{-1}(rhs), then inner-1 times z += ILU^{-1}(rhs - K_blk z), rhs = R[:,a] - acc[:,a].
-template <typename T, bool SMEM>
+template <typename T, bool SMEM, int RPT>
 __global__ void __launch_bounds__(256) ilu_block_solve_kernel(
-    int N, int P, int nnz, int a0, int fac_per_col, const int* __restrict__ rowptr,
-    const int* __restrict__ col, const int* __restrict__ diag, const int* __restrict__ lf_ptr,
-    const int* __restrict__ lf_rows, int nlf, const int* __restrict__ lb_ptr,
-    const int* __restrict__ lb_rows, int nlb, const T* __restrict__ facs,
-    const T* __restrict__ blks, const T* __restrict__ R, const T* __restrict__ acc,
-    T* __restrict__ Z, T* __restrict__ wglob, int inner, const int* __restrict__ done) {
+    int m, int N, int P, int nnz, int a0, int fac_per_col, const int* __restrict__ lev_off,
+    int nlev, int W, const T* __restrict__ lu9s, const int* __restrict__ rowptr,
+    const int* __restrict__ col, const T* __restrict__ blks, const T* __restrict__ R,
+    const T* __restrict__ acc, T* __restrict__ Z, T* __restrict__ wglob, int inner,
+    const int* __restrict__ done) {
   if (done != nullptr && *done) return;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int a = a0 + blockIdx.x;
-  const size_t fo = fac_per_col ? (size_t)a * nnz : 0;
-  const T* fac = facs + fo;
-  const T* blk = blks + fo;
+  const int fsel = fac_per_col ? a : 0;
+  const T* lu = lu9s + (size_t)fsel * 9 * N;
+  const T* blk = blks + (size_t)fsel * nnz;
   T* w = SMEM ? reinterpret_cast<T*>(smem_raw) : wglob + (size_t)a * N;
+  T* ring = reinterpret_cast<T*>(smem_raw + (SMEM ? sizeof(T) * (size_t)N : 0));
+  int* lev_s = reinterpret_cast<int*>(ring + (size_t)kAhead * 5 * W);
+  for (int l = threadIdx.x; l <= nlev; l += blockDim.x) lev_s[l] = lev_off[l];
+#pragma unroll 4
   for (int i = threadIdx.x; i < N; i += blockDim.x) {
     T v = R[(size_t)i * P + a];
     if (acc != nullptr) v -= acc[(size_t)i * P + a];
     w[i] = v;
   }
   __syncthreads();
-  ilu_sweeps<T>(w, fac, rowptr, col, diag, lf_ptr, lf_rows, nlf, lb_ptr, lb_rows, nlb);
+  ilu9_sweep<T, RPT, false>(w, ring, W, lu, m, N, lev_s, nlev);
+  ilu9_sweep<T, RPT, true>(w, ring, W, lu, m, N, lev_s, nlev);
+#pragma unroll 4
   for (int i = threadIdx.x; i < N; i += blockDim.x) Z[(size_t)i * P + a] = w[i];
   for (int it = 1; it < inner; ++it) {
     __syncthreads();
@@ -83,7 +147,8 @@ __global__ void __launch_bounds__(256) ilu_block_solve_kernel(
       w[i] = v;
     }
     __syncthreads();
-    ilu_sweeps<T>(w, fac, rowptr, col, diag, lf_ptr, lf_rows, nlf, lb_ptr, lb_rows, nlb);
+    ilu9_sweep<T, RPT, false>(w, ring, W, lu, m, N, lev_s, nlev);
+    ilu9_sweep<T, RPT, true>(w, ring, W, lu, m, N, lev_s, nlev);
     for (int i = threadIdx.x; i < N; i += blockDim.x) Z[(size_t)i * P + a] += w[i];
   }
 }
@@ -137,7 +202,7 @@ template <typename T>
 struct PcBufs;
 template <>
 struct PcBufs<double> {
-  static const double* fac(const System& s) { return s.fac.p; }
+  static const double* lu9(const System& s) { return s.lu9.p; }
   static const double* blk(const System& s) { return s.blk.p; }
   static double* acc(System& s) { return s.acc.p; }
   static double* tmp(System& s) { return s.tmp.p; }
@@ -148,7 +213,7 @@ struct PcBufs<double> {
 };
 template <>
 struct PcBufs<float> {
-  static const float* fac(const System& s) { return s.fac_f32.p; }
+  static const float* lu9(const System& s) { return s.lu9_f32.p; }
   static const float* blk(const System& s) { return s.blk_f32.p; }
   static float* acc(System& s) { return s.acc32.p; }
   static float* tmp(System& s) { return s.tmp32.p; }
@@ -158,28 +223,34 @@ struct PcBufs<float> {
   static bool smem(const System& s) { return s.tri_smem32; }
 };
 
+template <typename T, bool SMEM, int RPT>
+int launch_block_solve_t(System& s, int a0, int ncols, int fac_per_col, const T* R, const T* acc,
+                         T* Z, cudaStream_t st, const int* done) {
+  using B = PcBufs<T>;
+  const int W = s.pat.max_width;
+  size_t smem = (SMEM ? sizeof(T) * (size_t)s.N : 0) + sizeof(T) * (size_t)kAhead * 5 * W +
+                sizeof(int) * (size_t)(s.nlev9 + 1);
+  auto kern = ilu_block_solve_kernel<T, SMEM, RPT>;
+  SG_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  TimeScope ts(s.timer, K_ILU_SOLVE, st);
+  kern<<<ncols, 256, smem, st>>>(s.pat.m, s.N, s.P, s.pat.nnz, a0, fac_per_col, s.lev9_off.p,
+                                 s.nlev9, W, B::lu9(s), s.rowptr.p, s.col.p, B::blk(s), R, acc, Z,
+                                 SMEM ? nullptr : B::triw(s), std::max(1, s.prm.inner_iters), done);
+  return check_launch("ilu_block_solve");
+}
+
 template <typename T>
 int launch_block_solve(System& s, int a0, int ncols, int fac_per_col, const T* R, const T* acc,
                        T* Z, cudaStream_t st, const int* done) {
   using B = PcBufs<T>;
-  int nlf = (int)s.pat.lev_f_ptr.size() - 1, nlb = (int)s.pat.lev_b_ptr.size() - 1;
-  int inner = std::max(1, s.prm.inner_iters);
-  TimeScope ts(s.timer, K_ILU_SOLVE, st);
+  int rpt = (s.pat.max_width + 255) / 256;
   if (B::smem(s)) {
-    size_t smem = sizeof(T) * (size_t)s.N;
-    auto kern = ilu_block_solve_kernel<T, true>;
-    SG_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    kern<<<ncols, 256, smem, st>>>(s.N, s.P, s.pat.nnz, a0, fac_per_col, s.rowptr.p, s.col.p,
-                                   s.diag.p, s.lev_f_ptr.p, s.lev_f_rows.p, nlf, s.lev_b_ptr.p,
-                                   s.lev_b_rows.p, nlb, B::fac(s), B::blk(s), R, acc, Z, nullptr,
-                                   inner, done);
-  } else {
-    ilu_block_solve_kernel<T, false><<<ncols, 256, 0, st>>>(
-        s.N, s.P, s.pat.nnz, a0, fac_per_col, s.rowptr.p, s.col.p, s.diag.p, s.lev_f_ptr.p,
-        s.lev_f_rows.p, nlf, s.lev_b_ptr.p, s.lev_b_rows.p, nlb, B::fac(s), B::blk(s), R, acc, Z,
-        B::triw(s), inner, done);
+    if (rpt <= 1) return launch_block_solve_t<T, true, 1>(s, a0, ncols, fac_per_col, R, acc, Z, st, done);
+    return launch_block_solve_t<T, true, 4>(s, a0, ncols, fac_per_col, R, acc, Z, st, done);
   }
-  return check_launch("ilu_block_solve");
+  if (rpt <= 1) return launch_block_solve_t<T, false, 1>(s, a0, ncols, fac_per_col, R, acc, Z, st, done);
+  if (rpt <= 2) return launch_block_solve_t<T, false, 2>(s, a0, ncols, fac_per_col, R, acc, Z, st, done);
+  return launch_block_solve_t<T, false, 4>(s, a0, ncols, fac_per_col, R, acc, Z, st, done);
 }
 
 template <typename T>

@@ -2,6 +2,8 @@
 // stiffness stack A_q (Eq. A_q) on the shared 9-point Q1 pattern, the load vector F
 // (Eq. stochastic_matrix), the diagonal blocks used by the preconditioners and their ILU(0)
 // factors, and precision casts.
+#include <algorithm>
+
 #include "sg_internal.h"
 
 namespace sg {
@@ -181,6 +183,26 @@ __global__ void ilu0_kernel(int nnz, const int* __restrict__ rowptr, const int* 
   }
 }
 
+// CSR ILU(0) factors -> 9-slot level-major layout used by the wavefront solves (slot 4: 1/u_ii).
+__global__ void lu9_kernel(int m, int N, int nnz, int nfac, const int* __restrict__ rowptr,
+                           const int* __restrict__ col, const int* __restrict__ lev_off,
+                           const double* __restrict__ fac, double* __restrict__ lu9) {
+  long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= (long long)N * nfac) return;
+  int f = (int)(t / N), i = (int)(t % N);
+  int x = i % m, y = i / m;
+  int l = x + 2 * y;
+  int ylo = max(0, (l - (m - 1) + 1) >> 1);
+  int pos = lev_off[l] + (y - ylo);
+  for (int e = rowptr[i]; e < rowptr[i + 1]; ++e) {
+    int c = col[e];
+    int dx = c % m - x, dy = c / m - y;
+    int slot = (dy + 1) * 3 + (dx + 1);
+    double v = fac[(size_t)f * nnz + e];
+    lu9[((size_t)f * 9 + slot) * N + pos] = slot == 4 ? 1.0 / v : v;
+  }
+}
+
 template <typename S, typename D>
 __global__ void cast_kernel(const S* __restrict__ src, D* __restrict__ dst, size_t n) {
   for (size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x; t < n;
@@ -293,6 +315,30 @@ int launch_ilu0(System& s, cudaStream_t st) {
   ilu0_kernel<<<s.nfac, 256, 0, st>>>(s.pat.nnz, s.rowptr.p, s.col.p, s.diag.p, s.lev_f_ptr.p,
                                       s.lev_f_rows.p, nlev, s.fac.p);
   return check_launch("ilu0");
+}
+
+int launch_lu9(System& s, cudaStream_t st) {
+  const int m = s.pat.m;
+  s.nlev9 = 3 * m - 2;
+  std::vector<int> off(s.nlev9 + 1, 0);
+  int maxw = 0;
+  for (int l = 0; l < s.nlev9; ++l) {
+    int ylo = std::max(0, (l - (m - 1) + 1) >> 1);
+    int yhi = std::min(m - 1, l >> 1);
+    int cnt = yhi - ylo + 1;
+    maxw = std::max(maxw, cnt);
+    off[l + 1] = off[l] + cnt;
+  }
+  if (off[s.nlev9] != s.N) return fail(SG_ERR_ARG, "level schedule does not cover the mesh");
+  s.pat.max_width = maxw;
+  SG_TRY(s.lev9_off.alloc(off.size()));
+  SG_TRY(s.lev9_off.upload(off, st));
+  SG_TRY(s.lu9.alloc((size_t)s.nfac * 9 * s.N));
+  SG_CUDA(cudaMemsetAsync(s.lu9.p, 0, sizeof(double) * s.lu9.n, st));
+  long long total = (long long)s.N * s.nfac;
+  lu9_kernel<<<blocks_for(total, 256), 256, 0, st>>>(m, s.N, s.pat.nnz, s.nfac, s.rowptr.p, s.col.p,
+                                                     s.lev9_off.p, s.fac.p, s.lu9.p);
+  return check_launch("lu9");
 }
 
 int launch_cast_f32(const double* src, float* dst, size_t n, cudaStream_t st) {

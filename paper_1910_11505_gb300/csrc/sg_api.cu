@@ -234,11 +234,12 @@ static void free_system(System* s) {
                      &s->lev_b_rows, &s->pair_kb, &s->ent_ptr, &s->ent_u, &s->gs_kptr, &s->gs_k,
                      &s->gs_eptr, &s->gs_ea, &s->flags};
   for (auto* b : ib) b->release();
-  DBuf<double>* db[] = {&s->stack, &s->ent_g, &s->blk, &s->fac, &s->gs_eg, &s->acc, &s->tmp,
+  s->lev9_off.release();
+  DBuf<double>* db[] = {&s->stack, &s->ent_g, &s->blk, &s->fac, &s->lu9, &s->gs_eg, &s->acc, &s->tmp,
                         &s->tmp2, &s->tri_w, &s->V, &s->Z, &s->Hs, &s->cs, &s->sn, &s->g, &s->y,
                         &s->scal, &s->red, &s->rvec};
   for (auto* b : db) b->release();
-  DBuf<float>* fb[] = {&s->stack_f32, &s->ent_g_f32, &s->fac_f32, &s->blk_f32, &s->gs_eg_f32,
+  DBuf<float>* fb[] = {&s->stack_f32, &s->ent_g_f32, &s->lu9_f32, &s->blk_f32, &s->gs_eg_f32,
                        &s->acc32, &s->tmp32, &s->tmp232, &s->tri_w32, &s->V32, &s->Z32,
                        &s->mv32a, &s->mv32b};
   for (auto* b : fb) b->release();
@@ -265,8 +266,11 @@ static int setup_system(System& s, cudaStream_t st) {
   // smem budgets of the kernels
   size_t apply_smem = sizeof(double) * (9 * kChunkK + 9 * (size_t)s.P + kChunkPairs + s.P);
   if (apply_smem > 200 * 1024) return fail(SG_ERR_ARG, "P too large for the operator kernel");
-  s.tri_smem = (size_t)s.N * sizeof(double) <= 200 * 1024;
-  s.tri_smem32 = (size_t)s.N * sizeof(float) <= 200 * 1024;
+  {  // shared memory of the wavefront solve: column + factor ring (8 levels x 5 slots) + levels
+    size_t width = (size_t)(p.n + 2) / 2 + 1, lev = sizeof(int) * 3 * (size_t)(p.n + 1);
+    s.tri_smem = (size_t)s.N * 8 + 40 * 8 * width + lev <= 220 * 1024;
+    s.tri_smem32 = (size_t)s.N * 4 + 40 * 4 * width + lev <= 220 * 1024;
+  }
 
   SG_CUDA(cudaStreamCreateWithFlags(&s.stream, cudaStreamNonBlocking));
   SG_CUDA(cudaEventCreateWithFlags(&s.ev, cudaEventDisableTiming));
@@ -325,10 +329,11 @@ static int setup_system(System& s, cudaStream_t st) {
     SG_TRY(s.fac.alloc((size_t)s.nfac * s.pat.nnz));
     SG_TRY(launch_block_values(s, st));
     SG_TRY(launch_ilu0(s, st));
+    SG_TRY(launch_lu9(s, st));
     if (lowp) {
-      SG_TRY(s.fac_f32.alloc(s.fac.n));
+      SG_TRY(s.lu9_f32.alloc(s.lu9.n));
       SG_TRY(s.blk_f32.alloc(s.blk.n));
-      SG_TRY(launch_cast_f32(s.fac.p, s.fac_f32.p, s.fac.n, st));
+      SG_TRY(launch_cast_f32(s.lu9.p, s.lu9_f32.p, s.lu9.n, st));
       SG_TRY(launch_cast_f32(s.blk.p, s.blk_f32.p, s.blk.n, st));
     }
     if (p.precond == SG_PC_FS_GS) {

@@ -158,8 +158,11 @@ struct System {
   int nfac = 0;                // number of factor sets (1 for mean, P for field split)
   DBuf<double> blk;            // nfac x nnz block matrices (A_0 or K_aa) before factorisation
   DBuf<double> fac;            // nfac x nnz ILU(0) factors
-  DBuf<float> fac_f32;         // FP32 copy for the mixed inner solver
-  DBuf<float> blk_f32;
+  DBuf<float> blk_f32;         // FP32 copy for the mixed inner solver
+  DBuf<double> lu9;            // nfac x 9 x N level-major slot layout of the factors
+  DBuf<float> lu9_f32;
+  DBuf<int> lev9_off;          // start of each wavefront level in level-major order
+  int nlev9 = 0;
   // field-split Gauss-Seidel scatter tables, per source block b: k list and (a, g) entries
   DBuf<int> gs_kptr, gs_k, gs_eptr, gs_ea;
   DBuf<double> gs_eg;
@@ -203,6 +206,7 @@ int launch_assemble(System& s, const double* qp, cudaStream_t st);
 int launch_rhs(System& s, double* F, cudaStream_t st);
 int launch_block_values(System& s, cudaStream_t st);
 int launch_ilu0(System& s, cudaStream_t st);
+int launch_lu9(System& s, cudaStream_t st);
 int launch_cast_f32(const double* src, float* dst, size_t n, cudaStream_t st);
 int launch_cast_bf16(const double* src, __nv_bfloat16* dst, size_t n, cudaStream_t st);
 int launch_cast_f64(const float* src, double* dst, size_t n, cudaStream_t st);
