@@ -62,7 +62,7 @@ typedef struct {
   int precond;       /* SG_PC_*                                                                 */
   int inner_iters;   /* ILU(0)-Richardson steps per diagonal block, >= 1                       */
   int outer_sweeps;  /* steps of the level solver, Eq. level_solver (i_max), >= 1              */
-  int restart;       /* GMRES restart length m, 1 <= m <= 64                                   */
+  int restart;       /* GMRES restart length m, 1 <= m <= 1024                                 */
   int max_iters;     /* cap on GMRES iterations (inner iterations summed over restarts)       */
   double rtol;       /* stop when ||F - K x||_2 <= max(rtol ||F||_2, atol)                     */
   double atol;

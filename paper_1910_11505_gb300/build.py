@@ -36,16 +36,18 @@ def _newest_header() -> float:
     return max(os.path.getmtime(h) for h in hs)
 
 
-def build(verbose: bool = False, extra_flags=None) -> str:
-    """Compile every CUDA source for sm_103a and link the shared library; returns its path."""
-    os.makedirs(BUILD, exist_ok=True)
+def build(verbose: bool = False, extra_flags=None, out_dir: str = BUILD) -> str:
+    """Compile every CUDA source for sm_103a and link the shared library; returns its path.
+
+    ``extra_flags`` (e.g. compile-time tuning macros) and ``out_dir`` build a variant elsewhere."""
+    os.makedirs(out_dir, exist_ok=True)
     nvcc = _nvcc()
     srcs = sorted(glob.glob(os.path.join(CSRC, "*.cu")))
     hdr_time = _newest_header()
     flags = FLAGS + list(extra_flags or [])
     jobs = []
     for src in srcs:
-        obj = os.path.join(BUILD, os.path.basename(src)[:-3] + ".o")
+        obj = os.path.join(out_dir, os.path.basename(src)[:-3] + ".o")
         if (not os.path.exists(obj) or os.path.getmtime(obj) < os.path.getmtime(src)
                 or os.path.getmtime(obj) < hdr_time or extra_flags):
             jobs.append([nvcc, *ARCH, *flags, "-c", src, "-o", obj])
@@ -61,10 +63,11 @@ def build(verbose: bool = False, extra_flags=None) -> str:
 
     with ThreadPoolExecutor(max_workers=max(1, min(len(jobs), os.cpu_count() or 4))) as ex:
         list(ex.map(run, jobs))
-    objs = [os.path.join(BUILD, os.path.basename(s)[:-3] + ".o") for s in srcs]
-    if jobs or not os.path.exists(LIB):
-        run([nvcc, *ARCH, "-shared", "-o", LIB, *objs])
-    return LIB
+    objs = [os.path.join(out_dir, os.path.basename(s)[:-3] + ".o") for s in srcs]
+    lib = os.path.join(out_dir, os.path.basename(LIB))
+    if jobs or not os.path.exists(lib):
+        run([nvcc, *ARCH, "-shared", "-o", lib, *objs])
+    return lib
 
 
 if __name__ == "__main__":

@@ -12,7 +12,7 @@ namespace sg {
 
 constexpr int kRedBlocks = 304;   // 2 CTAs per SM on 152 SMs
 constexpr int kRedThreads = 256;
-constexpr int kMaxBasis = 65;     // restart <= 64 -> at most 65 basis vectors
+constexpr int kMaxBasis = 1025;   // restart <= 1024 -> at most 1025 basis vectors
 constexpr int kLT = 8;            // basis vectors per register tile
 
 namespace {
@@ -214,16 +214,27 @@ __global__ void init_cycle_kernel(size_t n, const double* __restrict__ r, double
   }
 }
 
-// y = H(0:k,0:k)^{-1} g(0:k), k = flags[1]; one thread.
-__global__ void backsolve_kernel(const double* __restrict__ Hs, int ldh,
-                                 const double* __restrict__ g, double* __restrict__ y,
-                                 const int* __restrict__ flags) {
-  if (threadIdx.x != 0 || blockIdx.x != 0) return;
-  int k = flags[1];
+// y = H(0:k,0:k)^{-1} g(0:k), k = flags[1]: column-oriented back substitution by one CTA;
+// after y_i is known every thread removes H(l,i) y_i from its own right-hand-side entries l < i.
+__global__ void __launch_bounds__(1024) backsolve_kernel(const double* __restrict__ Hs, int ldh,
+                                                         const double* __restrict__ g,
+                                                         double* __restrict__ y,
+                                                         const int* __restrict__ flags) {
+  __shared__ double rhs[kMaxBasis];
+  __shared__ double yi;
+  const int k = flags[1];
+  for (int l = threadIdx.x; l < k; l += blockDim.x) rhs[l] = g[l];
+  __syncthreads();
   for (int i = k - 1; i >= 0; --i) {
-    double s = g[i];
-    for (int l = i + 1; l < k; ++l) s -= Hs[(size_t)l * ldh + i] * y[l];
-    y[i] = s / Hs[(size_t)i * ldh + i];
+    const double* col = Hs + (size_t)i * ldh;
+    if (threadIdx.x == 0) {
+      yi = rhs[i] / col[i];
+      y[i] = yi;
+    }
+    __syncthreads();
+    const double v = yi;
+    for (int l = threadIdx.x; l < i; l += blockDim.x) rhs[l] -= col[l] * v;
+    __syncthreads();
   }
 }
 
@@ -310,7 +321,7 @@ int k_arnoldi(System& s, size_t n, int j, int last_col, cudaStream_t st) {
 
 int k_finish_cycle(System& s, size_t n, double* x, bool z32, cudaStream_t st) {
   TimeScope ts(s.timer, K_OTHER, st);
-  backsolve_kernel<<<1, 32, 0, st>>>(s.Hs.p, s.m + 1, s.g.p, s.y.p, s.flags.p);
+  backsolve_kernel<<<1, 1024, 0, st>>>(s.Hs.p, s.m + 1, s.g.p, s.y.p, s.flags.p);
   SG_TRY(check_launch("backsolve"));
   if (z32)
     update_x_kernel<float><<<kRedBlocks * 2, kRedThreads, 0, st>>>(n, s.Z32.p, s.y.p, s.flags.p, x);

@@ -36,7 +36,14 @@ __device__ __forceinline__ void level_range(int l, int m, int& ylo, int& cnt) {
 // for every load the thread has in flight, so each level would pay a full L2 round trip.  Each
 // thread copies and later reads only its own rows' factors, so the ring needs no barrier of its
 // own; cp.async.wait_group orders the copy before the read.
-constexpr int kAhead = 8;
+#ifndef SG_TRI_AHEAD
+#define SG_TRI_AHEAD 8
+#endif
+#ifndef SG_TRI_THREADS
+#define SG_TRI_THREADS 256
+#endif
+constexpr int kAhead = SG_TRI_AHEAD;
+constexpr int kTriThreads = SG_TRI_THREADS;
 
 template <typename T>
 __device__ __forceinline__ void cp_async_elem(T* dst, const T* src) {
@@ -111,7 +118,7 @@ __device__ __forceinline__ void ilu9_sweep(T* w, T* ring, int W, const T* __rest
 // CTA c solves column a = a0 + c with factor set (fac_per_col ? a : 0):
 //   z = ILU^{-1}(rhs), then inner-1 times z += ILU^{-1}(rhs - K_blk z), rhs = R[:,a] - acc[:,a].
 template <typename T, bool SMEM, int RPT>
-__global__ void __launch_bounds__(256) ilu_block_solve_kernel(
+__global__ void __launch_bounds__(kTriThreads) ilu_block_solve_kernel(
     int m, int N, int P, int nnz, int a0, int fac_per_col, const int* __restrict__ lev_off,
     int nlev, int W, const T* __restrict__ lu9s, const int* __restrict__ rowptr,
     const int* __restrict__ col, const T* __restrict__ blks, const T* __restrict__ R,
@@ -233,7 +240,7 @@ int launch_block_solve_t(System& s, int a0, int ncols, int fac_per_col, const T*
   auto kern = ilu_block_solve_kernel<T, SMEM, RPT>;
   SG_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   TimeScope ts(s.timer, K_ILU_SOLVE, st);
-  kern<<<ncols, 256, smem, st>>>(s.pat.m, s.N, s.P, s.pat.nnz, a0, fac_per_col, s.lev9_off.p,
+  kern<<<ncols, kTriThreads, smem, st>>>(s.pat.m, s.N, s.P, s.pat.nnz, a0, fac_per_col, s.lev9_off.p,
                                  s.nlev9, W, B::lu9(s), s.rowptr.p, s.col.p, B::blk(s), R, acc, Z,
                                  SMEM ? nullptr : B::triw(s), std::max(1, s.prm.inner_iters), done);
   return check_launch("ilu_block_solve");
@@ -243,7 +250,7 @@ template <typename T>
 int launch_block_solve(System& s, int a0, int ncols, int fac_per_col, const T* R, const T* acc,
                        T* Z, cudaStream_t st, const int* done) {
   using B = PcBufs<T>;
-  int rpt = (s.pat.max_width + 255) / 256;
+  int rpt = (s.pat.max_width + kTriThreads - 1) / kTriThreads;
   if (B::smem(s)) {
     if (rpt <= 1) return launch_block_solve_t<T, true, 1>(s, a0, ncols, fac_per_col, R, acc, Z, st, done);
     return launch_block_solve_t<T, true, 4>(s, a0, ncols, fac_per_col, R, acc, Z, st, done);

@@ -91,7 +91,7 @@ static int validate(const sg_params& p) {
   if (!std::isfinite(p.mu) || !std::isfinite(p.f)) return fail(SG_ERR_ARG, "mu and f must be finite");
   if (p.precond < SG_PC_NONE || p.precond > SG_PC_FS_JACOBI) return fail(SG_ERR_ARG, "unknown preconditioner");
   if (p.inner_iters < 1 || p.outer_sweeps < 1) return fail(SG_ERR_ARG, "inner_iters and outer_sweeps must be >= 1");
-  if (p.restart < 1 || p.restart > 64) return fail(SG_ERR_ARG, "restart must be in [1, 64]");
+  if (p.restart < 1 || p.restart > 1024) return fail(SG_ERR_ARG, "restart must be in [1, 1024]");
   if (p.max_iters < 1) return fail(SG_ERR_ARG, "max_iters must be >= 1");
   if (!(p.rtol >= 0.0) || !(p.atol >= 0.0)) return fail(SG_ERR_ARG, "rtol, atol must be >= 0");
   if (p.precision < SG_FP64 || p.precision > SG_MIXED_BF16) return fail(SG_ERR_ARG, "unknown precision");

@@ -11,7 +11,7 @@ import ctypes
 import os
 
 HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(HERE, "_build", "libsg_gb300.so")
+LIB_PATH = os.environ.get("SG_LIB_PATH") or os.path.join(HERE, "_build", "libsg_gb300.so")
 
 SG_OK = 0
 SG_ERR_ARG = -1
