@@ -112,6 +112,21 @@ int sg_matvec_lowp(sg_handle* h, int sys, const float* X, float* Y, void* stream
  * R, Z device N x P FP64, must not overlap.  Asynchronous on ``stream``. */
 int sg_precond_apply(sg_handle* h, int sys, const double* R, double* Z, void* stream);
 
+/* No counterpart in the paper: the same field-split Gauss-Seidel application as
+ * sg_precond_apply (outer_sweeps = 1), for callers that must not allocate device memory, such as
+ * a process whose device memory is already reserved by another allocator (a framework's caching
+ * pool) or code with a fixed memory budget that may not grow.  Its N x P off-diagonal scratch is
+ * a fixed array of SG_NOALLOC_MAX_ENTRIES doubles (8 MiB) inside this library, which every GPU
+ * that loads the library holds until the process exits; the call itself allocates nothing and
+ * clears the part it uses.  The first call on a device looks up that array's device address, so
+ * make that first call before any stream capture.  All calls share the one array: calls whose
+ * work overlaps on the GPU (other streams, other threads) race and give wrong results.
+ * SG_ERR_ARG if the system does not use SG_PC_FS_GS with outer_sweeps = 1, if N x P exceeds
+ * SG_NOALLOC_MAX_ENTRIES, if one column does not fit the shared-memory block solve, or if the
+ * handle's device is not current.  R, Z as for sg_precond_apply.  Asynchronous on ``stream``. */
+#define SG_NOALLOC_MAX_ENTRIES (1 << 20)
+int sg_precond_apply_noalloc(sg_handle* h, int sys, const double* R, double* Z, void* stream);
+
 /* F of Eq. stochastic_matrix: F[j*P + 0] = int f phi_j, other chaos terms 0, boundary rows 0.
  * F device N x P FP64.  Asynchronous on ``stream``. */
 int sg_rhs(sg_handle* h, int sys, double* F, void* stream);

@@ -353,6 +353,15 @@ int precond_apply_t(System& s, const T* R, T* Z, cudaStream_t st, const int* don
 
 }  // namespace
 
+int fs_gs_apply_f64_with(System& s, const double* R, double* Z, double* acc, cudaStream_t st) {
+  SG_CUDA(cudaMemsetAsync(acc, 0, sizeof(double) * (size_t)s.N * s.P, st));
+  for (int a = 0; a < s.P; ++a) {
+    SG_TRY(launch_block_solve<double>(s, a, 1, 1, R, a > 0 ? acc : nullptr, Z, st, nullptr));
+    if (a + 1 < s.P) SG_TRY(launch_scatter<double>(s, a, Z, acc, st, nullptr));
+  }
+  return SG_OK;
+}
+
 int precond_apply_f64(System& s, const double* R, double* Z, cudaStream_t st, const int* done) {
   return precond_apply_t<double>(s, R, Z, st, done);
 }

@@ -221,6 +221,9 @@ int precond_apply_f64(System& s, const double* R, double* Z, cudaStream_t st,
                       const int* done = nullptr);
 int precond_apply_f32(System& s, const float* R, float* Z, cudaStream_t st,
                       const int* done = nullptr);
+// One field-split Gauss-Seidel application (outer_sweeps = 1) whose off-diagonal accumulator is
+// the caller's N x P array ``acc`` (cleared here).
+int fs_gs_apply_f64_with(System& s, const double* R, double* Z, double* acc, cudaStream_t st);
 
 // Krylov launchers (k_krylov.cu)
 int k_norm(System& s, size_t n, const double* r, double* out, cudaStream_t st);

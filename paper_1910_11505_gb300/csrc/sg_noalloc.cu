@@ -1,0 +1,61 @@
+// sg_precond_apply_noalloc: the field-split Gauss-Seidel preconditioner with its scratch in a
+// fixed device array of this library instead of memory allocated for the handle.
+//
+// The Gauss-Seidel sweep needs an N x P accumulator for the coupling sum_{b<a} K_ab z_b.  Here it
+// is the file-scope array below, which every GPU that loads the library holds until the process
+// exits.  Host code cannot use the array's name as a device address (it names a host-side
+// stand-in), so the address is looked up once per device with cudaGetSymbolAddress, with that
+// device current, on the first call made on it.
+#include <mutex>
+
+#include "sg_internal.h"
+
+static __device__ __align__(256) double g_noalloc_scratch[SG_NOALLOC_MAX_ENTRIES];
+
+namespace {
+
+constexpr int kMaxDevices = 256;
+std::mutex g_mu;
+double* g_scratch_addr[kMaxDevices] = {};
+
+int scratch_for_current_device(int dev, double** out) {
+  if (dev < 0 || dev >= kMaxDevices) return sg::fail(SG_ERR_ARG, "device ordinal out of range");
+  std::lock_guard<std::mutex> lock(g_mu);
+  if (g_scratch_addr[dev] == nullptr) {
+    void* p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess || p == nullptr)
+      return sg::fail(SG_ERR_CUDA, std::string("cudaGetSymbolAddress of the scratch array failed: ") +
+                                       cudaGetErrorString(e));
+    g_scratch_addr[dev] = static_cast<double*>(p);
+  }
+  *out = g_scratch_addr[dev];
+  return SG_OK;
+}
+
+}  // namespace
+
+extern "C" int sg_precond_apply_noalloc(sg_handle* h, int sys, const double* R, double* Z,
+                                        void* stream) {
+  if (!h || sys < 0 || sys >= (int)h->sys.size() || !R || !Z)
+    return sg::fail(SG_ERR_ARG, "bad handle, system index or pointer");
+  sg::System& s = *h->sys[sys];
+  if (s.prm.precond != SG_PC_FS_GS || s.prm.outer_sweeps != 1)
+    return sg::fail(SG_ERR_ARG, "sg_precond_apply_noalloc serves the field-split Gauss-Seidel "
+                                "preconditioner with outer_sweeps = 1 only");
+  if (!s.tri_smem)
+    return sg::fail(SG_ERR_ARG, "sg_precond_apply_noalloc: the mesh is too large for the "
+                                "shared-memory block solve (it would need device scratch)");
+  const long long need = (long long)s.N * s.P;
+  if (need > SG_NOALLOC_MAX_ENTRIES)
+    return sg::fail(SG_ERR_ARG, "sg_precond_apply_noalloc: N x P = " + std::to_string(need) +
+                                    " exceeds the fixed scratch of " +
+                                    std::to_string(SG_NOALLOC_MAX_ENTRIES) + " doubles");
+  int dev = -1;
+  SG_CUDA(cudaGetDevice(&dev));
+  if (dev != h->device)
+    return sg::fail(SG_ERR_ARG, "the handle's device must be current");
+  double* acc = nullptr;
+  SG_TRY(scratch_for_current_device(dev, &acc));
+  return sg::fs_gs_apply_f64_with(s, R, Z, acc, (cudaStream_t)stream);
+}
