@@ -33,6 +33,9 @@ __device__ __forceinline__ TA warp_sum(TA v) {
   return v;
 }
 
+// Rows per tile: the pair and entry tables are read once per tile instead of once per row.
+constexpr int kRows = 4;
+
 template <typename TA, typename TV>
 __global__ void __launch_bounds__(256) sg_apply_kernel(
     int N, int P, int L, const int* __restrict__ rowptr, const int* __restrict__ col,
@@ -42,50 +45,72 @@ __global__ void __launch_bounds__(256) sg_apply_kernel(
     TA* __restrict__ Y, TA alpha, const TA* __restrict__ B, TA beta, const int* __restrict__ done) {
   if (done != nullptr && *done) return;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  TA* As = reinterpret_cast<TA*>(smem_raw);   // 9 x kChunkK
-  TA* Xs = As + 9 * kChunkK;                  // 9 x P
-  TA* Ts = Xs + 9 * P;                        // kChunkPairs
-  TA* Ys = Ts + kChunkPairs;                  // P
+  // stencil slots are padded to 9 per row with zeros, so every row runs the same unrolled loop
+  TA* As = reinterpret_cast<TA*>(smem_raw);   // kRows x 9 x kChunkK
+  TA* Xs = As + kRows * 9 * kChunkK;          // kRows x 9 x P
+  TA* Ts = Xs + kRows * 9 * P;                // kRows x kChunkPairs
+  TA* Ys = Ts + kRows * kChunkPairs;          // kRows x P
+  __shared__ int rs_e0[kRows], rs_ne[kRows];
   const int tid = threadIdx.x, nth = blockDim.x;
-  const int warp = tid >> 5, lane = tid & 31, nwarp = nth >> 5;
+  const int ntiles = (N + kRows - 1) / kRows;
 
-  for (int row = blockIdx.x; row < N; row += gridDim.x) {
-    const int e0 = rowptr[row];
-    const int ne = rowptr[row + 1] - e0;
-    for (int t = tid; t < ne * P; t += nth) {
-      int e = t / P, b = t - e * P;
-      Xs[t] = X[(size_t)col[e0 + e] * P + b];
+  for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    const int row0 = tile * kRows;
+    const int nr = min(kRows, N - row0);
+    if (tid < kRows) {
+      int r = row0 + tid;
+      rs_e0[tid] = tid < nr ? rowptr[r] : 0;
+      rs_ne[tid] = tid < nr ? rowptr[r + 1] - rowptr[r] : 0;
     }
-    for (int a = tid; a < P; a += nth) Ys[a] = TA(0);
+    __syncthreads();
+    for (int t = tid; t < kRows * 9 * P; t += nth) {
+      int re = t / P, b = t - re * P;
+      int r = re / 9, e = re - r * 9;
+      TA v = TA(0);
+      if (e < rs_ne[r]) v = X[(size_t)col[rs_e0[r] + e] * P + b];
+      Xs[t] = v;
+    }
+    for (int t = tid; t < kRows * P; t += nth) Ys[t] = TA(0);
     for (int c = 0; c < nchunks; ++c) {
       const int2 uu = chunks[c];
       const int2 kr = chunks_k[c];
       const int kw = kr.y - kr.x;
-      for (int t = tid; t < ne * kw; t += nth) {
-        int e = t / kw, kk = t - e * kw;
-        As[e * kChunkK + kk] = cvt<TA, TV>(stack + (size_t)(e0 + e) * L + kr.x + kk);
+      for (int t = tid; t < kRows * 9 * kw; t += nth) {
+        int re = t / kw, kk = t - re * kw;
+        int r = re / 9, e = re - r * 9;
+        TA v = TA(0);
+        if (e < rs_ne[r]) v = cvt<TA, TV>(stack + (size_t)(rs_e0[r] + e) * L + kr.x + kk);
+        As[re * kChunkK + kk] = v;
       }
       __syncthreads();
       for (int u = uu.x + tid; u < uu.y; u += nth) {
-        int kb = pair_kb[u];
-        int kk = (kb >> 16) - kr.x, b = kb & 0xffff;
-        TA s = TA(0);
-        for (int e = 0; e < ne; ++e) s = fma(As[e * kChunkK + kk], Xs[e * P + b], s);
-        Ts[u - uu.x] = s;
+        const int kb = pair_kb[u];
+        const int kk = (kb >> 16) - kr.x, b = kb & 0xffff;
+#pragma unroll
+        for (int r = 0; r < kRows; ++r) {
+          const TA* a = As + r * 9 * kChunkK + kk;
+          const TA* x = Xs + r * 9 * P + b;
+          TA s = a[0] * x[0];
+#pragma unroll
+          for (int e = 1; e < 9; ++e) s = fma(a[e * kChunkK], x[e * P], s);
+          Ts[r * kChunkPairs + (u - uu.x)] = s;
+        }
       }
       __syncthreads();
+      // one thread per (a, row): a sequential sum, no cross-lane reduction (on this GPU an FP64
+      // warp instruction costs the same whatever its active lanes, so shuffle trees are dear)
       const int* ep = ent_ptr + (size_t)c * (P + 1);
-      for (int a = warp; a < P; a += nwarp) {
-        TA s = TA(0);
-        for (int t = ep[a] + lane; t < ep[a + 1]; t += 32) s = fma(ent_g[t], Ts[ent_u[t]], s);
-        s = warp_sum(s);
-        if (lane == 0) Ys[a] += s;
+      for (int t = tid; t < kRows * P; t += nth) {
+        const int a = t / kRows, r = t - a * kRows;
+        TA acc = TA(0);
+        for (int q = ep[a]; q < ep[a + 1]; ++q) acc = fma(ent_g[q], Ts[r * kChunkPairs + ent_u[q]], acc);
+        Ys[r * P + a] += acc;
       }
       __syncthreads();
     }
-    for (int a = tid; a < P; a += nth) {
-      size_t o = (size_t)row * P + a;
-      TA v = alpha * Ys[a];
+    for (int t = tid; t < nr * P; t += nth) {
+      size_t o = (size_t)row0 * P + t;
+      TA v = alpha * Ys[t];
       if (B != nullptr) v = fma(beta, B[o], v);
       Y[o] = v;
     }
@@ -95,7 +120,8 @@ __global__ void __launch_bounds__(256) sg_apply_kernel(
 
 template <typename TA>
 size_t apply_smem(int P) {
-  return sizeof(TA) * (9 * kChunkK + 9 * (size_t)P + kChunkPairs + P);
+  return sizeof(TA) * ((size_t)kRows * 9 * kChunkK + (size_t)kRows * 9 * P +
+                       (size_t)kRows * kChunkPairs + (size_t)kRows * P);
 }
 
 int num_sms() {
@@ -115,8 +141,8 @@ int launch_apply(const System& s, const TV* stack, const TA* eg, const TA* X, TA
   size_t smem = apply_smem<TA>(s.P);
   auto kern = sg_apply_kernel<TA, TV>;
   SG_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  int per_sm = (int)std::max<size_t>(1, std::min<size_t>(8, (200 * 1024) / smem));
-  int grid = std::min(s.N, num_sms() * per_sm);
+  int per_sm = (int)std::max<size_t>(1, std::min<size_t>(8, (220 * 1024) / smem));
+  int grid = std::min((s.N + kRows - 1) / kRows, num_sms() * per_sm);
   TimeScope ts(s.timer, sizeof(TA) == 8 ? K_APPLY_F64 : K_APPLY_LOWP, st);
   kern<<<grid, 256, smem, st>>>(s.N, s.P, s.L, s.rowptr.p, s.col.p, stack, s.pair_kb.p, s.chunks.p,
                                 s.chunks_k.p, s.op.nchunks, s.ent_ptr.p, s.ent_u.p, eg, X, Y, alpha,

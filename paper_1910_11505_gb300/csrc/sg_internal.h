@@ -110,8 +110,8 @@ Pattern make_pattern(int n);
 // The SG operator per node row i: T[k,b] = sum_e A[e,k] X[col_e, b] for every (k,b) pair that
 // meets a nonzero G_k[a,b]; then Y[i,a] = sum G_k[a,b] T[k,b].  Pairs are sorted by (k, b) and cut
 // into chunks of at most kChunkPairs pairs spanning at most kChunkK consecutive k.
-constexpr int kChunkPairs = 2048;
-constexpr int kChunkK = 256;
+constexpr int kChunkPairs = 512;
+constexpr int kChunkK = 64;
 
 struct ChunkDesc {
   int u0, u1;  // pair range

@@ -1,0 +1,64 @@
+"""Small, self-contained cases of single kernels for profiling (e.g. under ``ncu``).
+
+    python -m paper_1910_11505_gb300.profile_cases precond [fs_gs|fs_jacobi|mean] [n]
+    python -m paper_1910_11505_gb300.profile_cases matvec [fp64|fp32|bf16] [n] [M] [p]
+
+Each case builds one SG system, runs three applications of the chosen operation on seeded
+inputs and exits 0.  Sizes stay at a few GB of device memory.
+"""
+
+from __future__ import annotations
+
+import os
+import sys
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+
+def main(argv):
+    import torch
+
+    from paper_1910_11505_gb300 import build as B
+    B.build()
+    from paper_1910_11505_gb300 import sg, workloads as W
+
+    what = argv[1] if len(argv) > 1 else "precond"
+    if what == "precond":
+        pc = argv[2] if len(argv) > 2 else "fs_gs"
+        n = int(argv[3]) if len(argv) > 3 else 128
+        h = sg.sg_setup(sg.sg_default_params(n=n, M=4, p=3, sigma=0.5, ell=0.5, precond=pc))
+        N, P, _ = sg.sg_dims(h)
+        R = torch.from_numpy(W.random_field(N, P, seed=1)).cuda()
+        Z = torch.empty_like(R)
+        for _ in range(3):
+            sg.sg_precond_apply(h, 0, R, Z)
+    elif what == "matvec":
+        prec = argv[2] if len(argv) > 2 else "fp64"
+        n = int(argv[3]) if len(argv) > 3 else 128
+        M = int(argv[4]) if len(argv) > 4 else 6
+        p = int(argv[5]) if len(argv) > 5 else 3
+        h = sg.sg_setup(sg.sg_default_params(n=n, M=M, p=p, sigma=1.0, ell=0.5, precond="none",
+                                             precision=prec))
+        N, P, _ = sg.sg_dims(h)
+        X = torch.from_numpy(W.random_field(N, P, seed=2)).cuda()
+        if prec == "fp64":
+            Y = torch.empty_like(X)
+            for _ in range(3):
+                sg.sg_matvec(h, 0, X, Y)
+        else:
+            X32 = X.float()
+            Y32 = torch.empty_like(X32)
+            for _ in range(3):
+                sg.sg_matvec_lowp(h, 0, X32, Y32)
+    else:
+        raise SystemExit(f"unknown case {what}")
+    torch.cuda.synchronize()
+    h.close()
+    print("ok", what)
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main(sys.argv))

@@ -61,8 +61,8 @@ def c2_params(sigma=None):
 
 
 def c3_params(precision="fp64"):
-    return dict(n=256, M=6, p=3, sigma=1.0, ell=0.5, precond="mean", rtol=1e-8,
-                precision=precision)
+    return dict(n=256, M=6, p=3, sigma=1.0, ell=0.5, precond="mean", rtol=1e-8, restart=100,
+                max_iters=6000, precision=precision)
 
 
 def c4_params(nsys: int = 64, seed: int = DEFAULT_SEED, precision="fp32"):
