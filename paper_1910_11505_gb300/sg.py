@@ -30,7 +30,10 @@ PRECISIONS = {"fp64": SG_FP64, "fp32": SG_MIXED_FP32, "bf16": SG_MIXED_BF16}
 EXPORTED = ["sg_default_params", "sg_setup", "sg_dims", "sg_nnz", "sg_matvec", "sg_matvec_lowp",
             "sg_precond_apply", "sg_precond_apply_noalloc", "sg_rhs", "sg_gmres_solve",
             "sg_export", "sg_launch_count",
-            "sg_timing_start", "sg_timing_stop", "sg_free", "sg_last_error"]
+            "sg_timing_start", "sg_timing_stop", "sg_free", "sg_last_error",
+            "sgnet_create", "sgnet_set_stats", "sgnet_forward", "sgnet_predict", "sgnet_loss_grad",
+            "sgnet_adam_step", "sgnet_train_step", "sgnet_num_params", "sgnet_get", "sgnet_set",
+            "sgnet_free"]
 
 K_CLASSES = ["apply_f64", "apply_lowp", "ilu_solve", "gs_scatter", "arnoldi", "other"]
 
@@ -92,6 +95,24 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
                                    ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(ctypes.c_longlong)]
     lib.sg_free.argtypes = [vp]
     lib.sg_free.restype = None
+    fp = ctypes.POINTER(ctypes.c_float)
+    lib.sgnet_create.argtypes = [c_int, c_int, c_int, c_int, c_int, c_int, ctypes.c_ulonglong,
+                                 ctypes.POINTER(vp)]
+    lib.sgnet_set_stats.argtypes = [vp, vp, vp, c_int, vp]
+    lib.sgnet_forward.argtypes = [vp, vp, c_int, vp, vp]
+    lib.sgnet_predict.argtypes = [vp, vp, c_int, vp, vp]
+    lib.sgnet_loss_grad.argtypes = [vp, vp, vp, c_int, fp, vp]
+    lib.sgnet_adam_step.argtypes = [vp, ctypes.c_float, vp]
+    lib.sgnet_train_step.argtypes = [vp, vp, vp, c_int, ctypes.c_float, fp, vp]
+    lib.sgnet_num_params.argtypes = [vp]
+    lib.sgnet_num_params.restype = ctypes.c_longlong
+    lib.sgnet_get.argtypes = [vp, c_int, fp, ctypes.c_size_t]
+    lib.sgnet_set.argtypes = [vp, c_int, fp, ctypes.c_size_t]
+    lib.sgnet_free.argtypes = [vp]
+    lib.sgnet_free.restype = None
+    for name in ("sgnet_create", "sgnet_set_stats", "sgnet_forward", "sgnet_predict",
+                 "sgnet_loss_grad", "sgnet_adam_step", "sgnet_train_step", "sgnet_get", "sgnet_set"):
+        getattr(lib, name).restype = c_int
     lib.sg_last_error.argtypes = []
     lib.sg_last_error.restype = ctypes.c_char_p
     for name in ("sg_setup", "sg_dims", "sg_nnz", "sg_matvec", "sg_matvec_lowp", "sg_precond_apply",
@@ -254,3 +275,74 @@ def sg_timing_stop(h: SGHandle):
 
 def sg_free(h: SGHandle):
     h.close()
+
+
+class SGNet:
+    """Owns an ``sgnet*`` (include/sgnet.h); methods marshal torch tensors to the C ABI."""
+
+    def __init__(self, in_dim, h1, h2, out_dim, max_batch, bf16=True, seed=1910115050):
+        raw = ctypes.c_void_p()
+        _check(load_library().sgnet_create(in_dim, h1, h2, out_dim, max_batch, int(bool(bf16)),
+                                           seed, ctypes.byref(raw)))
+        self.raw = raw
+        self.dims = (in_dim, h1, h2, out_dim)
+        self.max_batch = max_batch
+
+    def close(self):
+        if self.raw:
+            load_library().sgnet_free(self.raw)
+            self.raw = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def num_params(self):
+        return int(load_library().sgnet_num_params(self.raw))
+
+    def set_stats(self, Z, T, stream=None):
+        _check(load_library().sgnet_set_stats(self.raw, _ptr(Z, "f32"), _ptr(T, "f32"), Z.shape[0],
+                                              _stream_ptr(stream)))
+
+    def forward(self, Z, Y, stream=None):
+        _check(load_library().sgnet_forward(self.raw, _ptr(Z, "f32"), Z.shape[0], _ptr(Y, "f32"),
+                                            _stream_ptr(stream)))
+
+    def predict(self, Z, X, stream=None):
+        _check(load_library().sgnet_predict(self.raw, _ptr(Z, "f32"), Z.shape[0], _ptr(X, "f64"),
+                                            _stream_ptr(stream)))
+
+    def loss_grad(self, Z, T, stream=None, want_loss=True):
+        loss = ctypes.c_float()
+        _check(load_library().sgnet_loss_grad(self.raw, _ptr(Z, "f32"), _ptr(T, "f32"), Z.shape[0],
+                                              ctypes.byref(loss) if want_loss else None,
+                                              _stream_ptr(stream)))
+        return loss.value if want_loss else None
+
+    def adam_step(self, lr, stream=None):
+        _check(load_library().sgnet_adam_step(self.raw, ctypes.c_float(lr), _stream_ptr(stream)))
+
+    def train_step(self, Z, T, lr, stream=None, want_loss=False):
+        loss = ctypes.c_float()
+        _check(load_library().sgnet_train_step(self.raw, _ptr(Z, "f32"), _ptr(T, "f32"), Z.shape[0],
+                                               ctypes.c_float(lr),
+                                               ctypes.byref(loss) if want_loss else None,
+                                               _stream_ptr(stream)))
+        return loss.value if want_loss else None
+
+    def get(self, what):
+        import numpy as np
+        count = self.num_params if what in (0, 1) else 2 * self.dims[0]
+        out = np.empty(count, dtype=np.float32)
+        _check(load_library().sgnet_get(self.raw, what,
+                                        out.ctypes.data_as(ctypes.POINTER(ctypes.c_float)), count))
+        return out
+
+    def set(self, what, values):
+        import numpy as np
+        arr = np.ascontiguousarray(values, dtype=np.float32)
+        _check(load_library().sgnet_set(self.raw, what,
+                                        arr.ctypes.data_as(ctypes.POINTER(ctypes.c_float)), arr.size))

@@ -10,7 +10,7 @@ import sys
 import pytest
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
-HEADER = os.path.join(ROOT, "include", "sg.h")
+HEADERS = [os.path.join(ROOT, "include", h) for h in ("sg.h", "sgnet.h")]
 
 
 @pytest.fixture(scope="module")
@@ -22,8 +22,8 @@ def lib():
 
 
 def _declared():
-    text = open(HEADER).read()
-    return sorted(set(re.findall(r"^\s*(?:int|void|long long|const char\*)\s+(sg_\w+)\s*\(", text, re.M)))
+    text = "".join(open(h).read() for h in HEADERS)
+    return sorted(set(re.findall(r"^\s*(?:int|void|long long|const char\*)\s+(sg\w+)\s*\(", text, re.M)))
 
 
 def test_every_declared_symbol_is_exported(lib):
