@@ -1,0 +1,135 @@
+"""Measurement runs of the configurations other than the default bench workload.
+
+    python -m paper_1910_11505_gb300.experiments c3            # FP64 vs mixed FP32 / BF16 solves
+    python -m paper_1910_11505_gb300.experiments c5 [ntrain] [ntest] [steps]   # learned warm start
+    python -m paper_1910_11505_gb300.experiments c4 [nsys]     # batch of uneven systems
+
+Each prints one JSON line.  Times are wall-clock around the C-ABI solve calls (the calls
+synchronise), with setup excluded and reported separately.
+"""
+
+from __future__ import annotations
+
+import json
+import os
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+
+def _solve_one(sg, torch, d):
+    t0 = time.time()
+    h = sg.sg_setup(sg.sg_default_params(**d))
+    torch.cuda.synchronize()
+    setup = time.time() - t0
+    N, P, _ = sg.sg_dims(h)
+    F = torch.empty(N, P, dtype=torch.float64, device="cuda")
+    sg.sg_rhs(h, 0, F)
+    X = torch.zeros_like(F)
+    torch.cuda.synchronize()
+    t0 = time.time()
+    rc, info = sg.sg_gmres_solve(h, [F], [X], raise_on_error=False)
+    secs = time.time() - t0
+    return h, F, X, rc, info[0], secs, setup
+
+
+def run_c3():
+    import torch
+    from paper_1910_11505_gb300 import sg, workloads as W
+    out = {"config": "c3: 256x256 Q1, M=6, p=3 (P=84, L=924), sigma=1, ell=0.5, mean-based ILU(0), "
+                     "GMRES(100), relative residual 1e-8"}
+    ref = None
+    for prec in ("fp64", "fp32", "bf16"):
+        d = W.c3_params(prec)
+        if prec == "bf16":
+            d["max_iters"] = 600
+        h, F, X, rc, info, secs, setup = _solve_one(sg, torch, d)
+        rec = {"rc": rc, "iters": info["iters"], "refinements": info["restarts"],
+               "rel_resid": info["rel_resid"], "solve_s": secs, "setup_s": setup,
+               "solves_per_s": (1.0 / secs) if rc == 0 else 0.0}
+        if prec == "fp64":
+            ref = X.clone()
+        elif rc == 0:
+            rec["rel_err_vs_fp64"] = float((X - ref).norm() / ref.norm())
+        out[prec] = rec
+        h.close()
+        del F, X
+        torch.cuda.empty_cache()
+    print(json.dumps(out), flush=True)
+
+
+def run_c5(ntrain=4096, ntest=256, steps=3000):
+    import numpy as np
+    import torch
+    from paper_1910_11505_gb300 import learned, sg, workloads as W
+    draws = W.c5_draws(ntrain + ntest)
+    base = dict(n=64, M=4, p=3, precond="mean")
+    tr = [dict(base, sigma=s, ell=l) for s, l in draws[:ntrain]]
+    te = [dict(base, sigma=s, ell=l) for s, l in draws[ntrain:]]
+    Z, T, gen = learned.generate(tr, chunk=64, precision="fp32", rtol=1e-6)
+    net = sg.SGNet(Z.shape[1], 64, 64, T.shape[1], max_batch=256, bf16=True, seed=1910)
+    net.set_stats(Z, T)
+    torch.cuda.synchronize()
+    t0 = time.time()
+    losses = learned.train(net, Z, T, steps=steps, batch=256, lr=1e-3, log_every=max(1, steps // 10))
+    torch.cuda.synchronize()
+    train_s = time.time() - t0
+    res = {}
+    for prec in ("fp64", "fp32"):
+        zi, wi, zs, ws, zr, wr = [], [], 0.0, 0.0, [], []
+        for c0 in range(0, len(te), 64):
+            ev = learned.warm_start_eval(net, te[c0:c0 + 64], precision=prec, rtol=1e-8)
+            zi += ev["zero_iters"]
+            wi += ev["warm_iters"]
+            zr += ev["zero_resid"]
+            wr += ev["warm_resid"]
+            zs += ev["zero_seconds"]
+            ws += ev["warm_seconds"]
+        res[prec] = {"zero_mean_iters": float(np.mean(zi)), "warm_mean_iters": float(np.mean(wi)),
+                     "zero_solves_per_s": len(te) / zs, "warm_solves_per_s": len(te) / ws,
+                     "max_zero_resid": max(zr), "max_warm_resid": max(wr)}
+    print(json.dumps({"config": "c5: 64x64 Q1, M=4, p=3 (D=4225x35), sigma~U[0.1,1.5], "
+                                "ell~U[0.25,2]; MLP 6-64-64-D (tanh), BF16 output layer, Adam",
+                      "ntrain": ntrain, "ntest": ntest, "steps": steps,
+                      "generation": gen, "train_seconds": train_s, "losses": losses,
+                      "eval": res}), flush=True)
+    net.close()
+
+
+def run_c4(nsys=64):
+    import torch
+    from paper_1910_11505_gb300 import sg, workloads as W
+    ps = W.c4_params(nsys)
+    for d in ps:
+        d["restart"] = 30
+    t0 = time.time()
+    h = sg.sg_setup([sg.sg_default_params(**d) for d in ps])
+    torch.cuda.synchronize()
+    setup = time.time() - t0
+    Fs, Xs = [], []
+    for i in range(h.nsys):
+        N, P, _ = sg.sg_dims(h, i)
+        F = torch.empty(N, P, dtype=torch.float64, device="cuda")
+        sg.sg_rhs(h, i, F)
+        Fs.append(F)
+        Xs.append(torch.zeros_like(F))
+    torch.cuda.synchronize()
+    t0 = time.time()
+    rc, info = sg.sg_gmres_solve(h, Fs, Xs, raise_on_error=False)
+    secs = time.time() - t0
+    ok = sum(1 for i in info if i["status"] == 0)
+    print(json.dumps({"config": f"c4: {nsys} seeded systems, mixed FP32, mean ILU(0), GMRES(30), 1e-8",
+                      "setup_s": setup, "solve_s": secs, "converged": ok,
+                      "solves_per_s": ok / secs, "iters": [i["iters"] for i in info]}), flush=True)
+    h.close()
+
+
+if __name__ == "__main__":
+    from paper_1910_11505_gb300 import build as B
+    B.build()
+    what = sys.argv[1] if len(sys.argv) > 1 else "c3"
+    args = [int(a) for a in sys.argv[2:]]
+    {"c3": run_c3, "c5": run_c5, "c4": run_c4}[what](*args)
