@@ -34,6 +34,23 @@ WORKLOAD = ("c2: 128x128 Q1 mesh, M=4, p=3 (P=35, L=210), ell=0.5, sigma in {0.2
 PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
 DFMA_PEAK_GFLOPS = 1192.0   # FP64 FMA loop on this GB300 (2 flops per DFMA), see the design doc
 ITERS_FILE = os.path.join(ROOT, "oracle", "c2_iterations.json")
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "traffic.json")
+KERNEL_SOURCES = {"ilu_solve": "paper_1910_11505_gb300/csrc/k_precond.cu",
+                  "apply_f64": "paper_1910_11505_gb300/csrc/k_matvec.cu"}
+
+
+def measured_traffic(kernel):
+    """DRAM bytes per launch of ``kernel`` from the committed ncu summary, or None when the
+    kernel's source has changed since the counters were taken."""
+    import hashlib
+    try:
+        with open(TRAFFIC_FILE) as f:
+            rec = json.load(f)[kernel]
+        with open(os.path.join(ROOT, rec["source"]), "rb") as f:
+            sha = hashlib.sha256(f.read()).hexdigest()
+        return rec["bytes_per_launch"] if sha == rec["sha256"] else None
+    except Exception:
+        return None
 
 
 def _peaks():
@@ -265,8 +282,16 @@ def main():
             "achieved": (alg_bytes / d_avg_s / 1e9) if alg_bytes else None,
             "peak": hbm, "unit": "GB/s", "peak_kind": peak_kind,
             "frac": (alg_bytes / d_avg_s / 1e9 / hbm) if alg_bytes else None,
-            "traffic": None, "avg_launch_us": d_avg_s * 1e6,
+            "traffic": measured_traffic(dom), "avg_launch_us": d_avg_s * 1e6,
             "launches_timed": d_timed, "share_of_timed_gpu_time": est[dom] / max(1e-30, sum(est.values()))}
+    if dom == "ilu_solve":
+        # the block solve is bound by its dependency chain: 2 (3m - 2) wavefront levels, each
+        # at least 4-5 dependent FP64 operations (64 cycles each on this GPU) plus a barrier
+        m = int(round(N ** 0.5))
+        levels = 2 * (3 * m - 2)
+        roof["critical_path_levels"] = levels
+        roof["ns_per_level"] = d_avg_s * 1e9 / levels
+        roof["ns_per_level_floor"] = 420.0 / 2.07  # measured 4-DFMA level loop: ~420 cycles
 
     # the SG operator alone (K1): FP64 DFMA-bound, reported against the DFMA peak as well
     X = torch.from_numpy(W.random_field(N, P, seed=7)).cuda()

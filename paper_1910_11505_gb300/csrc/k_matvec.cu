@@ -63,21 +63,23 @@ __global__ void __launch_bounds__(256) sg_apply_kernel(
       rs_ne[tid] = tid < nr ? rowptr[r + 1] - rowptr[r] : 0;
     }
     __syncthreads();
-    for (int t = tid; t < kRows * 9 * P; t += nth) {
-      int re = t / P, b = t - re * P;
-      int r = re / 9, e = re - r * 9;
-      TA v = TA(0);
-      if (e < rs_ne[r]) v = X[(size_t)col[rs_e0[r] + e] * P + b];
-      Xs[t] = v;
+    // one warp per (row, slot), lanes over chaos index: no runtime division
+    for (int re = tid >> 5; re < kRows * 9; re += nth >> 5) {
+      const int r = re / 9, e = re - r * 9;
+      const bool have = e < rs_ne[r];
+      const TA* xr = have ? X + (size_t)col[rs_e0[r] + e] * P : nullptr;
+      for (int b = tid & 31; b < P; b += 32) Xs[re * P + b] = have ? xr[b] : TA(0);
     }
     for (int t = tid; t < kRows * P; t += nth) Ys[t] = TA(0);
     for (int c = 0; c < nchunks; ++c) {
       const int2 uu = chunks[c];
       const int2 kr = chunks_k[c];
       const int kw = kr.y - kr.x;
-      for (int t = tid; t < kRows * 9 * kw; t += nth) {
-        int re = t / kw, kk = t - re * kw;
-        int r = re / 9, e = re - r * 9;
+      static_assert((kChunkK & (kChunkK - 1)) == 0, "chunk width must be a power of two");
+      for (int t = tid; t < kRows * 9 * kChunkK; t += nth) {
+        const int re = t / kChunkK, kk = t & (kChunkK - 1);
+        if (kk >= kw) continue;
+        const int r = re / 9, e = re - r * 9;
         TA v = TA(0);
         if (e < rs_ne[r]) v = cvt<TA, TV>(stack + (size_t)(rs_e0[r] + e) * L + kr.x + kk);
         As[re * kChunkK + kk] = v;
