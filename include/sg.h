@@ -69,6 +69,8 @@ typedef struct {
   int precision;     /* SG_FP64 | SG_MIXED_FP32 | SG_MIXED_BF16                                */
   double inner_rtol; /* mixed precision: each inner FGMRES cycle stops once its residual       */
                      /* estimate drops below inner_rtol times the current true residual        */
+  int graphs;        /* 1: capture each GMRES cycle of this system once as a CUDA graph (keyed  */
+                     /* by cycle length and the F, X pointers) and replay it; 0: plain launches */
 } sg_params;
 
 typedef struct {
@@ -81,7 +83,7 @@ typedef struct {
 
 /* Fill ``prm`` with defaults: n=16, M=2, p=2, q=2p, sigma=0.5, ell=1, a_min=0, mu=0, f=1,
  * mean preconditioner, 1 inner / 1 outer step, restart 30, max_iters 2000, rtol 1e-10,
- * atol 0, FP64, inner_rtol 1e-4. */
+ * atol 0, FP64, inner_rtol 1e-4, graphs 0. */
 void sg_default_params(sg_params* prm);
 
 /* Build ``nsys`` independent SG systems (Sec. 2: KL modes of Eq. gen_eigen in closed form,

@@ -35,6 +35,7 @@ __device__ __forceinline__ TA warp_sum(TA v) {
 
 // Rows per tile: the pair and entry tables are read once per tile instead of once per row.
 constexpr int kRows = 4;
+constexpr int kTs = kChunkPairs + 1;  // row stride of T in shared memory
 
 template <typename TA, typename TV>
 __global__ void __launch_bounds__(256) sg_apply_kernel(
@@ -48,8 +49,8 @@ __global__ void __launch_bounds__(256) sg_apply_kernel(
   // stencil slots are padded to 9 per row with zeros, so every row runs the same unrolled loop
   TA* As = reinterpret_cast<TA*>(smem_raw);   // kRows x 9 x kChunkK
   TA* Xs = As + kRows * 9 * kChunkK;          // kRows x 9 x P
-  TA* Ts = Xs + kRows * 9 * P;                // kRows x kChunkPairs
-  TA* Ys = Ts + kRows * kChunkPairs;          // kRows x P
+  TA* Ts = Xs + kRows * 9 * P;                // kRows x kTs (padded against bank conflicts)
+  TA* Ys = Ts + kRows * kTs;                  // kRows x P
   __shared__ int rs_e0[kRows], rs_ne[kRows];
   const int tid = threadIdx.x, nth = blockDim.x;
   const int ntiles = (N + kRows - 1) / kRows;
@@ -85,9 +86,11 @@ __global__ void __launch_bounds__(256) sg_apply_kernel(
         As[re * kChunkK + kk] = v;
       }
       __syncthreads();
+      int kb = (uu.x + tid < uu.y) ? pair_kb[uu.x + tid] : 0;
       for (int u = uu.x + tid; u < uu.y; u += nth) {
-        const int kb = pair_kb[u];
+        const int kbn = (u + nth < uu.y) ? pair_kb[u + nth] : 0;  // next pair, loaded early
         const int kk = (kb >> 16) - kr.x, b = kb & 0xffff;
+        kb = kbn;
 #pragma unroll
         for (int r = 0; r < kRows; ++r) {
           const TA* a = As + r * 9 * kChunkK + kk;
@@ -95,7 +98,7 @@ __global__ void __launch_bounds__(256) sg_apply_kernel(
           TA s = a[0] * x[0];
 #pragma unroll
           for (int e = 1; e < 9; ++e) s = fma(a[e * kChunkK], x[e * P], s);
-          Ts[r * kChunkPairs + (u - uu.x)] = s;
+          Ts[r * kTs + (u - uu.x)] = s;
         }
       }
       __syncthreads();
@@ -105,7 +108,7 @@ __global__ void __launch_bounds__(256) sg_apply_kernel(
       for (int t = tid; t < kRows * P; t += nth) {
         const int a = t / kRows, r = t - a * kRows;
         TA acc = TA(0);
-        for (int q = ep[a]; q < ep[a + 1]; ++q) acc = fma(ent_g[q], Ts[r * kChunkPairs + ent_u[q]], acc);
+        for (int q = ep[a]; q < ep[a + 1]; ++q) acc = fma(ent_g[q], Ts[r * kTs + ent_u[q]], acc);
         Ys[r * P + a] += acc;
       }
       __syncthreads();
@@ -123,7 +126,7 @@ __global__ void __launch_bounds__(256) sg_apply_kernel(
 template <typename TA>
 size_t apply_smem(int P) {
   return sizeof(TA) * ((size_t)kRows * 9 * kChunkK + (size_t)kRows * 9 * P +
-                       (size_t)kRows * kChunkPairs + (size_t)kRows * P);
+                       (size_t)kRows * kTs + (size_t)kRows * P);
 }
 
 int num_sms() {

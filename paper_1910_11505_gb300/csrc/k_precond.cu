@@ -71,16 +71,20 @@ __device__ __forceinline__ void stage_level(T* ring, int slot, int W, int l, int
         T* d = ring + (size_t)slot * 5 * W + t;
 #pragma unroll
         for (int q = 0; q < 4; ++q) cp_async_elem(d + q * W, lu + (size_t)(s0 + q) * N + base + t);
-        if (UPPER) cp_async_elem(d + 4 * W, lu + (size_t)4 * N + base + t);
       }
     }
   }
   cp_async_commit();
 }
 
+// Barrier among the first ``nact`` threads only (the warps that own rows of some level).
+__device__ __forceinline__ void level_barrier(int nact) {
+  asm volatile("bar.sync 1, %0;\n" ::"r"(nact) : "memory");
+}
+
 template <typename T, int RPT, bool UPPER>
 __device__ __forceinline__ void ilu9_sweep(T* w, T* ring, int W, const T* __restrict__ lu, int m,
-                                           int N, const int* lev_off_s, int nlev) {
+                                           int N, const int* lev_off_s, int nlev, int nact) {
   const int o0 = UPPER ? 1 : -m - 1, o1 = UPPER ? m - 1 : -m, o2 = UPPER ? m : -m + 1,
             o3 = UPPER ? m + 1 : -1;
   auto lev = [&](int it) { return UPPER ? nlev - 1 - it : it; };
@@ -107,12 +111,35 @@ __device__ __forceinline__ void ilu9_sweep(T* w, T* ring, int W, const T* __rest
         s -= f[W + t] * w[min(max(i + o1, 0), N - 1)];
         s -= f[2 * W + t] * w[min(max(i + o2, 0), N - 1)];
         s -= f[3 * W + t] * w[min(max(i + o3, 0), N - 1)];
-        w[i] = UPPER ? s * f[4 * W + t] : s;
+        w[i] = s;
       }
     }
-    __syncthreads();
+    level_barrier(nact);
   }
   cp_async_wait<0>();
+}
+
+// Backward-sweep prologue: w_i *= 1/u_ii for every row (the upper slots hold u_ij / u_ii).
+template <typename T>
+__device__ __forceinline__ void scale_by_dinv(T* w, const T* __restrict__ lu, int m, int N,
+                                              const int* lev_off_s) {
+  for (int i = threadIdx.x; i < N; i += blockDim.x) {
+    int x = i % m, y = i / m, l = x + 2 * y;
+    int ylo = max(0, (l - (m - 1) + 1) >> 1);
+    w[i] *= lu[(size_t)4 * N + lev_off_s[l] + (y - ylo)];
+  }
+}
+
+// Forward and backward sweeps: the level loops run in the first nact threads.
+template <typename T, int RPT>
+__device__ __forceinline__ void ilu9_solve(T* w, T* ring, int W, const T* __restrict__ lu, int m,
+                                           int N, const int* lev_off_s, int nlev, int nact) {
+  if ((int)threadIdx.x < nact) ilu9_sweep<T, RPT, false>(w, ring, W, lu, m, N, lev_off_s, nlev, nact);
+  __syncthreads();
+  scale_by_dinv<T>(w, lu, m, N, lev_off_s);
+  __syncthreads();
+  if ((int)threadIdx.x < nact) ilu9_sweep<T, RPT, true>(w, ring, W, lu, m, N, lev_off_s, nlev, nact);
+  __syncthreads();
 }
 
 // CTA c solves column a = a0 + c with factor set (fac_per_col ? a : 0):
@@ -120,7 +147,7 @@ __device__ __forceinline__ void ilu9_sweep(T* w, T* ring, int W, const T* __rest
 template <typename T, bool SMEM, int RPT>
 __global__ void __launch_bounds__(kTriThreads) ilu_block_solve_kernel(
     int m, int N, int P, int nnz, int a0, int fac_per_col, const int* __restrict__ lev_off,
-    int nlev, int W, const T* __restrict__ lu9s, const int* __restrict__ rowptr,
+    int nlev, int W, int nact, const T* __restrict__ lu9s, const int* __restrict__ rowptr,
     const int* __restrict__ col, const T* __restrict__ blks, const T* __restrict__ R,
     const T* __restrict__ acc, T* __restrict__ Z, T* __restrict__ wglob, int inner,
     const int* __restrict__ done) {
@@ -141,8 +168,7 @@ __global__ void __launch_bounds__(kTriThreads) ilu_block_solve_kernel(
     w[i] = v;
   }
   __syncthreads();
-  ilu9_sweep<T, RPT, false>(w, ring, W, lu, m, N, lev_s, nlev);
-  ilu9_sweep<T, RPT, true>(w, ring, W, lu, m, N, lev_s, nlev);
+  ilu9_solve<T, RPT>(w, ring, W, lu, m, N, lev_s, nlev, nact);
 #pragma unroll 4
   for (int i = threadIdx.x; i < N; i += blockDim.x) Z[(size_t)i * P + a] = w[i];
   for (int it = 1; it < inner; ++it) {
@@ -154,8 +180,7 @@ __global__ void __launch_bounds__(kTriThreads) ilu_block_solve_kernel(
       w[i] = v;
     }
     __syncthreads();
-    ilu9_sweep<T, RPT, false>(w, ring, W, lu, m, N, lev_s, nlev);
-    ilu9_sweep<T, RPT, true>(w, ring, W, lu, m, N, lev_s, nlev);
+    ilu9_solve<T, RPT>(w, ring, W, lu, m, N, lev_s, nlev, nact);
     for (int i = threadIdx.x; i < N; i += blockDim.x) Z[(size_t)i * P + a] += w[i];
   }
 }
@@ -235,13 +260,14 @@ int launch_block_solve_t(System& s, int a0, int ncols, int fac_per_col, const T*
                          T* Z, cudaStream_t st, const int* done) {
   using B = PcBufs<T>;
   const int W = s.pat.max_width;
+  const int nact = std::min(kTriThreads, (W + 31) / 32 * 32);
   size_t smem = (SMEM ? sizeof(T) * (size_t)s.N : 0) + sizeof(T) * (size_t)kAhead * 5 * W +
                 sizeof(int) * (size_t)(s.nlev9 + 1);
   auto kern = ilu_block_solve_kernel<T, SMEM, RPT>;
   SG_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   TimeScope ts(s.timer, K_ILU_SOLVE, st);
   kern<<<ncols, kTriThreads, smem, st>>>(s.pat.m, s.N, s.P, s.pat.nnz, a0, fac_per_col, s.lev9_off.p,
-                                 s.nlev9, W, B::lu9(s), s.rowptr.p, s.col.p, B::blk(s), R, acc, Z,
+                                 s.nlev9, W, nact, B::lu9(s), s.rowptr.p, s.col.p, B::blk(s), R, acc, Z,
                                  SMEM ? nullptr : B::triw(s), std::max(1, s.prm.inner_iters), done);
   return check_launch("ilu_block_solve");
 }

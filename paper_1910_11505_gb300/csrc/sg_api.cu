@@ -97,6 +97,7 @@ static int validate(const sg_params& p) {
   if (p.precision < SG_FP64 || p.precision > SG_MIXED_BF16) return fail(SG_ERR_ARG, "unknown precision");
   if (p.precision != SG_FP64 && !(p.inner_rtol > 0.0 && p.inner_rtol < 1.0))
     return fail(SG_ERR_ARG, "inner_rtol must be in (0, 1)");
+  if (p.graphs != 0 && p.graphs != 1) return fail(SG_ERR_ARG, "graphs must be 0 or 1");
   return SG_OK;
 }
 
@@ -247,6 +248,8 @@ static void free_system(System* s) {
   s->chunks.release();
   s->chunks_k.release();
   s->ticket.release();
+  for (auto& g : s->graphs) cudaGraphExecDestroy(g.exec);
+  s->graphs.clear();
   if (s->hpin) cudaFreeHost(s->hpin);
   if (s->ev) cudaEventDestroy(s->ev);
   if (s->stream) cudaStreamDestroy(s->stream);
@@ -394,7 +397,7 @@ struct SolveState {
   double* X;
   double target = 0, bnorm = 0, beta = 0, prev_beta = 0;
   int iters = 0, restarts = 0, status = SG_OK;
-  bool active = true;
+  bool active = true, graphed = false;
   int jmax = 0;
 };
 
@@ -426,6 +429,46 @@ static int residual(SolveState& ss) {
   SG_TRY(k_norm(s, n, s.rvec.p, s.scal.p + 1, s.stream));
   SG_CUDA(cudaMemcpyAsync(s.hpin, s.scal.p, 4 * sizeof(double), cudaMemcpyDeviceToHost, s.stream));
   SG_CUDA(cudaMemcpyAsync(s.hpin + 4, s.flags.p, 4 * sizeof(int), cudaMemcpyDeviceToHost, s.stream));
+  return SG_OK;
+}
+
+// One whole cycle of a system on its stream: cycle target upload (from the pinned mirror),
+// V0 = r / beta, jmax Arnoldi steps, back-substitution and update, new residual and read-back.
+static int enqueue_cycle(SolveState& q) {
+  System& s = *q.s;
+  SG_CUDA(cudaMemcpyAsync(s.scal.p, s.hpin, sizeof(double), cudaMemcpyHostToDevice, s.stream));
+  SG_TRY(k_init_cycle(s, (size_t)s.N * s.P, s.rvec.p, s.stream));
+  for (int j = 0; j < q.jmax; ++j) SG_TRY(iteration(s, j, q.jmax - 1));
+  SG_TRY(k_finish_cycle(s, (size_t)s.N * s.P, q.X, s.prm.precision != SG_FP64, s.stream));
+  return residual(q);
+}
+
+// Replay the captured graph of this cycle shape, capturing it on first use.  Kernel timing is
+// suspended during capture (events recorded there would become graph nodes).
+static int launch_cycle_graph(SolveState& q) {
+  System& s = *q.s;
+  for (auto& g : s.graphs)
+    if (g.jmax == q.jmax && g.F == q.F && g.X == q.X) {
+      SG_CUDA(cudaGraphLaunch(g.exec, s.stream));
+      return SG_OK;
+    }
+  const bool timing = s.timer && s.timer->on;
+  if (timing) s.timer->on = false;
+  SG_CUDA(cudaStreamBeginCapture(s.stream, cudaStreamCaptureModeThreadLocal));
+  int rc = enqueue_cycle(q);
+  cudaGraph_t graph = nullptr;
+  cudaError_t e = cudaStreamEndCapture(s.stream, &graph);
+  if (timing) s.timer->on = true;
+  if (rc != SG_OK || e != cudaSuccess) {
+    if (graph) cudaGraphDestroy(graph);
+    return rc != SG_OK ? rc : fail(SG_ERR_CUDA, std::string("stream capture: ") + cudaGetErrorString(e));
+  }
+  cudaGraphExec_t exec = nullptr;
+  e = cudaGraphInstantiate(&exec, graph, 0);
+  cudaGraphDestroy(graph);
+  if (e != cudaSuccess) return fail(SG_ERR_CUDA, std::string("graph instantiate: ") + cudaGetErrorString(e));
+  s.graphs.push_back({q.jmax, q.F, q.X, exec});
+  SG_CUDA(cudaGraphLaunch(exec, s.stream));
   return SG_OK;
 }
 
@@ -469,17 +512,24 @@ int gmres_solve_all(sg_handle* h, const double* const* F, double* const* X, sg_s
       double cyc = q.target;
       if (s.prm.precision != SG_FP64) cyc = std::max(q.target, s.prm.inner_rtol * q.beta);
       s.hpin[0] = cyc;
+      q.jmax = std::min(s.m, s.prm.max_iters - q.iters);
+      q.graphed = s.prm.graphs != 0;
+      if (q.graphed) {
+        SG_TRY(launch_cycle_graph(q));
+        maxj = std::max(maxj, 1);
+        continue;
+      }
       SG_CUDA(cudaMemcpyAsync(s.scal.p, s.hpin, sizeof(double), cudaMemcpyHostToDevice, s.stream));
       SG_TRY(k_init_cycle(s, (size_t)s.N * s.P, s.rvec.p, s.stream));
-      q.jmax = std::min(s.m, s.prm.max_iters - q.iters);
       maxj = std::max(maxj, q.jmax);
     }
     if (maxj == 0) break;
+    // plain launches: the systems' Arnoldi steps are interleaved so their streams overlap
     for (int j = 0; j < maxj; ++j)
       for (auto& q : st)
-        if (q.active && j < q.jmax) SG_TRY(iteration(*q.s, j, q.jmax - 1));
+        if (q.active && !q.graphed && j < q.jmax) SG_TRY(iteration(*q.s, j, q.jmax - 1));
     for (auto& q : st) {
-      if (!q.active) continue;
+      if (!q.active || q.graphed) continue;
       System& s = *q.s;
       SG_TRY(k_finish_cycle(s, (size_t)s.N * s.P, q.X, s.prm.precision != SG_FP64, s.stream));
       SG_TRY(residual(q));
@@ -548,6 +598,7 @@ void sg_default_params(sg_params* p) {
   p->atol = 0.0;
   p->precision = SG_FP64;
   p->inner_rtol = 1e-4;
+  p->graphs = 0;
 }
 
 int sg_setup(const sg_params* prm, int nsys, void* stream, sg_handle** out) {

@@ -185,6 +185,13 @@ struct System {
   DBuf<float> mv32a, mv32b;    // FP32 operand / result of the inner operator
   double* hpin = nullptr;      // pinned host mirror of state[0..3] and flags[0..2]
   Timer* timer = nullptr;      // the handle's timer
+  struct CycleGraph {
+    int jmax;
+    const double* F;
+    double* X;
+    cudaGraphExec_t exec;
+  };
+  std::vector<CycleGraph> graphs;  // captured GMRES cycles (sg_params.graphs = 1)
   cudaStream_t stream = nullptr;
   cudaEvent_t ev = nullptr;
 };

@@ -51,7 +51,7 @@ class sg_params(ctypes.Structure):
                 ("inner_iters", ctypes.c_int), ("outer_sweeps", ctypes.c_int),
                 ("restart", ctypes.c_int), ("max_iters", ctypes.c_int), ("rtol", ctypes.c_double),
                 ("atol", ctypes.c_double), ("precision", ctypes.c_int),
-                ("inner_rtol", ctypes.c_double)]
+                ("inner_rtol", ctypes.c_double), ("graphs", ctypes.c_int)]
 
 
 class sg_solve_info(ctypes.Structure):

@@ -39,14 +39,15 @@ def test_struct_layout_matches_c(tmp_path):
     from paper_1910_11505_gb300 import sg
     src = tmp_path / "lay.c"
     src.write_text('#include <stdio.h>\n#include <stddef.h>\n#include "sg.h"\n'
-                   'int main(void){printf("%zu %zu %zu %zu %zu\\n", sizeof(sg_params),'
+                   'int main(void){printf("%zu %zu %zu %zu %zu %zu\\n", sizeof(sg_params),'
                    ' offsetof(sg_params, precision), offsetof(sg_params, inner_rtol),'
+                   ' offsetof(sg_params, graphs),'
                    ' sizeof(sg_solve_info), offsetof(sg_solve_info, seconds)); return 0;}\n')
     exe = tmp_path / "lay"
     subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
     out = subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split()
     got = [ctypes.sizeof(sg.sg_params), sg.sg_params.precision.offset, sg.sg_params.inner_rtol.offset,
-           ctypes.sizeof(sg.sg_solve_info), sg.sg_solve_info.seconds.offset]
+           sg.sg_params.graphs.offset, ctypes.sizeof(sg.sg_solve_info), sg.sg_solve_info.seconds.offset]
     assert [int(v) for v in out] == got
 
 

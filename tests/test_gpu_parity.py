@@ -260,3 +260,32 @@ def test_mixed_fp32_reaches_fp64_residual():
     assert true_res <= 1.2e-10
     assert info[0]["restarts"] >= 2  # at least one refinement step after the first inner solve
     h.close()
+
+
+@pytest.mark.parametrize("pc,prec", [("fs_gs", "fp64"), ("mean", "fp32")])
+def test_graph_replay_equals_plain_launches(pc, prec):
+    case = dict(n=12, M=2, p=2, sigma=0.7, ell=0.8)
+    outs = []
+    for graphs in (0, 1):
+        h = sg.sg_setup([_params(case, precond=pc, precision=prec, rtol=1e-10, restart=8,
+                                 graphs=graphs)] * 2)
+        res = []
+        Fs, Xs = [], []
+        for i in range(2):
+            N, P, _ = sg.sg_dims(h, i)
+            F = torch.empty(N, P, dtype=torch.float64, device="cuda")
+            sg.sg_rhs(h, i, F)
+            Fs.append(F)
+            Xs.append(torch.zeros_like(F))
+        for rep in range(2):  # same F, X: the second call replays the graphs of the first
+            for x in Xs:
+                x.zero_()
+            rc, info = sg.sg_gmres_solve(h, Fs, Xs)
+            assert rc == sg.SG_OK
+            res.append(([x.clone() for x in Xs], [d["iters"] for d in info]))
+        outs.append(res)
+        h.close()
+    for rep in range(2):
+        assert outs[0][rep][1] == outs[1][rep][1]
+        for a, b in zip(outs[0][rep][0], outs[1][rep][0]):
+            assert torch.equal(a, b)
