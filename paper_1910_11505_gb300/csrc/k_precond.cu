@@ -71,6 +71,7 @@ __device__ __forceinline__ void stage_level(T* ring, int slot, int W, int l, int
         T* d = ring + (size_t)slot * 5 * W + t;
 #pragma unroll
         for (int q = 0; q < 4; ++q) cp_async_elem(d + q * W, lu + (size_t)(s0 + q) * N + base + t);
+        if (UPPER) cp_async_elem(d + 4 * W, lu + (size_t)4 * N + base + t);
       }
     }
   }
@@ -78,8 +79,16 @@ __device__ __forceinline__ void stage_level(T* ring, int slot, int W, int l, int
 }
 
 // Barrier among the first ``nact`` threads only (the warps that own rows of some level).
+#ifndef SG_TRI_NAMED_BARRIER
+#define SG_TRI_NAMED_BARRIER 1
+#endif
 __device__ __forceinline__ void level_barrier(int nact) {
+#if SG_TRI_NAMED_BARRIER
   asm volatile("bar.sync 1, %0;\n" ::"r"(nact) : "memory");
+#else
+  (void)nact;
+  __syncthreads();
+#endif
 }
 
 template <typename T, int RPT, bool UPPER>
@@ -111,7 +120,7 @@ __device__ __forceinline__ void ilu9_sweep(T* w, T* ring, int W, const T* __rest
         s -= f[W + t] * w[min(max(i + o1, 0), N - 1)];
         s -= f[2 * W + t] * w[min(max(i + o2, 0), N - 1)];
         s -= f[3 * W + t] * w[min(max(i + o3, 0), N - 1)];
-        w[i] = s;
+        w[i] = UPPER ? s * f[4 * W + t] : s;
       }
     }
     level_barrier(nact);
@@ -119,26 +128,19 @@ __device__ __forceinline__ void ilu9_sweep(T* w, T* ring, int W, const T* __rest
   cp_async_wait<0>();
 }
 
-// Backward-sweep prologue: w_i *= 1/u_ii for every row (the upper slots hold u_ij / u_ii).
-template <typename T>
-__device__ __forceinline__ void scale_by_dinv(T* w, const T* __restrict__ lu, int m, int N,
-                                              const int* lev_off_s) {
-  for (int i = threadIdx.x; i < N; i += blockDim.x) {
-    int x = i % m, y = i / m, l = x + 2 * y;
-    int ylo = max(0, (l - (m - 1) + 1) >> 1);
-    w[i] *= lu[(size_t)4 * N + lev_off_s[l] + (y - ylo)];
-  }
-}
-
 // Forward and backward sweeps: the level loops run in the first nact threads.
 template <typename T, int RPT>
 __device__ __forceinline__ void ilu9_solve(T* w, T* ring, int W, const T* __restrict__ lu, int m,
                                            int N, const int* lev_off_s, int nlev, int nact) {
-  if ((int)threadIdx.x < nact) ilu9_sweep<T, RPT, false>(w, ring, W, lu, m, N, lev_off_s, nlev, nact);
-  __syncthreads();
-  scale_by_dinv<T>(w, lu, m, N, lev_off_s);
-  __syncthreads();
-  if ((int)threadIdx.x < nact) ilu9_sweep<T, RPT, true>(w, ring, W, lu, m, N, lev_off_s, nlev, nact);
+#if SG_TRI_NAMED_BARRIER
+  if ((int)threadIdx.x < nact) {
+    ilu9_sweep<T, RPT, false>(w, ring, W, lu, m, N, lev_off_s, nlev, nact);
+    ilu9_sweep<T, RPT, true>(w, ring, W, lu, m, N, lev_off_s, nlev, nact);
+  }
+#else
+  ilu9_sweep<T, RPT, false>(w, ring, W, lu, m, N, lev_off_s, nlev, nact);
+  ilu9_sweep<T, RPT, true>(w, ring, W, lu, m, N, lev_off_s, nlev, nact);
+#endif
   __syncthreads();
 }
 

@@ -183,8 +183,7 @@ __global__ void ilu0_kernel(int nnz, const int* __restrict__ rowptr, const int* 
   }
 }
 
-// CSR ILU(0) factors -> 9-slot level-major layout used by the wavefront solves (slot 4: 1/u_ii,
-// upper slots divided by u_ii).
+// CSR ILU(0) factors -> 9-slot level-major layout used by the wavefront solves (slot 4: 1/u_ii).
 __global__ void lu9_kernel(int m, int N, int nnz, int nfac, const int* __restrict__ rowptr,
                            const int* __restrict__ col, const int* __restrict__ lev_off,
                            const double* __restrict__ fac, double* __restrict__ lu9) {
@@ -203,8 +202,7 @@ __global__ void lu9_kernel(int m, int N, int nnz, int nfac, const int* __restric
     int dx = c % m - x, dy = c / m - y;
     int slot = (dy + 1) * 3 + (dx + 1);
     double v = fac[(size_t)f * nnz + e];
-    // upper slots hold u_ij / u_ii: the backward sweep scales the row once, before its level
-    lu9[((size_t)f * 9 + slot) * N + pos] = slot == 4 ? dinv : (slot > 4 ? v * dinv : v);
+    lu9[((size_t)f * 9 + slot) * N + pos] = slot == 4 ? dinv : v;
   }
 }
 
