@@ -1,6 +1,8 @@
 """Write oracle/c2_iterations.json: GMRES iteration counts of the FP64 oracle on the four c2
-systems (128 x 128 Q1, M = 4, p = 3, ell = 0.5, field-split Gauss-Seidel + ILU(0), GMRES(300),
+systems (128 x 128 Q1, M = 4, p = 3, ell = 0.5, field-split Gauss-Seidel + ILU(0), GMRES(restart),
 relative residual 1e-10).  Used only to scale the timed CPU sample of bench.py to full solves.
+
+    python oracle/c2_iterations.py [restart]      (default 1024)
 
 Calls nothing but the oracle.  Runs the four systems in parallel processes (about an hour of CPU).
 """
@@ -14,7 +16,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, os.path.dirname(HERE))
 
 SIGMAS = (0.25, 0.5, 1.0, 1.5)
-RESTART = 300
+RESTART = int(sys.argv[1]) if len(sys.argv) > 1 else 1024
 
 
 def solve(sigma):
