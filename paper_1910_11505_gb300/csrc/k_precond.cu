@@ -30,11 +30,32 @@ namespace {
 constexpr long long kSpinLimit = 1ll << 26;   // polls of a progress counter before giving up
 constexpr int kSolveThreads = 256;            // CTA size when one warp per grid row suffices
 
+template <typename T>
+__device__ __forceinline__ void cp_async_elem(T* dst, const T* src) {
+  unsigned sa = (unsigned)__cvta_generic_to_shared(dst);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], %2;\n" ::"r"(sa), "l"(src), "n"(sizeof(T)));
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::); }
+template <int K>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(K)); }
+__device__ __forceinline__ int ld_acquire(const int* p) {
+  int v;
+  unsigned a = (unsigned)__cvta_generic_to_shared(p);
+  asm volatile("ld.acquire.cta.shared::cta.u32 %0, [%1];\n" : "=r"(v) : "r"(a) : "memory");
+  return v;
+}
+__device__ __forceinline__ void st_release(int* p, int v) {
+  unsigned a = (unsigned)__cvta_generic_to_shared(p);
+  asm volatile("st.release.cta.shared::cta.u32 [%0], %1;\n" ::"r"(a), "r"(v) : "memory");
+}
+
 // Factors are stored per factor set as 9 node-major slot arrays (slot (dy+1)*3 + (dx+1) of node
-// x + m y; slot 4 holds 1/u_ii; absent neighbours 0).
+// x + m y; slot 4 holds 1/u_ii; absent neighbours 0).  Each lane copies the factors of its
+// next AHEAD columns into a per-warp shared-memory ring with cp.async (loads held in registers
+// would be drained by every release/acquire of the hand-off and cost an L2 round trip a step).
 template <typename T, int AHEAD, bool UPPER>
-__device__ __forceinline__ void pipe_sweep(T* w, const T* __restrict__ lu, int m, int N,
-                                           volatile int* progress, int* err) {
+__device__ __forceinline__ void pipe_sweep(T* w, T* ring, const T* __restrict__ lu, int m, int N,
+                                           int* progress, int* err) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int yy = warp * 32 + lane;  // rank of this lane's row in sweep order
   const bool row_ok = yy < m;
@@ -43,19 +64,21 @@ __device__ __forceinline__ void pipe_sweep(T* w, const T* __restrict__ lu, int m
             o3 = UPPER ? m + 1 : -1;
   const int sbase = UPPER ? 5 : 0;
   const int nsteps = m + 62;
-  T f[AHEAD][4], dv[AHEAD];
-  auto fetch = [&](int st, T(&ff)[4], T& dd) {
+  T* myring = ring + (size_t)warp * AHEAD * 5 * 32 + lane;  // [d][q][lane]
+  auto stage = [&](int st, int d) {
     const int xx = st - 2 * lane;
     if (row_ok && xx >= 0 && xx < m) {
       const int x = UPPER ? m - 1 - xx : xx;
       const size_t i = (size_t)x + (size_t)m * y;
+      T* dst = myring + d * 5 * 32;
 #pragma unroll
-      for (int q = 0; q < 4; ++q) ff[q] = lu[(size_t)(sbase + q) * N + i];
-      dd = UPPER ? lu[(size_t)4 * N + i] : T(1);
+      for (int q = 0; q < 4; ++q) cp_async_elem(dst + q * 32, lu + (size_t)(sbase + q) * N + i);
+      if (UPPER) cp_async_elem(dst + 4 * 32, lu + (size_t)4 * N + i);
     }
+    cp_async_commit();
   };
 #pragma unroll
-  for (int d = 0; d < AHEAD; ++d) fetch(d, f[d], dv[d]);
+  for (int d = 0; d < AHEAD; ++d) stage(d, d);
   for (int s0 = 0; s0 < nsteps; s0 += AHEAD) {
 #pragma unroll
     for (int d = 0; d < AHEAD; ++d) {
@@ -64,49 +87,48 @@ __device__ __forceinline__ void pipe_sweep(T* w, const T* __restrict__ lu, int m
         if (warp > 0) {
           const int need = min(st + 64, nsteps);
           long long spins = 0;
-          while (progress[warp - 1] < need) {
+          while (ld_acquire(progress + warp - 1) < need) {
             if (++spins > kSpinLimit) {
               *err = 1;
               break;
             }
           }
-          __threadfence_block();
         }
+        cp_async_wait<AHEAD - 1>();
         const int xx = st - 2 * lane;
         if (row_ok && xx >= 0 && xx < m) {
           const int x = UPPER ? m - 1 - xx : xx;
           const int i = x + m * y;
+          const T* f = myring + d * 5 * 32;
           T v = w[i];
-          v -= f[d][0] * w[min(max(i + o0, 0), N - 1)];
-          v -= f[d][1] * w[min(max(i + o1, 0), N - 1)];
-          v -= f[d][2] * w[min(max(i + o2, 0), N - 1)];
-          v -= f[d][3] * w[min(max(i + o3, 0), N - 1)];
-          w[i] = UPPER ? v * dv[d] : v;
+          v -= f[0] * w[min(max(i + o0, 0), N - 1)];
+          v -= f[32] * w[min(max(i + o1, 0), N - 1)];
+          v -= f[64] * w[min(max(i + o2, 0), N - 1)];
+          v -= f[96] * w[min(max(i + o3, 0), N - 1)];
+          w[i] = UPPER ? v * f[128] : v;
         }
         __syncwarp();
-        if (lane == 0) {
-          __threadfence_block();
-          progress[warp] = st + 1;
-        }
-        fetch(st + AHEAD, f[d], dv[d]);
+        if (lane == 0) st_release(progress + warp, st + 1);
+        stage(st + AHEAD, d);
       }
     }
   }
+  cp_async_wait<0>();
 }
 
 // Both sweeps on the column in w; the first ceil(m/32) warps sweep, the others wait.
 template <typename T, int AHEAD>
-__device__ __forceinline__ void ilu_solve_column(T* w, const T* __restrict__ lu, int m, int N,
-                                                 volatile int* progress, int* err) {
+__device__ __forceinline__ void ilu_solve_column(T* w, T* ring, const T* __restrict__ lu, int m,
+                                                 int N, int* progress, int* err) {
   const int nw = (m + 31) >> 5;
   const int warp = threadIdx.x >> 5;
   for (int q = threadIdx.x; q < nw; q += blockDim.x) progress[q] = 0;
   __syncthreads();
-  if (warp < nw) pipe_sweep<T, AHEAD, false>(w, lu, m, N, progress, err);
+  if (warp < nw) pipe_sweep<T, AHEAD, false>(w, ring, lu, m, N, progress, err);
   __syncthreads();
   for (int q = threadIdx.x; q < nw; q += blockDim.x) progress[q] = 0;
   __syncthreads();
-  if (warp < nw) pipe_sweep<T, AHEAD, true>(w, lu, m, N, progress, err);
+  if (warp < nw) pipe_sweep<T, AHEAD, true>(w, ring, lu, m, N, progress, err);
   __syncthreads();
 }
 
@@ -125,14 +147,15 @@ __global__ void __launch_bounds__(MAXT) ilu_block_solve_kernel(
   const int fsel = fac_per_col ? a : 0;
   const T* lu = lu9s + (size_t)fsel * 9 * N;
   const T* blk = blks + (size_t)fsel * nnz;
-  T* w = SMEM ? reinterpret_cast<T*>(smem_raw) : wglob + (size_t)a * N;
+  T* ring = reinterpret_cast<T*>(smem_raw);  // ceil(m/32) warps x AHEAD x 5 x 32
+  T* w = SMEM ? ring + (size_t)((m + 31) >> 5) * AHEAD * 5 * 32 : wglob + (size_t)a * N;
 #pragma unroll 4
   for (int i = threadIdx.x; i < N; i += blockDim.x) {
     T v = R[(size_t)i * P + a];
     if (acc != nullptr) v -= acc[(size_t)i * P + a];
     w[i] = v;
   }
-  ilu_solve_column<T, AHEAD>(w, lu, m, N, progress, err);
+  ilu_solve_column<T, AHEAD>(w, ring, lu, m, N, progress, err);
 #pragma unroll 4
   for (int i = threadIdx.x; i < N; i += blockDim.x) Z[(size_t)i * P + a] = w[i];
   for (int it = 1; it < inner; ++it) {
@@ -143,7 +166,7 @@ __global__ void __launch_bounds__(MAXT) ilu_block_solve_kernel(
       for (int e = rowptr[i]; e < rowptr[i + 1]; ++e) v -= blk[e] * Z[(size_t)col[e] * P + a];
       w[i] = v;
     }
-    ilu_solve_column<T, AHEAD>(w, lu, m, N, progress, err);
+    ilu_solve_column<T, AHEAD>(w, ring, lu, m, N, progress, err);
     for (int i = threadIdx.x; i < N; i += blockDim.x) Z[(size_t)i * P + a] += w[i];
   }
 }
@@ -224,7 +247,7 @@ int launch_block_solve_t(System& s, int a0, int ncols, int fac_per_col, const T*
   using B = PcBufs<T>;
   const int m = s.pat.m;
   const int threads = std::max(kSolveThreads, (m + 31) / 32 * 32);
-  size_t smem = SMEM ? sizeof(T) * (size_t)s.N : 0;
+  size_t smem = sizeof(T) * ((size_t)((m + 31) / 32) * AHEAD * 5 * 32 + (SMEM ? (size_t)s.N : 0));
   auto kern = ilu_block_solve_kernel<T, SMEM, MAXT, AHEAD>;
   SG_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   TimeScope ts(s.timer, K_ILU_SOLVE, st);

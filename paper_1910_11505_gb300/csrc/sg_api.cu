@@ -268,9 +268,13 @@ static int setup_system(System& s, cudaStream_t st) {
   // smem budgets of the kernels
   size_t apply_smem = sizeof(double) * 4 * (9 * kChunkK + 9 * (size_t)s.P + kChunkPairs + s.P);
   if (apply_smem > 220 * 1024) return fail(SG_ERR_ARG, "P too large for the operator kernel");
-  // the pipelined block solve keeps one column in shared memory when it fits
-  s.tri_smem = (size_t)s.N * 8 <= 224 * 1024;
-  s.tri_smem32 = (size_t)s.N * 4 <= 224 * 1024;
+  // the pipelined block solve keeps one column in shared memory when it fits next to its
+  // factor ring (ceil(m/32) warps x up to 8 columns x 5 slots x 32 lanes)
+  {
+    size_t ringn = (size_t)((p.n + 1 + 31) / 32) * (p.n + 1 <= 256 ? 8 : (p.n + 1 <= 512 ? 4 : 2)) * 160;
+    s.tri_smem = ((size_t)s.N + ringn) * 8 <= 224 * 1024;
+    s.tri_smem32 = ((size_t)s.N + ringn) * 4 <= 224 * 1024;
+  }
 
   SG_CUDA(cudaStreamCreateWithFlags(&s.stream, cudaStreamNonBlocking));
   SG_CUDA(cudaEventCreateWithFlags(&s.ev, cudaEventDisableTiming));
