@@ -7,17 +7,9 @@
 //    block K_aa approximated by its ILU(0) factors with ``inner_iters`` Richardson steps;
 //  * both wrapped in ``outer_sweeps`` steps of the level solver of Eq. level_solver.
 //
-// The ILU(0) triangular solves are pipelined wavefronts.  With the 9-point Q1 pattern in natural
-// order, row (x, y) of the lower factor depends on (x-1, y-1), (x, y-1), (x+1, y-1), (x-1, y).
-// One CTA owns one chaos column; lane j of warp w owns grid row y = 32 w + j and walks it in x,
-// two columns behind the lane below it: at step s it solves x = s - 2j.  The row below then
-// finished x + 1 one step earlier, so inside a warp the lockstep order alone satisfies every
-// dependency (a __syncwarp publishes the step's writes).  Only lane 0 depends on another warp:
-// it needs column x + 1 of the last row of warp w - 1, i.e. that warp's step s + 63, which it
-// reads from a progress counter in shared memory (a bounded spin: past the limit the kernel sets
-// an error flag and carries on, it never hangs).  The upper factor runs the same scheme mirrored
-// (rows top down, x from right to left).  No CTA-wide barrier sits inside a sweep, so each lane
-// keeps the factors of its next AHEAD columns in flight in registers.
+// The ILU(0) triangular solves run as wavefronts: rows of one level of the lower (upper) graph
+// of the pattern depend only on rows of earlier levels.  One CTA owns one chaos column and walks
+// all levels with a CTA barrier in between, holding the column in shared memory when it fits.
 // The off-diagonal coupling of the Gauss-Seidel sweep, sum_{b<a} K_ab z_b, is pushed forward
 // after each block b by a grid-wide kernel: T[k] = sum_e A[e,k] z_b[j_e] once per (row, k), then
 // acc[:,a] += G_k[a,b] T[k] for every a > b.
@@ -27,8 +19,31 @@ namespace sg {
 
 namespace {
 
-constexpr long long kSpinLimit = 1ll << 26;   // polls of a progress counter before giving up
-constexpr int kSolveThreads = 256;            // CTA size when one warp per grid row suffices
+// Wavefront schedule of the 9-point Q1 pattern in natural order: row (x, y) of the lower factor
+// depends on (x-1, y-1), (x, y-1), (x+1, y-1), (x-1, y), so the rows with x + 2y = l form level l
+// (3m - 2 levels); the upper factor uses the same levels in reverse.  Factors are stored per
+// factor set as 9 slot arrays in level-major row order (slot (dy+1)*3 + (dx+1); slot 4 holds
+// 1/u_ii; absent neighbours hold 0), so a level needs no index loads and its factors can be
+// fetched one level ahead.
+__device__ __forceinline__ void level_range(int l, int m, int& ylo, int& cnt) {
+  ylo = max(0, (l - (m - 1) + 1) >> 1);
+  int yhi = min(m - 1, l >> 1);
+  cnt = yhi - ylo + 1;
+}
+
+// Factors of the next kAhead levels are copied into a shared-memory ring with cp.async while the
+// current level is computed.  Ordinary loads cannot run ahead like this: the level barrier waits
+// for every load the thread has in flight, so each level would pay a full L2 round trip.  Each
+// thread copies and later reads only its own rows' factors, so the ring needs no barrier of its
+// own; cp.async.wait_group orders the copy before the read.
+#ifndef SG_TRI_AHEAD
+#define SG_TRI_AHEAD 8
+#endif
+#ifndef SG_TRI_THREADS
+#define SG_TRI_THREADS 256
+#endif
+constexpr int kAhead = SG_TRI_AHEAD;
+constexpr int kTriThreads = SG_TRI_THREADS;
 
 template <typename T>
 __device__ __forceinline__ void cp_async_elem(T* dst, const T* src) {
@@ -36,126 +51,126 @@ __device__ __forceinline__ void cp_async_elem(T* dst, const T* src) {
   asm volatile("cp.async.ca.shared.global [%0], [%1], %2;\n" ::"r"(sa), "l"(src), "n"(sizeof(T)));
 }
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::); }
-template <int K>
-__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(K)); }
-__device__ __forceinline__ int ld_acquire(const int* p) {
-  int v;
-  unsigned a = (unsigned)__cvta_generic_to_shared(p);
-  asm volatile("ld.acquire.cta.shared::cta.u32 %0, [%1];\n" : "=r"(v) : "r"(a) : "memory");
-  return v;
-}
-__device__ __forceinline__ void st_release(int* p, int v) {
-  unsigned a = (unsigned)__cvta_generic_to_shared(p);
-  asm volatile("st.release.cta.shared::cta.u32 [%0], %1;\n" ::"r"(a), "r"(v) : "memory");
-}
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N)); }
 
-// Factors are stored per factor set as 9 node-major slot arrays (slot (dy+1)*3 + (dx+1) of node
-// x + m y; slot 4 holds 1/u_ii; absent neighbours 0).  Each lane copies the factors of its
-// next AHEAD columns into a per-warp shared-memory ring with cp.async (loads held in registers
-// would be drained by every release/acquire of the hand-off and cost an L2 round trip a step).
-template <typename T, int AHEAD, bool UPPER>
-__device__ __forceinline__ void pipe_sweep(T* w, T* ring, const T* __restrict__ lu, int m, int N,
-                                           int* progress, int* err) {
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int yy = warp * 32 + lane;  // rank of this lane's row in sweep order
-  const bool row_ok = yy < m;
-  const int y = UPPER ? m - 1 - yy : yy;
-  const int o0 = UPPER ? 1 : -m - 1, o1 = UPPER ? m - 1 : -m, o2 = UPPER ? m : -m + 1,
-            o3 = UPPER ? m + 1 : -1;
-  const int sbase = UPPER ? 5 : 0;
-  const int nsteps = m + 62;
-  T* myring = ring + (size_t)warp * AHEAD * 5 * 32 + lane;  // [d][q][lane]
-  auto stage = [&](int st, int d) {
-    const int xx = st - 2 * lane;
-    if (row_ok && xx >= 0 && xx < m) {
-      const int x = UPPER ? m - 1 - xx : xx;
-      const size_t i = (size_t)x + (size_t)m * y;
-      T* dst = myring + d * 5 * 32;
+// Copy the factors of level l (4 off-diagonal slots, plus 1/u_ii for the upper sweep) of the rows
+// this thread owns into ring slot ``slot``; always commits one group (possibly empty).
+template <typename T, int RPT, bool UPPER>
+__device__ __forceinline__ void stage_level(T* ring, int slot, int W, int l, int nlev, int m,
+                                            int N, const T* __restrict__ lu, const int* lev_off_s) {
+  if (l >= 0 && l < nlev) {
+    int ylo, cnt;
+    level_range(l, m, ylo, cnt);
+    const int base = lev_off_s[l];
+    const int s0 = UPPER ? 5 : 0;
 #pragma unroll
-      for (int q = 0; q < 4; ++q) cp_async_elem(dst + q * 32, lu + (size_t)(sbase + q) * N + i);
-      if (UPPER) cp_async_elem(dst + 4 * 32, lu + (size_t)4 * N + i);
-    }
-    cp_async_commit();
-  };
+    for (int r = 0; r < RPT; ++r) {
+      int t = threadIdx.x + r * blockDim.x;
+      if (t < cnt) {
+        T* d = ring + (size_t)slot * 5 * W + t;
 #pragma unroll
-  for (int d = 0; d < AHEAD; ++d) stage(d, d);
-  for (int s0 = 0; s0 < nsteps; s0 += AHEAD) {
-#pragma unroll
-    for (int d = 0; d < AHEAD; ++d) {
-      const int st = s0 + d;
-      if (st < nsteps) {
-        if (warp > 0) {
-          const int need = min(st + 64, nsteps);
-          long long spins = 0;
-          while (ld_acquire(progress + warp - 1) < need) {
-            if (++spins > kSpinLimit) {
-              *err = 1;
-              break;
-            }
-          }
-        }
-        cp_async_wait<AHEAD - 1>();
-        const int xx = st - 2 * lane;
-        if (row_ok && xx >= 0 && xx < m) {
-          const int x = UPPER ? m - 1 - xx : xx;
-          const int i = x + m * y;
-          const T* f = myring + d * 5 * 32;
-          T v = w[i];
-          v -= f[0] * w[min(max(i + o0, 0), N - 1)];
-          v -= f[32] * w[min(max(i + o1, 0), N - 1)];
-          v -= f[64] * w[min(max(i + o2, 0), N - 1)];
-          v -= f[96] * w[min(max(i + o3, 0), N - 1)];
-          w[i] = UPPER ? v * f[128] : v;
-        }
-        __syncwarp();
-        if (lane == 0) st_release(progress + warp, st + 1);
-        stage(st + AHEAD, d);
+        for (int q = 0; q < 4; ++q) cp_async_elem(d + q * W, lu + (size_t)(s0 + q) * N + base + t);
+        if (UPPER) cp_async_elem(d + 4 * W, lu + (size_t)4 * N + base + t);
       }
     }
+  }
+  cp_async_commit();
+}
+
+// Barrier among the first ``nact`` threads only (the warps that own rows of some level).
+#ifndef SG_TRI_NAMED_BARRIER
+#define SG_TRI_NAMED_BARRIER 0
+#endif
+__device__ __forceinline__ void level_barrier(int nact) {
+#if SG_TRI_NAMED_BARRIER
+  asm volatile("bar.sync 1, %0;\n" ::"r"(nact) : "memory");
+#else
+  (void)nact;
+  __syncthreads();
+#endif
+}
+
+template <typename T, int RPT, bool UPPER>
+__device__ __forceinline__ void ilu9_sweep(T* w, T* ring, int W, const T* __restrict__ lu, int m,
+                                           int N, const int* lev_off_s, int nlev, int nact) {
+  const int o0 = UPPER ? 1 : -m - 1, o1 = UPPER ? m - 1 : -m, o2 = UPPER ? m : -m + 1,
+            o3 = UPPER ? m + 1 : -1;
+  auto lev = [&](int it) { return UPPER ? nlev - 1 - it : it; };
+#pragma unroll
+  for (int d = 0; d < kAhead - 1; ++d)
+    stage_level<T, RPT, UPPER>(ring, d, W, d < nlev ? lev(d) : -1, nlev, m, N, lu, lev_off_s);
+  for (int it = 0; it < nlev; ++it) {
+    int ahead = it + kAhead - 1;
+    stage_level<T, RPT, UPPER>(ring, ahead % kAhead, W, ahead < nlev ? lev(ahead) : -1, nlev, m,
+                               N, lu, lev_off_s);
+    cp_async_wait<kAhead - 1>();
+    const int l = lev(it);
+    int ylo, cnt;
+    level_range(l, m, ylo, cnt);
+    const T* f = ring + (size_t)(it % kAhead) * 5 * W;
+#pragma unroll
+    for (int r = 0; r < RPT; ++r) {
+      int t = threadIdx.x + r * blockDim.x;
+      if (t < cnt) {
+        int y = ylo + t, x = l - 2 * y;
+        int i = x + m * y;
+        T s = w[i];
+        s -= f[t] * w[min(max(i + o0, 0), N - 1)];
+        s -= f[W + t] * w[min(max(i + o1, 0), N - 1)];
+        s -= f[2 * W + t] * w[min(max(i + o2, 0), N - 1)];
+        s -= f[3 * W + t] * w[min(max(i + o3, 0), N - 1)];
+        w[i] = UPPER ? s * f[4 * W + t] : s;
+      }
+    }
+    level_barrier(nact);
   }
   cp_async_wait<0>();
 }
 
-// Both sweeps on the column in w; the first ceil(m/32) warps sweep, the others wait.
-template <typename T, int AHEAD>
-__device__ __forceinline__ void ilu_solve_column(T* w, T* ring, const T* __restrict__ lu, int m,
-                                                 int N, int* progress, int* err) {
-  const int nw = (m + 31) >> 5;
-  const int warp = threadIdx.x >> 5;
-  for (int q = threadIdx.x; q < nw; q += blockDim.x) progress[q] = 0;
-  __syncthreads();
-  if (warp < nw) pipe_sweep<T, AHEAD, false>(w, ring, lu, m, N, progress, err);
-  __syncthreads();
-  for (int q = threadIdx.x; q < nw; q += blockDim.x) progress[q] = 0;
-  __syncthreads();
-  if (warp < nw) pipe_sweep<T, AHEAD, true>(w, ring, lu, m, N, progress, err);
+// Forward and backward sweeps: the level loops run in the first nact threads.
+template <typename T, int RPT>
+__device__ __forceinline__ void ilu9_solve(T* w, T* ring, int W, const T* __restrict__ lu, int m,
+                                           int N, const int* lev_off_s, int nlev, int nact) {
+#if SG_TRI_NAMED_BARRIER
+  if ((int)threadIdx.x < nact) {
+    ilu9_sweep<T, RPT, false>(w, ring, W, lu, m, N, lev_off_s, nlev, nact);
+    ilu9_sweep<T, RPT, true>(w, ring, W, lu, m, N, lev_off_s, nlev, nact);
+  }
+#else
+  ilu9_sweep<T, RPT, false>(w, ring, W, lu, m, N, lev_off_s, nlev, nact);
+  ilu9_sweep<T, RPT, true>(w, ring, W, lu, m, N, lev_off_s, nlev, nact);
+#endif
   __syncthreads();
 }
 
 // CTA c solves column a = a0 + c with factor set (fac_per_col ? a : 0):
 //   z = ILU^{-1}(rhs), then inner-1 times z += ILU^{-1}(rhs - K_blk z), rhs = R[:,a] - acc[:,a].
-template <typename T, bool SMEM, int MAXT, int AHEAD>
-__global__ void __launch_bounds__(MAXT) ilu_block_solve_kernel(
-    int m, int N, int P, int nnz, int a0, int fac_per_col, const T* __restrict__ lu9s,
-    const int* __restrict__ rowptr, const int* __restrict__ col, const T* __restrict__ blks,
-    const T* __restrict__ R, const T* __restrict__ acc, T* __restrict__ Z, T* __restrict__ wglob,
-    int inner, const int* __restrict__ done, int* __restrict__ err) {
+template <typename T, bool SMEM, int RPT>
+__global__ void __launch_bounds__(kTriThreads) ilu_block_solve_kernel(
+    int m, int N, int P, int nnz, int a0, int fac_per_col, const int* __restrict__ lev_off,
+    int nlev, int W, int nact, const T* __restrict__ lu9s, const int* __restrict__ rowptr,
+    const int* __restrict__ col, const T* __restrict__ blks, const T* __restrict__ R,
+    const T* __restrict__ acc, T* __restrict__ Z, T* __restrict__ wglob, int inner,
+    const int* __restrict__ done) {
   if (done != nullptr && *done) return;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  __shared__ int progress[32];
   const int a = a0 + blockIdx.x;
   const int fsel = fac_per_col ? a : 0;
   const T* lu = lu9s + (size_t)fsel * 9 * N;
   const T* blk = blks + (size_t)fsel * nnz;
-  T* ring = reinterpret_cast<T*>(smem_raw);  // ceil(m/32) warps x AHEAD x 5 x 32
-  T* w = SMEM ? ring + (size_t)((m + 31) >> 5) * AHEAD * 5 * 32 : wglob + (size_t)a * N;
+  T* w = SMEM ? reinterpret_cast<T*>(smem_raw) : wglob + (size_t)a * N;
+  T* ring = reinterpret_cast<T*>(smem_raw + (SMEM ? sizeof(T) * (size_t)N : 0));
+  int* lev_s = reinterpret_cast<int*>(ring + (size_t)kAhead * 5 * W);
+  for (int l = threadIdx.x; l <= nlev; l += blockDim.x) lev_s[l] = lev_off[l];
 #pragma unroll 4
   for (int i = threadIdx.x; i < N; i += blockDim.x) {
     T v = R[(size_t)i * P + a];
     if (acc != nullptr) v -= acc[(size_t)i * P + a];
     w[i] = v;
   }
-  ilu_solve_column<T, AHEAD>(w, ring, lu, m, N, progress, err);
+  __syncthreads();
+  ilu9_solve<T, RPT>(w, ring, W, lu, m, N, lev_s, nlev, nact);
 #pragma unroll 4
   for (int i = threadIdx.x; i < N; i += blockDim.x) Z[(size_t)i * P + a] = w[i];
   for (int it = 1; it < inner; ++it) {
@@ -166,7 +181,8 @@ __global__ void __launch_bounds__(MAXT) ilu_block_solve_kernel(
       for (int e = rowptr[i]; e < rowptr[i + 1]; ++e) v -= blk[e] * Z[(size_t)col[e] * P + a];
       w[i] = v;
     }
-    ilu_solve_column<T, AHEAD>(w, ring, lu, m, N, progress, err);
+    __syncthreads();
+    ilu9_solve<T, RPT>(w, ring, W, lu, m, N, lev_s, nlev, nact);
     for (int i = threadIdx.x; i < N; i += blockDim.x) Z[(size_t)i * P + a] += w[i];
   }
 }
@@ -241,20 +257,20 @@ struct PcBufs<float> {
   static bool smem(const System& s) { return s.tri_smem32; }
 };
 
-template <typename T, bool SMEM, int MAXT, int AHEAD>
+template <typename T, bool SMEM, int RPT>
 int launch_block_solve_t(System& s, int a0, int ncols, int fac_per_col, const T* R, const T* acc,
                          T* Z, cudaStream_t st, const int* done) {
   using B = PcBufs<T>;
-  const int m = s.pat.m;
-  const int threads = std::max(kSolveThreads, (m + 31) / 32 * 32);
-  size_t smem = sizeof(T) * ((size_t)((m + 31) / 32) * AHEAD * 5 * 32 + (SMEM ? (size_t)s.N : 0));
-  auto kern = ilu_block_solve_kernel<T, SMEM, MAXT, AHEAD>;
+  const int W = s.pat.max_width;
+  const int nact = std::min(kTriThreads, (W + 31) / 32 * 32);
+  size_t smem = (SMEM ? sizeof(T) * (size_t)s.N : 0) + sizeof(T) * (size_t)kAhead * 5 * W +
+                sizeof(int) * (size_t)(s.nlev9 + 1);
+  auto kern = ilu_block_solve_kernel<T, SMEM, RPT>;
   SG_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   TimeScope ts(s.timer, K_ILU_SOLVE, st);
-  kern<<<ncols, threads, smem, st>>>(m, s.N, s.P, s.pat.nnz, a0, fac_per_col, B::lu9(s),
-                                     s.rowptr.p, s.col.p, B::blk(s), R, acc, Z,
-                                     SMEM ? nullptr : B::triw(s), std::max(1, s.prm.inner_iters),
-                                     done, s.flags.p + 3);
+  kern<<<ncols, kTriThreads, smem, st>>>(s.pat.m, s.N, s.P, s.pat.nnz, a0, fac_per_col, s.lev9_off.p,
+                                 s.nlev9, W, nact, B::lu9(s), s.rowptr.p, s.col.p, B::blk(s), R, acc, Z,
+                                 SMEM ? nullptr : B::triw(s), std::max(1, s.prm.inner_iters), done);
   return check_launch("ilu_block_solve");
 }
 
@@ -262,15 +278,14 @@ template <typename T>
 int launch_block_solve(System& s, int a0, int ncols, int fac_per_col, const T* R, const T* acc,
                        T* Z, cudaStream_t st, const int* done) {
   using B = PcBufs<T>;
-  const int m = s.pat.m;
+  int rpt = (s.pat.max_width + kTriThreads - 1) / kTriThreads;
   if (B::smem(s)) {
-    if (m <= 256) return launch_block_solve_t<T, true, 256, 8>(s, a0, ncols, fac_per_col, R, acc, Z, st, done);
-    if (m <= 512) return launch_block_solve_t<T, true, 512, 4>(s, a0, ncols, fac_per_col, R, acc, Z, st, done);
-    return launch_block_solve_t<T, true, 1024, 2>(s, a0, ncols, fac_per_col, R, acc, Z, st, done);
+    if (rpt <= 1) return launch_block_solve_t<T, true, 1>(s, a0, ncols, fac_per_col, R, acc, Z, st, done);
+    return launch_block_solve_t<T, true, 4>(s, a0, ncols, fac_per_col, R, acc, Z, st, done);
   }
-  if (m <= 256) return launch_block_solve_t<T, false, 256, 8>(s, a0, ncols, fac_per_col, R, acc, Z, st, done);
-  if (m <= 512) return launch_block_solve_t<T, false, 512, 4>(s, a0, ncols, fac_per_col, R, acc, Z, st, done);
-  return launch_block_solve_t<T, false, 1024, 2>(s, a0, ncols, fac_per_col, R, acc, Z, st, done);
+  if (rpt <= 1) return launch_block_solve_t<T, false, 1>(s, a0, ncols, fac_per_col, R, acc, Z, st, done);
+  if (rpt <= 2) return launch_block_solve_t<T, false, 2>(s, a0, ncols, fac_per_col, R, acc, Z, st, done);
+  return launch_block_solve_t<T, false, 4>(s, a0, ncols, fac_per_col, R, acc, Z, st, done);
 }
 
 template <typename T>

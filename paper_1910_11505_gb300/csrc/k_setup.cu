@@ -183,21 +183,26 @@ __global__ void ilu0_kernel(int nnz, const int* __restrict__ rowptr, const int* 
   }
 }
 
-// CSR ILU(0) factors -> 9 node-major slot arrays used by the pipelined solves (slot
-// (dy+1)*3 + (dx+1) of node x + m y; slot 4 holds 1/u_ii; absent neighbours stay 0).
+// CSR ILU(0) factors -> 9-slot level-major layout used by the wavefront solves (slot 4: 1/u_ii).
 __global__ void lu9_kernel(int m, int N, int nnz, int nfac, const int* __restrict__ rowptr,
-                           const int* __restrict__ col, const double* __restrict__ fac,
-                           double* __restrict__ lu9) {
+                           const int* __restrict__ col, const int* __restrict__ lev_off,
+                           const double* __restrict__ fac, double* __restrict__ lu9) {
   long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= (long long)N * nfac) return;
   int f = (int)(t / N), i = (int)(t % N);
   int x = i % m, y = i / m;
+  int l = x + 2 * y;
+  int ylo = max(0, (l - (m - 1) + 1) >> 1);
+  int pos = lev_off[l] + (y - ylo);
+  double dinv = 0.0;
+  for (int e = rowptr[i]; e < rowptr[i + 1]; ++e)
+    if (col[e] == i) dinv = 1.0 / fac[(size_t)f * nnz + e];
   for (int e = rowptr[i]; e < rowptr[i + 1]; ++e) {
     int c = col[e];
     int dx = c % m - x, dy = c / m - y;
     int slot = (dy + 1) * 3 + (dx + 1);
     double v = fac[(size_t)f * nnz + e];
-    lu9[((size_t)f * 9 + slot) * N + i] = slot == 4 ? 1.0 / v : v;
+    lu9[((size_t)f * 9 + slot) * N + pos] = slot == 4 ? dinv : v;
   }
 }
 
@@ -316,11 +321,26 @@ int launch_ilu0(System& s, cudaStream_t st) {
 }
 
 int launch_lu9(System& s, cudaStream_t st) {
+  const int m = s.pat.m;
+  s.nlev9 = 3 * m - 2;
+  std::vector<int> off(s.nlev9 + 1, 0);
+  int maxw = 0;
+  for (int l = 0; l < s.nlev9; ++l) {
+    int ylo = std::max(0, (l - (m - 1) + 1) >> 1);
+    int yhi = std::min(m - 1, l >> 1);
+    int cnt = yhi - ylo + 1;
+    maxw = std::max(maxw, cnt);
+    off[l + 1] = off[l] + cnt;
+  }
+  if (off[s.nlev9] != s.N) return fail(SG_ERR_ARG, "level schedule does not cover the mesh");
+  s.pat.max_width = maxw;
+  SG_TRY(s.lev9_off.alloc(off.size()));
+  SG_TRY(s.lev9_off.upload(off, st));
   SG_TRY(s.lu9.alloc((size_t)s.nfac * 9 * s.N));
   SG_CUDA(cudaMemsetAsync(s.lu9.p, 0, sizeof(double) * s.lu9.n, st));
   long long total = (long long)s.N * s.nfac;
-  lu9_kernel<<<blocks_for(total, 256), 256, 0, st>>>(s.pat.m, s.N, s.pat.nnz, s.nfac, s.rowptr.p,
-                                                     s.col.p, s.fac.p, s.lu9.p);
+  lu9_kernel<<<blocks_for(total, 256), 256, 0, st>>>(m, s.N, s.pat.nnz, s.nfac, s.rowptr.p, s.col.p,
+                                                     s.lev9_off.p, s.fac.p, s.lu9.p);
   return check_launch("lu9");
 }
 

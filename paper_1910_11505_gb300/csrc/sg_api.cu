@@ -82,7 +82,7 @@ template struct DBuf<__nv_bfloat16>;
 // ------------------------------------------------------------------ host tables
 
 static int validate(const sg_params& p) {
-  if (p.n < 2 || p.n > 1023) return fail(SG_ERR_ARG, "n must be in [2, 1023]");
+  if (p.n < 2 || p.n > 1024) return fail(SG_ERR_ARG, "n must be in [2, 1024]");
   if (p.M < 1 || p.M > 8) return fail(SG_ERR_ARG, "M must be in [1, 8]");
   if (p.p < 0 || p.p > 6) return fail(SG_ERR_ARG, "p must be in [0, 6]");
   if (p.q > 12) return fail(SG_ERR_ARG, "q must be <= 12");
@@ -235,6 +235,7 @@ static void free_system(System* s) {
                      &s->lev_b_rows, &s->pair_kb, &s->ent_ptr, &s->ent_u, &s->gs_kptr, &s->gs_k,
                      &s->gs_eptr, &s->gs_ea, &s->flags};
   for (auto* b : ib) b->release();
+  s->lev9_off.release();
   DBuf<double>* db[] = {&s->stack, &s->ent_g, &s->blk, &s->fac, &s->lu9, &s->gs_eg, &s->acc, &s->tmp,
                         &s->tmp2, &s->tri_w, &s->V, &s->Z, &s->Hs, &s->cs, &s->sn, &s->g, &s->y,
                         &s->scal, &s->red, &s->rvec};
@@ -268,12 +269,10 @@ static int setup_system(System& s, cudaStream_t st) {
   // smem budgets of the kernels
   size_t apply_smem = sizeof(double) * 4 * (9 * kChunkK + 9 * (size_t)s.P + kChunkPairs + s.P);
   if (apply_smem > 220 * 1024) return fail(SG_ERR_ARG, "P too large for the operator kernel");
-  // the pipelined block solve keeps one column in shared memory when it fits next to its
-  // factor ring (ceil(m/32) warps x up to 8 columns x 5 slots x 32 lanes)
-  {
-    size_t ringn = (size_t)((p.n + 1 + 31) / 32) * (p.n + 1 <= 256 ? 8 : (p.n + 1 <= 512 ? 4 : 2)) * 160;
-    s.tri_smem = ((size_t)s.N + ringn) * 8 <= 224 * 1024;
-    s.tri_smem32 = ((size_t)s.N + ringn) * 4 <= 224 * 1024;
+  {  // shared memory of the wavefront solve: column + factor ring (8 levels x 5 slots) + levels
+    size_t width = (size_t)(p.n + 2) / 2 + 1, lev = sizeof(int) * 3 * (size_t)(p.n + 1);
+    s.tri_smem = (size_t)s.N * 8 + 40 * 8 * width + lev <= 220 * 1024;
+    s.tri_smem32 = (size_t)s.N * 4 + 40 * 4 * width + lev <= 220 * 1024;
   }
 
   SG_CUDA(cudaStreamCreateWithFlags(&s.stream, cudaStreamNonBlocking));
@@ -487,7 +486,6 @@ int gmres_solve_all(sg_handle* h, const double* const* F, double* const* X, sg_s
     st[i].F = F[i];
     st[i].X = X[i];
     SG_CUDA(cudaStreamWaitEvent(s.stream, start, 0));
-    SG_CUDA(cudaMemsetAsync(s.flags.p + 3, 0, sizeof(int), s.stream));  // wait-limit flag
     SG_TRY(k_norm(s, (size_t)s.N * s.P, F[i], s.scal.p + 2, s.stream));
     SG_TRY(residual(st[i]));
   }
@@ -546,10 +544,6 @@ int gmres_solve_all(sg_handle* h, const double* const* F, double* const* X, sg_s
       q.prev_beta = q.beta;
       q.beta = s.hpin[1];
       if (fl[2] != SG_OK || !std::isfinite(q.beta)) q.status = SG_ERR_NAN;
-      if (fl[3] != 0) {
-        q.status = SG_ERR_CUDA;
-        set_error("a wavefront solve gave up waiting for its neighbour warp");
-      }
       // a refinement step that does not reduce the true residual cannot make progress
       if (s.prm.precision != SG_FP64 && q.beta > q.target && q.beta >= q.prev_beta)
         q.status = SG_ERR_NOT_CONVERGED;

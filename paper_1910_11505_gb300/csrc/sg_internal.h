@@ -159,8 +159,10 @@ struct System {
   DBuf<double> blk;            // nfac x nnz block matrices (A_0 or K_aa) before factorisation
   DBuf<double> fac;            // nfac x nnz ILU(0) factors
   DBuf<float> blk_f32;         // FP32 copy for the mixed inner solver
-  DBuf<double> lu9;            // nfac x 9 x N node-major slot layout of the factors
+  DBuf<double> lu9;            // nfac x 9 x N level-major slot layout of the factors
   DBuf<float> lu9_f32;
+  DBuf<int> lev9_off;          // start of each wavefront level in level-major order
+  int nlev9 = 0;
   // field-split Gauss-Seidel scatter tables, per source block b: k list and (a, g) entries
   DBuf<int> gs_kptr, gs_k, gs_eptr, gs_ea;
   DBuf<double> gs_eg;
