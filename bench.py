@@ -179,6 +179,23 @@ def reference_arm(args):
     return 0
 
 
+# ---------------------------------------------------------------- multi-rank aggregation
+
+def aggregate_ranks(ms_local: float, systems_local: int, device="cpu"):
+    """Whole-job figures over the ranks of the default process group (if any): the slowest
+    rank's time and the systems solved by all ranks.  Only these two numbers cross ranks; the
+    data path has no collective (every rank solves its own systems)."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return ms_local, systems_local
+    t = torch.tensor([ms_local], dtype=torch.float64, device=device)
+    n = torch.tensor([systems_local], dtype=torch.int64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.all_reduce(n, op=dist.ReduceOp.SUM)
+    return float(t.item()), int(n.item())
+
+
 # ---------------------------------------------------------------- GPU arm
 
 def algorithmic_bytes_apply(nnzA, N, P, L, s):
@@ -260,12 +277,9 @@ def main():
     launches = sg.sg_launch_count() - l0
     ktimes = sg.sg_timing_stop(h)
     clk = clocks.stop()
+    ms, systems = aggregate_ranks(ms, ns * args.steps, device="cuda")
     if world > 1:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
         dist.barrier()
-    systems = ns * args.steps * world
     value = systems / (ms / 1000.0)
 
     # dominant kernel class by estimated total time

@@ -2,6 +2,8 @@
 
     python -m paper_1910_11505_gb300.profile_cases precond [fs_gs|fs_jacobi|mean] [n]
     python -m paper_1910_11505_gb300.profile_cases matvec [fp64|fp32|bf16] [n] [M] [p]
+    python -m paper_1910_11505_gb300.profile_cases gmres [n] [iters]      # Arnoldi kernels
+    python -m paper_1910_11505_gb300.profile_cases net [batch]            # network training step
 
 Each case builds one SG system, runs three applications of the chosen operation on seeded
 inputs and exits 0.  Sizes stay at a few GB of device memory.
@@ -52,6 +54,29 @@ def main(argv):
             Y32 = torch.empty_like(X32)
             for _ in range(3):
                 sg.sg_matvec_lowp(h, 0, X32, Y32)
+    elif what == "gmres":
+        n = int(argv[2]) if len(argv) > 2 else 128
+        iters = int(argv[3]) if len(argv) > 3 else 40
+        h = sg.sg_setup(sg.sg_default_params(n=n, M=4, p=3, sigma=0.5, ell=0.5, precond="mean",
+                                             restart=64, max_iters=iters))
+        N, P, _ = sg.sg_dims(h)
+        F = torch.empty(N, P, dtype=torch.float64, device="cuda")
+        sg.sg_rhs(h, 0, F)
+        X = torch.zeros_like(F)
+        sg.sg_gmres_solve(h, [F], [X], raise_on_error=False)
+    elif what == "net":
+        B = int(argv[2]) if len(argv) > 2 else 256
+        D = 4225 * 35
+        net = sg.SGNet(6, 64, 64, D, max_batch=B, bf16=True, seed=1)
+        Z = torch.from_numpy(W.random_field(B, 6, seed=3)).float().cuda()
+        T = 0.01 * torch.from_numpy(W.random_field(B, D, seed=4)).float().cuda()
+        net.set_stats(Z, T)
+        for _ in range(3):
+            net.train_step(Z, T, 1e-3)
+        torch.cuda.synchronize()
+        net.close()
+        print("ok", what)
+        return 0
     else:
         raise SystemExit(f"unknown case {what}")
     torch.cuda.synchronize()
