@@ -30,7 +30,7 @@ sys.path.insert(0, ROOT)
 
 METRIC = "SG solves/sec & matvec HBM GB/s, mixed/learned vs FP64 GMRES at 1e-8 residual"
 WORKLOAD = ("c2: 128x128 Q1 mesh, M=4, p=3 (P=35, L=210), ell=0.5, sigma in {0.25,0.5,1.0,1.5}, "
-            "FP64 GMRES(1024) with field-split Gauss-Seidel + ILU(0), rel. residual 1e-10, x0 = 0")
+            "FP64 GMRES(300) with field-split Gauss-Seidel + ILU(0), rel. residual 1e-10, x0 = 0")
 PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
 DFMA_PEAK_GFLOPS = 1192.0   # FP64 FMA loop on this GB300 (2 flops per DFMA), see the design doc
 ITERS_FILE = os.path.join(ROOT, "oracle", "c2_iterations.json")
@@ -122,7 +122,7 @@ def cpu_oracle_sample(iters_cap: int, sigma: float):
         "K=lambda v:O.sg_matvec(prob,v.reshape(N,P)).ravel()\n"
         "M=lambda v:O.fs_precond(prob,v.reshape(N,P),blocks=blocks).ravel()\n"
         "t=time.perf_counter()\n"
-        f"x,info=O.gmres(K,M,prob.F.ravel(),rtol=1e-10,restart=1024,max_iters={iters_cap})\n"
+        f"x,info=O.gmres(K,M,prob.F.ravel(),rtol=1e-10,restart=300,max_iters={iters_cap})\n"
         "dt=time.perf_counter()-t\n"
         "print(json.dumps({'seconds':dt,'iters':info['iters']}))\n")
     env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
@@ -134,7 +134,7 @@ def cpu_oracle_sample(iters_cap: int, sigma: float):
     return d["seconds"] / max(1, d["iters"]), d
 
 
-C2_RESTART = 1024
+C2_RESTART = 300
 
 
 def oracle_iterations():

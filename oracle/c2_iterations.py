@@ -2,7 +2,7 @@
 systems (128 x 128 Q1, M = 4, p = 3, ell = 0.5, field-split Gauss-Seidel + ILU(0), GMRES(restart),
 relative residual 1e-10).  Used only to scale the timed CPU sample of bench.py to full solves.
 
-    python oracle/c2_iterations.py [restart]      (default 1024)
+    python oracle/c2_iterations.py [restart]      (default 300)
 
 Calls nothing but the oracle.  Runs the four systems in parallel processes (about an hour of CPU).
 """
@@ -16,7 +16,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, os.path.dirname(HERE))
 
 SIGMAS = (0.25, 0.5, 1.0, 1.5)
-RESTART = int(sys.argv[1]) if len(sys.argv) > 1 else 1024
+RESTART = int(sys.argv[1]) if len(sys.argv) > 1 else 300
 
 
 def solve(sigma):
