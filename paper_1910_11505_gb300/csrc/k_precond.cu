@@ -190,11 +190,13 @@ __global__ void __launch_bounds__(kTriThreads) ilu_block_solve_kernel(
 constexpr int kScatterRows = 8;
 
 // After block b of the Gauss-Seidel sweep: for every row i and every a > b,
-// acc[i,a] += sum_k G_k[a,b] (A_k z_b)[i].
+// acc[i,a] += sum_k G_k[a,b] (A_k z_b)[i].  The stiffness values are read from the k-major copy
+// of the stack (stack_km[k*nnz + e]): the block needs only the k of its list, and consecutive
+// threads take consecutive rows of one k, so each k reads one contiguous run of entries.
 template <typename T, typename TV>
 __global__ void __launch_bounds__(128) fs_scatter_kernel(
-    int N, int P, int L, int b, const int* __restrict__ rowptr, const int* __restrict__ col,
-    const TV* __restrict__ stack, const int* __restrict__ kptr, const int* __restrict__ klist,
+    int N, int P, int nnz, int b, const int* __restrict__ rowptr, const int* __restrict__ col,
+    const TV* __restrict__ stack_km, const int* __restrict__ kptr, const int* __restrict__ klist,
     const int* __restrict__ eptr, const int* __restrict__ ek, const T* __restrict__ eg,
     const T* __restrict__ Z, T* __restrict__ acc, const int* __restrict__ done) {
   if (done != nullptr && *done) return;
@@ -203,13 +205,15 @@ __global__ void __launch_bounds__(128) fs_scatter_kernel(
   const int k0 = kptr[b], klen = kptr[b + 1] - k0;
   const int r0 = blockIdx.x * kScatterRows;
   const int nr = min(kScatterRows, N - r0);
-  for (int t = threadIdx.x; t < nr * klen; t += blockDim.x) {
-    int rr = t / klen, kk = t - rr * klen;
-    int i = r0 + rr;
-    int k = klist[k0 + kk];
+  for (int t = threadIdx.x; t < kScatterRows * klen; t += blockDim.x) {
+    const int rr = t % kScatterRows, kk = t / kScatterRows;
     T s = T(0);
-    for (int e = rowptr[i]; e < rowptr[i + 1]; ++e)
-      s += (T)stack[(size_t)e * L + k] * Z[(size_t)col[e] * P + b];
+    if (rr < nr) {
+      const int i = r0 + rr;
+      const TV* ak = stack_km + (size_t)klist[k0 + kk] * nnz;
+      for (int e = rowptr[i]; e < rowptr[i + 1]; ++e)
+        s += (T)ak[e] * Z[(size_t)col[e] * P + b];
+    }
     Ts[rr * klen + kk] = s;
   }
   __syncthreads();
@@ -298,8 +302,9 @@ int launch_scatter<double>(System& s, int b, const double* Z, double* acc, cudaS
   SG_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   int grid = (s.N + kScatterRows - 1) / kScatterRows;
   TimeScope ts(s.timer, K_GS_SCATTER, st);
-  kern<<<grid, 128, smem, st>>>(s.N, s.P, s.L, b, s.rowptr.p, s.col.p, s.stack.p, s.gs_kptr.p,
-                                s.gs_k.p, s.gs_eptr.p, s.gs_ea.p, s.gs_eg.p, Z, acc, done);
+  kern<<<grid, 128, smem, st>>>(s.N, s.P, s.pat.nnz, b, s.rowptr.p, s.col.p, s.stack_km.p,
+                                s.gs_kptr.p, s.gs_k.p, s.gs_eptr.p, s.gs_ea.p, s.gs_eg.p, Z, acc,
+                                done);
   return check_launch("fs_scatter");
 }
 template <>
@@ -311,13 +316,13 @@ int launch_scatter<float>(System& s, int b, const float* Z, float* acc, cudaStre
   if (s.prm.precision == SG_MIXED_BF16) {
     auto kern = fs_scatter_kernel<float, __nv_bfloat16>;
     SG_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    kern<<<grid, 128, smem, st>>>(s.N, s.P, s.L, b, s.rowptr.p, s.col.p, s.stack_bf16.p,
+    kern<<<grid, 128, smem, st>>>(s.N, s.P, s.pat.nnz, b, s.rowptr.p, s.col.p, s.stack_km16.p,
                                   s.gs_kptr.p, s.gs_k.p, s.gs_eptr.p, s.gs_ea.p, s.gs_eg_f32.p, Z,
                                   acc, done);
   } else {
     auto kern = fs_scatter_kernel<float, float>;
     SG_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    kern<<<grid, 128, smem, st>>>(s.N, s.P, s.L, b, s.rowptr.p, s.col.p, s.stack_f32.p,
+    kern<<<grid, 128, smem, st>>>(s.N, s.P, s.pat.nnz, b, s.rowptr.p, s.col.p, s.stack_km32.p,
                                   s.gs_kptr.p, s.gs_k.p, s.gs_eptr.p, s.gs_ea.p, s.gs_eg_f32.p, Z,
                                   acc, done);
   }

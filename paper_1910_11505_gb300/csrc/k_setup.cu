@@ -206,6 +206,25 @@ __global__ void lu9_kernel(int m, int N, int nnz, int nfac, const int* __restric
   }
 }
 
+// 32 x 32 tiles through shared memory (padded against bank conflicts).
+__global__ void transpose_kernel(const double* __restrict__ src, double* __restrict__ dst,
+                                 size_t rows, int cols) {
+  __shared__ double tile[32][33];
+  size_t r0 = (size_t)blockIdx.x * 32;  // rows can exceed the grid's y limit, columns cannot
+  int c0 = blockIdx.y * 32;
+  for (int dy = threadIdx.y; dy < 32; dy += blockDim.y) {
+    size_t r = r0 + dy;
+    int c = c0 + threadIdx.x;
+    tile[dy][threadIdx.x] = (r < rows && c < cols) ? src[r * cols + c] : 0.0;
+  }
+  __syncthreads();
+  for (int dy = threadIdx.y; dy < 32; dy += blockDim.y) {
+    int c = c0 + dy;
+    size_t r = r0 + threadIdx.x;
+    if (r < rows && c < cols) dst[(size_t)c * rows + r] = tile[threadIdx.x][dy];
+  }
+}
+
 template <typename S, typename D>
 __global__ void cast_kernel(const S* __restrict__ src, D* __restrict__ dst, size_t n) {
   for (size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x; t < n;
@@ -342,6 +361,12 @@ int launch_lu9(System& s, cudaStream_t st) {
   lu9_kernel<<<blocks_for(total, 256), 256, 0, st>>>(m, s.N, s.pat.nnz, s.nfac, s.rowptr.p, s.col.p,
                                                      s.lev9_off.p, s.fac.p, s.lu9.p);
   return check_launch("lu9");
+}
+
+int launch_transpose(const double* src, double* dst, size_t rows, int cols, cudaStream_t st) {
+  dim3 block(32, 8), grid((unsigned)((rows + 31) / 32), (cols + 31) / 32);
+  transpose_kernel<<<grid, block, 0, st>>>(src, dst, rows, cols);
+  return check_launch("transpose");
 }
 
 int launch_cast_f32(const double* src, float* dst, size_t n, cudaStream_t st) {

@@ -236,11 +236,12 @@ static void free_system(System* s) {
                      &s->gs_eptr, &s->gs_ea, &s->flags};
   for (auto* b : ib) b->release();
   s->lev9_off.release();
-  DBuf<double>* db[] = {&s->stack, &s->ent_g, &s->blk, &s->fac, &s->lu9, &s->gs_eg, &s->acc, &s->tmp,
+  s->stack_km16.release();
+  DBuf<double>* db[] = {&s->stack, &s->stack_km, &s->ent_g, &s->blk, &s->fac, &s->lu9, &s->gs_eg, &s->acc, &s->tmp,
                         &s->tmp2, &s->tri_w, &s->V, &s->Z, &s->Hs, &s->cs, &s->sn, &s->g, &s->y,
                         &s->scal, &s->red, &s->rvec};
   for (auto* b : db) b->release();
-  DBuf<float>* fb[] = {&s->stack_f32, &s->ent_g_f32, &s->lu9_f32, &s->blk_f32, &s->gs_eg_f32,
+  DBuf<float>* fb[] = {&s->stack_f32, &s->stack_km32, &s->ent_g_f32, &s->lu9_f32, &s->blk_f32, &s->gs_eg_f32,
                        &s->acc32, &s->tmp32, &s->tmp232, &s->tri_w32, &s->V32, &s->Z32,
                        &s->mv32a, &s->mv32b};
   for (auto* b : fb) b->release();
@@ -341,6 +342,15 @@ static int setup_system(System& s, cudaStream_t st) {
     }
     if (p.precond == SG_PC_FS_GS) {
       SG_TRY(build_gs_tables(s, st));
+      SG_TRY(s.stack_km.alloc(nnzL));
+      SG_TRY(launch_transpose(s.stack.p, s.stack_km.p, (size_t)s.pat.nnz, s.L, st));
+      if (p.precision == SG_MIXED_FP32) {
+        SG_TRY(s.stack_km32.alloc(nnzL));
+        SG_TRY(launch_cast_f32(s.stack_km.p, s.stack_km32.p, nnzL, st));
+      } else if (p.precision == SG_MIXED_BF16) {
+        SG_TRY(s.stack_km16.alloc(nnzL));
+        SG_TRY(launch_cast_bf16(s.stack_km.p, s.stack_km16.p, nnzL, st));
+      }
       SG_TRY(s.acc.alloc(NP));
       if (lowp) SG_TRY(s.acc32.alloc(NP));
     }

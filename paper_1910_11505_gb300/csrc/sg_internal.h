@@ -149,6 +149,9 @@ struct System {
   DBuf<double> stack;          // nnz x L
   DBuf<float> stack_f32;       // nnz x L (SG_MIXED_FP32)
   DBuf<__nv_bfloat16> stack_bf16;  // nnz x L (SG_MIXED_BF16)
+  DBuf<double> stack_km;       // L x nnz k-major copy for the Gauss-Seidel scatter
+  DBuf<float> stack_km32;
+  DBuf<__nv_bfloat16> stack_km16;
   DBuf<int> pair_kb, ent_ptr, ent_u;
   DBuf<int2> chunks;           // (u0 | u1 packed as two ints), k range in chunks_k
   DBuf<int2> chunks_k;
@@ -217,6 +220,8 @@ int launch_lu9(System& s, cudaStream_t st);
 int launch_cast_f32(const double* src, float* dst, size_t n, cudaStream_t st);
 int launch_cast_bf16(const double* src, __nv_bfloat16* dst, size_t n, cudaStream_t st);
 int launch_cast_f64(const float* src, double* dst, size_t n, cudaStream_t st);
+// dst[c * rows + r] = src[r * cols + c]  (rows x cols -> cols x rows)
+int launch_transpose(const double* src, double* dst, size_t rows, int cols, cudaStream_t st);
 
 // Y = alpha * K X + beta * B  (B may be null when beta == 0)
 int launch_matvec_f64(const System& s, const double* X, double* Y, double alpha, const double* B,
