@@ -145,7 +145,7 @@ int launch_apply(const System& s, const TV* stack, const TA* eg, const TA* X, TA
                  const TA* B, TA beta, cudaStream_t st, const int* done) {
   size_t smem = apply_smem<TA>(s.P);
   auto kern = sg_apply_kernel<TA, TV>;
-  SG_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  SG_TRY(ensure_smem((const void*)kern, smem));
   int per_sm = (int)std::max<size_t>(1, std::min<size_t>(8, (220 * 1024) / smem));
   int grid = std::min((s.N + kRows - 1) / kRows, num_sms() * per_sm);
   TimeScope ts(s.timer, sizeof(TA) == 8 ? K_APPLY_F64 : K_APPLY_LOWP, st);

@@ -270,7 +270,7 @@ int launch_block_solve_t(System& s, int a0, int ncols, int fac_per_col, const T*
   size_t smem = (SMEM ? sizeof(T) * (size_t)s.N : 0) + sizeof(T) * (size_t)kAhead * 5 * W +
                 sizeof(int) * (size_t)(s.nlev9 + 1);
   auto kern = ilu_block_solve_kernel<T, SMEM, RPT>;
-  SG_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  SG_TRY(ensure_smem((const void*)kern, smem));
   TimeScope ts(s.timer, K_ILU_SOLVE, st);
   kern<<<ncols, kTriThreads, smem, st>>>(s.pat.m, s.N, s.P, s.pat.nnz, a0, fac_per_col, s.lev9_off.p,
                                  s.nlev9, W, nact, B::lu9(s), s.rowptr.p, s.col.p, B::blk(s), R, acc, Z,
@@ -299,7 +299,7 @@ int launch_scatter<double>(System& s, int b, const double* Z, double* acc, cudaS
                            const int* done) {
   size_t smem = sizeof(double) * kScatterRows * std::max(1, s.gs_max_klen);
   auto kern = fs_scatter_kernel<double, double>;
-  SG_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  SG_TRY(ensure_smem((const void*)kern, smem));
   int grid = (s.N + kScatterRows - 1) / kScatterRows;
   TimeScope ts(s.timer, K_GS_SCATTER, st);
   kern<<<grid, 128, smem, st>>>(s.N, s.P, s.pat.nnz, b, s.rowptr.p, s.col.p, s.stack_km.p,
@@ -315,13 +315,13 @@ int launch_scatter<float>(System& s, int b, const float* Z, float* acc, cudaStre
   TimeScope ts(s.timer, K_GS_SCATTER, st);
   if (s.prm.precision == SG_MIXED_BF16) {
     auto kern = fs_scatter_kernel<float, __nv_bfloat16>;
-    SG_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    SG_TRY(ensure_smem((const void*)kern, smem));
     kern<<<grid, 128, smem, st>>>(s.N, s.P, s.pat.nnz, b, s.rowptr.p, s.col.p, s.stack_km16.p,
                                   s.gs_kptr.p, s.gs_k.p, s.gs_eptr.p, s.gs_ea.p, s.gs_eg_f32.p, Z,
                                   acc, done);
   } else {
     auto kern = fs_scatter_kernel<float, float>;
-    SG_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    SG_TRY(ensure_smem((const void*)kern, smem));
     kern<<<grid, 128, smem, st>>>(s.N, s.P, s.pat.nnz, b, s.rowptr.p, s.col.p, s.stack_km32.p,
                                   s.gs_kptr.p, s.gs_k.p, s.gs_eptr.p, s.gs_ea.p, s.gs_eg_f32.p, Z,
                                   acc, done);

@@ -31,6 +31,20 @@ int check_launch(const char* what) {
   return SG_OK;
 }
 
+int ensure_smem(const void* kernel, size_t bytes) {
+  static std::mutex mu;
+  static std::map<std::pair<const void*, int>, size_t> done;
+  int dev = 0;
+  cudaGetDevice(&dev);
+  std::lock_guard<std::mutex> lock(mu);
+  auto key = std::make_pair(kernel, dev);
+  auto it = done.find(key);
+  if (it != done.end() && it->second >= bytes) return SG_OK;
+  SG_CUDA(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
+  done[key] = bytes;
+  return SG_OK;
+}
+
 TimeScope::TimeScope(Timer* t_, int cls_, cudaStream_t st_) : t(t_), cls(cls_), st(st_) {
   if (!t || !t->on) return;
   long long c = t->count[cls]++;

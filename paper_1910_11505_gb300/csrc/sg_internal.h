@@ -38,6 +38,9 @@ struct Status {
 
 void count_launch(int n = 1);
 int check_launch(const char* what);
+// Raise a kernel's dynamic shared-memory limit on the current device to ``bytes`` unless an
+// earlier call already set at least that much (the attribute call is not repeated per launch).
+int ensure_smem(const void* kernel, size_t bytes);
 
 // ------------------------------------------------------------------ live kernel timing
 
