@@ -119,18 +119,33 @@ __global__ void __launch_bounds__(256) sg_apply_kernel(
         kb = kbn;
         const TA* a = As + kk * kRE;
         const TA* x = Xs + b * XS;
-        // two rows at a time: 18 values of A and of X in registers
+        // 16-byte loads only at 16-byte-aligned offsets: a run starts at a multiple of 144 bytes
+        // (36 floats or 36 / 38 doubles), so FP32 loads the whole run of 36 and FP64 two halves
+        // of 18 doubles (144 bytes each)
+        if constexpr (sizeof(TA) == 4) {
+          TA av[kRE], xv[kRE];
+          load_run<TA, 0, kRE>(a, av);
+          load_run<TA, 0, kRE>(x, xv);
 #pragma unroll
-        for (int h = 0; h < 2; ++h) {
-          TA av[18], xv[18];
-          load_run<TA, 0, 18>(a + 18 * h, av);
-          load_run<TA, 0, 18>(x + 18 * h, xv);
+          for (int r = 0; r < kRows; ++r) {
+            TA s = av[r * 9] * xv[r * 9];
 #pragma unroll
-          for (int rr = 0; rr < 2; ++rr) {
-            TA s = av[rr * 9] * xv[rr * 9];
+            for (int e = 1; e < 9; ++e) s = fma(av[r * 9 + e], xv[r * 9 + e], s);
+            Ts[r * kTs + (u - uu.x)] = s;
+          }
+        } else {
 #pragma unroll
-            for (int e = 1; e < 9; ++e) s = fma(av[rr * 9 + e], xv[rr * 9 + e], s);
-            Ts[(2 * h + rr) * kTs + (u - uu.x)] = s;
+          for (int h = 0; h < 2; ++h) {
+            TA av[18], xv[18];
+            load_run<TA, 0, 18>(a + 18 * h, av);
+            load_run<TA, 0, 18>(x + 18 * h, xv);
+#pragma unroll
+            for (int rr = 0; rr < 2; ++rr) {
+              TA s = av[rr * 9] * xv[rr * 9];
+#pragma unroll
+              for (int e = 1; e < 9; ++e) s = fma(av[rr * 9 + e], xv[rr * 9 + e], s);
+              Ts[(2 * h + rr) * kTs + (u - uu.x)] = s;
+            }
           }
         }
       }
