@@ -35,31 +35,7 @@ __device__ __forceinline__ TA warp_sum(TA v) {
 
 // Rows per tile: the pair and entry tables are read once per tile instead of once per row.
 constexpr int kRows = 4;
-constexpr int kRE = kRows * 9;        // stencil values of a tile for one k (or one b)
 constexpr int kTs = kChunkPairs + 1;  // row stride of T in shared memory
-// Row stride of the staged X values (per chaos index b): 36 floats or 38 doubles keep the
-// 16-byte loads of consecutive b conflict-free.
-template <typename TA> struct XStride;
-template <> struct XStride<float> { static constexpr int v = 36; };
-template <> struct XStride<double> { static constexpr int v = 38; };
-
-// The 36 (As) or 36 of the first XStride (Xs) values of one k / one b, as 16-byte loads.
-template <typename TA, int N0, int CNT>
-__device__ __forceinline__ void load_run(const TA* p, TA (&v)[CNT]) {
-  if constexpr (sizeof(TA) == 4) {
-#pragma unroll
-    for (int q = 0; q < CNT / 4; ++q) {
-      float4 t = reinterpret_cast<const float4*>(p + N0)[q];
-      v[4 * q] = t.x; v[4 * q + 1] = t.y; v[4 * q + 2] = t.z; v[4 * q + 3] = t.w;
-    }
-  } else {
-#pragma unroll
-    for (int q = 0; q < CNT / 2; ++q) {
-      double2 t = reinterpret_cast<const double2*>(p + N0)[q];
-      v[2 * q] = t.x; v[2 * q + 1] = t.y;
-    }
-  }
-}
 
 template <typename TA, typename TV>
 __global__ void __launch_bounds__(256) sg_apply_kernel(
@@ -69,13 +45,11 @@ __global__ void __launch_bounds__(256) sg_apply_kernel(
     const int* __restrict__ ent_u, const TA* __restrict__ ent_g, const TA* __restrict__ X,
     TA* __restrict__ Y, TA alpha, const TA* __restrict__ B, TA beta, const int* __restrict__ done) {
   if (done != nullptr && *done) return;
-  constexpr int XS = XStride<TA>::v;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  // stencil slots are padded to 9 per row with zeros, so every row runs the same unrolled loop;
-  // a tile's 36 values of one k (As) and of one b (Xs) are contiguous for 16-byte loads
-  TA* As = reinterpret_cast<TA*>(smem_raw);   // kChunkK x 36
-  TA* Xs = As + kChunkK * kRE;                // P x XS
-  TA* Ts = Xs + (size_t)P * XS;               // kRows x kTs (padded against bank conflicts)
+  // stencil slots are padded to 9 per row with zeros, so every row runs the same unrolled loop
+  TA* As = reinterpret_cast<TA*>(smem_raw);   // kRows x 9 x kChunkK
+  TA* Xs = As + kRows * 9 * kChunkK;          // kRows x 9 x P
+  TA* Ts = Xs + kRows * 9 * P;                // kRows x kTs (padded against bank conflicts)
   TA* Ys = Ts + kRows * kTs;                  // kRows x P
   __shared__ int rs_e0[kRows], rs_ne[kRows];
   const int tid = threadIdx.x, nth = blockDim.x;
@@ -91,11 +65,11 @@ __global__ void __launch_bounds__(256) sg_apply_kernel(
     }
     __syncthreads();
     // one warp per (row, slot), lanes over chaos index: no runtime division
-    for (int re = tid >> 5; re < kRE; re += nth >> 5) {
+    for (int re = tid >> 5; re < kRows * 9; re += nth >> 5) {
       const int r = re / 9, e = re - r * 9;
       const bool have = e < rs_ne[r];
       const TA* xr = have ? X + (size_t)col[rs_e0[r] + e] * P : nullptr;
-      for (int b = tid & 31; b < P; b += 32) Xs[b * XS + re] = have ? xr[b] : TA(0);
+      for (int b = tid & 31; b < P; b += 32) Xs[re * P + b] = have ? xr[b] : TA(0);
     }
     for (int t = tid; t < kRows * P; t += nth) Ys[t] = TA(0);
     for (int c = 0; c < nchunks; ++c) {
@@ -103,13 +77,13 @@ __global__ void __launch_bounds__(256) sg_apply_kernel(
       const int2 kr = chunks_k[c];
       const int kw = kr.y - kr.x;
       static_assert((kChunkK & (kChunkK - 1)) == 0, "chunk width must be a power of two");
-      for (int t = tid; t < kRE * kChunkK; t += nth) {
+      for (int t = tid; t < kRows * 9 * kChunkK; t += nth) {
         const int re = t / kChunkK, kk = t & (kChunkK - 1);
         if (kk >= kw) continue;
         const int r = re / 9, e = re - r * 9;
         TA v = TA(0);
         if (e < rs_ne[r]) v = cvt<TA, TV>(stack + (size_t)(rs_e0[r] + e) * L + kr.x + kk);
-        As[kk * kRE + re] = v;
+        As[re * kChunkK + kk] = v;
       }
       __syncthreads();
       int kb = (uu.x + tid < uu.y) ? pair_kb[uu.x + tid] : 0;
@@ -117,36 +91,14 @@ __global__ void __launch_bounds__(256) sg_apply_kernel(
         const int kbn = (u + nth < uu.y) ? pair_kb[u + nth] : 0;  // next pair, loaded early
         const int kk = (kb >> 16) - kr.x, b = kb & 0xffff;
         kb = kbn;
-        const TA* a = As + kk * kRE;
-        const TA* x = Xs + b * XS;
-        // 16-byte loads only at 16-byte-aligned offsets: a run starts at a multiple of 144 bytes
-        // (36 floats or 36 / 38 doubles), so FP32 loads the whole run of 36 and FP64 two halves
-        // of 18 doubles (144 bytes each)
-        if constexpr (sizeof(TA) == 4) {
-          TA av[kRE], xv[kRE];
-          load_run<TA, 0, kRE>(a, av);
-          load_run<TA, 0, kRE>(x, xv);
 #pragma unroll
-          for (int r = 0; r < kRows; ++r) {
-            TA s = av[r * 9] * xv[r * 9];
+        for (int r = 0; r < kRows; ++r) {
+          const TA* a = As + r * 9 * kChunkK + kk;
+          const TA* x = Xs + r * 9 * P + b;
+          TA s = a[0] * x[0];
 #pragma unroll
-            for (int e = 1; e < 9; ++e) s = fma(av[r * 9 + e], xv[r * 9 + e], s);
-            Ts[r * kTs + (u - uu.x)] = s;
-          }
-        } else {
-#pragma unroll
-          for (int h = 0; h < 2; ++h) {
-            TA av[18], xv[18];
-            load_run<TA, 0, 18>(a + 18 * h, av);
-            load_run<TA, 0, 18>(x + 18 * h, xv);
-#pragma unroll
-            for (int rr = 0; rr < 2; ++rr) {
-              TA s = av[rr * 9] * xv[rr * 9];
-#pragma unroll
-              for (int e = 1; e < 9; ++e) s = fma(av[rr * 9 + e], xv[rr * 9 + e], s);
-              Ts[(2 * h + rr) * kTs + (u - uu.x)] = s;
-            }
-          }
+          for (int e = 1; e < 9; ++e) s = fma(a[e * kChunkK], x[e * P], s);
+          Ts[r * kTs + (u - uu.x)] = s;
         }
       }
       __syncthreads();
@@ -173,8 +125,8 @@ __global__ void __launch_bounds__(256) sg_apply_kernel(
 
 template <typename TA>
 size_t apply_smem(int P) {
-  return sizeof(TA) * ((size_t)kChunkK * kRE + (size_t)P * XStride<TA>::v + (size_t)kRows * kTs +
-                       (size_t)kRows * P);
+  return sizeof(TA) * ((size_t)kRows * 9 * kChunkK + (size_t)kRows * 9 * P +
+                       (size_t)kRows * kTs + (size_t)kRows * P);
 }
 
 int num_sms() {

@@ -282,7 +282,7 @@ static int setup_system(System& s, cudaStream_t st) {
   SG_TRY(build_tables(s));
   const bool lowp = p.precision != SG_FP64;
   // smem budgets of the kernels
-  size_t apply_smem = sizeof(double) * (36 * kChunkK + 38 * (size_t)s.P + 4 * (kChunkPairs + 1) + 4 * s.P);
+  size_t apply_smem = sizeof(double) * 4 * (9 * kChunkK + 9 * (size_t)s.P + kChunkPairs + s.P);
   if (apply_smem > 220 * 1024) return fail(SG_ERR_ARG, "P too large for the operator kernel");
   {  // shared memory of the wavefront solve: column + factor ring (8 levels x 5 slots) + levels
     size_t width = (size_t)(p.n + 2) / 2 + 1, lev = sizeof(int) * 3 * (size_t)(p.n + 1);
