@@ -290,8 +290,10 @@ def main():
     hbm, peak_kind = _peaks()
     N, P, L = sg.sg_dims(h, 0)
     if dom == "ilu_solve":
-        # one block solve: factor values + pattern (col, rowptr, diag, level rows) + rhs, acc, z
-        alg_bytes = nnzA * 8 + 4 * nnzA + 4 * (N + 1) + 4 * N + 8 * N + 3 * N * 8
+        # one block solve: 9 factor values per row (lower 4, upper 4, 1/u_ii), the right-hand
+        # side column and z, and the level table
+        m = int(round(N ** 0.5))
+        alg_bytes = 9 * N * 8 + 2 * N * 8 + 4 * (3 * m - 1)
     elif dom == "apply_f64":
         alg_bytes = algorithmic_bytes_apply(nnzA, N, P, L, 8)
     else:
@@ -303,13 +305,15 @@ def main():
             "traffic": measured_traffic(dom), "avg_launch_us": d_avg_s * 1e6,
             "launches_timed": d_timed, "share_of_timed_gpu_time": est[dom] / max(1e-30, sum(est.values()))}
     if dom == "ilu_solve":
-        # the block solve is bound by its dependency chain: 2 (3m - 2) wavefront levels, each
-        # at least 4-5 dependent FP64 operations (64 cycles each on this GPU) plus a barrier
+        # the block solve is bound by its dependency chain: two sweeps of 3m - 8 interior
+        # wavefront levels, one barrier step each plus one, and per step two dependent FP64 FMAs
+        # (64 cycles each on this GPU), a shared-memory load and store (~50 cycles) and the
+        # barrier (~50 cycles): an estimated floor of ~230 cycles per step at 2.07 GHz
         m = int(round(N ** 0.5))
-        levels = 2 * (3 * m - 2)
-        roof["critical_path_levels"] = levels
-        roof["ns_per_level"] = d_avg_s * 1e9 / levels
-        roof["ns_per_level_floor"] = 420.0 / 2.07  # measured 4-DFMA level loop: ~420 cycles
+        steps = 2 * (3 * m - 8) + 2
+        roof["critical_path_steps"] = steps
+        roof["ns_per_step"] = d_avg_s * 1e9 / steps
+        roof["ns_per_step_floor_est"] = (2 * 64 + 50 + 50) / 2.07
 
     # the SG operator alone (K1): FP64 DFMA-bound, reported against the DFMA peak as well
     X = torch.from_numpy(W.random_field(N, P, seed=7)).cuda()

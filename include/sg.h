@@ -117,13 +117,14 @@ int sg_precond_apply(sg_handle* h, int sys, const double* R, double* Z, void* st
 /* No counterpart in the paper: the same field-split Gauss-Seidel application as
  * sg_precond_apply (outer_sweeps = 1), for callers that must not allocate device memory, such as
  * a process whose device memory is already reserved by another allocator (a framework's caching
- * pool) or code with a fixed memory budget that may not grow.  Its N x P off-diagonal scratch is
- * a fixed array of SG_NOALLOC_MAX_ENTRIES doubles (8 MiB) inside this library, which every GPU
- * that loads the library holds until the process exits; the call itself allocates nothing and
- * clears the part it uses.  The first call on a device looks up that array's device address, so
+ * pool) or code with a fixed memory budget that may not grow.  Its scratch, the P right-hand
+ * sides of the block solves as columns of ldN = N rounded up to a multiple of 4 entries, is a
+ * fixed array of SG_NOALLOC_MAX_ENTRIES doubles (8 MiB) inside this library, which every GPU that
+ * loads the library holds until the process exits; the call itself allocates nothing and
+ * overwrites the part it uses from R before reading it.  The first call on a device looks up that array's device address, so
  * make that first call before any stream capture.  All calls share the one array: calls whose
  * work overlaps on the GPU (other streams, other threads) race and give wrong results.
- * SG_ERR_ARG if the system does not use SG_PC_FS_GS with outer_sweeps = 1, if N x P exceeds
+ * SG_ERR_ARG if the system does not use SG_PC_FS_GS with outer_sweeps = 1, if P x ldN exceeds
  * SG_NOALLOC_MAX_ENTRIES, if one column does not fit the shared-memory block solve, or if the
  * handle's device is not current.  R, Z as for sg_precond_apply.  Asynchronous on ``stream``. */
 #define SG_NOALLOC_MAX_ENTRIES (1 << 20)
@@ -160,7 +161,7 @@ long long sg_launch_count(void);
 #define SG_K_ILU_SOLVE 2   /* ILU(0) block solves of the preconditioners                    */
 #define SG_K_GS_SCATTER 3  /* field-split Gauss-Seidel off-diagonal push                   */
 #define SG_K_ARNOLDI 4     /* CGS2 dot products, updates, Givens step, normalisation        */
-#define SG_K_OTHER 5       /* norms, cycle start and end, casts                             */
+#define SG_K_OTHER 5       /* norms, cycle start and end, casts, preconditioner transposes  */
 #define SG_K_NCLASS 6
 /* Start timing: from now on every ``stride``-th launch of each class queued through handle h is
  * bracketed by CUDA events recorded on the stream it is launched on (up to 2^15 timed launches).

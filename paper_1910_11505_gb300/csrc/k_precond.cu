@@ -7,12 +7,14 @@
 //    block K_aa approximated by its ILU(0) factors with ``inner_iters`` Richardson steps;
 //  * both wrapped in ``outer_sweeps`` steps of the level solver of Eq. level_solver.
 //
-// The ILU(0) triangular solves run as wavefronts: rows of one level of the lower (upper) graph
-// of the pattern depend only on rows of earlier levels.  One CTA owns one chaos column and walks
-// all levels with a CTA barrier in between, holding the column in shared memory when it fits.
-// The off-diagonal coupling of the Gauss-Seidel sweep, sum_{b<a} K_ab z_b, is pushed forward
-// after each block b by a grid-wide kernel: T[k] = sum_e A[e,k] z_b[j_e] once per (row, k), then
-// acc[:,a] += G_k[a,b] T[k] for every a > b.
+// The block solves read their right-hand sides as contiguous columns (rhs_t, P columns of stride
+// ldN, filled from the N x P residual by a tiled transpose), so one CTA loads its column with a
+// burst of 16-byte copies.  The ILU(0) triangular solves run as wavefronts: rows of one level of
+// the lower (upper) graph of the pattern depend only on rows of earlier levels; one CTA owns one
+// chaos column and walks all levels with a CTA barrier in between, holding the column in shared
+// memory when it fits.  The off-diagonal coupling of the Gauss-Seidel sweep, sum_{b<a} K_ab z_b,
+// is subtracted from the later columns of rhs_t after each block b by a grid-wide kernel:
+// T[k] = sum_e A[e,k] z_b[j_e] once per (row, k), then rhs_t[a] -= G_k[a,b] T[k] for a > b.
 #include "sg_internal.h"
 
 namespace sg {
@@ -20,15 +22,34 @@ namespace sg {
 namespace {
 
 // Wavefront schedule of the 9-point Q1 pattern in natural order: row (x, y) of the lower factor
-// depends on (x-1, y-1), (x, y-1), (x+1, y-1), (x-1, y), so the rows with x + 2y = l form level l
-// (3m - 2 levels); the upper factor uses the same levels in reverse.  Factors are stored per
-// factor set as 9 slot arrays in level-major row order (slot (dy+1)*3 + (dx+1); slot 4 holds
-// 1/u_ii; absent neighbours hold 0), so a level needs no index loads and its factors can be
-// fetched one level ahead.
-__device__ __forceinline__ void level_range(int l, int m, int& ylo, int& cnt) {
-  ylo = max(0, (l - (m - 1) + 1) >> 1);
-  int yhi = min(m - 1, l >> 1);
-  cnt = yhi - ylo + 1;
+// depends on (x-1, y-1), (x, y-1), (x+1, y-1), (x-1, y), so the rows with x + 2y = l form level l;
+// the upper factor uses the same levels in reverse.  Factors are stored per factor set as 9 slot
+// arrays in level-major row order (slot (dy+1)*3 + (dx+1), absent neighbours 0; slot 4 holds
+// 1/u_ii and the upper slots u_ij/u_ii), so a level needs no index loads and its factors can be
+// fetched ahead.
+//
+// Only interior rows (1 <= x, y <= m-2) take part.  Dirichlet rows and columns are eliminated at
+// assembly, so every block has the rows d e_i on the boundary and no coupling from an interior
+// row to a boundary node, and ILU(0) keeps both (L = I and U = d there, couplings exactly 0): a
+// boundary row's solve is its scaling by 1/u_ii.
+//
+// Two thread groups share each level.  On level l the lower factor reads two rows of level l-1
+// ((x+1, y-1), (x-1, y)), one of level l-2 ((x, y-1)) and one of level l-3 ((x-1, y-1)); the
+// upper factor mirrors this with (x+1, y), (x-1, y+1) | (x, y+1) | (x+1, y+1).  The critical
+// group applies the two level-(l-1) couplings on level l.  The lookahead group owns level l+1,
+// next in sweep order: one step before it, it forms w_i - f * z for the level-(l-2) neighbour
+// (w_i / u_ii - ... in the upper sweep) and keeps it in a register; in the step itself it applies
+// the remaining coupling.  So the dependent chain after each barrier is two FMAs for the critical
+// group and one for the lookahead group, where one thread per row would have four (an FP64
+// instruction holds its SM sub-partition for many cycles, and the groups' warps issue on
+// different sub-partitions).  No thread writes a row that another reads in the same step.
+__device__ __forceinline__ void interior_level(int l, int m, const int* lev_off, int& y0, int& cnt,
+                                               int& pos0) {
+  const int ylo = max(0, (l - (m - 1) + 1) >> 1);  // first row of the full level
+  y0 = max(1, (l - (m - 2) + 1) >> 1);
+  const int y1 = min(m - 2, (l - 1) >> 1);
+  cnt = y1 - y0 + 1;
+  pos0 = lev_off[l] + (y0 - ylo);
 }
 
 // Factors of the next kAhead levels are copied into a shared-memory ring with cp.async while the
@@ -36,169 +57,217 @@ __device__ __forceinline__ void level_range(int l, int m, int& ylo, int& cnt) {
 // for every load the thread has in flight, so each level would pay a full L2 round trip.  Each
 // thread copies and later reads only its own rows' factors, so the ring needs no barrier of its
 // own; cp.async.wait_group orders the copy before the read.
-#ifndef SG_TRI_AHEAD
-#define SG_TRI_AHEAD 8
-#endif
-#ifndef SG_TRI_THREADS
-#define SG_TRI_THREADS 256
-#endif
-constexpr int kAhead = SG_TRI_AHEAD;
-constexpr int kTriThreads = SG_TRI_THREADS;
+constexpr int kAhead = kTriAhead;
+constexpr int kTriMaxThreads = 1024;
 
 template <typename T>
 __device__ __forceinline__ void cp_async_elem(T* dst, const T* src) {
   unsigned sa = (unsigned)__cvta_generic_to_shared(dst);
   asm volatile("cp.async.ca.shared.global [%0], [%1], %2;\n" ::"r"(sa), "l"(src), "n"(sizeof(T)));
 }
+__device__ __forceinline__ void cp_async_16(void* dst, const void* src) {
+  unsigned sa = (unsigned)__cvta_generic_to_shared(dst);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(src));
+}
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::); }
 template <int N>
 __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N)); }
 
-// Copy the factors of level l (4 off-diagonal slots, plus 1/u_ii for the upper sweep) of the rows
-// this thread owns into ring slot ``slot``; always commits one group (possibly empty).
-template <typename T, int RPT, bool UPPER>
-__device__ __forceinline__ void stage_level(T* ring, int slot, int W, int l, int nlev, int m,
-                                            int N, const T* __restrict__ lu, const int* lev_off_s) {
-  if (l >= 0 && l < nlev) {
-    int ylo, cnt;
-    level_range(l, m, ylo, cnt);
-    const int base = lev_off_s[l];
-    const int s0 = UPPER ? 5 : 0;
-#pragma unroll
-    for (int r = 0; r < RPT; ++r) {
-      int t = threadIdx.x + r * blockDim.x;
-      if (t < cnt) {
-        T* d = ring + (size_t)slot * 5 * W + t;
-#pragma unroll
-        for (int q = 0; q < 4; ++q) cp_async_elem(d + q * W, lu + (size_t)(s0 + q) * N + base + t);
-        if (UPPER) cp_async_elem(d + 4 * W, lu + (size_t)4 * N + base + t);
+// One sweep (lower or upper) over the nl interior levels; every thread of the CTA calls it and
+// passes nl + 1 barriers.  List position j is level 3 + j (lower) or 3m - 6 - j (upper).  The
+// critical group takes position j at step j; the lookahead group prepares position j at step
+// j - 2 and finishes it at step j - 1.  Ring: kAhead x 2 x wc critical, kAhead x 3 x wc lookahead.
+template <typename T, bool UPPER>
+__device__ __forceinline__ void ilu9_sweep(T* w, T* ring, int wc, const T* __restrict__ lu, int m,
+                                           int N, const int* lev_s, int nl, bool crit, int t) {
+  auto level = [&](int j) { return UPPER ? 3 * m - 6 - j : 3 + j; };
+  if (crit) {
+    // lower: slots 2, 3 at i - m + 1, i - 1; upper: slots 5, 6 at i + 1, i + m - 1
+    const int oA = UPPER ? 1 : -m + 1, oB = UPPER ? m - 1 : -1;
+    const T* fA = lu + (size_t)(UPPER ? 5 : 2) * N;
+    const T* fB = fA + N;
+    auto stage = [&](int j) {
+      if (j < nl) {
+        int y0, cnt, pos0;
+        interior_level(level(j), m, lev_s, y0, cnt, pos0);
+        if (t < cnt) {
+          T* d = ring + (size_t)(j % kAhead) * 2 * wc + t;
+          cp_async_elem(d, fA + pos0 + t);
+          cp_async_elem(d + wc, fB + pos0 + t);
+        }
       }
-    }
-  }
-  cp_async_commit();
-}
-
-// Barrier among the first ``nact`` threads only (the warps that own rows of some level).
-#ifndef SG_TRI_NAMED_BARRIER
-#define SG_TRI_NAMED_BARRIER 0
-#endif
-__device__ __forceinline__ void level_barrier(int nact) {
-#if SG_TRI_NAMED_BARRIER
-  asm volatile("bar.sync 1, %0;\n" ::"r"(nact) : "memory");
-#else
-  (void)nact;
-  __syncthreads();
-#endif
-}
-
-template <typename T, int RPT, bool UPPER>
-__device__ __forceinline__ void ilu9_sweep(T* w, T* ring, int W, const T* __restrict__ lu, int m,
-                                           int N, const int* lev_off_s, int nlev, int nact) {
-  const int o0 = UPPER ? 1 : -m - 1, o1 = UPPER ? m - 1 : -m, o2 = UPPER ? m : -m + 1,
-            o3 = UPPER ? m + 1 : -1;
-  auto lev = [&](int it) { return UPPER ? nlev - 1 - it : it; };
+      cp_async_commit();
+    };
 #pragma unroll
-  for (int d = 0; d < kAhead - 1; ++d)
-    stage_level<T, RPT, UPPER>(ring, d, W, d < nlev ? lev(d) : -1, nlev, m, N, lu, lev_off_s);
-  for (int it = 0; it < nlev; ++it) {
-    int ahead = it + kAhead - 1;
-    stage_level<T, RPT, UPPER>(ring, ahead % kAhead, W, ahead < nlev ? lev(ahead) : -1, nlev, m,
-                               N, lu, lev_off_s);
-    cp_async_wait<kAhead - 1>();
-    const int l = lev(it);
-    int ylo, cnt;
-    level_range(l, m, ylo, cnt);
-    const T* f = ring + (size_t)(it % kAhead) * 5 * W;
-#pragma unroll
-    for (int r = 0; r < RPT; ++r) {
-      int t = threadIdx.x + r * blockDim.x;
-      if (t < cnt) {
-        int y = ylo + t, x = l - 2 * y;
-        int i = x + m * y;
-        T s = w[i];
-        s -= f[t] * w[min(max(i + o0, 0), N - 1)];
-        s -= f[W + t] * w[min(max(i + o1, 0), N - 1)];
-        s -= f[2 * W + t] * w[min(max(i + o2, 0), N - 1)];
-        s -= f[3 * W + t] * w[min(max(i + o3, 0), N - 1)];
-        w[i] = UPPER ? s * f[4 * W + t] : s;
+    for (int d = 0; d < kAhead - 1; ++d) stage(d);
+    for (int step = -1; step < nl; ++step) {
+      if (step >= 0) {
+        stage(step + kAhead - 1);
+        cp_async_wait<kAhead - 1>();
+        const int l = level(step);
+        int y0, cnt, pos0;
+        interior_level(l, m, lev_s, y0, cnt, pos0);
+        if (t < cnt) {
+          const int y = y0 + t, i = (l - 2 * y) + m * y;
+          const T* f = ring + (size_t)(step % kAhead) * 2 * wc + t;
+          T v = w[i];
+          v -= f[0] * w[i + oA];
+          v -= f[wc] * w[i + oB];
+          w[i] = v;
+        }
       }
+      __syncthreads();
     }
-    level_barrier(nact);
+  } else {
+    // early coupling (level l-3 / l+3 of the row's own level) and, upper, 1/u_ii: slot 0 at
+    // i - m - 1 or slot 8 at i + m + 1 with slot 4; late coupling: slot 1 at i - m or slot 7 at i + m
+    const int oE = UPPER ? m + 1 : -m - 1, oL = UPPER ? m : -m;
+    const T* fE = lu + (size_t)(UPPER ? 8 : 0) * N;
+    const T* fL = lu + (size_t)(UPPER ? 7 : 1) * N;
+    const T* fD = lu + (size_t)4 * N;
+    T* lring = ring + (size_t)kAhead * 2 * wc;
+    auto stage = [&](int j) {
+      if (j < nl) {
+        int y0, cnt, pos0;
+        interior_level(level(j), m, lev_s, y0, cnt, pos0);
+        if (t < cnt) {
+          T* d = lring + (size_t)(j % kAhead) * 3 * wc + t;
+          cp_async_elem(d, fE + pos0 + t);
+          cp_async_elem(d + wc, fL + pos0 + t);
+          if (UPPER) cp_async_elem(d + 2 * wc, fD + pos0 + t);
+        }
+      }
+      cp_async_commit();
+    };
+    int pi = -1;
+    T pp = T(0), pf = T(0);
+    auto prepare = [&](int j) {  // partial result and late factor of position j, in registers
+      stage(j + kAhead - 1);
+      cp_async_wait<kAhead - 1>();
+      const int l = level(j);
+      int y0, cnt, pos0;
+      interior_level(l, m, lev_s, y0, cnt, pos0);
+      pi = -1;
+      if (t < cnt) {
+        const int y = y0 + t;
+        pi = (l - 2 * y) + m * y;
+        const T* f = lring + (size_t)(j % kAhead) * 3 * wc + t;
+        const T base = UPPER ? w[pi] * f[2 * wc] : w[pi];
+        pp = base - f[0] * w[pi + oE];
+        pf = f[wc];
+      }
+    };
+#pragma unroll
+    for (int d = 0; d < kAhead - 1; ++d) stage(d);
+    prepare(0);
+    for (int step = -1; step < nl; ++step) {
+      const int j = step + 1;
+      if (j < nl && pi >= 0) w[pi] = pp - pf * w[pi + oL];
+      if (j + 1 < nl) prepare(j + 1);
+      __syncthreads();
+    }
   }
   cp_async_wait<0>();
 }
 
-// Forward and backward sweeps: the level loops run in the first nact threads.
-template <typename T, int RPT>
-__device__ __forceinline__ void ilu9_solve(T* w, T* ring, int W, const T* __restrict__ lu, int m,
-                                           int N, const int* lev_off_s, int nlev, int nact) {
-#if SG_TRI_NAMED_BARRIER
-  if ((int)threadIdx.x < nact) {
-    ilu9_sweep<T, RPT, false>(w, ring, W, lu, m, N, lev_off_s, nlev, nact);
-    ilu9_sweep<T, RPT, true>(w, ring, W, lu, m, N, lev_off_s, nlev, nact);
+// w <- U^{-1} L^{-1} w for one column: boundary rows by their scaling, interior rows by the two
+// sweeps.  Threads [0, wc) form the critical group, [wc, 2wc) the lookahead group.
+template <typename T>
+__device__ __forceinline__ void ilu9_solve(T* w, T* ring, int wc, const T* __restrict__ lu, int m,
+                                           int N, const int* lev_s) {
+  const int nb = 4 * (m - 1);
+  for (int k = threadIdx.x; k < nb; k += blockDim.x) {
+    const int side = k / (m - 1), s = k - side * (m - 1);
+    const int x = side == 0 ? s : side == 1 ? m - 1 : side == 2 ? m - 1 - s : 0;
+    const int y = side == 0 ? 0 : side == 1 ? s : side == 2 ? m - 1 : m - 1 - s;
+    const int l = x + 2 * y, ylo = max(0, (l - (m - 1) + 1) >> 1);
+    w[x + m * y] *= lu[(size_t)4 * N + lev_s[l] + (y - ylo)];
   }
-#else
-  ilu9_sweep<T, RPT, false>(w, ring, W, lu, m, N, lev_off_s, nlev, nact);
-  ilu9_sweep<T, RPT, true>(w, ring, W, lu, m, N, lev_off_s, nlev, nact);
-#endif
   __syncthreads();
+  const int nl = 3 * m - 8;
+  const bool crit = (int)threadIdx.x < wc;
+  const int t = crit ? (int)threadIdx.x : (int)threadIdx.x - wc;
+  ilu9_sweep<T, false>(w, ring, wc, lu, m, N, lev_s, nl, crit, t);
+  ilu9_sweep<T, true>(w, ring, wc, lu, m, N, lev_s, nl, crit, t);
 }
 
-// CTA c solves column a = a0 + c with factor set (fac_per_col ? a : 0):
-//   z = ILU^{-1}(rhs), then inner-1 times z += ILU^{-1}(rhs - K_blk z), rhs = R[:,a] - acc[:,a].
-template <typename T, bool SMEM, int RPT>
-__global__ void __launch_bounds__(kTriThreads) ilu_block_solve_kernel(
-    int m, int N, int P, int nnz, int a0, int fac_per_col, const int* __restrict__ lev_off,
-    int nlev, int W, int nact, const T* __restrict__ lu9s, const int* __restrict__ rowptr,
-    const int* __restrict__ col, const T* __restrict__ blks, const T* __restrict__ R,
-    const T* __restrict__ acc, T* __restrict__ Z, T* __restrict__ wglob, int inner,
-    const int* __restrict__ done) {
+// CTA c solves column a = a0 + c with factor set (fac_per_col ? a : 0) and right-hand side
+// rhs = Rt[a * ldN ...]:  z = ILU^{-1}(rhs), then inner-1 times z += ILU^{-1}(rhs - K_blk z).
+template <typename T, bool SMEM>
+__global__ void __launch_bounds__(kTriMaxThreads) ilu_block_solve_kernel(
+    int m, int N, int ldN, int P, int nnz, int a0, int fac_per_col, const int* __restrict__ lev_off,
+    int nlev, int wc, const T* __restrict__ lu9s, const int* __restrict__ rowptr,
+    const int* __restrict__ col, const T* __restrict__ blks, const T* __restrict__ Rt,
+    T* __restrict__ Z, T* __restrict__ wglob, int inner, const int* __restrict__ done) {
   if (done != nullptr && *done) return;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int a = a0 + blockIdx.x;
   const int fsel = fac_per_col ? a : 0;
   const T* lu = lu9s + (size_t)fsel * 9 * N;
   const T* blk = blks + (size_t)fsel * nnz;
-  T* w = SMEM ? reinterpret_cast<T*>(smem_raw) : wglob + (size_t)a * N;
-  T* ring = reinterpret_cast<T*>(smem_raw + (SMEM ? sizeof(T) * (size_t)N : 0));
-  int* lev_s = reinterpret_cast<int*>(ring + (size_t)kAhead * 5 * W);
+  const T* rhs = Rt + (size_t)a * ldN;
+  T* w = SMEM ? reinterpret_cast<T*>(smem_raw) : wglob + (size_t)a * ldN;
+  T* ring = reinterpret_cast<T*>(smem_raw + (SMEM ? sizeof(T) * (size_t)ldN : 0));
+  int* lev_s = reinterpret_cast<int*>(ring + (size_t)kAhead * 5 * wc);
   for (int l = threadIdx.x; l <= nlev; l += blockDim.x) lev_s[l] = lev_off[l];
-#pragma unroll 4
-  for (int i = threadIdx.x; i < N; i += blockDim.x) {
-    T v = R[(size_t)i * P + a];
-    if (acc != nullptr) v -= acc[(size_t)i * P + a];
-    w[i] = v;
+  if (SMEM) {  // the column (ldN * sizeof(T) bytes, 16-byte aligned) in one burst of copies
+    const int nchunk = (int)((size_t)ldN * sizeof(T) / 16);
+    for (int c = threadIdx.x; c < nchunk; c += blockDim.x)
+      cp_async_16(reinterpret_cast<unsigned char*>(w) + 16 * (size_t)c,
+                  reinterpret_cast<const unsigned char*>(rhs) + 16 * (size_t)c);
+    cp_async_commit();
+    cp_async_wait<0>();
+  } else {
+    for (int i = threadIdx.x; i < N; i += blockDim.x) w[i] = rhs[i];
   }
   __syncthreads();
-  ilu9_solve<T, RPT>(w, ring, W, lu, m, N, lev_s, nlev, nact);
+  ilu9_solve<T>(w, ring, wc, lu, m, N, lev_s);
 #pragma unroll 4
   for (int i = threadIdx.x; i < N; i += blockDim.x) Z[(size_t)i * P + a] = w[i];
   for (int it = 1; it < inner; ++it) {
     __syncthreads();
     for (int i = threadIdx.x; i < N; i += blockDim.x) {
-      T v = R[(size_t)i * P + a];
-      if (acc != nullptr) v -= acc[(size_t)i * P + a];
+      T v = rhs[i];
       for (int e = rowptr[i]; e < rowptr[i + 1]; ++e) v -= blk[e] * Z[(size_t)col[e] * P + a];
       w[i] = v;
     }
     __syncthreads();
-    ilu9_solve<T, RPT>(w, ring, W, lu, m, N, lev_s, nlev, nact);
+    ilu9_solve<T>(w, ring, wc, lu, m, N, lev_s);
     for (int i = threadIdx.x; i < N; i += blockDim.x) Z[(size_t)i * P + a] += w[i];
+  }
+}
+
+// Rt[c * ld + r] = R[r * P + c] for the N x P residual: 32 x 32 tiles through shared memory.
+template <typename T>
+__global__ void columns_kernel(const T* __restrict__ R, T* __restrict__ Rt, int N, int P, int ld,
+                               const int* __restrict__ done) {
+  if (done != nullptr && *done) return;
+  __shared__ T tile[32][33];
+  const int r0 = blockIdx.x * 32, c0 = blockIdx.y * 32;
+  for (int dy = threadIdx.y; dy < 32; dy += blockDim.y) {
+    const int r = r0 + dy, c = c0 + threadIdx.x;
+    tile[dy][threadIdx.x] = (r < N && c < P) ? R[(size_t)r * P + c] : T(0);
+  }
+  __syncthreads();
+  for (int dy = threadIdx.y; dy < 32; dy += blockDim.y) {
+    const int c = c0 + dy, r = r0 + threadIdx.x;
+    if (r < N && c < P) Rt[(size_t)c * ld + r] = tile[threadIdx.x][dy];
   }
 }
 
 constexpr int kScatterRows = 8;
 
 // After block b of the Gauss-Seidel sweep: for every row i and every a > b,
-// acc[i,a] += sum_k G_k[a,b] (A_k z_b)[i].  The stiffness values are read from the k-major copy
+// Rt[a, i] -= sum_k G_k[a,b] (A_k z_b)[i].  The stiffness values are read from the k-major copy
 // of the stack (stack_km[k*nnz + e]): the block needs only the k of its list, and consecutive
 // threads take consecutive rows of one k, so each k reads one contiguous run of entries.
 template <typename T, typename TV>
 __global__ void __launch_bounds__(128) fs_scatter_kernel(
-    int N, int P, int nnz, int b, const int* __restrict__ rowptr, const int* __restrict__ col,
-    const TV* __restrict__ stack_km, const int* __restrict__ kptr, const int* __restrict__ klist,
-    const int* __restrict__ eptr, const int* __restrict__ ek, const T* __restrict__ eg,
-    const T* __restrict__ Z, T* __restrict__ acc, const int* __restrict__ done) {
+    int N, int P, int ldN, int nnz, int b, const int* __restrict__ rowptr,
+    const int* __restrict__ col, const TV* __restrict__ stack_km, const int* __restrict__ kptr,
+    const int* __restrict__ klist, const int* __restrict__ eptr, const int* __restrict__ ek,
+    const T* __restrict__ eg, const T* __restrict__ Z, T* __restrict__ Rt,
+    const int* __restrict__ done) {
   if (done != nullptr && *done) return;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T* Ts = reinterpret_cast<T*>(smem_raw);
@@ -219,11 +288,11 @@ __global__ void __launch_bounds__(128) fs_scatter_kernel(
   __syncthreads();
   const int na = P - 1 - b;
   const int* ep = eptr + (size_t)b * (P + 1);
-  for (int t = threadIdx.x; t < nr * na; t += blockDim.x) {
-    int rr = t / na, a = b + 1 + (t - rr * na);
+  for (int t = threadIdx.x; t < nr * na; t += blockDim.x) {  // rows fastest: runs of nr entries
+    const int a = b + 1 + t / nr, rr = t - (a - b - 1) * nr;
     T s = T(0);
     for (int q = ep[a]; q < ep[a + 1]; ++q) s += eg[q] * Ts[rr * klen + ek[q]];
-    acc[(size_t)(r0 + rr) * P + a] += s;
+    Rt[(size_t)a * ldN + r0 + rr] -= s;
   }
 }
 
@@ -242,7 +311,7 @@ template <>
 struct PcBufs<double> {
   static const double* lu9(const System& s) { return s.lu9.p; }
   static const double* blk(const System& s) { return s.blk.p; }
-  static double* acc(System& s) { return s.acc.p; }
+  static double* rhs_t(System& s) { return s.rhs_t.p; }
   static double* tmp(System& s) { return s.tmp.p; }
   static double* tmp2(System& s) { return s.tmp2.p; }
   static double* triw(System& s) { return s.tri_w.p; }
@@ -253,7 +322,7 @@ template <>
 struct PcBufs<float> {
   static const float* lu9(const System& s) { return s.lu9_f32.p; }
   static const float* blk(const System& s) { return s.blk_f32.p; }
-  static float* acc(System& s) { return s.acc32.p; }
+  static float* rhs_t(System& s) { return s.rhs_t32.p; }
   static float* tmp(System& s) { return s.tmp32.p; }
   static float* tmp2(System& s) { return s.tmp232.p; }
   static float* triw(System& s) { return s.tri_w32.p; }
@@ -261,54 +330,58 @@ struct PcBufs<float> {
   static bool smem(const System& s) { return s.tri_smem32; }
 };
 
-template <typename T, bool SMEM, int RPT>
-int launch_block_solve_t(System& s, int a0, int ncols, int fac_per_col, const T* R, const T* acc,
-                         T* Z, cudaStream_t st, const int* done) {
+template <typename T>
+int launch_columns(System& s, const T* R, T* Rt, cudaStream_t st, const int* done) {
+  dim3 block(32, 8), grid((unsigned)((s.N + 31) / 32), (unsigned)((s.P + 31) / 32));
+  TimeScope ts(s.timer, K_OTHER, st);
+  columns_kernel<T><<<grid, block, 0, st>>>(R, Rt, s.N, s.P, s.ldN, done);
+  return check_launch("columns");
+}
+
+template <typename T, bool SMEM>
+int launch_block_solve_t(System& s, int a0, int ncols, int fac_per_col, const T* Rt, T* Z,
+                         cudaStream_t st, const int* done) {
   using B = PcBufs<T>;
-  const int W = s.pat.max_width;
-  const int nact = std::min(kTriThreads, (W + 31) / 32 * 32);
-  size_t smem = (SMEM ? sizeof(T) * (size_t)s.N : 0) + sizeof(T) * (size_t)kAhead * 5 * W +
+  const int wc = s.tri_wc;
+  size_t smem = (SMEM ? sizeof(T) * (size_t)s.ldN : 0) + sizeof(T) * tri_ring_entries(wc) +
                 sizeof(int) * (size_t)(s.nlev9 + 1);
-  auto kern = ilu_block_solve_kernel<T, SMEM, RPT>;
+  auto kern = ilu_block_solve_kernel<T, SMEM>;
   SG_TRY(ensure_smem((const void*)kern, smem));
   TimeScope ts(s.timer, K_ILU_SOLVE, st);
-  kern<<<ncols, kTriThreads, smem, st>>>(s.pat.m, s.N, s.P, s.pat.nnz, a0, fac_per_col, s.lev9_off.p,
-                                 s.nlev9, W, nact, B::lu9(s), s.rowptr.p, s.col.p, B::blk(s), R, acc, Z,
-                                 SMEM ? nullptr : B::triw(s), std::max(1, s.prm.inner_iters), done);
+  kern<<<ncols, 2 * wc, smem, st>>>(s.pat.m, s.N, s.ldN, s.P, s.pat.nnz, a0, fac_per_col,
+                                    s.lev9_off.p, s.nlev9, wc, B::lu9(s), s.rowptr.p, s.col.p,
+                                    B::blk(s), Rt, Z, SMEM ? nullptr : B::triw(s),
+                                    std::max(1, s.prm.inner_iters), done);
   return check_launch("ilu_block_solve");
 }
 
 template <typename T>
-int launch_block_solve(System& s, int a0, int ncols, int fac_per_col, const T* R, const T* acc,
-                       T* Z, cudaStream_t st, const int* done) {
+int launch_block_solve(System& s, int a0, int ncols, int fac_per_col, const T* Rt, T* Z,
+                       cudaStream_t st, const int* done) {
   using B = PcBufs<T>;
-  int rpt = (s.pat.max_width + kTriThreads - 1) / kTriThreads;
-  if (B::smem(s)) {
-    if (rpt <= 1) return launch_block_solve_t<T, true, 1>(s, a0, ncols, fac_per_col, R, acc, Z, st, done);
-    return launch_block_solve_t<T, true, 4>(s, a0, ncols, fac_per_col, R, acc, Z, st, done);
-  }
-  if (rpt <= 1) return launch_block_solve_t<T, false, 1>(s, a0, ncols, fac_per_col, R, acc, Z, st, done);
-  if (rpt <= 2) return launch_block_solve_t<T, false, 2>(s, a0, ncols, fac_per_col, R, acc, Z, st, done);
-  return launch_block_solve_t<T, false, 4>(s, a0, ncols, fac_per_col, R, acc, Z, st, done);
+  if (s.tri_wc < 32 || 2 * s.tri_wc > kTriMaxThreads || s.ldN % 4 != 0)
+    return fail(SG_ERR_ARG, "wavefront solve: unsupported mesh width");
+  if (B::smem(s)) return launch_block_solve_t<T, true>(s, a0, ncols, fac_per_col, Rt, Z, st, done);
+  return launch_block_solve_t<T, false>(s, a0, ncols, fac_per_col, Rt, Z, st, done);
 }
 
 template <typename T>
-int launch_scatter(System& s, int b, const T* Z, T* acc, cudaStream_t st, const int* done);
+int launch_scatter(System& s, int b, const T* Z, T* Rt, cudaStream_t st, const int* done);
 template <>
-int launch_scatter<double>(System& s, int b, const double* Z, double* acc, cudaStream_t st,
+int launch_scatter<double>(System& s, int b, const double* Z, double* Rt, cudaStream_t st,
                            const int* done) {
   size_t smem = sizeof(double) * kScatterRows * std::max(1, s.gs_max_klen);
   auto kern = fs_scatter_kernel<double, double>;
   SG_TRY(ensure_smem((const void*)kern, smem));
   int grid = (s.N + kScatterRows - 1) / kScatterRows;
   TimeScope ts(s.timer, K_GS_SCATTER, st);
-  kern<<<grid, 128, smem, st>>>(s.N, s.P, s.pat.nnz, b, s.rowptr.p, s.col.p, s.stack_km.p,
-                                s.gs_kptr.p, s.gs_k.p, s.gs_eptr.p, s.gs_ea.p, s.gs_eg.p, Z, acc,
+  kern<<<grid, 128, smem, st>>>(s.N, s.P, s.ldN, s.pat.nnz, b, s.rowptr.p, s.col.p, s.stack_km.p,
+                                s.gs_kptr.p, s.gs_k.p, s.gs_eptr.p, s.gs_ea.p, s.gs_eg.p, Z, Rt,
                                 done);
   return check_launch("fs_scatter");
 }
 template <>
-int launch_scatter<float>(System& s, int b, const float* Z, float* acc, cudaStream_t st,
+int launch_scatter<float>(System& s, int b, const float* Z, float* Rt, cudaStream_t st,
                           const int* done) {
   size_t smem = sizeof(float) * kScatterRows * std::max(1, s.gs_max_klen);
   int grid = (s.N + kScatterRows - 1) / kScatterRows;
@@ -316,17 +389,29 @@ int launch_scatter<float>(System& s, int b, const float* Z, float* acc, cudaStre
   if (s.prm.precision == SG_MIXED_BF16) {
     auto kern = fs_scatter_kernel<float, __nv_bfloat16>;
     SG_TRY(ensure_smem((const void*)kern, smem));
-    kern<<<grid, 128, smem, st>>>(s.N, s.P, s.pat.nnz, b, s.rowptr.p, s.col.p, s.stack_km16.p,
-                                  s.gs_kptr.p, s.gs_k.p, s.gs_eptr.p, s.gs_ea.p, s.gs_eg_f32.p, Z,
-                                  acc, done);
+    kern<<<grid, 128, smem, st>>>(s.N, s.P, s.ldN, s.pat.nnz, b, s.rowptr.p, s.col.p,
+                                  s.stack_km16.p, s.gs_kptr.p, s.gs_k.p, s.gs_eptr.p, s.gs_ea.p,
+                                  s.gs_eg_f32.p, Z, Rt, done);
   } else {
     auto kern = fs_scatter_kernel<float, float>;
     SG_TRY(ensure_smem((const void*)kern, smem));
-    kern<<<grid, 128, smem, st>>>(s.N, s.P, s.pat.nnz, b, s.rowptr.p, s.col.p, s.stack_km32.p,
-                                  s.gs_kptr.p, s.gs_k.p, s.gs_eptr.p, s.gs_ea.p, s.gs_eg_f32.p, Z,
-                                  acc, done);
+    kern<<<grid, 128, smem, st>>>(s.N, s.P, s.ldN, s.pat.nnz, b, s.rowptr.p, s.col.p,
+                                  s.stack_km32.p, s.gs_kptr.p, s.gs_k.p, s.gs_eptr.p, s.gs_ea.p,
+                                  s.gs_eg_f32.p, Z, Rt, done);
   }
   return check_launch("fs_scatter");
+}
+
+// Field-split Gauss-Seidel: block a solved from column a of Rt, then its coupling subtracted from
+// the later columns.
+template <typename T>
+int fs_gs_sweep(System& s, const T* R, T* D, T* Rt, cudaStream_t st, const int* done) {
+  SG_TRY(launch_columns<T>(s, R, Rt, st, done));
+  for (int a = 0; a < s.P; ++a) {
+    SG_TRY(launch_block_solve<T>(s, a, 1, 1, Rt, D, st, done));
+    if (a + 1 < s.P) SG_TRY(launch_scatter<T>(s, a, D, Rt, st, done));
+  }
+  return SG_OK;
 }
 
 // One application of P^{-1} (no outer sweeps): D = P^{-1} R.
@@ -335,18 +420,12 @@ int apply_once(System& s, const T* R, T* D, cudaStream_t st, const int* done) {
   using B = PcBufs<T>;
   switch (s.prm.precond) {
     case SG_PC_MEAN:
-      return launch_block_solve<T>(s, 0, s.P, 0, R, nullptr, D, st, done);
     case SG_PC_FS_JACOBI:
-      return launch_block_solve<T>(s, 0, s.P, 1, R, nullptr, D, st, done);
-    case SG_PC_FS_GS: {
-      T* acc = B::acc(s);
-      SG_CUDA(cudaMemsetAsync(acc, 0, sizeof(T) * (size_t)s.N * s.P, st));
-      for (int a = 0; a < s.P; ++a) {
-        SG_TRY(launch_block_solve<T>(s, a, 1, 1, R, a > 0 ? acc : nullptr, D, st, done));
-        if (a + 1 < s.P) SG_TRY(launch_scatter<T>(s, a, D, acc, st, done));
-      }
-      return SG_OK;
-    }
+      SG_TRY(launch_columns<T>(s, R, B::rhs_t(s), st, done));
+      return launch_block_solve<T>(s, 0, s.P, s.prm.precond == SG_PC_FS_JACOBI ? 1 : 0,
+                                   B::rhs_t(s), D, st, done);
+    case SG_PC_FS_GS:
+      return fs_gs_sweep<T>(s, R, D, B::rhs_t(s), st, done);
     default: {
       SG_CUDA(cudaMemcpyAsync(D, R, sizeof(T) * (size_t)s.N * s.P, cudaMemcpyDeviceToDevice, st));
       return SG_OK;
@@ -386,13 +465,8 @@ int precond_apply_t(System& s, const T* R, T* Z, cudaStream_t st, const int* don
 
 }  // namespace
 
-int fs_gs_apply_f64_with(System& s, const double* R, double* Z, double* acc, cudaStream_t st) {
-  SG_CUDA(cudaMemsetAsync(acc, 0, sizeof(double) * (size_t)s.N * s.P, st));
-  for (int a = 0; a < s.P; ++a) {
-    SG_TRY(launch_block_solve<double>(s, a, 1, 1, R, a > 0 ? acc : nullptr, Z, st, nullptr));
-    if (a + 1 < s.P) SG_TRY(launch_scatter<double>(s, a, Z, acc, st, nullptr));
-  }
-  return SG_OK;
+int fs_gs_apply_f64_with(System& s, const double* R, double* Z, double* rhs_t, cudaStream_t st) {
+  return fs_gs_sweep<double>(s, R, Z, rhs_t, st, nullptr);
 }
 
 int precond_apply_f64(System& s, const double* R, double* Z, cudaStream_t st, const int* done) {

@@ -183,7 +183,9 @@ __global__ void ilu0_kernel(int nnz, const int* __restrict__ rowptr, const int* 
   }
 }
 
-// CSR ILU(0) factors -> 9-slot level-major layout used by the wavefront solves (slot 4: 1/u_ii).
+// CSR ILU(0) factors -> 9-slot level-major layout used by the wavefront solves: the unit lower
+// factor in slots 0-3 and the upper factor as D^{-1} U (slot 4 holds 1 / u_ii, slots 5-8 hold
+// u_ij / u_ii), so that U z = w reads z = D^{-1} w - (D^{-1} U - I) z.
 __global__ void lu9_kernel(int m, int N, int nnz, int nfac, const int* __restrict__ rowptr,
                            const int* __restrict__ col, const int* __restrict__ lev_off,
                            const double* __restrict__ fac, double* __restrict__ lu9) {
@@ -202,7 +204,7 @@ __global__ void lu9_kernel(int m, int N, int nnz, int nfac, const int* __restric
     int dx = c % m - x, dy = c / m - y;
     int slot = (dy + 1) * 3 + (dx + 1);
     double v = fac[(size_t)f * nnz + e];
-    lu9[((size_t)f * 9 + slot) * N + pos] = slot == 4 ? dinv : v;
+    lu9[((size_t)f * 9 + slot) * N + pos] = slot == 4 ? dinv : slot > 4 ? v * dinv : v;
   }
 }
 

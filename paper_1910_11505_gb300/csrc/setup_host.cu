@@ -170,4 +170,13 @@ Pattern make_pattern(int n) {
   return pt;
 }
 
+int interior_level_width(int m) {
+  int w = 0;
+  for (int l = 3; l <= 3 * m - 6; ++l) {
+    int y0 = std::max(1, (l - (m - 2) + 1) >> 1), y1 = std::min(m - 2, (l - 1) >> 1);
+    w = std::max(w, y1 - y0 + 1);
+  }
+  return w;
+}
+
 }  // namespace sg

@@ -251,12 +251,12 @@ static void free_system(System* s) {
   for (auto* b : ib) b->release();
   s->lev9_off.release();
   s->stack_km16.release();
-  DBuf<double>* db[] = {&s->stack, &s->stack_km, &s->ent_g, &s->blk, &s->fac, &s->lu9, &s->gs_eg, &s->acc, &s->tmp,
+  DBuf<double>* db[] = {&s->stack, &s->stack_km, &s->ent_g, &s->blk, &s->fac, &s->lu9, &s->gs_eg, &s->rhs_t, &s->tmp,
                         &s->tmp2, &s->tri_w, &s->V, &s->Z, &s->Hs, &s->cs, &s->sn, &s->g, &s->y,
                         &s->scal, &s->red, &s->rvec};
   for (auto* b : db) b->release();
   DBuf<float>* fb[] = {&s->stack_f32, &s->stack_km32, &s->ent_g_f32, &s->lu9_f32, &s->blk_f32, &s->gs_eg_f32,
-                       &s->acc32, &s->tmp32, &s->tmp232, &s->tri_w32, &s->V32, &s->Z32,
+                       &s->rhs_t32, &s->tmp32, &s->tmp232, &s->tri_w32, &s->V32, &s->Z32,
                        &s->mv32a, &s->mv32b};
   for (auto* b : fb) b->release();
   s->stack_bf16.release();
@@ -284,10 +284,14 @@ static int setup_system(System& s, cudaStream_t st) {
   // smem budgets of the kernels
   size_t apply_smem = sizeof(double) * 4 * (9 * kChunkK + 9 * (size_t)s.P + kChunkPairs + s.P);
   if (apply_smem > 220 * 1024) return fail(SG_ERR_ARG, "P too large for the operator kernel");
-  {  // shared memory of the wavefront solve: column + factor ring (8 levels x 5 slots) + levels
-    size_t width = (size_t)(p.n + 2) / 2 + 1, lev = sizeof(int) * 3 * (size_t)(p.n + 1);
-    s.tri_smem = (size_t)s.N * 8 + 40 * 8 * width + lev <= 220 * 1024;
-    s.tri_smem32 = (size_t)s.N * 4 + 40 * 4 * width + lev <= 220 * 1024;
+  {  // shared memory of the wavefront solve: column + factor rings + level offsets
+    s.ldN = (s.N + 3) / 4 * 4;
+    s.tri_wc = (interior_level_width(p.n + 1) + 31) / 32 * 32;
+    size_t ring = tri_ring_entries(s.tri_wc), lev = sizeof(int) * 3 * (size_t)(p.n + 1);
+    if (8 * ring + lev > 220 * 1024 || 2 * s.tri_wc > 1024)
+      return fail(SG_ERR_ARG, "mesh too large for the wavefront solve");
+    s.tri_smem = (size_t)s.ldN * 8 + 8 * ring + lev <= 220 * 1024;
+    s.tri_smem32 = (size_t)s.ldN * 4 + 4 * ring + lev <= 220 * 1024;
   }
 
   SG_CUDA(cudaStreamCreateWithFlags(&s.stream, cudaStreamNonBlocking));
@@ -365,11 +369,12 @@ static int setup_system(System& s, cudaStream_t st) {
         SG_TRY(s.stack_km16.alloc(nnzL));
         SG_TRY(launch_cast_bf16(s.stack_km.p, s.stack_km16.p, nnzL, st));
       }
-      SG_TRY(s.acc.alloc(NP));
-      if (lowp) SG_TRY(s.acc32.alloc(NP));
     }
-    if (!s.tri_smem) SG_TRY(s.tri_w.alloc(NP));
-    if (lowp && !s.tri_smem32) SG_TRY(s.tri_w32.alloc(NP));
+    const size_t PL = (size_t)s.P * s.ldN;
+    SG_TRY(s.rhs_t.alloc(PL));
+    if (lowp) SG_TRY(s.rhs_t32.alloc(PL));
+    if (!s.tri_smem) SG_TRY(s.tri_w.alloc(PL));
+    if (lowp && !s.tri_smem32) SG_TRY(s.tri_w32.alloc(PL));
   }
   if (p.outer_sweeps > 1) {
     SG_TRY(s.tmp.alloc(NP));

@@ -107,6 +107,12 @@ struct Pattern {  // 9-point Q1 pattern, CSR with sorted columns
   int max_width = 0;
 };
 Pattern make_pattern(int n);
+// Largest number of interior nodes (1 <= x, y <= m - 2) on one wavefront level x + 2y = l.
+int interior_level_width(int m);
+// Factor-ring depth (levels fetched ahead) of the wavefront solve and its ring size in elements
+// for wc threads per thread group (2 slots per level for one group, 3 for the other).
+constexpr int kTriAhead = 8;
+inline size_t tri_ring_entries(int wc) { return (size_t)kTriAhead * 5 * wc; }
 
 // ------------------------------------------------------------------ matvec work tables
 
@@ -169,16 +175,19 @@ struct System {
   DBuf<float> lu9_f32;
   DBuf<int> lev9_off;          // start of each wavefront level in level-major order
   int nlev9 = 0;
+  int tri_wc = 0;              // threads per group of the wavefront solve (multiple of 32)
+  int ldN = 0;                 // column stride of rhs_t / tri_w: N rounded up to a multiple of 4
   // field-split Gauss-Seidel scatter tables, per source block b: k list and (a, g) entries
   DBuf<int> gs_kptr, gs_k, gs_eptr, gs_ea;
   DBuf<double> gs_eg;
   DBuf<float> gs_eg_f32;
   int gs_max_klen = 0;
   // device scratch
-  DBuf<double> acc;            // N x P  field-split off-diagonal accumulator
+  DBuf<double> rhs_t;          // P columns of stride ldN: right-hand sides of the block solves
+                               // (the Gauss-Seidel sweep subtracts sum_{b<a} K_ab z_b in place)
   DBuf<double> tmp, tmp2;      // N x P
-  DBuf<double> tri_w;          // N x P  triangular-solve work (global variant)
-  DBuf<float> acc32, tmp32, tmp232, tri_w32;
+  DBuf<double> tri_w;          // P x ldN triangular-solve work (global variant)
+  DBuf<float> rhs_t32, tmp32, tmp232, tri_w32;
   bool tri_smem = true;        // whether one column fits in shared memory
   bool tri_smem32 = true;
   // GMRES workspace
@@ -236,9 +245,9 @@ int precond_apply_f64(System& s, const double* R, double* Z, cudaStream_t st,
                       const int* done = nullptr);
 int precond_apply_f32(System& s, const float* R, float* Z, cudaStream_t st,
                       const int* done = nullptr);
-// One field-split Gauss-Seidel application (outer_sweeps = 1) whose off-diagonal accumulator is
-// the caller's N x P array ``acc`` (cleared here).
-int fs_gs_apply_f64_with(System& s, const double* R, double* Z, double* acc, cudaStream_t st);
+// One field-split Gauss-Seidel application (outer_sweeps = 1) whose right-hand-side columns live
+// in the caller's array ``rhs_t`` of P x ldN doubles (filled here from R).
+int fs_gs_apply_f64_with(System& s, const double* R, double* Z, double* rhs_t, cudaStream_t st);
 
 // Krylov launchers (k_krylov.cu)
 int k_norm(System& s, size_t n, const double* r, double* out, cudaStream_t st);

@@ -1,9 +1,10 @@
 // sg_precond_apply_noalloc: the field-split Gauss-Seidel preconditioner with its scratch in a
 // fixed device array of this library instead of memory allocated for the handle.
 //
-// The Gauss-Seidel sweep needs an N x P accumulator for the coupling sum_{b<a} K_ab z_b.  Here it
-// is the file-scope array below, which every GPU that loads the library holds until the process
-// exits.  Host code cannot use the array's name as a device address (it names a host-side
+// The Gauss-Seidel sweep keeps the right-hand sides of its P block solves as contiguous columns
+// (stride ldN = N rounded up to a multiple of 4), from which it subtracts the coupling
+// sum_{b<a} K_ab z_b.  Here they live in the file-scope array below, which every GPU that loads
+// the library holds until the process exits.  Host code cannot use the array's name as a device address (it names a host-side
 // stand-in), so the address is looked up once per device with cudaGetSymbolAddress, with that
 // device current, on the first call made on it.
 #include <mutex>
@@ -46,16 +47,16 @@ extern "C" int sg_precond_apply_noalloc(sg_handle* h, int sys, const double* R, 
   if (!s.tri_smem)
     return sg::fail(SG_ERR_ARG, "sg_precond_apply_noalloc: the mesh is too large for the "
                                 "shared-memory block solve (it would need device scratch)");
-  const long long need = (long long)s.N * s.P;
+  const long long need = (long long)s.P * s.ldN;
   if (need > SG_NOALLOC_MAX_ENTRIES)
-    return sg::fail(SG_ERR_ARG, "sg_precond_apply_noalloc: N x P = " + std::to_string(need) +
+    return sg::fail(SG_ERR_ARG, "sg_precond_apply_noalloc: P x ldN = " + std::to_string(need) +
                                     " exceeds the fixed scratch of " +
                                     std::to_string(SG_NOALLOC_MAX_ENTRIES) + " doubles");
   int dev = -1;
   SG_CUDA(cudaGetDevice(&dev));
   if (dev != h->device)
     return sg::fail(SG_ERR_ARG, "the handle's device must be current");
-  double* acc = nullptr;
-  SG_TRY(scratch_for_current_device(dev, &acc));
-  return sg::fs_gs_apply_f64_with(s, R, Z, acc, (cudaStream_t)stream);
+  double* rhs_t = nullptr;
+  SG_TRY(scratch_for_current_device(dev, &rhs_t));
+  return sg::fs_gs_apply_f64_with(s, R, Z, rhs_t, (cudaStream_t)stream);
 }
