@@ -50,7 +50,7 @@ typedef struct sg_handle sg_handle;
 
 /* Parameters of one SG system.  a = a_min + exp(mu + sum_n sqrt(lambda_n) b_n(x) y_n). */
 typedef struct {
-  int n;             /* cells per side of the uniform Q1 mesh of [0,1]^2, 2 <= n <= 1024      */
+  int n;             /* cells per side of the Q1 mesh of [0,1]^2: 2..1024, with ILU(0) 2..992  */
   int M;             /* KL terms kept, 1 <= M <= 8                                             */
   int p;             /* total degree of the solution chaos, 0 <= p <= 6                        */
   int q;             /* total degree of the coefficient chaos; <= 0 selects 2p                 */

@@ -52,11 +52,11 @@ __device__ __forceinline__ void interior_level(int l, int m, const int* lev_off,
   pos0 = lev_off[l] + (y0 - ylo);
 }
 
-// Factors of the next kAhead levels are copied into a shared-memory ring with cp.async while the
+// Factors of the next kAhead levels are copied into shared-memory rings with cp.async while the
 // current level is computed.  Ordinary loads cannot run ahead like this: the level barrier waits
-// for every load the thread has in flight, so each level would pay a full L2 round trip.  Each
-// thread copies and later reads only its own rows' factors, so the ring needs no barrier of its
-// own; cp.async.wait_group orders the copy before the read.
+// for every load the thread has in flight, so each level would pay a full L2 round trip.  One
+// warp issues all copies and waits for them (cp.async.wait_group) before a level barrier, which
+// then publishes them to the compute threads.
 constexpr int kAhead = kTriAhead;
 constexpr int kTriMaxThreads = 1024;
 
@@ -69,109 +69,139 @@ __device__ __forceinline__ void cp_async_16(void* dst, const void* src) {
   unsigned sa = (unsigned)__cvta_generic_to_shared(dst);
   asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(src));
 }
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::); }
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
 template <int N>
-__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N)); }
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+}
+
+// Interior rows of level l for the compute threads, from l alone: row of thread t, or -1.
+__device__ __forceinline__ int interior_row(int l, int m, int t) {
+  const int y0 = max(1, (l - (m - 2) + 1) >> 1), y1 = min(m - 2, (l - 1) >> 1);
+  return t <= y1 - y0 ? l + (m - 2) * (y0 + t) : -1;  // x + m y with x = l - 2y
+}
 
 // One sweep (lower or upper) over the nl interior levels; every thread of the CTA calls it and
-// passes nl + 1 barriers.  List position j is level 3 + j (lower) or 3m - 6 - j (upper).  The
-// critical group takes position j at step j; the lookahead group prepares position j at step
-// j - 2 and finishes it at step j - 1.  Ring: kAhead x 2 x wc critical, kAhead x 3 x wc lookahead.
+// passes nl + 2 barriers.  List position j is level 3 + j (lower) or 3m - 6 - j (upper).  The
+// critical group (role 0) takes position j at step j; the lookahead group (role 1) works on
+// position j during steps j - 3 .. j - 1.  The staging warp (role 2) copies the factors of both
+// groups into the rings (kAhead x 2 x wc critical, kAhead x 3 x wc lookahead), position
+// s + kAhead - 1 at step s, and before the barrier that ends step s waits until position s + 4
+// has landed; the barrier then makes it visible to the compute threads, which therefore neither
+// issue copies nor wait for them.
 template <typename T, bool UPPER>
 __device__ __forceinline__ void ilu9_sweep(T* w, T* ring, int wc, const T* __restrict__ lu, int m,
-                                           int N, const int* lev_s, int nl, bool crit, int t) {
+                                           int N, const int* lev_s, int nl, int role, int t) {
   auto level = [&](int j) { return UPPER ? 3 * m - 6 - j : 3 + j; };
-  if (crit) {
-    // lower: slots 2, 3 at i - m + 1, i - 1; upper: slots 5, 6 at i + 1, i + m - 1
-    const int oA = UPPER ? 1 : -m + 1, oB = UPPER ? m - 1 : -1;
+  auto row = [&](int j) { return j < nl ? interior_row(level(j), m, t) : -1; };
+  T* cring = ring;
+  T* lring = ring + (size_t)kAhead * 2 * wc;
+  if (role == 2) {
+    // critical: lower slots 2, 3 / upper 5, 6; lookahead: early lower 0 / upper 8, late lower 1 /
+    // upper 7, and upper 1/u_ii (slot 4)
     const T* fA = lu + (size_t)(UPPER ? 5 : 2) * N;
-    const T* fB = fA + N;
+    const T* fE = lu + (size_t)(UPPER ? 8 : 0) * N;
+    const T* fL = lu + (size_t)(UPPER ? 7 : 1) * N;
+    const T* fD = lu + (size_t)4 * N;
     auto stage = [&](int j) {
       if (j < nl) {
         int y0, cnt, pos0;
         interior_level(level(j), m, lev_s, y0, cnt, pos0);
-        if (t < cnt) {
-          T* d = ring + (size_t)(j % kAhead) * 2 * wc + t;
-          cp_async_elem(d, fA + pos0 + t);
-          cp_async_elem(d + wc, fB + pos0 + t);
+        T* c = cring + (size_t)(j % kAhead) * 2 * wc;
+        T* d = lring + (size_t)(j % kAhead) * 3 * wc;
+        for (int r = t; r < cnt; r += 32) {
+          cp_async_elem(c + r, fA + pos0 + r);
+          cp_async_elem(c + wc + r, fA + N + pos0 + r);
+          cp_async_elem(d + r, fE + pos0 + r);
+          cp_async_elem(d + wc + r, fL + pos0 + r);
+          if (UPPER) cp_async_elem(d + 2 * wc + r, fD + pos0 + r);
         }
       }
       cp_async_commit();
     };
 #pragma unroll
-    for (int d = 0; d < kAhead - 1; ++d) stage(d);
+    for (int d = 0; d < kAhead - 2; ++d) stage(d);
+    cp_async_wait<kAhead - 5>();  // positions 0 .. 2 landed
+    __syncthreads();
+    for (int step = -1; step < nl; ++step) {
+      stage(step + kAhead - 1);
+      cp_async_wait<kAhead - 5>();  // positions up to step + 4 landed
+      __syncthreads();
+    }
+    cp_async_wait<0>();
+  } else if (role == 0) {
+    // lower: slots 2, 3 at i - m + 1, i - 1; upper: slots 5, 6 at i + 1, i + m - 1
+    const int oA = UPPER ? 1 : -m + 1, oB = UPPER ? m - 1 : -1;
+    __syncthreads();
+    int ci = row(0);
     for (int step = -1; step < nl; ++step) {
       if (step >= 0) {
-        stage(step + kAhead - 1);
-        cp_async_wait<kAhead - 1>();
-        const int l = level(step);
-        int y0, cnt, pos0;
-        interior_level(l, m, lev_s, y0, cnt, pos0);
-        if (t < cnt) {
-          const int y = y0 + t, i = (l - 2 * y) + m * y;
-          const T* f = ring + (size_t)(step % kAhead) * 2 * wc + t;
-          T v = w[i];
-          v -= f[0] * w[i + oA];
-          v -= f[wc] * w[i + oB];
-          w[i] = v;
+        const int cur = ci;
+        if (cur >= 0) {
+          const T* f = cring + (size_t)(step % kAhead) * 2 * wc + t;
+          const T fa = f[0], fb = f[wc];
+          T v = w[cur];
+          const T zA = w[cur + oA], zB = w[cur + oB];
+          ci = row(step + 1);
+          v -= fa * zA;
+          v -= fb * zB;
+          w[cur] = v;
+        } else {
+          ci = row(step + 1);
         }
       }
       __syncthreads();
     }
   } else {
-    // early coupling (level l-3 / l+3 of the row's own level) and, upper, 1/u_ii: slot 0 at
-    // i - m - 1 or slot 8 at i + m + 1 with slot 4; late coupling: slot 1 at i - m or slot 7 at i + m
+    // position j in three steps, so that no step holds a dependent FP64 pair:
+    //   A (step j - 3): w_i, times 1/u_ii (slot 4) in the upper sweep;
+    //   B (step j - 2): minus the early coupling, slot 0 at i - m - 1 / slot 8 at i + m + 1;
+    //   C (step j - 1): minus the late coupling, slot 1 at i - m / slot 7 at i + m, stored.
     const int oE = UPPER ? m + 1 : -m - 1, oL = UPPER ? m : -m;
-    const T* fE = lu + (size_t)(UPPER ? 8 : 0) * N;
-    const T* fL = lu + (size_t)(UPPER ? 7 : 1) * N;
-    const T* fD = lu + (size_t)4 * N;
-    T* lring = ring + (size_t)kAhead * 2 * wc;
-    auto stage = [&](int j) {
-      if (j < nl) {
-        int y0, cnt, pos0;
-        interior_level(level(j), m, lev_s, y0, cnt, pos0);
-        if (t < cnt) {
-          T* d = lring + (size_t)(j % kAhead) * 3 * wc + t;
-          cp_async_elem(d, fE + pos0 + t);
-          cp_async_elem(d + wc, fL + pos0 + t);
-          if (UPPER) cp_async_elem(d + 2 * wc, fD + pos0 + t);
-        }
+    auto stage_a = [&](int j, int& r, T& v) {
+      r = row(j);
+      if (r >= 0) {
+        v = w[r];
+        if (UPPER) v *= lring[(size_t)(j % kAhead) * 3 * wc + 2 * wc + t];
       }
-      cp_async_commit();
     };
-    int pi = -1;
-    T pp = T(0), pf = T(0);
-    auto prepare = [&](int j) {  // partial result and late factor of position j, in registers
-      stage(j + kAhead - 1);
-      cp_async_wait<kAhead - 1>();
-      const int l = level(j);
-      int y0, cnt, pos0;
-      interior_level(l, m, lev_s, y0, cnt, pos0);
-      pi = -1;
-      if (t < cnt) {
-        const int y = y0 + t;
-        pi = (l - 2 * y) + m * y;
+    auto stage_b = [&](int j, int r, T v, int& ro, T& po, T& fo) {
+      ro = r;
+      if (r >= 0) {
         const T* f = lring + (size_t)(j % kAhead) * 3 * wc + t;
-        const T base = UPPER ? w[pi] * f[2 * wc] : w[pi];
-        pp = base - f[0] * w[pi + oE];
-        pf = f[wc];
+        po = v - f[0] * w[r + oE];
+        fo = f[wc];
       }
     };
-#pragma unroll
-    for (int d = 0; d < kAhead - 1; ++d) stage(d);
-    prepare(0);
+    int rb = -1, rc = -1;
+    T vb = T(0), pc = T(0), fc = T(0);
+    __syncthreads();
+    {
+      int r0;
+      T v0 = T(0);
+      stage_a(0, r0, v0);
+      stage_b(0, r0, v0, rc, pc, fc);
+      if (1 < nl) stage_a(1, rb, vb);
+    }
     for (int step = -1; step < nl; ++step) {
       const int j = step + 1;
-      if (j < nl && pi >= 0) w[pi] = pp - pf * w[pi + oL];
-      if (j + 1 < nl) prepare(j + 1);
+      const int cur = j < nl ? rc : -1;
+      const T cpc = pc, cfc = fc;
+      T zl = T(0);
+      if (cur >= 0) zl = w[cur + oL];
+      rc = -1;
+      if (j + 1 < nl) stage_b(j + 1, rb, vb, rc, pc, fc);
+      rb = -1;
+      if (j + 2 < nl) stage_a(j + 2, rb, vb);
+      if (cur >= 0) w[cur] = cpc - cfc * zl;
       __syncthreads();
     }
   }
-  cp_async_wait<0>();
 }
 
 // w <- U^{-1} L^{-1} w for one column: boundary rows by their scaling, interior rows by the two
-// sweeps.  Threads [0, wc) form the critical group, [wc, 2wc) the lookahead group.
+// sweeps.  Threads [0, wc) form the critical group, [wc, 2wc) the lookahead group, the last warp
+// stages the factors.
 template <typename T>
 __device__ __forceinline__ void ilu9_solve(T* w, T* ring, int wc, const T* __restrict__ lu, int m,
                                            int N, const int* lev_s) {
@@ -185,10 +215,11 @@ __device__ __forceinline__ void ilu9_solve(T* w, T* ring, int wc, const T* __res
   }
   __syncthreads();
   const int nl = 3 * m - 8;
-  const bool crit = (int)threadIdx.x < wc;
-  const int t = crit ? (int)threadIdx.x : (int)threadIdx.x - wc;
-  ilu9_sweep<T, false>(w, ring, wc, lu, m, N, lev_s, nl, crit, t);
-  ilu9_sweep<T, true>(w, ring, wc, lu, m, N, lev_s, nl, crit, t);
+  const int tid = threadIdx.x;
+  const int role = tid < wc ? 0 : tid < 2 * wc ? 1 : 2;
+  const int t = tid - role * wc;
+  ilu9_sweep<T, false>(w, ring, wc, lu, m, N, lev_s, nl, role, t);
+  ilu9_sweep<T, true>(w, ring, wc, lu, m, N, lev_s, nl, role, t);
 }
 
 // CTA c solves column a = a0 + c with factor set (fac_per_col ? a : 0) and right-hand side
@@ -257,13 +288,14 @@ __global__ void columns_kernel(const T* __restrict__ R, T* __restrict__ Rt, int 
 
 constexpr int kScatterRows = 8;
 
-// After block b of the Gauss-Seidel sweep: for every row i and every a > b,
-// Rt[a, i] -= sum_k G_k[a,b] (A_k z_b)[i].  The stiffness values are read from the k-major copy
-// of the stack (stack_km[k*nnz + e]): the block needs only the k of its list, and consecutive
-// threads take consecutive rows of one k, so each k reads one contiguous run of entries.
+// After block b of the Gauss-Seidel sweep, for the target columns a_lo <= a <= a_hi (all > b):
+// Rt[a, i] -= sum_k G_k[a,b] (A_k z_b)[i] for every row i.  kptr / klist / eptr / ek / eg are the
+// tables of those targets.  The stiffness values are read from the k-major copy of the stack
+// (stack_km[k*nnz + e]): the block needs only the k of its list, and consecutive threads take
+// consecutive rows of one k, so each k reads one contiguous run of entries.
 template <typename T, typename TV>
 __global__ void __launch_bounds__(128) fs_scatter_kernel(
-    int N, int P, int ldN, int nnz, int b, const int* __restrict__ rowptr,
+    int N, int P, int ldN, int nnz, int b, int a_lo, int a_hi, const int* __restrict__ rowptr,
     const int* __restrict__ col, const TV* __restrict__ stack_km, const int* __restrict__ kptr,
     const int* __restrict__ klist, const int* __restrict__ eptr, const int* __restrict__ ek,
     const T* __restrict__ eg, const T* __restrict__ Z, T* __restrict__ Rt,
@@ -286,10 +318,10 @@ __global__ void __launch_bounds__(128) fs_scatter_kernel(
     Ts[rr * klen + kk] = s;
   }
   __syncthreads();
-  const int na = P - 1 - b;
+  const int na = a_hi - a_lo + 1;
   const int* ep = eptr + (size_t)b * (P + 1);
   for (int t = threadIdx.x; t < nr * na; t += blockDim.x) {  // rows fastest: runs of nr entries
-    const int a = b + 1 + t / nr, rr = t - (a - b - 1) * nr;
+    const int a = a_lo + t / nr, rr = t - (a - a_lo) * nr;
     T s = T(0);
     for (int q = ep[a]; q < ep[a + 1]; ++q) s += eg[q] * Ts[rr * klen + ek[q]];
     Rt[(size_t)a * ldN + r0 + rr] -= s;
@@ -345,10 +377,13 @@ int launch_block_solve_t(System& s, int a0, int ncols, int fac_per_col, const T*
   const int wc = s.tri_wc;
   size_t smem = (SMEM ? sizeof(T) * (size_t)s.ldN : 0) + sizeof(T) * tri_ring_entries(wc) +
                 sizeof(int) * (size_t)(s.nlev9 + 1);
+  // a single-column (Gauss-Seidel) solve takes a whole SM: other kernels' CTAs that shared it
+  // would take issue slots from its dependency chain
+  if (ncols == 1) smem = std::max(smem, smem_optin_max());
   auto kern = ilu_block_solve_kernel<T, SMEM>;
   SG_TRY(ensure_smem((const void*)kern, smem));
   TimeScope ts(s.timer, K_ILU_SOLVE, st);
-  kern<<<ncols, 2 * wc, smem, st>>>(s.pat.m, s.N, s.ldN, s.P, s.pat.nnz, a0, fac_per_col,
+  kern<<<ncols, 2 * wc + 32, smem, st>>>(s.pat.m, s.N, s.ldN, s.P, s.pat.nnz, a0, fac_per_col,
                                     s.lev9_off.p, s.nlev9, wc, B::lu9(s), s.rowptr.p, s.col.p,
                                     B::blk(s), Rt, Z, SMEM ? nullptr : B::triw(s),
                                     std::max(1, s.prm.inner_iters), done);
@@ -359,58 +394,77 @@ template <typename T>
 int launch_block_solve(System& s, int a0, int ncols, int fac_per_col, const T* Rt, T* Z,
                        cudaStream_t st, const int* done) {
   using B = PcBufs<T>;
-  if (s.tri_wc < 32 || 2 * s.tri_wc > kTriMaxThreads || s.ldN % 4 != 0)
+  if (s.tri_wc < 32 || 2 * s.tri_wc + 32 > kTriMaxThreads || s.ldN % 4 != 0)
     return fail(SG_ERR_ARG, "wavefront solve: unsupported mesh width");
   if (B::smem(s)) return launch_block_solve_t<T, true>(s, a0, ncols, fac_per_col, Rt, Z, st, done);
   return launch_block_solve_t<T, false>(s, a0, ncols, fac_per_col, Rt, Z, st, done);
 }
 
-template <typename T>
-int launch_scatter(System& s, int b, const T* Z, T* Rt, cudaStream_t st, const int* done);
-template <>
-int launch_scatter<double>(System& s, int b, const double* Z, double* Rt, cudaStream_t st,
-                           const int* done) {
-  size_t smem = sizeof(double) * kScatterRows * std::max(1, s.gs_max_klen);
-  auto kern = fs_scatter_kernel<double, double>;
+// Scatter of block b into column b + 1 (next = true) or into columns b + 2 .. P - 1.
+template <typename T, typename TV>
+int launch_scatter_t(System& s, int b, bool next, const TV* stack_km, const T* eg_next,
+                     const T* eg_later, const T* Z, T* Rt, cudaStream_t st, const int* done) {
+  size_t smem = sizeof(T) * kScatterRows * std::max(1, s.gs_max_klen);
+  auto kern = fs_scatter_kernel<T, TV>;
   SG_TRY(ensure_smem((const void*)kern, smem));
-  int grid = (s.N + kScatterRows - 1) / kScatterRows;
+  const int grid = (s.N + kScatterRows - 1) / kScatterRows;
+  const int a_lo = next ? b + 1 : b + 2, a_hi = next ? b + 1 : s.P - 1;
   TimeScope ts(s.timer, K_GS_SCATTER, st);
-  kern<<<grid, 128, smem, st>>>(s.N, s.P, s.ldN, s.pat.nnz, b, s.rowptr.p, s.col.p, s.stack_km.p,
-                                s.gs_kptr.p, s.gs_k.p, s.gs_eptr.p, s.gs_ea.p, s.gs_eg.p, Z, Rt,
-                                done);
-  return check_launch("fs_scatter");
-}
-template <>
-int launch_scatter<float>(System& s, int b, const float* Z, float* Rt, cudaStream_t st,
-                          const int* done) {
-  size_t smem = sizeof(float) * kScatterRows * std::max(1, s.gs_max_klen);
-  int grid = (s.N + kScatterRows - 1) / kScatterRows;
-  TimeScope ts(s.timer, K_GS_SCATTER, st);
-  if (s.prm.precision == SG_MIXED_BF16) {
-    auto kern = fs_scatter_kernel<float, __nv_bfloat16>;
-    SG_TRY(ensure_smem((const void*)kern, smem));
-    kern<<<grid, 128, smem, st>>>(s.N, s.P, s.ldN, s.pat.nnz, b, s.rowptr.p, s.col.p,
-                                  s.stack_km16.p, s.gs_kptr.p, s.gs_k.p, s.gs_eptr.p, s.gs_ea.p,
-                                  s.gs_eg_f32.p, Z, Rt, done);
-  } else {
-    auto kern = fs_scatter_kernel<float, float>;
-    SG_TRY(ensure_smem((const void*)kern, smem));
-    kern<<<grid, 128, smem, st>>>(s.N, s.P, s.ldN, s.pat.nnz, b, s.rowptr.p, s.col.p,
-                                  s.stack_km32.p, s.gs_kptr.p, s.gs_k.p, s.gs_eptr.p, s.gs_ea.p,
-                                  s.gs_eg_f32.p, Z, Rt, done);
-  }
+  if (next)
+    kern<<<grid, 128, smem, st>>>(s.N, s.P, s.ldN, s.pat.nnz, b, a_lo, a_hi, s.rowptr.p, s.col.p,
+                                  stack_km, s.gsn_kptr.p, s.gsn_k.p, s.gsn_eptr.p, s.gsn_ea.p,
+                                  eg_next, Z, Rt, done);
+  else
+    kern<<<grid, 128, smem, st>>>(s.N, s.P, s.ldN, s.pat.nnz, b, a_lo, a_hi, s.rowptr.p, s.col.p,
+                                  stack_km, s.gs_kptr.p, s.gs_k.p, s.gs_eptr.p, s.gs_ea.p,
+                                  eg_later, Z, Rt, done);
   return check_launch("fs_scatter");
 }
 
-// Field-split Gauss-Seidel: block a solved from column a of Rt, then its coupling subtracted from
-// the later columns.
 template <typename T>
-int fs_gs_sweep(System& s, const T* R, T* D, T* Rt, cudaStream_t st, const int* done) {
+int launch_scatter(System& s, int b, bool next, const T* Z, T* Rt, cudaStream_t st,
+                   const int* done);
+template <>
+int launch_scatter<double>(System& s, int b, bool next, const double* Z, double* Rt,
+                           cudaStream_t st, const int* done) {
+  return launch_scatter_t<double, double>(s, b, next, s.stack_km.p, s.gsn_eg.p, s.gs_eg.p, Z, Rt,
+                                          st, done);
+}
+template <>
+int launch_scatter<float>(System& s, int b, bool next, const float* Z, float* Rt, cudaStream_t st,
+                          const int* done) {
+  if (s.prm.precision == SG_MIXED_BF16)
+    return launch_scatter_t<float, __nv_bfloat16>(s, b, next, s.stack_km16.p, s.gsn_eg_f32.p,
+                                                  s.gs_eg_f32.p, Z, Rt, st, done);
+  return launch_scatter_t<float, float>(s, b, next, s.stack_km32.p, s.gsn_eg_f32.p,
+                                        s.gs_eg_f32.p, Z, Rt, st, done);
+}
+
+// Field-split Gauss-Seidel: block a solved from column a of Rt, then its coupling subtracted from
+// the later columns.  Only column a + 1 must be complete before block a + 1 starts; with ``fork``
+// the scatter into columns a + 2 .. runs on the system's second stream, overlapping the solve of
+// block a + 1.  Ordering: that scatter waits for z_a; the next-column scatter of block a waits for
+// the later-column scatter of block a - 1, which also subtracts into column a + 1; the sweep ends
+// by joining the second stream.
+template <typename T>
+int fs_gs_sweep(System& s, const T* R, T* D, T* Rt, cudaStream_t st, const int* done, bool fork) {
   SG_TRY(launch_columns<T>(s, R, Rt, st, done));
+  cudaStream_t s2 = fork ? s.stream2 : st;
   for (int a = 0; a < s.P; ++a) {
     SG_TRY(launch_block_solve<T>(s, a, 1, 1, Rt, D, st, done));
-    if (a + 1 < s.P) SG_TRY(launch_scatter<T>(s, a, D, Rt, st, done));
+    if (a + 1 >= s.P) break;
+    if (a + 2 < s.P) {
+      if (fork) {
+        SG_CUDA(cudaEventRecord(s.ev_z, st));
+        SG_CUDA(cudaStreamWaitEvent(s2, s.ev_z, 0));
+      }
+      SG_TRY(launch_scatter<T>(s, a, false, D, Rt, s2, done));
+      if (fork) SG_CUDA(cudaEventRecord(s.ev_r[a & 1], s2));
+    }
+    if (fork && a >= 1) SG_CUDA(cudaStreamWaitEvent(st, s.ev_r[(a - 1) & 1], 0));
+    SG_TRY(launch_scatter<T>(s, a, true, D, Rt, st, done));
   }
+  if (fork && s.P >= 3) SG_CUDA(cudaStreamWaitEvent(st, s.ev_r[(s.P - 3) & 1], 0));
   return SG_OK;
 }
 
@@ -425,7 +479,7 @@ int apply_once(System& s, const T* R, T* D, cudaStream_t st, const int* done) {
       return launch_block_solve<T>(s, 0, s.P, s.prm.precond == SG_PC_FS_JACOBI ? 1 : 0,
                                    B::rhs_t(s), D, st, done);
     case SG_PC_FS_GS:
-      return fs_gs_sweep<T>(s, R, D, B::rhs_t(s), st, done);
+      return fs_gs_sweep<T>(s, R, D, B::rhs_t(s), st, done, true);
     default: {
       SG_CUDA(cudaMemcpyAsync(D, R, sizeof(T) * (size_t)s.N * s.P, cudaMemcpyDeviceToDevice, st));
       return SG_OK;
@@ -466,7 +520,7 @@ int precond_apply_t(System& s, const T* R, T* Z, cudaStream_t st, const int* don
 }  // namespace
 
 int fs_gs_apply_f64_with(System& s, const double* R, double* Z, double* rhs_t, cudaStream_t st) {
-  return fs_gs_sweep<double>(s, R, Z, rhs_t, st, nullptr);
+  return fs_gs_sweep<double>(s, R, Z, rhs_t, st, nullptr, false);
 }
 
 int precond_apply_f64(System& s, const double* R, double* Z, cudaStream_t st, const int* done) {

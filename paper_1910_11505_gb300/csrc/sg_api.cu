@@ -45,6 +45,20 @@ int ensure_smem(const void* kernel, size_t bytes) {
   return SG_OK;
 }
 
+size_t smem_optin_max() {
+  static std::mutex mu;
+  static std::map<int, size_t> cache;
+  int dev = 0;
+  cudaGetDevice(&dev);
+  std::lock_guard<std::mutex> lock(mu);
+  auto it = cache.find(dev);
+  if (it != cache.end()) return it->second;
+  int v = 0;
+  if (cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess) v = 0;
+  cache[dev] = (size_t)v;
+  return (size_t)v;
+}
+
 TimeScope::TimeScope(Timer* t_, int cls_, cudaStream_t st_) : t(t_), cls(cls_), st(st_) {
   if (!t || !t->on) return;
   long long c = t->count[cls]++;
@@ -203,14 +217,19 @@ static int upload_f(DBuf<float>& d, const std::vector<double>& h, cudaStream_t s
 
 // Field-split Gauss-Seidel tables: for source block b, the k that couple b to some a > b and,
 // per a > b, the (k index, G_k[a,b]) entries.
-static int build_gs_tables(System& s, cudaStream_t st) {
+// Scatter tables of the Gauss-Seidel sweep for the target columns a = b + 1 (next) or
+// a >= b + 2 (later): per source block b the k with a nonzero G_k[a,b] and per a the
+// (local k index, G_k[a,b]) entries.
+static int build_scatter_tables(System& s, bool next, DBuf<int>& dkptr, DBuf<int>& dk,
+                                DBuf<int>& deptr, DBuf<int>& dea, DBuf<double>& deg,
+                                DBuf<float>& deg32, cudaStream_t st) {
   std::vector<int> kptr(s.P + 1, 0), klist, eptr((size_t)s.P * (s.P + 1), 0), ea;
   std::vector<double> eg;
-  s.gs_max_klen = 0;
+  auto target = [&](int a, int b) { return next ? a == b + 1 : a > b + 1; };
   for (int b = 0; b < s.P; ++b) {
     std::vector<int> ks;
     for (auto& t : s.triples)
-      if (t.b == b && t.a > b) ks.push_back(t.k);
+      if (t.b == b && target(t.a, b)) ks.push_back(t.k);
     std::sort(ks.begin(), ks.end());
     ks.erase(std::unique(ks.begin(), ks.end()), ks.end());
     kptr[b] = (int)klist.size();
@@ -218,7 +237,7 @@ static int build_gs_tables(System& s, cudaStream_t st) {
     s.gs_max_klen = std::max(s.gs_max_klen, (int)ks.size());
     std::vector<std::vector<std::pair<int, double>>> per_a(s.P);
     for (auto& t : s.triples)
-      if (t.b == b && t.a > b) {
+      if (t.b == b && target(t.a, b)) {
         int kl = (int)(std::lower_bound(ks.begin(), ks.end(), t.k) - ks.begin());
         per_a[t.a].push_back({kl, t.g});
       }
@@ -233,29 +252,46 @@ static int build_gs_tables(System& s, cudaStream_t st) {
     eptr[(size_t)b * (s.P + 1) + s.P] = (int)ea.size();
   }
   kptr[s.P] = (int)klist.size();
-  SG_TRY(upload_i(s.gs_kptr, kptr, st));
-  SG_TRY(upload_i(s.gs_k, klist, st));
-  SG_TRY(upload_i(s.gs_eptr, eptr, st));
-  SG_TRY(upload_i(s.gs_ea, ea, st));
-  SG_TRY(upload_d(s.gs_eg, eg, st));
-  if (s.prm.precision != SG_FP64) SG_TRY(upload_f(s.gs_eg_f32, eg, st));
+  SG_TRY(upload_i(dkptr, kptr, st));
+  SG_TRY(upload_i(dk, klist, st));
+  SG_TRY(upload_i(deptr, eptr, st));
+  SG_TRY(upload_i(dea, ea, st));
+  SG_TRY(upload_d(deg, eg, st));
+  if (s.prm.precision != SG_FP64) SG_TRY(upload_f(deg32, eg, st));
+  return SG_OK;
+}
+
+static int build_gs_tables(System& s, cudaStream_t st) {
+  s.gs_max_klen = 0;
+  SG_TRY(build_scatter_tables(s, false, s.gs_kptr, s.gs_k, s.gs_eptr, s.gs_ea, s.gs_eg,
+                              s.gs_eg_f32, st));
+  SG_TRY(build_scatter_tables(s, true, s.gsn_kptr, s.gsn_k, s.gsn_eptr, s.gsn_ea, s.gsn_eg,
+                              s.gsn_eg_f32, st));
+  int prio_low = 0, prio_high = 0;
+  SG_CUDA(cudaDeviceGetStreamPriorityRange(&prio_low, &prio_high));
+  SG_CUDA(cudaStreamCreateWithPriority(&s.stream2, cudaStreamNonBlocking, prio_low));
+  SG_CUDA(cudaEventCreateWithFlags(&s.ev_z, cudaEventDisableTiming));
+  SG_CUDA(cudaEventCreateWithFlags(&s.ev_r[0], cudaEventDisableTiming));
+  SG_CUDA(cudaEventCreateWithFlags(&s.ev_r[1], cudaEventDisableTiming));
   return SG_OK;
 }
 
 static void free_system(System* s) {
   if (!s) return;
   if (s->stream) cudaStreamSynchronize(s->stream);
+  if (s->stream2) cudaStreamSynchronize(s->stream2);
   DBuf<int>* ib[] = {&s->rowptr, &s->col, &s->diag, &s->lev_f_ptr, &s->lev_f_rows, &s->lev_b_ptr,
                      &s->lev_b_rows, &s->pair_kb, &s->ent_ptr, &s->ent_u, &s->gs_kptr, &s->gs_k,
-                     &s->gs_eptr, &s->gs_ea, &s->flags};
+                     &s->gs_eptr, &s->gs_ea, &s->gsn_kptr, &s->gsn_k, &s->gsn_eptr,
+                     &s->gsn_ea, &s->flags};
   for (auto* b : ib) b->release();
   s->lev9_off.release();
   s->stack_km16.release();
-  DBuf<double>* db[] = {&s->stack, &s->stack_km, &s->ent_g, &s->blk, &s->fac, &s->lu9, &s->gs_eg, &s->rhs_t, &s->tmp,
+  DBuf<double>* db[] = {&s->stack, &s->stack_km, &s->ent_g, &s->blk, &s->fac, &s->lu9, &s->gs_eg, &s->gsn_eg, &s->rhs_t, &s->tmp,
                         &s->tmp2, &s->tri_w, &s->V, &s->Z, &s->Hs, &s->cs, &s->sn, &s->g, &s->y,
                         &s->scal, &s->red, &s->rvec};
   for (auto* b : db) b->release();
-  DBuf<float>* fb[] = {&s->stack_f32, &s->stack_km32, &s->ent_g_f32, &s->lu9_f32, &s->blk_f32, &s->gs_eg_f32,
+  DBuf<float>* fb[] = {&s->stack_f32, &s->stack_km32, &s->ent_g_f32, &s->lu9_f32, &s->blk_f32, &s->gs_eg_f32, &s->gsn_eg_f32,
                        &s->rhs_t32, &s->tmp32, &s->tmp232, &s->tri_w32, &s->V32, &s->Z32,
                        &s->mv32a, &s->mv32b};
   for (auto* b : fb) b->release();
@@ -267,6 +303,9 @@ static void free_system(System* s) {
   s->graphs.clear();
   if (s->hpin) cudaFreeHost(s->hpin);
   if (s->ev) cudaEventDestroy(s->ev);
+  if (s->stream2) cudaStreamDestroy(s->stream2);
+  for (cudaEvent_t e : {s->ev_z, s->ev_r[0], s->ev_r[1]})
+    if (e) cudaEventDestroy(e);
   if (s->stream) cudaStreamDestroy(s->stream);
   delete s;
 }
@@ -288,13 +327,19 @@ static int setup_system(System& s, cudaStream_t st) {
     s.ldN = (s.N + 3) / 4 * 4;
     s.tri_wc = (interior_level_width(p.n + 1) + 31) / 32 * 32;
     size_t ring = tri_ring_entries(s.tri_wc), lev = sizeof(int) * 3 * (size_t)(p.n + 1);
-    if (8 * ring + lev > 220 * 1024 || 2 * s.tri_wc > 1024)
-      return fail(SG_ERR_ARG, "mesh too large for the wavefront solve");
+    const bool ilu = p.precond == SG_PC_MEAN || p.precond == SG_PC_FS_GS ||
+                     p.precond == SG_PC_FS_JACOBI;
+    if (ilu && (8 * ring + lev > 220 * 1024 || 2 * s.tri_wc + 32 > 1024))
+      return fail(SG_ERR_ARG, "n must be at most 992 for the ILU(0) preconditioners");
     s.tri_smem = (size_t)s.ldN * 8 + 8 * ring + lev <= 220 * 1024;
     s.tri_smem32 = (size_t)s.ldN * 4 + 4 * ring + lev <= 220 * 1024;
   }
 
-  SG_CUDA(cudaStreamCreateWithFlags(&s.stream, cudaStreamNonBlocking));
+  // the system's own stream carries the critical path (GMRES, block solves); the second stream of
+  // the Gauss-Seidel sweep (later-column scatters) fills idle SMs at the lowest priority
+  int prio_low = 0, prio_high = 0;
+  SG_CUDA(cudaDeviceGetStreamPriorityRange(&prio_low, &prio_high));
+  SG_CUDA(cudaStreamCreateWithPriority(&s.stream, cudaStreamNonBlocking, prio_high));
   SG_CUDA(cudaEventCreateWithFlags(&s.ev, cudaEventDisableTiming));
   SG_CUDA(cudaMallocHost((void**)&s.hpin, 16 * sizeof(double)));
 

@@ -41,6 +41,8 @@ int check_launch(const char* what);
 // Raise a kernel's dynamic shared-memory limit on the current device to ``bytes`` unless an
 // earlier call already set at least that much (the attribute call is not repeated per launch).
 int ensure_smem(const void* kernel, size_t bytes);
+// Largest dynamic shared memory one CTA may opt into on the current device.
+size_t smem_optin_max();
 
 // ------------------------------------------------------------------ live kernel timing
 
@@ -177,10 +179,14 @@ struct System {
   int nlev9 = 0;
   int tri_wc = 0;              // threads per group of the wavefront solve (multiple of 32)
   int ldN = 0;                 // column stride of rhs_t / tri_w: N rounded up to a multiple of 4
-  // field-split Gauss-Seidel scatter tables, per source block b: k list and (a, g) entries
+  // field-split Gauss-Seidel scatter tables, per source block b: k list and (a, g) entries, for
+  // the later columns a >= b + 2 (gs_*) and for the next column a = b + 1 (gsn_*)
   DBuf<int> gs_kptr, gs_k, gs_eptr, gs_ea;
   DBuf<double> gs_eg;
   DBuf<float> gs_eg_f32;
+  DBuf<int> gsn_kptr, gsn_k, gsn_eptr, gsn_ea;
+  DBuf<double> gsn_eg;
+  DBuf<float> gsn_eg_f32;
   int gs_max_klen = 0;
   // device scratch
   DBuf<double> rhs_t;          // P columns of stride ldN: right-hand sides of the block solves
@@ -209,6 +215,10 @@ struct System {
   std::vector<CycleGraph> graphs;  // captured GMRES cycles (sg_params.graphs = 1)
   cudaStream_t stream = nullptr;
   cudaEvent_t ev = nullptr;
+  // Gauss-Seidel sweep: second stream for the later-column scatters, which overlap the next
+  // block solve, and the events ordering the two streams
+  cudaStream_t stream2 = nullptr;
+  cudaEvent_t ev_z = nullptr, ev_r[2] = {nullptr, nullptr};
 };
 
 }  // namespace sg
