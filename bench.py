@@ -306,11 +306,11 @@ def main():
             "launches_timed": d_timed, "share_of_timed_gpu_time": est[dom] / max(1e-30, sum(est.values()))}
     if dom == "ilu_solve":
         # the block solve is bound by its dependency chain: two sweeps of 3m - 8 interior
-        # wavefront levels, one barrier step each plus one, and per step two dependent FP64 FMAs
+        # wavefront levels, one barrier step each plus two, and per step two dependent FP64 FMAs
         # (64 cycles each on this GPU), a shared-memory load and store (~50 cycles) and the
         # barrier (~50 cycles): an estimated floor of ~230 cycles per step at 2.07 GHz
         m = int(round(N ** 0.5))
-        steps = 2 * (3 * m - 8) + 2
+        steps = 2 * (3 * m - 8) + 4
         roof["critical_path_steps"] = steps
         roof["ns_per_step"] = d_avg_s * 1e9 / steps
         roof["ns_per_step_floor_est"] = (2 * 64 + 50 + 50) / 2.07
