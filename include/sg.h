@@ -50,7 +50,7 @@ typedef struct sg_handle sg_handle;
 
 /* Parameters of one SG system.  a = a_min + exp(mu + sum_n sqrt(lambda_n) b_n(x) y_n). */
 typedef struct {
-  int n;             /* cells per side of the Q1 mesh of [0,1]^2: 2..1024, with ILU(0) 2..992  */
+  int n;             /* cells per side of the Q1 mesh of [0,1]^2: 2..1024, with ILU(0) 2..769  */
   int M;             /* KL terms kept, 1 <= M <= 8                                             */
   int p;             /* total degree of the solution chaos, 0 <= p <= 6                        */
   int q;             /* total degree of the coefficient chaos; <= 0 selects 2p                 */
@@ -125,8 +125,7 @@ int sg_precond_apply(sg_handle* h, int sys, const double* R, double* Z, void* st
  * make that first call before any stream capture.  All calls share the one array: calls whose
  * work overlaps on the GPU (other streams, other threads) race and give wrong results.
  * SG_ERR_ARG if the system does not use SG_PC_FS_GS with outer_sweeps = 1, if P x ldN exceeds
- * SG_NOALLOC_MAX_ENTRIES, if one column does not fit the shared-memory block solve, or if the
- * handle's device is not current.  R, Z as for sg_precond_apply.  Asynchronous on ``stream``. */
+ * SG_NOALLOC_MAX_ENTRIES, or if the handle's device is not current.  R, Z as for sg_precond_apply.  Asynchronous on ``stream``. */
 #define SG_NOALLOC_MAX_ENTRIES (1 << 20)
 int sg_precond_apply_noalloc(sg_handle* h, int sys, const double* R, double* Z, void* stream);
 

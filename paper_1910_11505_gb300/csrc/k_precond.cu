@@ -7,13 +7,13 @@
 //    block K_aa approximated by its ILU(0) factors with ``inner_iters`` Richardson steps;
 //  * both wrapped in ``outer_sweeps`` steps of the level solver of Eq. level_solver.
 //
-// The block solves read their right-hand sides as contiguous columns (rhs_t, P columns of stride
-// ldN, filled from the N x P residual by a tiled transpose), so one CTA loads its column with a
-// burst of 16-byte copies.  The ILU(0) triangular solves run as wavefronts: rows of one level of
-// the lower (upper) graph of the pattern depend only on rows of earlier levels; one CTA owns one
-// chaos column and walks all levels with a CTA barrier in between, holding the column in shared
-// memory when it fits.  The off-diagonal coupling of the Gauss-Seidel sweep, sum_{b<a} K_ab z_b,
-// is subtracted from the later columns of rhs_t after each block b by a grid-wide kernel:
+// The block solves read their right-hand sides from contiguous columns (rhs_t, P columns of
+// stride ldN, filled from the N x P residual by a tiled transpose).  The ILU(0) triangular solves
+// run as wavefronts: rows of one level of the lower (upper) graph of the pattern depend only on
+// rows of earlier levels; one CTA owns one chaos column and walks all levels with a CTA barrier
+// in between, keeping only a window of level rows in shared memory, so any mesh takes the same
+// path.  The off-diagonal coupling of the Gauss-Seidel sweep, sum_{b<a} K_ab z_b, is subtracted
+// from the later columns of rhs_t after each block b by a grid-wide kernel:
 // T[k] = sum_e A[e,k] z_b[j_e] once per (row, k), then rhs_t[a] -= G_k[a,b] T[k] for a > b.
 #include "sg_internal.h"
 
@@ -63,17 +63,21 @@ constexpr int kTriMaxThreads = 1024;
 template <typename T>
 __device__ __forceinline__ void cp_async_elem(T* dst, const T* src) {
   unsigned sa = (unsigned)__cvta_generic_to_shared(dst);
-  asm volatile("cp.async.ca.shared.global [%0], [%1], %2;\n" ::"r"(sa), "l"(src), "n"(sizeof(T)));
+  asm volatile("cp.async.ca.shared.global [%0], [%1], %2;\n" ::"r"(sa), "l"(src), "n"(sizeof(T))
+               : "memory");
 }
 __device__ __forceinline__ void cp_async_16(void* dst, const void* src) {
   unsigned sa = (unsigned)__cvta_generic_to_shared(dst);
-  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(src));
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(src) : "memory");
 }
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
 template <int N>
 __device__ __forceinline__ void cp_async_wait() {
   asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
 }
+
+// ---------------------------------------------------------------- whole column in shared memory
+// (meshes whose column fits: the staging warp streams only factors)
 
 // Interior rows of level l for the compute threads, from l alone: row of thread t, or -1.
 __device__ __forceinline__ int interior_row(int l, int m, int t) {
@@ -90,7 +94,7 @@ __device__ __forceinline__ int interior_row(int l, int m, int t) {
 // has landed; the barrier then makes it visible to the compute threads, which therefore neither
 // issue copies nor wait for them.
 template <typename T, bool UPPER>
-__device__ __forceinline__ void ilu9_sweep(T* w, T* ring, int wc, const T* __restrict__ lu, int m,
+__device__ __forceinline__ void column_sweep(T* w, T* ring, int wc, const T* __restrict__ lu, int m,
                                            int N, const int* lev_s, int nl, int role, int t) {
   auto level = [&](int j) { return UPPER ? 3 * m - 6 - j : 3 + j; };
   auto row = [&](int j) { return j < nl ? interior_row(level(j), m, t) : -1; };
@@ -203,7 +207,7 @@ __device__ __forceinline__ void ilu9_sweep(T* w, T* ring, int wc, const T* __res
 // sweeps.  Threads [0, wc) form the critical group, [wc, 2wc) the lookahead group, the last warp
 // stages the factors.
 template <typename T>
-__device__ __forceinline__ void ilu9_solve(T* w, T* ring, int wc, const T* __restrict__ lu, int m,
+__device__ __forceinline__ void column_solve(T* w, T* ring, int wc, const T* __restrict__ lu, int m,
                                            int N, const int* lev_s) {
   const int nb = 4 * (m - 1);
   for (int k = threadIdx.x; k < nb; k += blockDim.x) {
@@ -218,14 +222,264 @@ __device__ __forceinline__ void ilu9_solve(T* w, T* ring, int wc, const T* __res
   const int tid = threadIdx.x;
   const int role = tid < wc ? 0 : tid < 2 * wc ? 1 : 2;
   const int t = tid - role * wc;
-  ilu9_sweep<T, false>(w, ring, wc, lu, m, N, lev_s, nl, role, t);
-  ilu9_sweep<T, true>(w, ring, wc, lu, m, N, lev_s, nl, role, t);
+  column_sweep<T, false>(w, ring, wc, lu, m, N, lev_s, nl, role, t);
+  column_sweep<T, true>(w, ring, wc, lu, m, N, lev_s, nl, role, t);
 }
 
 // CTA c solves column a = a0 + c with factor set (fac_per_col ? a : 0) and right-hand side
-// rhs = Rt[a * ldN ...]:  z = ILU^{-1}(rhs), then inner-1 times z += ILU^{-1}(rhs - K_blk z).
-template <typename T, bool SMEM>
-__global__ void __launch_bounds__(kTriMaxThreads) ilu_block_solve_kernel(
+// rhs = Rt[a * ldN ...], holding the whole column in shared memory:  z = ILU^{-1}(rhs), then
+// inner-1 times z += ILU^{-1}(rhs - K_blk z).
+template <typename T>
+__global__ void __launch_bounds__(kTriMaxThreads) ilu_column_kernel(
+    int m, int N, int ldN, int P, int nnz, int a0, int fac_per_col, const int* __restrict__ lev_off,
+    int nlev, int wc, const T* __restrict__ lu9s, const int* __restrict__ rowptr,
+    const int* __restrict__ col, const T* __restrict__ blks, const T* __restrict__ Rt,
+    T* __restrict__ Z, int inner, const int* __restrict__ done) {
+  if (done != nullptr && *done) return;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int a = a0 + blockIdx.x;
+  const int fsel = fac_per_col ? a : 0;
+  const T* lu = lu9s + (size_t)fsel * 9 * N;
+  const T* blk = blks + (size_t)fsel * nnz;
+  const T* rhs = Rt + (size_t)a * ldN;
+  T* w = reinterpret_cast<T*>(smem_raw);
+  T* ring = reinterpret_cast<T*>(smem_raw + sizeof(T) * (size_t)ldN);
+  int* lev_s = reinterpret_cast<int*>(ring + (size_t)kAhead * 5 * wc);
+  for (int l = threadIdx.x; l <= nlev; l += blockDim.x) lev_s[l] = lev_off[l];
+  {  // the column (ldN * sizeof(T) bytes, 16-byte aligned) in one burst of copies
+    const int nchunk = (int)((size_t)ldN * sizeof(T) / 16);
+    for (int c = threadIdx.x; c < nchunk; c += blockDim.x)
+      cp_async_16(reinterpret_cast<unsigned char*>(w) + 16 * (size_t)c,
+                  reinterpret_cast<const unsigned char*>(rhs) + 16 * (size_t)c);
+    cp_async_commit();
+    cp_async_wait<0>();
+  }
+  __syncthreads();
+  column_solve<T>(w, ring, wc, lu, m, N, lev_s);
+#pragma unroll 4
+  for (int i = threadIdx.x; i < N; i += blockDim.x) Z[(size_t)i * P + a] = w[i];
+  for (int it = 1; it < inner; ++it) {
+    __syncthreads();
+    for (int i = threadIdx.x; i < N; i += blockDim.x) {
+      T v = rhs[i];
+      for (int e = rowptr[i]; e < rowptr[i + 1]; ++e) v -= blk[e] * Z[(size_t)col[e] * P + a];
+      w[i] = v;
+    }
+    __syncthreads();
+    column_solve<T>(w, ring, wc, lu, m, N, lev_s);
+    for (int i = threadIdx.x; i < N; i += blockDim.x) Z[(size_t)i * P + a] += w[i];
+  }
+}
+
+// ---------------------------------------------------------------- level window
+// (larger meshes: the column stays in global memory, a window of level rows on chip)
+
+// Row y of thread t on level l (interior rows only), or -1; the row's node is x + m y, x = l - 2y.
+__device__ __forceinline__ int interior_y(int l, int m, int t) {
+  const int y0 = max(1, (l - (m - 2) + 1) >> 1), y1 = min(m - 2, (l - 1) >> 1);
+  return t <= y1 - y0 ? y0 + t : -1;
+}
+
+// Level window: the sweep at step s touches only list positions s-1 .. s+3 (neighbours one to
+// three levels back and the lookahead's rows), so the working values live in a shared-memory
+// ring of kWin level rows indexed by y (window row p & (kWin-1) holds list position p).  The
+// staging threads gather the values of position s + kWin - 2 into the window at step s (ten
+// steps before their first reader, which hides the strided reads' L2 latency) and write
+// position s-2, whose last reader was step s-1, back to global memory; the compute threads read
+// and write only the window.  Entries outside a level's interior rows hold 0 or an earlier
+// level's value (their factors are exactly 0).
+constexpr int kWin = kTriWin;
+
+// One sweep (lower or upper) over the nl interior levels; every thread of the CTA calls it and
+// passes nl + 4 barriers.  List position j is level 3 + j (lower) or 3m - 6 - j (upper).  The
+// critical group (role 0) takes position j at step j; the lookahead group (role 1) works on
+// position j during steps j - 3 .. j - 1.  The staging threads (role 2) copy, at step s, the
+// factors of position s + kAhead - 1 into the rings (kAhead x 2 x wc critical, kAhead x 3 x wc
+// lookahead) and the values of position s + kWin - 2 from ``src`` into the window, then wait
+// until everything for positions up to s + 4 has landed (copy groups of step s - 3 and before);
+// the barrier that ends step s publishes it.
+// Values are read from src[i * ss]; final values of each position go to dst[i * ds] (added to it
+// when ``acc``).
+template <typename T, bool UPPER>
+__device__ __forceinline__ void window_sweep(T* win, T* ring, int wc, const T* __restrict__ lu,
+                                           int m, int N, const int* lev_s, int nl, int role, int t,
+                                           const T* src, int ss, T* dst, int ds, bool acc) {
+  auto level = [&](int j) { return UPPER ? 3 * m - 6 - j : 3 + j; };
+  auto wrow = [&](int p) { return win + (size_t)(p & (kWin - 1)) * m; };
+  const int nst = (int)blockDim.x - 2 * wc;  // staging threads
+  auto ypos = [&](int j) { return j < nl ? interior_y(level(j), m, t) : -1; };
+  T* cring = ring;
+  T* lring = ring + (size_t)kAhead * 2 * wc;
+  for (int k = threadIdx.x; k < kWin * m; k += blockDim.x) win[k] = T(0);
+  __syncthreads();
+  if (role == 2) {
+    // critical: lower slots 2, 3 / upper 5, 6; lookahead: early lower 0 / upper 8, late lower 1 /
+    // upper 7, and upper 1/u_ii (slot 4)
+    const T* fA = lu + (size_t)(UPPER ? 5 : 2) * N;
+    const T* fE = lu + (size_t)(UPPER ? 8 : 0) * N;
+    const T* fL = lu + (size_t)(UPPER ? 7 : 1) * N;
+    const T* fD = lu + (size_t)4 * N;
+    auto factors = [&](int j) {
+      if (j < nl) {
+        int y0, cnt, pos0;
+        interior_level(level(j), m, lev_s, y0, cnt, pos0);
+        T* c = cring + (size_t)(j % kAhead) * 2 * wc;
+        T* d = lring + (size_t)(j % kAhead) * 3 * wc;
+        for (int r = t; r < cnt; r += nst) {
+          cp_async_elem(c + r, fA + pos0 + r);
+          cp_async_elem(c + wc + r, fA + N + pos0 + r);
+          cp_async_elem(d + r, fE + pos0 + r);
+          cp_async_elem(d + wc + r, fL + pos0 + r);
+          if (UPPER) cp_async_elem(d + 2 * wc + r, fD + pos0 + r);
+        }
+      }
+    };
+    auto gather = [&](int j) {
+      if (j < nl) {
+        const int l = level(j);
+        const int y0 = max(1, (l - (m - 2) + 1) >> 1), y1 = min(m - 2, (l - 1) >> 1);
+        T* wr = wrow(j);
+        for (int y = y0 + t; y <= y1; y += nst)
+          cp_async_elem(wr + y, src + ((size_t)l + (size_t)(m - 2) * y) * ss);
+      }
+    };
+    auto writeout = [&](int j) {
+      if (j >= 0 && j < nl) {
+        const int l = level(j);
+        const int y0 = max(1, (l - (m - 2) + 1) >> 1), y1 = min(m - 2, (l - 1) >> 1);
+        const T* wr = wrow(j);
+        for (int y = y0 + t; y <= y1; y += nst) {
+          T* d = dst + ((size_t)l + (size_t)(m - 2) * y) * ds;
+          const T v = wr[y];
+          *d = acc ? *d + v : v;
+        }
+      }
+    };
+    factors(0);
+    for (int j = 0; j < kWin - 3; ++j) gather(j);
+    cp_async_commit();
+#pragma unroll 1
+    for (int j = 1; j < kAhead - 2; ++j) {
+      factors(j);
+      cp_async_commit();
+    }
+    cp_async_wait<3>();  // positions 0 .. 2 landed
+    __syncthreads();
+    for (int step = -1; step < nl; ++step) {
+      writeout(step - 2);
+      factors(step + kAhead - 1);
+      gather(step + kWin - 2);
+      cp_async_commit();
+      cp_async_wait<3>();  // positions up to step + 4 landed
+      __syncthreads();
+    }
+    cp_async_wait<0>();
+    writeout(nl - 2);
+    writeout(nl - 1);
+  } else if (role == 0) {
+    // lower: slot 2 at (x+1, y-1), slot 3 at (x-1, y); upper: slot 5 at (x+1, y), slot 6 at
+    // (x-1, y+1); both neighbours on the previous position
+    const int dA = UPPER ? 0 : -1, dB = UPPER ? 1 : 0;
+    __syncthreads();
+    for (int step = -1; step < nl; ++step) {
+      if (step >= 0) {
+        const int y = ypos(step);
+        if (y >= 0) {
+          const T* f = cring + (size_t)(step % kAhead) * 2 * wc + t;
+          T* cur = wrow(step);
+          const T* prev = wrow(step - 1);
+          const T fa = f[0], fb = f[wc];
+          T v = cur[y];
+          const T zA = prev[y + dA], zB = prev[y + dB];
+          v -= fa * zA;
+          v -= fb * zB;
+          cur[y] = v;
+        }
+      }
+      __syncthreads();
+    }
+  } else {
+    // position j in three steps, so that no step holds a dependent FP64 pair:
+    //   A (step j - 3): the row's value, times 1/u_ii (slot 4) in the upper sweep;
+    //   B (step j - 2): minus the early coupling, slot 0 at (x-1, y-1) / slot 8 at (x+1, y+1),
+    //                   three positions back;
+    //   C (step j - 1): minus the late coupling, slot 1 at (x, y-1) / slot 7 at (x, y+1), two
+    //                   positions back, stored.
+    const int dE = UPPER ? 1 : -1;
+    auto stage_a = [&](int j, int& y, T& v) {
+      y = ypos(j);
+      if (y >= 0) {
+        v = wrow(j)[y];
+        if (UPPER) v *= lring[(size_t)(j % kAhead) * 3 * wc + 2 * wc + t];
+      }
+    };
+    auto stage_b = [&](int j, int y, T v, int& yo, T& po, T& fo) {
+      yo = y;
+      if (y >= 0) {
+        const T* f = lring + (size_t)(j % kAhead) * 3 * wc + t;
+        po = v - f[0] * wrow(j - 3)[y + dE];
+        fo = f[wc];
+      }
+    };
+    int yb = -1, yc = -1;
+    T vb = T(0), pc = T(0), fc = T(0);
+    __syncthreads();
+    {
+      int y0;
+      T v0 = T(0);
+      stage_a(0, y0, v0);
+      stage_b(0, y0, v0, yc, pc, fc);
+      if (1 < nl) stage_a(1, yb, vb);
+    }
+    for (int step = -1; step < nl; ++step) {
+      const int j = step + 1;
+      const int ycur = j < nl ? yc : -1;
+      const T cpc = pc, cfc = fc;
+      T zl = T(0);
+      if (ycur >= 0) zl = wrow(j - 2)[ycur + dE];
+      yc = -1;
+      if (j + 1 < nl) stage_b(j + 1, yb, vb, yc, pc, fc);
+      yb = -1;
+      if (j + 2 < nl) stage_a(j + 2, yb, vb);
+      if (ycur >= 0) wrow(j)[ycur] = cpc - cfc * zl;
+      __syncthreads();
+    }
+  }
+  __syncthreads();  // the staging warp's last write-outs before the window is reused
+}
+
+// One column: z = U^{-1} L^{-1} src, written to out[i * P] (added to it when ``acc``).  Boundary
+// rows are solved by their scaling; the forward values of interior rows pass through fwd[i * fs]
+// on their way to the upper sweep.  Threads [0, wc) form the critical group, [wc, 2wc) the
+// lookahead group, the remaining threads stage factors and values.
+template <typename T>
+__device__ __forceinline__ void window_solve(T* win, T* ring, int wc, const T* __restrict__ lu,
+                                           int m, int N, const int* lev_s, const T* src, T* fwd,
+                                           int fs, T* out, int P, bool acc) {
+  const int nb = 4 * (m - 1);
+  for (int k = threadIdx.x; k < nb; k += blockDim.x) {
+    const int side = k / (m - 1), s = k - side * (m - 1);
+    const int x = side == 0 ? s : side == 1 ? m - 1 : side == 2 ? m - 1 - s : 0;
+    const int y = side == 0 ? 0 : side == 1 ? s : side == 2 ? m - 1 : m - 1 - s;
+    const int l = x + 2 * y, ylo = max(0, (l - (m - 1) + 1) >> 1), i = x + m * y;
+    const T v = src[i] * lu[(size_t)4 * N + lev_s[l] + (y - ylo)];
+    T* d = out + (size_t)i * P;
+    *d = acc ? *d + v : v;
+  }
+  const int nl = 3 * m - 8;
+  const int tid = threadIdx.x;
+  const int role = tid < wc ? 0 : tid < 2 * wc ? 1 : 2;
+  const int t = tid - role * wc;
+  window_sweep<T, false>(win, ring, wc, lu, m, N, lev_s, nl, role, t, src, 1, fwd, fs, false);
+  window_sweep<T, true>(win, ring, wc, lu, m, N, lev_s, nl, role, t, fwd, fs, out, P, acc);
+}
+
+// CTA c solves column a = a0 + c with factor set (fac_per_col ? a : 0) and right-hand side
+// rhs = Rt[a * ldN ...]:  z = ILU^{-1}(rhs), then inner-1 times z += ILU^{-1}(rhs - K_blk z)
+// (the residual and the forward values of those passes in wglob[a * ldN ...]).  The first pass
+// keeps its forward values in the output column itself.
+template <typename T>
+__global__ void __launch_bounds__(kTriMaxThreads) ilu_window_kernel(
     int m, int N, int ldN, int P, int nnz, int a0, int fac_per_col, const int* __restrict__ lev_off,
     int nlev, int wc, const T* __restrict__ lu9s, const int* __restrict__ rowptr,
     const int* __restrict__ col, const T* __restrict__ blks, const T* __restrict__ Rt,
@@ -237,34 +491,23 @@ __global__ void __launch_bounds__(kTriMaxThreads) ilu_block_solve_kernel(
   const T* lu = lu9s + (size_t)fsel * 9 * N;
   const T* blk = blks + (size_t)fsel * nnz;
   const T* rhs = Rt + (size_t)a * ldN;
-  T* w = SMEM ? reinterpret_cast<T*>(smem_raw) : wglob + (size_t)a * ldN;
-  T* ring = reinterpret_cast<T*>(smem_raw + (SMEM ? sizeof(T) * (size_t)ldN : 0));
+  T* zc = Z + a;
+  T* win = reinterpret_cast<T*>(smem_raw);
+  T* ring = win + (size_t)kWin * m;
   int* lev_s = reinterpret_cast<int*>(ring + (size_t)kAhead * 5 * wc);
   for (int l = threadIdx.x; l <= nlev; l += blockDim.x) lev_s[l] = lev_off[l];
-  if (SMEM) {  // the column (ldN * sizeof(T) bytes, 16-byte aligned) in one burst of copies
-    const int nchunk = (int)((size_t)ldN * sizeof(T) / 16);
-    for (int c = threadIdx.x; c < nchunk; c += blockDim.x)
-      cp_async_16(reinterpret_cast<unsigned char*>(w) + 16 * (size_t)c,
-                  reinterpret_cast<const unsigned char*>(rhs) + 16 * (size_t)c);
-    cp_async_commit();
-    cp_async_wait<0>();
-  } else {
-    for (int i = threadIdx.x; i < N; i += blockDim.x) w[i] = rhs[i];
-  }
   __syncthreads();
-  ilu9_solve<T>(w, ring, wc, lu, m, N, lev_s);
-#pragma unroll 4
-  for (int i = threadIdx.x; i < N; i += blockDim.x) Z[(size_t)i * P + a] = w[i];
+  window_solve<T>(win, ring, wc, lu, m, N, lev_s, rhs, zc, P, zc, P, false);
   for (int it = 1; it < inner; ++it) {
-    __syncthreads();
+    T* wg = wglob + (size_t)a * ldN;
     for (int i = threadIdx.x; i < N; i += blockDim.x) {
       T v = rhs[i];
-      for (int e = rowptr[i]; e < rowptr[i + 1]; ++e) v -= blk[e] * Z[(size_t)col[e] * P + a];
-      w[i] = v;
+      for (int e = rowptr[i]; e < rowptr[i + 1]; ++e) v -= blk[e] * zc[(size_t)col[e] * P];
+      wg[i] = v;
     }
     __syncthreads();
-    ilu9_solve<T>(w, ring, wc, lu, m, N, lev_s);
-    for (int i = threadIdx.x; i < N; i += blockDim.x) Z[(size_t)i * P + a] += w[i];
+    window_solve<T>(win, ring, wc, lu, m, N, lev_s, wg, wg, 1, zc, P, true);
+    __syncthreads();
   }
 }
 
@@ -347,8 +590,8 @@ struct PcBufs<double> {
   static double* tmp(System& s) { return s.tmp.p; }
   static double* tmp2(System& s) { return s.tmp2.p; }
   static double* triw(System& s) { return s.tri_w.p; }
+  static bool full(const System& s) { return s.tri_full; }
   static const double* eg(const System& s) { return s.gs_eg.p; }
-  static bool smem(const System& s) { return s.tri_smem; }
 };
 template <>
 struct PcBufs<float> {
@@ -358,8 +601,8 @@ struct PcBufs<float> {
   static float* tmp(System& s) { return s.tmp32.p; }
   static float* tmp2(System& s) { return s.tmp232.p; }
   static float* triw(System& s) { return s.tri_w32.p; }
+  static bool full(const System& s) { return s.tri_full32; }
   static const float* eg(const System& s) { return s.gs_eg_f32.p; }
-  static bool smem(const System& s) { return s.tri_smem32; }
 };
 
 template <typename T>
@@ -370,34 +613,40 @@ int launch_columns(System& s, const T* R, T* Rt, cudaStream_t st, const int* don
   return check_launch("columns");
 }
 
-template <typename T, bool SMEM>
-int launch_block_solve_t(System& s, int a0, int ncols, int fac_per_col, const T* Rt, T* Z,
-                         cudaStream_t st, const int* done) {
-  using B = PcBufs<T>;
-  const int wc = s.tri_wc;
-  size_t smem = (SMEM ? sizeof(T) * (size_t)s.ldN : 0) + sizeof(T) * tri_ring_entries(wc) +
-                sizeof(int) * (size_t)(s.nlev9 + 1);
-  // a single-column (Gauss-Seidel) solve takes a whole SM: other kernels' CTAs that shared it
-  // would take issue slots from its dependency chain
-  if (ncols == 1) smem = std::max(smem, smem_optin_max());
-  auto kern = ilu_block_solve_kernel<T, SMEM>;
-  SG_TRY(ensure_smem((const void*)kern, smem));
-  TimeScope ts(s.timer, K_ILU_SOLVE, st);
-  kern<<<ncols, 2 * wc + 32, smem, st>>>(s.pat.m, s.N, s.ldN, s.P, s.pat.nnz, a0, fac_per_col,
-                                    s.lev9_off.p, s.nlev9, wc, B::lu9(s), s.rowptr.p, s.col.p,
-                                    B::blk(s), Rt, Z, SMEM ? nullptr : B::triw(s),
-                                    std::max(1, s.prm.inner_iters), done);
-  return check_launch("ilu_block_solve");
-}
-
 template <typename T>
 int launch_block_solve(System& s, int a0, int ncols, int fac_per_col, const T* Rt, T* Z,
                        cudaStream_t st, const int* done) {
   using B = PcBufs<T>;
-  if (s.tri_wc < 32 || 2 * s.tri_wc + 32 > kTriMaxThreads || s.ldN % 4 != 0)
+  const int wc = s.tri_wc;
+  const bool full = B::full(s);
+  const int nthreads = 2 * wc + (full ? 32 : tri_staging_threads(wc));
+  if (wc < 32 || nthreads > kTriMaxThreads || s.ldN % 4 != 0)
     return fail(SG_ERR_ARG, "wavefront solve: unsupported mesh width");
-  if (B::smem(s)) return launch_block_solve_t<T, true>(s, a0, ncols, fac_per_col, Rt, Z, st, done);
-  return launch_block_solve_t<T, false>(s, a0, ncols, fac_per_col, Rt, Z, st, done);
+  if (!full && s.prm.inner_iters > 1 && B::triw(s) == nullptr)
+    return fail(SG_ERR_ARG, "wavefront solve: no work column for inner iterations");
+  size_t smem = full ? sizeof(T) * ((size_t)s.ldN + tri_ring_entries(wc)) +
+                           sizeof(int) * (size_t)(s.nlev9 + 1)
+                     : tri_smem_bytes(s.pat.m, wc, sizeof(T));
+  // a single-column (Gauss-Seidel) solve takes a whole SM: other kernels' CTAs that shared it
+  // would take issue slots from its dependency chain
+  if (ncols == 1) smem = std::max(smem, smem_optin_max());
+  const int inner = std::max(1, s.prm.inner_iters);
+  if (full) {
+    auto kern = ilu_column_kernel<T>;
+    SG_TRY(ensure_smem((const void*)kern, smem));
+    TimeScope ts(s.timer, K_ILU_SOLVE, st);
+    kern<<<ncols, nthreads, smem, st>>>(s.pat.m, s.N, s.ldN, s.P, s.pat.nnz, a0, fac_per_col,
+                                        s.lev9_off.p, s.nlev9, wc, B::lu9(s), s.rowptr.p, s.col.p,
+                                        B::blk(s), Rt, Z, inner, done);
+  } else {
+    auto kern = ilu_window_kernel<T>;
+    SG_TRY(ensure_smem((const void*)kern, smem));
+    TimeScope ts(s.timer, K_ILU_SOLVE, st);
+    kern<<<ncols, nthreads, smem, st>>>(s.pat.m, s.N, s.ldN, s.P, s.pat.nnz, a0, fac_per_col,
+                                        s.lev9_off.p, s.nlev9, wc, B::lu9(s), s.rowptr.p, s.col.p,
+                                        B::blk(s), Rt, Z, B::triw(s), inner, done);
+  }
+  return check_launch("ilu_block_solve");
 }
 
 // Scatter of block b into column b + 1 (next = true) or into columns b + 2 .. P - 1.

@@ -323,16 +323,22 @@ static int setup_system(System& s, cudaStream_t st) {
   // smem budgets of the kernels
   size_t apply_smem = sizeof(double) * 4 * (9 * kChunkK + 9 * (size_t)s.P + kChunkPairs + s.P);
   if (apply_smem > 220 * 1024) return fail(SG_ERR_ARG, "P too large for the operator kernel");
-  {  // shared memory of the wavefront solve: column + factor rings + level offsets
+  {  // the wavefront solve: 2 wc compute and some staging threads; shared memory for its level
+     // window, factor rings and level offsets
     s.ldN = (s.N + 3) / 4 * 4;
     s.tri_wc = (interior_level_width(p.n + 1) + 31) / 32 * 32;
-    size_t ring = tri_ring_entries(s.tri_wc), lev = sizeof(int) * 3 * (size_t)(p.n + 1);
     const bool ilu = p.precond == SG_PC_MEAN || p.precond == SG_PC_FS_GS ||
                      p.precond == SG_PC_FS_JACOBI;
-    if (ilu && (8 * ring + lev > 220 * 1024 || 2 * s.tri_wc + 32 > 1024))
-      return fail(SG_ERR_ARG, "n must be at most 992 for the ILU(0) preconditioners");
-    s.tri_smem = (size_t)s.ldN * 8 + 8 * ring + lev <= 220 * 1024;
-    s.tri_smem32 = (size_t)s.ldN * 4 + 4 * ring + lev <= 220 * 1024;
+    if (ilu && (2 * s.tri_wc + tri_staging_threads(s.tri_wc) > 1024 ||
+                tri_smem_bytes(p.n + 1, s.tri_wc, 8) > 227 * 1024))
+      return fail(SG_ERR_ARG, "n must be at most 769 for the ILU(0) preconditioners");
+    auto column_fits = [&](size_t elem) {
+      return 2 * s.tri_wc + 32 <= 1024 &&
+             elem * ((size_t)s.ldN + tri_ring_entries(s.tri_wc)) + sizeof(int) * 3 * (size_t)(p.n + 1) <=
+                 227 * 1024;
+    };
+    s.tri_full = column_fits(8);
+    s.tri_full32 = column_fits(4);
   }
 
   // the system's own stream carries the critical path (GMRES, block solves); the second stream of
@@ -418,8 +424,10 @@ static int setup_system(System& s, cudaStream_t st) {
     const size_t PL = (size_t)s.P * s.ldN;
     SG_TRY(s.rhs_t.alloc(PL));
     if (lowp) SG_TRY(s.rhs_t32.alloc(PL));
-    if (!s.tri_smem) SG_TRY(s.tri_w.alloc(PL));
-    if (lowp && !s.tri_smem32) SG_TRY(s.tri_w32.alloc(PL));
+    if (p.inner_iters > 1) {
+      SG_TRY(s.tri_w.alloc(PL));
+      if (lowp) SG_TRY(s.tri_w32.alloc(PL));
+    }
   }
   if (p.outer_sweeps > 1) {
     SG_TRY(s.tmp.alloc(NP));

@@ -115,6 +115,14 @@ int interior_level_width(int m);
 // for wc threads per thread group (2 slots per level for one group, 3 for the other).
 constexpr int kTriAhead = 8;
 inline size_t tri_ring_entries(int wc) { return (size_t)kTriAhead * 5 * wc; }
+// Level rows held in shared memory by the wavefront solve, and its shared memory in bytes for a
+// mesh of m x m nodes: level window, factor rings, level offsets.
+constexpr int kTriWin = 16;
+// Staging threads of the wavefront solve: one warp per 64 rows of group width.
+inline int tri_staging_threads(int wc) { return 32 * (wc > 64 ? wc / 64 : 1); }
+inline size_t tri_smem_bytes(int m, int wc, size_t elem) {
+  return elem * ((size_t)kTriWin * m + tri_ring_entries(wc)) + sizeof(int) * (size_t)(3 * m - 1);
+}
 
 // ------------------------------------------------------------------ matvec work tables
 
@@ -179,6 +187,8 @@ struct System {
   int nlev9 = 0;
   int tri_wc = 0;              // threads per group of the wavefront solve (multiple of 32)
   int ldN = 0;                 // column stride of rhs_t / tri_w: N rounded up to a multiple of 4
+  bool tri_full = false;       // the FP64 (FP32) block solve holds the whole column on chip
+  bool tri_full32 = false;
   // field-split Gauss-Seidel scatter tables, per source block b: k list and (a, g) entries, for
   // the later columns a >= b + 2 (gs_*) and for the next column a = b + 1 (gsn_*)
   DBuf<int> gs_kptr, gs_k, gs_eptr, gs_ea;
@@ -192,10 +202,8 @@ struct System {
   DBuf<double> rhs_t;          // P columns of stride ldN: right-hand sides of the block solves
                                // (the Gauss-Seidel sweep subtracts sum_{b<a} K_ab z_b in place)
   DBuf<double> tmp, tmp2;      // N x P
-  DBuf<double> tri_w;          // P x ldN triangular-solve work (global variant)
+  DBuf<double> tri_w;          // P x ldN work columns of the inner ILU iterations
   DBuf<float> rhs_t32, tmp32, tmp232, tri_w32;
-  bool tri_smem = true;        // whether one column fits in shared memory
-  bool tri_smem32 = true;
   // GMRES workspace
   int m = 0;
   DBuf<double> V, Z, Hs, cs, sn, g, y, scal, red;  // see krylov.cu

@@ -44,9 +44,6 @@ extern "C" int sg_precond_apply_noalloc(sg_handle* h, int sys, const double* R, 
   if (s.prm.precond != SG_PC_FS_GS || s.prm.outer_sweeps != 1)
     return sg::fail(SG_ERR_ARG, "sg_precond_apply_noalloc serves the field-split Gauss-Seidel "
                                 "preconditioner with outer_sweeps = 1 only");
-  if (!s.tri_smem)
-    return sg::fail(SG_ERR_ARG, "sg_precond_apply_noalloc: the mesh is too large for the "
-                                "shared-memory block solve (it would need device scratch)");
   const long long need = (long long)s.P * s.ldN;
   if (need > SG_NOALLOC_MAX_ENTRIES)
     return sg::fail(SG_ERR_ARG, "sg_precond_apply_noalloc: P x ldN = " + std::to_string(need) +

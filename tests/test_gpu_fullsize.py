@@ -78,6 +78,34 @@ def test_fullsize_mean_preconditioner_defining_property():
     h.close()
 
 
+def test_large_mesh_block_solve_and_inner_iterations():
+    # n = 200 (40 401 nodes): the wavefront solve keeps only a window of level rows on chip.
+    # Defining property on sampled rows, then inner_iters = 2 against its definition
+    # z2 = z1 + ILU^{-1}(r - A_0 z1) built from two single applications.
+    d = dict(n=200, M=2, p=2, sigma=0.5, ell=0.5, precond="mean")
+    h1 = sg.sg_setup(sg.sg_default_params(**d))
+    N, P, _ = sg.sg_dims(h1)
+    R = W.random_field(N, P, seed=11)
+    Z1 = torch.empty(N, P, dtype=torch.float64, device="cuda")
+    sg.sg_precond_apply(h1, 0, torch.from_numpy(R).cuda(), Z1)
+    z1 = Z1.cpu().numpy()
+    A0 = _mean_stiffness(d)
+    Lo, Up = O.ilu0(A0)
+    rows = _sample_rows(d["n"], seed=12)
+    lhs = Lo[rows] @ (Up @ z1)
+    assert np.abs(lhs - R[rows]).max() <= 1e-11 * np.abs(R).max()
+    R2 = R - A0 @ z1
+    Z2 = torch.empty_like(Z1)
+    sg.sg_precond_apply(h1, 0, torch.from_numpy(R2).cuda(), Z2)
+    ref = z1 + Z2.cpu().numpy()
+    h2 = sg.sg_setup(sg.sg_default_params(**d, inner_iters=2))
+    Zi = torch.empty_like(Z1)
+    sg.sg_precond_apply(h2, 0, torch.from_numpy(R).cuda(), Zi)
+    assert np.abs(Zi.cpu().numpy() - ref).max() <= 1e-12 * np.abs(ref).max()
+    h1.close()
+    h2.close()
+
+
 def _mean_stiffness(d):
     """A_0 of the full mesh (the oracle's own assembly, chaos index 0 only)."""
     import scipy.sparse
