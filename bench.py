@@ -32,7 +32,7 @@ METRIC = "SG solves/sec & matvec HBM GB/s, mixed/learned vs FP64 GMRES at 1e-8 r
 WORKLOAD = ("c2: 128x128 Q1 mesh, M=4, p=3 (P=35, L=210), ell=0.5, sigma in {0.25,0.5,1.0,1.5}, "
             "FP64 GMRES(300) with field-split Gauss-Seidel + ILU(0), rel. residual 1e-10, x0 = 0")
 PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
-DFMA_PEAK_GFLOPS = 1192.0   # FP64 FMA loop on this GB300 (2 flops per DFMA), see the design doc
+DFMA_PEAK_GFLOPS = 1192.0   # measured FP64 FMA loop on GB300 (2 DFMA per clock per SM, 2 flops each)
 ITERS_FILE = os.path.join(ROOT, "oracle", "c2_iterations.json")
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "traffic.json")
 KERNEL_SOURCES = {"ilu_solve": "paper_1910_11505_gb300/csrc/k_precond.cu",
