@@ -571,6 +571,39 @@ __global__ void __launch_bounds__(128) fs_scatter_kernel(
   }
 }
 
+// After block b, for the next column only: Rt[b+1, i] -= sum_k G_k[b+1,b] (A_k z_b)[i], one
+// thread per row (the row's stencil values of z_b loaded once, then the short k list of the
+// next-column tables).  Same arithmetic order as fs_scatter_kernel: per k the stencil sum in
+// entry order, then the G-weighted sum in table order.
+template <typename T, typename TV>
+__global__ void __launch_bounds__(256) fs_next_kernel(
+    int N, int P, int ldN, int nnz, int b, const int* __restrict__ rowptr,
+    const int* __restrict__ col, const TV* __restrict__ stack_km, const int* __restrict__ kptr,
+    const int* __restrict__ klist, const int* __restrict__ eptr, const int* __restrict__ ek,
+    const T* __restrict__ eg, const T* __restrict__ Z, T* __restrict__ Rt,
+    const int* __restrict__ done) {
+  if (done != nullptr && *done) return;
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= N) return;
+  const int a = b + 1;
+  const int e0 = rowptr[i], ne = rowptr[i + 1] - e0;  // at most 9
+  T zc[9];
+#pragma unroll
+  for (int e = 0; e < 9; ++e) zc[e] = e < ne ? Z[(size_t)col[e0 + e] * P + b] : T(0);
+  const int k0 = kptr[b];
+  const int* ep = eptr + (size_t)b * (P + 1);
+  T s = T(0);
+  for (int q = ep[a]; q < ep[a + 1]; ++q) {
+    const TV* ak = stack_km + (size_t)klist[k0 + ek[q]] * nnz + e0;
+    T t = T(0);
+#pragma unroll
+    for (int e = 0; e < 9; ++e)
+      if (e < ne) t += (T)ak[e] * zc[e];
+    s += eg[q] * t;
+  }
+  Rt[(size_t)a * ldN + i] -= s;
+}
+
 template <typename T>
 __global__ void axpy_kernel(size_t n, const T* __restrict__ x, T* __restrict__ y,
                             const int* __restrict__ done) {
@@ -660,9 +693,9 @@ int launch_scatter_t(System& s, int b, bool next, const TV* stack_km, const T* e
   const int a_lo = next ? b + 1 : b + 2, a_hi = next ? b + 1 : s.P - 1;
   TimeScope ts(s.timer, K_GS_SCATTER, st);
   if (next)
-    kern<<<grid, 128, smem, st>>>(s.N, s.P, s.ldN, s.pat.nnz, b, a_lo, a_hi, s.rowptr.p, s.col.p,
-                                  stack_km, s.gsn_kptr.p, s.gsn_k.p, s.gsn_eptr.p, s.gsn_ea.p,
-                                  eg_next, Z, Rt, done);
+    fs_next_kernel<T, TV><<<(s.N + 255) / 256, 256, 0, st>>>(
+        s.N, s.P, s.ldN, s.pat.nnz, b, s.rowptr.p, s.col.p, stack_km, s.gsn_kptr.p, s.gsn_k.p,
+        s.gsn_eptr.p, s.gsn_ea.p, eg_next, Z, Rt, done);
   else
     kern<<<grid, 128, smem, st>>>(s.N, s.P, s.ldN, s.pat.nnz, b, a_lo, a_hi, s.rowptr.p, s.col.p,
                                   stack_km, s.gs_kptr.p, s.gs_k.p, s.gs_eptr.p, s.gs_ea.p,
