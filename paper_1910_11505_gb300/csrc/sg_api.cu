@@ -126,6 +126,13 @@ static int validate(const sg_params& p) {
   if (p.precision != SG_FP64 && !(p.inner_rtol > 0.0 && p.inner_rtol < 1.0))
     return fail(SG_ERR_ARG, "inner_rtol must be in (0, 1)");
   if (p.graphs != 0 && p.graphs != 1) return fail(SG_ERR_ARG, "graphs must be 0 or 1");
+  if (p.precond == SG_PC_MEAN || p.precond == SG_PC_FS_GS || p.precond == SG_PC_FS_JACOBI) {
+    // the wavefront solve: 2 wc compute and some staging threads; shared memory for its level
+    // window, factor rings and level offsets
+    const int wc = (interior_level_width(p.n + 1) + 31) / 32 * 32;
+    if (2 * wc + tri_staging_threads(wc) > 1024 || tri_smem_bytes(p.n + 1, wc, 8) > 227 * 1024)
+      return fail(SG_ERR_ARG, "n must be at most 769 for the ILU(0) preconditioners");
+  }
   return SG_OK;
 }
 
@@ -323,15 +330,10 @@ static int setup_system(System& s, cudaStream_t st) {
   // smem budgets of the kernels
   size_t apply_smem = sizeof(double) * 4 * (9 * kChunkK + 9 * (size_t)s.P + kChunkPairs + s.P);
   if (apply_smem > 220 * 1024) return fail(SG_ERR_ARG, "P too large for the operator kernel");
-  {  // the wavefront solve: 2 wc compute and some staging threads; shared memory for its level
-     // window, factor rings and level offsets
+  {  // wavefront solve: group width, and whether a whole column fits on chip (mesh size limits
+     // are checked in validate)
     s.ldN = (s.N + 3) / 4 * 4;
     s.tri_wc = (interior_level_width(p.n + 1) + 31) / 32 * 32;
-    const bool ilu = p.precond == SG_PC_MEAN || p.precond == SG_PC_FS_GS ||
-                     p.precond == SG_PC_FS_JACOBI;
-    if (ilu && (2 * s.tri_wc + tri_staging_threads(s.tri_wc) > 1024 ||
-                tri_smem_bytes(p.n + 1, s.tri_wc, 8) > 227 * 1024))
-      return fail(SG_ERR_ARG, "n must be at most 769 for the ILU(0) preconditioners");
     auto column_fits = [&](size_t elem) {
       return 2 * s.tri_wc + 32 <= 1024 &&
              elem * ((size_t)s.ldN + tri_ring_entries(s.tri_wc)) + sizeof(int) * 3 * (size_t)(p.n + 1) <=

@@ -58,7 +58,8 @@ def test_defaults_and_argument_errors_without_gpu(lib):
     assert p.rtol == 1e-10 and p.inner_rtol == 1e-4
     bad = [dict(n=1), dict(M=0), dict(M=9), dict(p=7), dict(ell=0.0), dict(sigma=-1.0),
            dict(restart=0), dict(restart=1025), dict(precond=9), dict(precision=3),
-           dict(inner_iters=0), dict(max_iters=0)]
+           dict(inner_iters=0), dict(max_iters=0), dict(n=1025),
+           dict(n=770, precond=sg.SG_PC_MEAN), dict(n=770, precond=sg.SG_PC_FS_GS)]
     for kw in bad:
         with pytest.raises(sg.SGError) as ei:
             sg.sg_setup(sg.sg_default_params(**kw), stream=0)
