@@ -1,8 +1,8 @@
 """Measurement runs of the configurations other than the default bench workload.
 
-    python -m paper_1910_11505_gb300.experiments c3            # FP64 vs mixed FP32 / BF16 solves
-    python -m paper_1910_11505_gb300.experiments c5 [ntrain] [ntest] [steps]   # learned warm start
-    python -m paper_1910_11505_gb300.experiments c4 [nsys]     # batch of uneven systems
+    python experiments.py c3            # FP64 vs mixed FP32 / BF16 solves
+    python experiments.py c5 [ntrain] [ntest] [steps]   # learned warm start
+    python experiments.py c4 [nsys]     # batch of uneven systems
 
 Each prints one JSON line.  Times are wall-clock around the C-ABI solve calls (the calls
 synchronise), with setup excluded and reported separately.
@@ -15,7 +15,7 @@ import os
 import sys
 import time
 
-ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+ROOT = os.path.dirname(os.path.abspath(__file__))
 if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 

@@ -114,6 +114,12 @@ int sg_matvec_lowp(sg_handle* h, int sys, const float* X, float* Y, void* stream
  * R, Z device N x P FP64, must not overlap.  Asynchronous on ``stream``. */
 int sg_precond_apply(sg_handle* h, int sys, const double* R, double* Z, void* stream);
 
+/* The same preconditioner application in FP32 arithmetic with the FP32 ILU(0) factors and the
+ * FP32 (SG_MIXED_FP32) or BF16 (SG_MIXED_BF16) stack copy used by the inner solver of the mixed
+ * forms; R, Z device N x P FP32, must not overlap.  SG_ERR_ARG for an FP64 system.
+ * Asynchronous on ``stream``. */
+int sg_precond_apply_lowp(sg_handle* h, int sys, const float* R, float* Z, void* stream);
+
 /* No counterpart in the paper: the same field-split Gauss-Seidel application as
  * sg_precond_apply (outer_sweeps = 1), for callers that must not allocate device memory, such as
  * a process whose device memory is already reserved by another allocator (a framework's caching
@@ -121,8 +127,9 @@ int sg_precond_apply(sg_handle* h, int sys, const double* R, double* Z, void* st
  * sides of the block solves as columns of ldN = N rounded up to a multiple of 4 entries, is a
  * fixed array of SG_NOALLOC_MAX_ENTRIES doubles (8 MiB) inside this library, which every GPU that
  * loads the library holds until the process exits; the call itself allocates nothing and
- * overwrites the part it uses from R before reading it.  The first call on a device looks up that array's device address, so
- * make that first call before any stream capture.  All calls share the one array: calls whose
+ * overwrites the part it uses from R before reading it.  Every call looks up that array's device
+ * address on the current device (the lookup allocates nothing); the first lookup on a device
+ * loads the library's module there, so make that first call before any stream capture.  All calls share the one array: calls whose
  * work overlaps on the GPU (other streams, other threads) race and give wrong results.
  * SG_ERR_ARG if the system does not use SG_PC_FS_GS with outer_sweeps = 1, if P x ldN exceeds
  * SG_NOALLOC_MAX_ENTRIES, or if the handle's device is not current.  R, Z as for sg_precond_apply.  Asynchronous on ``stream``. */

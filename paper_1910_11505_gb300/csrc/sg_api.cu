@@ -745,6 +745,13 @@ int sg_precond_apply(sg_handle* h, int sys, const double* R, double* Z, void* st
   return precond_apply_f64(*s, R, Z, (cudaStream_t)stream);
 }
 
+int sg_precond_apply_lowp(sg_handle* h, int sys, const float* R, float* Z, void* stream) {
+  System* s = get_sys(h, sys);
+  if (!s || !R || !Z) return fail(SG_ERR_ARG, "bad handle, system index or pointer");
+  if (s->prm.precision == SG_FP64) return fail(SG_ERR_ARG, "system has no low-precision factors");
+  return precond_apply_f32(*s, R, Z, (cudaStream_t)stream);
+}
+
 int sg_rhs(sg_handle* h, int sys, double* F, void* stream) {
   System* s = get_sys(h, sys);
   if (!s || !F) return fail(SG_ERR_ARG, "bad handle, system index or pointer");

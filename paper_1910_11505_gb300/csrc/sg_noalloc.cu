@@ -4,33 +4,25 @@
 // The Gauss-Seidel sweep keeps the right-hand sides of its P block solves as contiguous columns
 // (stride ldN = N rounded up to a multiple of 4), from which it subtracts the coupling
 // sum_{b<a} K_ab z_b.  Here they live in the file-scope array below, which every GPU that loads
-// the library holds until the process exits.  Host code cannot use the array's name as a device address (it names a host-side
-// stand-in), so the address is looked up once per device with cudaGetSymbolAddress, with that
-// device current, on the first call made on it.
-#include <mutex>
-
+// the library holds until the process exits.  Host code cannot use the array's name as a device
+// address (it names a host-side stand-in), so every call looks the address up with
+// cudaGetSymbolAddress on the current device.  The lookup allocates nothing, and since it is not
+// cached a context torn down and created again (cudaDeviceReset) never leaves a stale address.
+// The first lookup on a device loads the library's module there, so that first call should come
+// before any stream capture.
 #include "sg_internal.h"
 
 static __device__ __align__(256) double g_noalloc_scratch[SG_NOALLOC_MAX_ENTRIES];
 
 namespace {
 
-constexpr int kMaxDevices = 256;
-std::mutex g_mu;
-double* g_scratch_addr[kMaxDevices] = {};
-
-int scratch_for_current_device(int dev, double** out) {
-  if (dev < 0 || dev >= kMaxDevices) return sg::fail(SG_ERR_ARG, "device ordinal out of range");
-  std::lock_guard<std::mutex> lock(g_mu);
-  if (g_scratch_addr[dev] == nullptr) {
-    void* p = nullptr;
-    cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-    if (e != cudaSuccess || p == nullptr)
-      return sg::fail(SG_ERR_CUDA, std::string("cudaGetSymbolAddress of the scratch array failed: ") +
-                                       cudaGetErrorString(e));
-    g_scratch_addr[dev] = static_cast<double*>(p);
-  }
-  *out = g_scratch_addr[dev];
+int scratch_for_current_device(double** out) {
+  void* p = nullptr;
+  cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+  if (e != cudaSuccess || p == nullptr)
+    return sg::fail(SG_ERR_CUDA, std::string("cudaGetSymbolAddress of the scratch array failed: ") +
+                                     cudaGetErrorString(e));
+  *out = static_cast<double*>(p);
   return SG_OK;
 }
 
@@ -54,6 +46,6 @@ extern "C" int sg_precond_apply_noalloc(sg_handle* h, int sys, const double* R, 
   if (dev != h->device)
     return sg::fail(SG_ERR_ARG, "the handle's device must be current");
   double* rhs_t = nullptr;
-  SG_TRY(scratch_for_current_device(dev, &rhs_t));
+  SG_TRY(scratch_for_current_device(&rhs_t));
   return sg::fs_gs_apply_f64_with(s, R, Z, rhs_t, (cudaStream_t)stream);
 }

@@ -28,7 +28,8 @@ PRECONDS = {"none": SG_PC_NONE, "mean": SG_PC_MEAN, "fs_gs": SG_PC_FS_GS,
 PRECISIONS = {"fp64": SG_FP64, "fp32": SG_MIXED_FP32, "bf16": SG_MIXED_BF16}
 
 EXPORTED = ["sg_default_params", "sg_setup", "sg_dims", "sg_nnz", "sg_matvec", "sg_matvec_lowp",
-            "sg_precond_apply", "sg_precond_apply_noalloc", "sg_rhs", "sg_gmres_solve",
+            "sg_precond_apply", "sg_precond_apply_lowp", "sg_precond_apply_noalloc", "sg_rhs",
+            "sg_gmres_solve",
             "sg_export", "sg_launch_count",
             "sg_timing_start", "sg_timing_stop", "sg_free", "sg_last_error",
             "sgnet_create", "sgnet_set_stats", "sgnet_forward", "sgnet_predict", "sgnet_loss_grad",
@@ -83,6 +84,7 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.sg_matvec.argtypes = [vp, c_int, vp, vp, vp]
     lib.sg_matvec_lowp.argtypes = [vp, c_int, vp, vp, vp]
     lib.sg_precond_apply.argtypes = [vp, c_int, vp, vp, vp]
+    lib.sg_precond_apply_lowp.argtypes = [vp, c_int, vp, vp, vp]
     lib.sg_precond_apply_noalloc.argtypes = [vp, c_int, vp, vp, vp]
     lib.sg_rhs.argtypes = [vp, c_int, vp, vp]
     lib.sg_gmres_solve.argtypes = [vp, ctypes.POINTER(vp), ctypes.POINTER(vp),
@@ -116,7 +118,7 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.sg_last_error.argtypes = []
     lib.sg_last_error.restype = ctypes.c_char_p
     for name in ("sg_setup", "sg_dims", "sg_nnz", "sg_matvec", "sg_matvec_lowp", "sg_precond_apply",
-                 "sg_precond_apply_noalloc",
+                 "sg_precond_apply_lowp", "sg_precond_apply_noalloc",
                  "sg_rhs", "sg_gmres_solve", "sg_export", "sg_timing_start", "sg_timing_stop"):
         getattr(lib, name).restype = c_int
     _ = c_dbl
@@ -219,6 +221,11 @@ def sg_matvec_lowp(h: SGHandle, sys: int, X, Y, stream=None):
 def sg_precond_apply(h: SGHandle, sys: int, R, Z, stream=None):
     _check(load_library().sg_precond_apply(h.raw, sys, _ptr(R, "f64"), _ptr(Z, "f64"),
                                            _stream_ptr(stream)))
+
+
+def sg_precond_apply_lowp(h: SGHandle, sys: int, R, Z, stream=None):
+    _check(load_library().sg_precond_apply_lowp(h.raw, sys, _ptr(R, "f32"), _ptr(Z, "f32"),
+                                                _stream_ptr(stream)))
 
 
 def sg_precond_apply_noalloc(h: SGHandle, sys: int, R, Z, stream=None):

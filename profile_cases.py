@@ -1,9 +1,9 @@
 """Small, self-contained cases of single kernels for profiling (e.g. under ``ncu``).
 
-    python -m paper_1910_11505_gb300.profile_cases precond [fs_gs|fs_jacobi|mean] [n]
-    python -m paper_1910_11505_gb300.profile_cases matvec [fp64|fp32|bf16] [n] [M] [p]
-    python -m paper_1910_11505_gb300.profile_cases gmres [n] [iters]      # Arnoldi kernels
-    python -m paper_1910_11505_gb300.profile_cases net [batch]            # network training step
+    python profile_cases.py precond [fs_gs|fs_jacobi|mean] [n]
+    python profile_cases.py matvec [fp64|fp32|bf16] [n] [M] [p]
+    python profile_cases.py gmres [n] [iters]      # Arnoldi kernels
+    python profile_cases.py net [batch]            # network training step
 
 Each case builds one SG system, runs three applications of the chosen operation on seeded
 inputs and exits 0.  Sizes stay at a few GB of device memory.
@@ -14,7 +14,7 @@ from __future__ import annotations
 import os
 import sys
 
-ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+ROOT = os.path.dirname(os.path.abspath(__file__))
 if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 

@@ -114,6 +114,6 @@ def test_trained_network_reduces_gmres_iterations():
     assert ev["rc"] == (sg.SG_OK, sg.SG_OK)
     assert max(ev["warm_resid"]) <= 1e-8  # the final FP64 residual still decides
     zero, warm = np.array(ev["zero_iters"]), np.array(ev["warm_iters"])
-    assert warm.mean() < zero.mean(), ev
+    assert warm.mean() < 0.9 * zero.mean(), ev
     assert (warm <= zero).mean() >= 0.75, ev
     net.close()

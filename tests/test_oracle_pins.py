@@ -154,6 +154,75 @@ def test_kl_2d_ordering_and_ties():
     assert abs(kl.lam[0] - 0.25 * mu0 * mu0) < 1e-16
 
 
+def _gl01(npts, lo=0.0, hi=1.0):
+    t, w = np.polynomial.legendre.leggauss(npts)
+    return lo + (hi - lo) * (0.5 + 0.5 * t), 0.5 * (hi - lo) * w
+
+
+def test_kl_fields_are_sqrt_lambda_scaled_2d_eigenfunctions():
+    # Eq. aKL with Eq. standard_deviation: g_n = sqrt(lambda_n) b_n with b_n orthonormal on
+    # [0,1]^2 and C b_n = lambda_n b_n for C(x, y) = sigma^2 exp(-(|x1-y1| + |x2-y2|)/ell).
+    # So int g_n g_m = lambda_n delta_nm (fixes the sqrt(lambda) scaling), and the 2-D
+    # eigen-equation holds for g_n as written out from the covariance, not from the 1-D factors.
+    sigma, ell, M = 0.7, 0.5, 6
+    kl = O.kl_modes_2d(sigma, ell, M)
+    xs, ws = _gl01(60)
+    X1, X2 = np.meshgrid(xs, xs, indexing="ij")
+    W2 = np.outer(ws, ws)
+    g = O.kl_fields(kl, X1.ravel(), X2.ravel()).reshape(M, 60, 60)
+    gram = np.einsum("nij,mij,ij->nm", g, g, W2)
+    assert np.allclose(gram, np.diag(kl.lam), rtol=0, atol=1e-13)
+    for x in [(0.2, 0.7), (0.55, 0.31), (0.9, 0.05)]:
+        lhs = np.zeros(M)
+        # the kernel has kinks at y = x: split both directions there
+        for lo1, hi1 in ((0.0, x[0]), (x[0], 1.0)):
+            for lo2, hi2 in ((0.0, x[1]), (x[1], 1.0)):
+                y1, w1 = _gl01(40, lo1, hi1)
+                y2, w2 = _gl01(40, lo2, hi2)
+                Y1, Y2 = np.meshgrid(y1, y2, indexing="ij")
+                C = sigma ** 2 * np.exp(-(np.abs(x[0] - Y1) + np.abs(x[1] - Y2)) / ell)
+                gy = O.kl_fields(kl, Y1.ravel(), Y2.ravel()).reshape(M, *Y1.shape)
+                lhs += np.einsum("ij,nij->n", C * np.outer(w1, w2), gy)
+        gx = O.kl_fields(kl, [x[0]], [x[1]])[:, 0]
+        assert np.allclose(lhs, kl.lam * gx, rtol=0, atol=1e-12)
+
+
+def test_kl_fields_orientation_of_reading_r2():
+    # Reading R2 puts the first 1-D factor on x1.  The first 1-D mode is even about 1/2 and the
+    # second odd, so the mode with factors (0, 1) is even in x1 and odd in x2, and (1, 0) the
+    # reverse; a swap of x1 and x2 anywhere in the oracle flips these parities.
+    kl = O.kl_modes_2d(1.0, 1.0, 3)
+    assert kl.ij[1] == (0, 1) and kl.ij[2] == (1, 0)
+    rng = np.random.default_rng(5)
+    x1, x2 = rng.random(20), rng.random(20)
+    g = O.kl_fields(kl, x1, x2)
+    g_m1 = O.kl_fields(kl, 1.0 - x1, x2)
+    g_m2 = O.kl_fields(kl, x1, 1.0 - x2)
+    assert np.allclose(g_m1[1], g[1], atol=1e-14) and np.allclose(g_m2[1], -g[1], atol=1e-14)
+    assert np.allclose(g_m1[2], -g[2], atol=1e-14) and np.allclose(g_m2[2], g[2], atol=1e-14)
+    assert np.abs(g[1]).max() > 0.1 and np.abs(g[2]).max() > 0.1
+
+
+def test_kl_fields_mercer_partial_sums():
+    # Mercer: sum_n g_n(x)^2 -> C(x, x) = sigma^2 from below; the remainder is
+    # sum_{n>M} lambda_n b_n(x)^2 <= max|b|^2 (sigma^2 - sum_{n<=M} lambda_n).
+    sigma, ell = 0.8, 0.5
+    rng = np.random.default_rng(9)
+    x1, x2 = rng.random(15), rng.random(15)
+    prev = None
+    for M in (10, 60, 300):
+        kl = O.kl_modes_2d(sigma, ell, M)
+        s = np.sum(O.kl_fields(kl, x1, x2) ** 2, axis=0)
+        tail = sigma ** 2 - kl.lam.sum()
+        # |f| <= 1 / sqrt(1/2 - 1/(2 w)) for the normalised 1-D modes, so |b|^2 <= 4 here
+        assert np.all(s <= sigma ** 2 + 1e-12)
+        assert np.all(sigma ** 2 - s <= 4.0 * tail + 1e-12), (M, (sigma ** 2 - s).max(), tail)
+        if prev is not None:
+            assert np.all(s >= prev - 1e-14)
+        prev = s
+    assert tail < 0.03 * sigma ** 2
+
+
 # ------------------------------------------------------------------ FE assembly (Eq. A_q) and boundary data
 
 def test_sigma_zero_gives_q1_laplacian_stencil():
@@ -415,3 +484,23 @@ def test_sg_moments_converge_to_gauss_hermite_collocation():
     for (e1, e2), (f1, f2) in zip(errs, errs[1:]):
         assert f1 < 0.5 * e1 and f2 < 0.5 * e2, errs
     assert errs[-1][0] < 2e-6 * np.abs(Eu).max(), errs
+
+
+@pytest.mark.parametrize("n", [3, 4, 5, 6, 7, 8])
+def test_sampled_rows_equal_rows_of_the_assembled_operator(n):
+    # the row-sampled operator (built from the cells around each node) must reproduce every row
+    # of the pinned full operator: corner, edge, next-to-boundary and interior rows
+    prob = O.build_problem(n, M=2, p=2, sigma=0.6, ell=0.7, a_min=0.02, mu=0.05)
+    rng = np.random.default_rng(n)
+    X = rng.normal(size=(prob.N, prob.P))
+    Y = O.sg_matvec(prob, X)
+    rows = np.arange(prob.N)
+    got = O.sg_matvec_rows(n, rows, prob.kl, prob.Jq, prob.G, prob.a_min, prob.mu, X)
+    assert np.allclose(got, Y, rtol=0, atol=1e-13 * np.abs(Y).max())
+    cols, vals = O.stack_rows_dense(n, rows, prob.kl, prob.Jq, prob.a_min, prob.mu)
+    for r in rows:
+        for k in range(prob.L):
+            dense = prob.A[k].getrow(r).toarray()[0]
+            ref = np.zeros_like(dense)
+            ref[cols[r]] = vals[r][k]
+            assert np.allclose(dense, ref, rtol=0, atol=1e-14), (r, k)

@@ -24,14 +24,21 @@ def _built():
     assert torch.cuda.is_available()
 
 
-def test_noalloc_matches_regular_entry_point_twice():
-    prm = sg.sg_default_params(n=24, M=3, p=2, sigma=0.8, ell=0.7, precond="fs_gs")
+@pytest.mark.parametrize("n,M,p,inner", [
+    (24, 3, 2, 1),    # whole column of each block solve in shared memory
+    (24, 3, 2, 2),    # two ILU(0)-Richardson steps per block: the work columns are used too
+    (200, 3, 3, 1),   # a column too large for shared memory: the level-window kernel
+])
+def test_noalloc_matches_regular_entry_point_twice(n, M, p, inner):
+    prm = sg.sg_default_params(n=n, M=M, p=p, sigma=0.8, ell=0.7, precond="fs_gs",
+                               inner_iters=inner)
     h = sg.sg_setup(prm)
     N, P, _ = sg.sg_dims(h)
     for seed in (1, 2):  # two calls in a row with different inputs
         R = torch.from_numpy(W.random_field(N, P, seed=seed)).cuda()
         Zref = torch.empty_like(R)
         Z = torch.full_like(R, float("nan"))
+        assert P * ((N + 3) // 4 * 4) <= (1 << 20)
         sg.sg_precond_apply(h, 0, R, Zref)
         sg.sg_precond_apply_noalloc(h, 0, R, Z)
         torch.cuda.synchronize()
