@@ -42,6 +42,7 @@ __all__ = [
     "chaos_coefficients", "gauss_legendre_3", "q1_local_stiffness_stack",
     "SGProblem", "build_problem", "stack_rows_dense", "sg_matvec", "sg_matvec_rows",
     "ilu0", "ilu0_solve", "mean_precond", "fs_blocks", "fs_precond", "gmres", "boundary_mask",
+    "prolongation", "mg_levels", "mg_setup", "mg_vcycle",
 ]
 
 
@@ -577,3 +578,91 @@ def gmres(apply_K, apply_M, F, x0=None, restart=30, rtol=1e-10, atol=0.0, max_it
         restarts += 1
     return x, dict(iters=iters, restarts=restarts, rel_resid=beta / bnorm,
                    converged=beta <= target, history=history)
+
+
+# ----------------------------------------------------------------------------------------------
+# Geometric multigrid V-cycle (Sec. 3: GMRES preconditioned by MG, the level solver of
+# Eq. level_solver as smoother with i_max = 1 pre- and post-smoothing step, a direct solve on the
+# coarsest level; Sec. 4: V-cycle on the midpoint-refined hierarchy that starts from 2 x 2 cells).
+# Readings where the paper is silent:
+#   R16 each level is the same SG problem discretised on its own mesh (the paper's FE library
+#       assembles every level); the coarse space is the nested Q1 space, so the prolongation is
+#       bilinear interpolation and the restriction its transpose; boundary nodes carry no coarse
+#       unknowns (the coarse space keeps the zero Dirichlet condition).
+#   R17 pre- and post-smoothing are one step each of Eq. level_solver with the chosen block
+#       preconditioner (mean-based, field-split Gauss-Seidel or Jacobi), from zero for the
+#       pre-smoothing step.
+# ----------------------------------------------------------------------------------------------
+
+def prolongation(nc: int) -> scipy.sparse.csr_matrix:
+    """Bilinear interpolation from the nc x nc mesh to the 2nc x 2nc mesh (reading R16): an
+    (N_fine x N_coarse) matrix whose columns of coarse boundary nodes are zero."""
+    mc, mf = nc + 1, 2 * nc + 1
+    bc = boundary_mask(nc)
+    rows, cols, vals = [], [], []
+    for jf in range(mf):
+        for i_f in range(mf):
+            # coarse nodes around the fine node and their bilinear weights
+            xs = [(i_f // 2, 1.0)] if i_f % 2 == 0 else [(i_f // 2, 0.5), (i_f // 2 + 1, 0.5)]
+            ys = [(jf // 2, 1.0)] if jf % 2 == 0 else [(jf // 2, 0.5), (jf // 2 + 1, 0.5)]
+            for ic, wx in xs:
+                for jc, wy in ys:
+                    c = ic + mc * jc
+                    if not bc[c]:
+                        rows.append(i_f + mf * jf)
+                        cols.append(c)
+                        vals.append(wx * wy)
+    return scipy.sparse.csr_matrix((vals, (rows, cols)), shape=(mf * mf, mc * mc))
+
+
+def mg_levels(n, M, p, coarse=2, **kw):
+    """The SG problem on every mesh of the hierarchy coarse, 2 coarse, ..., n (reading R16),
+    coarsest first."""
+    sizes = [n]
+    while sizes[-1] > coarse:
+        if sizes[-1] % 2:
+            raise ValueError("n must be coarse times a power of two")
+        sizes.append(sizes[-1] // 2)
+    if sizes[-1] != coarse:
+        raise ValueError("n must be coarse times a power of two")
+    return [build_problem(s, M, p, **kw) for s in reversed(sizes)]
+
+
+def mg_setup(levels, smoother="fs_gs"):
+    """Per level: smoother data (ILU(0) factors), the prolongation from the level below, and the
+    dense coarsest-level operator for the direct solve."""
+    data = []
+    for li, prob in enumerate(levels):
+        d = {"P": prolongation(levels[li - 1].n) if li > 0 else None}
+        if li == 0:
+            d["K"] = sum(np.kron(prob.G[k], prob.A[k].toarray()) for k in range(prob.L))
+        elif smoother == "mean":
+            d["LU"] = ilu0(prob.A[0])
+        else:
+            d["blocks"] = fs_blocks(prob)
+        data.append(d)
+    return data
+
+
+def _smooth(prob, d, smoother, r):
+    if smoother == "mean":
+        return mean_precond(prob, r, LU=d["LU"])
+    return fs_precond(prob, r, mode="gs" if smoother == "fs_gs" else "jacobi", blocks=d["blocks"])
+
+
+def mg_vcycle(levels, data, b, smoother="fs_gs", level=None):
+    """One V-cycle for K u = b on ``level`` (default: finest) from u = 0 (Sec. 3): pre-smoothing,
+    restriction of the residual, the V-cycle of the level below, prolongation of its correction,
+    post-smoothing; the direct solve on the coarsest level."""
+    if level is None:
+        level = len(levels) - 1
+    prob, d = levels[level], data[level]
+    if level == 0:
+        x = np.linalg.solve(d["K"], b.T.ravel())          # mode-major unknown vector
+        return x.reshape(prob.P, prob.N).T
+    u = _smooth(prob, d, smoother, b)                     # Eq. level_solver from zero
+    r = b - sg_matvec(prob, u)
+    bc = d["P"].T @ r                                      # restriction = transpose
+    uc = mg_vcycle(levels, data, bc, smoother, level - 1)
+    u = u + d["P"] @ uc
+    return u + _smooth(prob, d, smoother, b - sg_matvec(prob, u))

@@ -504,3 +504,89 @@ def test_sampled_rows_equal_rows_of_the_assembled_operator(n):
             ref = np.zeros_like(dense)
             ref[cols[r]] = vals[r][k]
             assert np.allclose(dense, ref, rtol=0, atol=1e-14), (r, k)
+
+
+# ------------------------------------------------------------------ multigrid V-cycle (Sec. 3, Sec. 4)
+
+def test_prolongation_reproduces_the_coarse_finite_element_function():
+    # the fine nodal values of a coarse Q1 function are its values at the fine nodes; the coarse
+    # function is written out with hat functions, boundary nodes carrying zero (reading R16)
+    nc = 4
+    mc, mf, H = nc + 1, 2 * nc + 1, 1.0 / nc
+    rng = np.random.default_rng(2)
+    uc = rng.normal(size=mc * mc)
+    uc[O.boundary_mask(nc)] = 0.0
+    xf = (np.arange(mf * mf) % mf) / (2 * nc)
+    yf = (np.arange(mf * mf) // mf) / (2 * nc)
+    ref = np.zeros(mf * mf)
+    for c in range(mc * mc):
+        xc, yc = (c % mc) * H, (c // mc) * H
+        hat = np.clip(1 - np.abs(xf - xc) / H, 0, None) * np.clip(1 - np.abs(yf - yc) / H, 0, None)
+        ref += uc[c] * hat
+    assert np.allclose(O.prolongation(nc) @ uc, ref, rtol=0, atol=1e-15)
+
+
+def test_restricted_fine_stiffness_is_the_coarse_stiffness_for_constant_coefficient():
+    # Galerkin property of nested conforming spaces: with a constant coefficient (sigma = 0) the
+    # 3x3 Gauss rule integrates the Q1 stiffness exactly, so P^T A_h P = A_H on interior nodes
+    for nc in (2, 3, 5):
+        fine = O.build_problem(2 * nc, 1, 0, sigma=0.0, mu=0.3)
+        coarse = O.build_problem(nc, 1, 0, sigma=0.0, mu=0.3)
+        Pm = O.prolongation(nc)
+        galerkin = (Pm.T @ fine.A[0] @ Pm).toarray()
+        inner = ~O.boundary_mask(nc)
+        ref = coarse.A[0].toarray()[np.ix_(inner, inner)]
+        assert np.allclose(galerkin[np.ix_(inner, inner)], ref, rtol=0, atol=1e-13)
+
+
+def test_one_level_vcycle_is_the_direct_solve():
+    levels = O.mg_levels(2, 2, 2, coarse=2, sigma=0.6, ell=0.8)
+    data = O.mg_setup(levels)
+    prob = levels[0]
+    b = np.random.default_rng(4).normal(size=(prob.N, prob.P))
+    b[prob.boundary] = 0.0
+    u = O.mg_vcycle(levels, data, b)
+    assert np.allclose(O.sg_matvec(prob, u), b, rtol=0, atol=1e-13 * np.abs(b).max())
+
+
+@pytest.mark.parametrize("smoother,sigma", [("fs_gs", 0.5), ("fs_jacobi", 0.3), ("mean", 0.2)])
+def test_vcycle_iteration_contracts_independently_of_the_mesh(smoother, sigma):
+    # the V-cycle as a stationary iteration u <- u + V(F - K u): its error contraction per step
+    # must stay well below one and not degrade as the mesh is refined (Table 1's trend).  The
+    # mean-based smoother ignores the stochastic coupling, so it is checked at a smaller sigma.
+    rates = []
+    for n in (8, 16, 32):
+        levels = O.mg_levels(n, 2, 2, sigma=sigma, ell=0.7)
+        data = O.mg_setup(levels, smoother)
+        prob = levels[-1]
+        u = np.zeros_like(prob.F)
+        ref = scipy.sparse.linalg.spsolve(
+            scipy.sparse.csr_matrix(sum(scipy.sparse.kron(prob.G[k], prob.A[k])
+                                        for k in range(prob.L))).tocsc(),
+            prob.F.T.ravel()).reshape(prob.P, prob.N).T
+        errs = []
+        for _ in range(6):
+            u = u + O.mg_vcycle(levels, data, prob.F - O.sg_matvec(prob, u), smoother)
+            errs.append(np.linalg.norm(u - ref))
+        rates.append((errs[-1] / errs[1]) ** 0.25)
+    assert max(rates) < 0.5, rates
+    assert rates[-1] < rates[0] + 0.1, rates
+
+
+def test_mg_preconditioned_gmres_iterations_stay_flat_in_the_mesh():
+    its = []
+    for n in (8, 16, 32):
+        levels = O.mg_levels(n, 2, 2, sigma=0.5, ell=0.7)
+        data = O.mg_setup(levels, "fs_gs")
+        prob = levels[-1]
+
+        def apply_M(v, prob=prob, levels=levels, data=data):
+            V = v.reshape(prob.N, prob.P)
+            return O.mg_vcycle(levels, data, V).ravel()
+
+        _, info = O.gmres(lambda v, prob=prob: O.sg_matvec(prob, v.reshape(prob.N, prob.P)).ravel(),
+                          apply_M, prob.F, rtol=1e-10, restart=30)
+        assert info["converged"]
+        its.append(info["iters"])
+    assert max(its) - min(its) <= 2, its
+    assert max(its) <= 12, its
