@@ -41,6 +41,9 @@ extern "C" {
 #define SG_PC_MEAN 1       /* mean-based block diagonal I (x) ILU0(A_0) (Sec. 1, cited there)   */
 #define SG_PC_FS_GS 2      /* field split, block lower triangular P of Eq. P_preconditioner     */
 #define SG_PC_FS_JACOBI 3  /* field split, block diagonal of K                                  */
+#define SG_PC_MG 4         /* geometric multigrid V-cycle (Sec. 3): on every level one pre- and */
+                           /* one post-smoothing step of Eq. level_solver with the block        */
+                           /* preconditioner mg_smoother, a direct solve on the coarsest mesh   */
 
 #define SG_FP64 0          /* every step in FP64                                                */
 #define SG_MIXED_FP32 1    /* FP32 operator / preconditioner inside FP64 flexible GMRES + IR    */
@@ -71,6 +74,11 @@ typedef struct {
                      /* estimate drops below inner_rtol times the current true residual        */
   int graphs;        /* 1: capture each GMRES cycle of this system once as a CUDA graph (keyed  */
                      /* by cycle length and the F, X pointers) and replay it; 0: plain launches */
+  int mg_smoother;   /* SG_PC_MG: smoother of every level, SG_PC_MEAN | SG_PC_FS_GS |           */
+                     /* SG_PC_FS_JACOBI (G-M-F-I of the paper is SG_PC_FS_GS)                   */
+  int mg_coarse;     /* SG_PC_MG: cells per side of the coarsest mesh (the paper: 2); n must be  */
+                     /* mg_coarse times a power of two, and the coarsest interior system of     */
+                     /* (mg_coarse - 1)^2 P unknowns is solved with its dense inverse (<= 4096)  */
 } sg_params;
 
 typedef struct {
@@ -83,7 +91,7 @@ typedef struct {
 
 /* Fill ``prm`` with defaults: n=16, M=2, p=2, q=2p, sigma=0.5, ell=1, a_min=0, mu=0, f=1,
  * mean preconditioner, 1 inner / 1 outer step, restart 30, max_iters 2000, rtol 1e-10,
- * atol 0, FP64, inner_rtol 1e-4, graphs 0. */
+ * atol 0, FP64, inner_rtol 1e-4, graphs 0, mg_smoother SG_PC_FS_GS, mg_coarse 2. */
 void sg_default_params(sg_params* prm);
 
 /* Build ``nsys`` independent SG systems (Sec. 2: KL modes of Eq. gen_eigen in closed form,

@@ -750,15 +750,15 @@ int fs_gs_sweep(System& s, const T* R, T* D, T* Rt, cudaStream_t st, const int* 
   return SG_OK;
 }
 
-// One application of P^{-1} (no outer sweeps): D = P^{-1} R.
+// One application of the block preconditioner whose factors the system holds: D = P^{-1} R.
 template <typename T>
-int apply_once(System& s, const T* R, T* D, cudaStream_t st, const int* done) {
+int apply_block(System& s, const T* R, T* D, cudaStream_t st, const int* done) {
   using B = PcBufs<T>;
-  switch (s.prm.precond) {
+  switch (s.pc_fac) {
     case SG_PC_MEAN:
     case SG_PC_FS_JACOBI:
       SG_TRY(launch_columns<T>(s, R, B::rhs_t(s), st, done));
-      return launch_block_solve<T>(s, 0, s.P, s.prm.precond == SG_PC_FS_JACOBI ? 1 : 0,
+      return launch_block_solve<T>(s, 0, s.P, s.pc_fac == SG_PC_FS_JACOBI ? 1 : 0,
                                    B::rhs_t(s), D, st, done);
     case SG_PC_FS_GS:
       return fs_gs_sweep<T>(s, R, D, B::rhs_t(s), st, done, true);
@@ -783,6 +783,61 @@ int matvec_t<float>(const System& s, const float* X, float* Y, float alpha, cons
   return launch_matvec_f32(s, X, Y, alpha, Bv, beta, st, done);
 }
 
+template <typename T>
+int launch_axpy(System& s, size_t n, const T* x, T* y, cudaStream_t st, const int* done) {
+  TimeScope ts(s.timer, K_OTHER, st);
+  axpy_kernel<T><<<1216, 256, 0, st>>>(n, x, y, done);
+  return check_launch("axpy");
+}
+
+// Multigrid vectors of one level in the working precision.
+template <typename T>
+struct MgBufs;
+template <>
+struct MgBufs<double> {
+  static double* b(System& s) { return s.mg_b.p; }
+  static double* u(System& s) { return s.mg_u.p; }
+  static double* r(System& s) { return s.mg_r.p; }
+  static double* d(System& s) { return s.mg_d.p; }
+};
+template <>
+struct MgBufs<float> {
+  static float* b(System& s) { return s.mg_b32.p; }
+  static float* u(System& s) { return s.mg_u32.p; }
+  static float* r(System& s) { return s.mg_r32.p; }
+  static float* d(System& s) { return s.mg_d32.p; }
+};
+
+// One V-cycle (Sec. 3) for K u = b on level li of the hierarchy top.mg[0 .. ] + top, from u = 0:
+// one pre-smoothing step of Eq. level_solver (from zero: u = S^{-1} b), restriction of the
+// residual, the V-cycle of the level below, prolongation of its correction, one post-smoothing
+// step; the coarsest level is solved directly.
+template <typename T>
+int vcycle(System& top, int li, const T* b, T* u, cudaStream_t st, const int* done) {
+  using G = MgBufs<T>;
+  System& s = li == (int)top.mg.size() ? top : *top.mg[li];
+  if (li == 0) return launch_coarse_solve<T>(s, b, u, st, done);
+  System& c = *top.mg[li - 1];
+  T* r = G::r(s);
+  T* d = G::d(s);
+  const size_t n = (size_t)s.N * s.P;
+  SG_TRY(apply_block<T>(s, b, u, st, done));
+  SG_TRY(matvec_t<T>(s, u, r, T(-1), b, T(1), st, done));
+  SG_TRY(launch_restrict<T>(r, G::b(c), c.n, s.P, st, done, s.timer));
+  SG_TRY(vcycle<T>(top, li - 1, G::b(c), G::u(c), st, done));
+  SG_TRY(launch_prolong_add<T>(G::u(c), u, c.n, s.P, st, done, s.timer));
+  SG_TRY(matvec_t<T>(s, u, r, T(-1), b, T(1), st, done));
+  SG_TRY(apply_block<T>(s, r, d, st, done));
+  return launch_axpy<T>(s, n, d, u, st, done);
+}
+
+// One application of the system's preconditioner (no outer sweeps).
+template <typename T>
+int apply_once(System& s, const T* R, T* D, cudaStream_t st, const int* done) {
+  if (s.prm.precond == SG_PC_MG) return vcycle<T>(s, (int)s.mg.size(), R, D, st, done);
+  return apply_block<T>(s, R, D, st, done);
+}
+
 // Eq. level_solver from zero: Z = D_0; for i >= 1: Z += P^{-1}(R - K Z).
 template <typename T>
 int precond_apply_t(System& s, const T* R, T* Z, cudaStream_t st, const int* done) {
@@ -792,9 +847,7 @@ int precond_apply_t(System& s, const T* R, T* Z, cudaStream_t st, const int* don
   for (int sw = 1; sw < s.prm.outer_sweeps; ++sw) {
     SG_TRY(matvec_t<T>(s, Z, B::tmp(s), T(-1), R, T(1), st, done));
     SG_TRY(apply_once<T>(s, B::tmp(s), B::tmp2(s), st, done));
-    TimeScope ts(s.timer, K_OTHER, st);
-    axpy_kernel<T><<<1216, 256, 0, st>>>(n, B::tmp2(s), Z, done);
-    SG_TRY(check_launch("axpy"));
+    SG_TRY(launch_axpy<T>(s, n, B::tmp2(s), Z, st, done));
   }
   return SG_OK;
 }

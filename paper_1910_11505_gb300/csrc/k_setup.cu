@@ -300,7 +300,7 @@ int launch_rhs(System& s, double* F, cudaStream_t st) {
 int launch_block_values(System& s, cudaStream_t st) {
   std::vector<int> lptr(1, 0), lk;
   std::vector<double> lg;
-  if (s.prm.precond == SG_PC_MEAN) {
+  if (s.pc_fac == SG_PC_MEAN) {
     lk.push_back(0);
     lg.push_back(1.0);
     lptr.push_back(1);

@@ -117,7 +117,16 @@ static int validate(const sg_params& p) {
   if (!(p.sigma >= 0.0) || !(p.ell > 0.0) || !(p.a_min >= 0.0))
     return fail(SG_ERR_ARG, "need sigma >= 0, ell > 0, a_min >= 0");
   if (!std::isfinite(p.mu) || !std::isfinite(p.f)) return fail(SG_ERR_ARG, "mu and f must be finite");
-  if (p.precond < SG_PC_NONE || p.precond > SG_PC_FS_JACOBI) return fail(SG_ERR_ARG, "unknown preconditioner");
+  if (p.precond < SG_PC_NONE || p.precond > SG_PC_MG) return fail(SG_ERR_ARG, "unknown preconditioner");
+  if (p.precond == SG_PC_MG) {
+    if (p.mg_smoother != SG_PC_MEAN && p.mg_smoother != SG_PC_FS_GS && p.mg_smoother != SG_PC_FS_JACOBI)
+      return fail(SG_ERR_ARG, "mg_smoother must be SG_PC_MEAN, SG_PC_FS_GS or SG_PC_FS_JACOBI");
+    if (p.mg_coarse < 2) return fail(SG_ERR_ARG, "mg_coarse must be >= 2");
+    int nn = p.n;
+    while (nn > p.mg_coarse && nn % 2 == 0) nn /= 2;
+    if (nn != p.mg_coarse || p.n == p.mg_coarse)
+      return fail(SG_ERR_ARG, "multigrid needs n = mg_coarse * 2^k with k >= 1");
+  }
   if (p.inner_iters < 1 || p.outer_sweeps < 1) return fail(SG_ERR_ARG, "inner_iters and outer_sweeps must be >= 1");
   if (p.restart < 1 || p.restart > 1024) return fail(SG_ERR_ARG, "restart must be in [1, 1024]");
   if (p.max_iters < 1) return fail(SG_ERR_ARG, "max_iters must be >= 1");
@@ -126,7 +135,8 @@ static int validate(const sg_params& p) {
   if (p.precision != SG_FP64 && !(p.inner_rtol > 0.0 && p.inner_rtol < 1.0))
     return fail(SG_ERR_ARG, "inner_rtol must be in (0, 1)");
   if (p.graphs != 0 && p.graphs != 1) return fail(SG_ERR_ARG, "graphs must be 0 or 1");
-  if (p.precond == SG_PC_MEAN || p.precond == SG_PC_FS_GS || p.precond == SG_PC_FS_JACOBI) {
+  if (p.precond == SG_PC_MEAN || p.precond == SG_PC_FS_GS || p.precond == SG_PC_FS_JACOBI ||
+      p.precond == SG_PC_MG) {
     // the wavefront solve: 2 wc compute and some staging threads; shared memory for its level
     // window, factor rings and level offsets
     const int wc = (interior_level_width(p.n + 1) + 31) / 32 * 32;
@@ -285,6 +295,11 @@ static int build_gs_tables(System& s, cudaStream_t st) {
 
 static void free_system(System* s) {
   if (!s) return;
+  for (System* c : s->mg) free_system(c);
+  s->mg.clear();
+  for (auto* b : {&s->mg_b, &s->mg_u, &s->mg_r, &s->mg_d, &s->mg_inv}) b->release();
+  for (auto* b : {&s->mg_b32, &s->mg_u32, &s->mg_r32, &s->mg_d32, &s->mg_inv32}) b->release();
+  s->mg_nodes.release();
   if (s->stream) cudaStreamSynchronize(s->stream);
   if (s->stream2) cudaStreamSynchronize(s->stream2);
   DBuf<int>* ib[] = {&s->rowptr, &s->col, &s->diag, &s->lev_f_ptr, &s->lev_f_rows, &s->lev_b_ptr,
@@ -317,9 +332,10 @@ static void free_system(System* s) {
   delete s;
 }
 
-static int setup_system(System& s, cudaStream_t st) {
+static int setup_system(System& s, cudaStream_t st, bool krylov = true) {
   sg_params& p = s.prm;
   if (p.q <= 0) p.q = 2 * p.p;
+  s.pc_fac = p.precond == SG_PC_MG ? p.mg_smoother : p.precond;
   s.n = p.n;
   s.M = p.M;
   s.pat = make_pattern(p.n);
@@ -398,8 +414,8 @@ static int setup_system(System& s, cudaStream_t st) {
 
   // preconditioner blocks and factors
   const size_t NP = (size_t)s.N * s.P;
-  if (p.precond == SG_PC_MEAN || p.precond == SG_PC_FS_GS || p.precond == SG_PC_FS_JACOBI) {
-    s.nfac = p.precond == SG_PC_MEAN ? 1 : s.P;
+  if (s.pc_fac == SG_PC_MEAN || s.pc_fac == SG_PC_FS_GS || s.pc_fac == SG_PC_FS_JACOBI) {
+    s.nfac = s.pc_fac == SG_PC_MEAN ? 1 : s.P;
     SG_TRY(s.blk.alloc((size_t)s.nfac * s.pat.nnz));
     SG_TRY(s.fac.alloc((size_t)s.nfac * s.pat.nnz));
     SG_TRY(launch_block_values(s, st));
@@ -411,7 +427,7 @@ static int setup_system(System& s, cudaStream_t st) {
       SG_TRY(launch_cast_f32(s.lu9.p, s.lu9_f32.p, s.lu9.n, st));
       SG_TRY(launch_cast_f32(s.blk.p, s.blk_f32.p, s.blk.n, st));
     }
-    if (p.precond == SG_PC_FS_GS) {
+    if (s.pc_fac == SG_PC_FS_GS) {
       SG_TRY(build_gs_tables(s, st));
       SG_TRY(s.stack_km.alloc(nnzL));
       SG_TRY(launch_transpose(s.stack.p, s.stack_km.p, (size_t)s.pat.nnz, s.L, st));
@@ -438,6 +454,12 @@ static int setup_system(System& s, cudaStream_t st) {
       SG_TRY(s.tmp32.alloc(NP));
       SG_TRY(s.tmp232.alloc(NP));
     }
+  }
+
+  if (p.precond == SG_PC_MG) SG_TRY(mg_setup_levels(s, st));
+  if (!krylov) {
+    SG_CUDA(cudaStreamSynchronize(st));
+    return SG_OK;
   }
 
   // GMRES workspace
@@ -467,6 +489,9 @@ static int setup_system(System& s, cudaStream_t st) {
   SG_CUDA(cudaStreamSynchronize(st));
   return SG_OK;
 }
+
+int setup_system_public(System& s, cudaStream_t st, bool krylov) { return setup_system(s, st, krylov); }
+void free_system_public(System* s) { free_system(s); }
 
 static System* get_sys(const sg_handle* h, int sys) {
   if (!h || sys < 0 || sys >= (int)h->sys.size()) return nullptr;
@@ -683,6 +708,8 @@ void sg_default_params(sg_params* p) {
   p->precision = SG_FP64;
   p->inner_rtol = 1e-4;
   p->graphs = 0;
+  p->mg_smoother = SG_PC_FS_GS;
+  p->mg_coarse = 2;
 }
 
 int sg_setup(const sg_params* prm, int nsys, void* stream, sg_handle** out) {

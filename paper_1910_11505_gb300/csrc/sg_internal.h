@@ -155,6 +155,8 @@ struct Triple {
 
 struct System {
   sg_params prm;
+  int pc_fac = SG_PC_NONE;     // block preconditioner whose factors this system holds: prm.precond,
+                               // or the smoother of a multigrid system (prm.mg_smoother)
   int N = 0, P = 0, L = 0, M = 0, n = 0;
   long long nnzG = 0;
   Pattern pat;
@@ -227,6 +229,18 @@ struct System {
   // block solve, and the events ordering the two streams
   cudaStream_t stream2 = nullptr;
   cudaEvent_t ev_z = nullptr, ev_r[2] = {nullptr, nullptr};
+  // multigrid (SG_PC_MG): the coarser levels, coarsest first, each a System on its own mesh with
+  // the same stochastic data; per level the V-cycle's right-hand side b, iterate u, residual r and
+  // smoother correction d (the finest level uses the caller's R and Z as b and u)
+  std::vector<System*> mg;
+  DBuf<double> mg_b, mg_u, mg_r, mg_d;
+  DBuf<float> mg_b32, mg_u32, mg_r32, mg_d32;
+  // coarsest level only: dense inverse of its interior SG matrix (nint P x nint P, row-major,
+  // unknown index t * P + a for interior node t) and the interior node ids
+  int mg_nint = 0;
+  DBuf<double> mg_inv;
+  DBuf<float> mg_inv32;
+  DBuf<int> mg_nodes;
 };
 
 }  // namespace sg
@@ -266,6 +280,21 @@ int precond_apply_f32(System& s, const float* R, float* Z, cudaStream_t st,
 // One field-split Gauss-Seidel application (outer_sweeps = 1) whose right-hand-side columns live
 // in the caller's array ``rhs_t`` of P x ldN doubles (filled here from R).
 int fs_gs_apply_f64_with(System& s, const double* R, double* Z, double* rhs_t, cudaStream_t st);
+
+// Multigrid (k_mg.cu): the level hierarchy and dense coarsest inverse (setup), and the grid
+// transfers: restriction (transpose of bilinear interpolation, zero on coarse boundary nodes)
+// and prolongation added into the fine iterate.
+int mg_setup_levels(System& s, cudaStream_t st);
+template <typename T>
+int launch_restrict(const T* rf, T* bc, int nc, int P, cudaStream_t st, const int* done,
+                    Timer* timer);
+template <typename T>
+int launch_prolong_add(const T* uc, T* uf, int nc, int P, cudaStream_t st, const int* done,
+                       Timer* timer);
+template <typename T>
+int launch_coarse_solve(const System& c, const T* b, T* u, cudaStream_t st, const int* done);
+void free_system_public(System* s);
+int setup_system_public(System& s, cudaStream_t st, bool krylov);
 
 // Krylov launchers (k_krylov.cu)
 int k_norm(System& s, size_t n, const double* r, double* out, cudaStream_t st);

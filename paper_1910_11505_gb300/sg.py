@@ -20,11 +20,11 @@ SG_ERR_OOM = -3
 SG_ERR_NAN = -4
 SG_ERR_NOT_CONVERGED = -5
 
-SG_PC_NONE, SG_PC_MEAN, SG_PC_FS_GS, SG_PC_FS_JACOBI = 0, 1, 2, 3
+SG_PC_NONE, SG_PC_MEAN, SG_PC_FS_GS, SG_PC_FS_JACOBI, SG_PC_MG = 0, 1, 2, 3, 4
 SG_FP64, SG_MIXED_FP32, SG_MIXED_BF16 = 0, 1, 2
 
 PRECONDS = {"none": SG_PC_NONE, "mean": SG_PC_MEAN, "fs_gs": SG_PC_FS_GS,
-            "fs_jacobi": SG_PC_FS_JACOBI}
+            "fs_jacobi": SG_PC_FS_JACOBI, "mg": SG_PC_MG}
 PRECISIONS = {"fp64": SG_FP64, "fp32": SG_MIXED_FP32, "bf16": SG_MIXED_BF16}
 
 EXPORTED = ["sg_default_params", "sg_setup", "sg_dims", "sg_nnz", "sg_matvec", "sg_matvec_lowp",
@@ -52,7 +52,8 @@ class sg_params(ctypes.Structure):
                 ("inner_iters", ctypes.c_int), ("outer_sweeps", ctypes.c_int),
                 ("restart", ctypes.c_int), ("max_iters", ctypes.c_int), ("rtol", ctypes.c_double),
                 ("atol", ctypes.c_double), ("precision", ctypes.c_int),
-                ("inner_rtol", ctypes.c_double), ("graphs", ctypes.c_int)]
+                ("inner_rtol", ctypes.c_double), ("graphs", ctypes.c_int),
+                ("mg_smoother", ctypes.c_int), ("mg_coarse", ctypes.c_int)]
 
 
 class sg_solve_info(ctypes.Structure):
@@ -157,7 +158,7 @@ def sg_default_params(**overrides) -> sg_params:
     p = sg_params()
     load_library().sg_default_params(ctypes.byref(p))
     for k, v in overrides.items():
-        if k == "precond" and isinstance(v, str):
+        if k in ("precond", "mg_smoother") and isinstance(v, str):
             v = PRECONDS[v]
         if k == "precision" and isinstance(v, str):
             v = PRECISIONS[v]

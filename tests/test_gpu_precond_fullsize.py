@@ -64,8 +64,9 @@ def test_field_split_elementwise_at_solver_sizes(d, mode, inner):
 # FP32 bound: each block solve is two triangular sweeps over ~3m levels in FP32 (unit roundoff
 # u = 6e-8); the forward error of a triangular solve grows with the number of dependent steps and
 # the factors' condition, and the Gauss-Seidel sweep carries the error of each block into the
-# right-hand sides of the later ones.  The bound 1e-4 relative is ~1700 u.
-FP32_TOL = 1e-4
+# right-hand sides of the later ones.  These blocks are diagonally dominant, so the factors are
+# well conditioned and the error stays at a few u (1.4 u measured); the bound is 17 u.
+FP32_TOL = 1e-6
 
 
 @pytest.mark.parametrize("d,mode", [(C2, "gs"), (WIN, "jacobi")])
