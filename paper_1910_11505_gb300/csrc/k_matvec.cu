@@ -159,11 +159,14 @@ int launch_apply(const System& s, const TV* stack, const TA* eg, const TA* X, TA
 
 int launch_matvec_f64(const System& s, const double* X, double* Y, double alpha, const double* B,
                       double beta, cudaStream_t st, const int* done) {
+  if (s.tile64.ready) return launch_tile_op<double>(s, s.tile64, X, Y, alpha, B, beta, st, done);
   return launch_apply<double, double>(s, s.stack.p, s.ent_g.p, X, Y, alpha, B, beta, st, done);
 }
 
 int launch_matvec_f32(const System& s, const float* X, float* Y, float alpha, const float* B,
                       float beta, cudaStream_t st, const int* done) {
+  if (s.tile32.ready && s.prm.precision == SG_MIXED_FP32)
+    return launch_tile_op<float>(s, s.tile32, X, Y, alpha, B, beta, st, done);
   if (s.prm.precision == SG_MIXED_BF16)
     return launch_apply<float, __nv_bfloat16>(s, s.stack_bf16.p, s.ent_g_f32.p, X, Y, alpha, B,
                                               beta, st, done);

@@ -104,6 +104,7 @@ template struct DBuf<double>;
 template struct DBuf<float>;
 template struct DBuf<int>;
 template struct DBuf<int2>;
+template struct DBuf<int4>;
 template struct DBuf<unsigned int>;
 template struct DBuf<__nv_bfloat16>;
 
@@ -295,6 +296,8 @@ static int build_gs_tables(System& s, cudaStream_t st) {
 
 static void free_system(System* s) {
   if (!s) return;
+  free_tile_op(s->tile64);
+  free_tile_op(s->tile32);
   for (System* c : s->mg) free_system(c);
   s->mg.clear();
   for (auto* b : {&s->mg_b, &s->mg_u, &s->mg_r, &s->mg_d, &s->mg_inv}) b->release();
@@ -410,6 +413,18 @@ static int setup_system(System& s, cudaStream_t st, bool krylov = true) {
   } else if (p.precision == SG_MIXED_BF16) {
     SG_TRY(s.stack_bf16.alloc(nnzL));
     SG_TRY(launch_cast_bf16(s.stack.p, s.stack_bf16.p, nnzL, st));
+  }
+  // the row-tiled operator where its shared-memory budget allows (else the pair kernel serves)
+  {
+    const size_t smax = smem_optin_max();
+    if (build_tile_op(s, s.tile64, 2, 8, smax, st) != SG_OK) {
+      free_tile_op(s.tile64);
+      set_error("");
+    }
+    if (p.precision == SG_MIXED_FP32 && build_tile_op(s, s.tile32, 4, 4, smax, st) != SG_OK) {
+      free_tile_op(s.tile32);
+      set_error("");
+    }
   }
 
   // preconditioner blocks and factors

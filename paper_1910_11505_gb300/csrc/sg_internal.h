@@ -151,6 +151,23 @@ struct Triple {
   double g;
 };
 
+// Row-tiled operator (k_apply_tile.cu): k permuted into groups of kappa with similar b lists,
+// chunks of at most 8 groups, per group the union b list (b | mask << 16, first slot), per
+// (chunk, a) the stage-2 entries (slot, G), and the stack stored per tile of 32 interior rows of
+// one grid line as [k position][entry][row].
+struct TileOp {
+  bool ready = false;
+  int kappa = 0, elem = 0, tiles_per_line = 0, ntiles = 0, Pp = 0, Lu = 0;
+  int nchunks = 0, ngroups = 0, max_chunk_k = 0, max_slots = 0, apw = 0;
+  int abuf_elems = 0, tbuf_elems = 0, xslab_elems = 0;
+  size_t smem = 0;
+  DBuf<int4> chunk, group;
+  DBuf<int2> ulist;
+  DBuf<int> ent_ptr, ent_slot, err;
+  DBuf<double> ent_g, stack;
+  DBuf<float> ent_g32, stack32;
+};
+
 // ------------------------------------------------------------------ per-system state
 
 struct System {
@@ -178,6 +195,7 @@ struct System {
   DBuf<int2> chunks_k;
   DBuf<double> ent_g;
   DBuf<float> ent_g_f32;
+  TileOp tile64, tile32;       // row-tiled operator in FP64 / FP32 (when built)
   // device: preconditioner
   int nfac = 0;                // number of factor sets (1 for mean, P for field split)
   DBuf<double> blk;            // nfac x nnz block matrices (A_0 or K_aa) before factorisation
@@ -295,6 +313,13 @@ template <typename T>
 int launch_coarse_solve(const System& c, const T* b, T* u, cudaStream_t st, const int* done);
 void free_system_public(System* s);
 int setup_system_public(System& s, cudaStream_t st, bool krylov);
+
+// Row-tiled operator (k_apply_tile.cu)
+int build_tile_op(System& s, TileOp& op, int kappa, int elem, size_t smem_max, cudaStream_t st);
+void free_tile_op(TileOp& op);
+template <typename T>
+int launch_tile_op(const System& s, const TileOp& op, const T* X, T* Y, T alpha, const T* B,
+                   T beta, cudaStream_t st, const int* done);
 
 // Krylov launchers (k_krylov.cu)
 int k_norm(System& s, size_t n, const double* r, double* out, cudaStream_t st);
