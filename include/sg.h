@@ -166,6 +166,20 @@ int sg_gmres_solve(sg_handle* h, const double* const* F, double* const* X, sg_so
  * k then a then b (nnz_G x 4 doubles).  Synchronous.  SG_ERR_ARG if ``bytes`` is too small. */
 int sg_export(const sg_handle* h, int sys, int what, void* dst, size_t bytes);
 
+/* Which SG operator kernel system ``sys`` runs: info[0..3] for the FP64 operator and info[4..7]
+ * for the FP32 one, each {kernel (0 none, 1 pair kernel, 2 row-tiled kernel), kappa, shared
+ * memory bytes, chunks}; ``msg`` (msg_len bytes, may be NULL) receives why a row-tiled operator
+ * was not built ("" if it was). */
+int sg_op_info(const sg_handle* h, int sys, long long* info, char* msg, int msg_len);
+
+/* For tests and the operator tuner, host only (no device work): plan the row-tiled operator of a
+ * system with these sizes for kappa = 1..4 k per register group, in FP64 (precision SG_FP64) or
+ * FP32 (any other precision), under a shared-memory budget of smem_max bytes per CTA.  For each
+ * kappa, out[8 (kappa - 1) + i] is {fits, shared-memory bytes, chunks, largest chunk's T slots,
+ * (k, b) pairs placed, stage-2 entries placed, k kept, k groups} (fits = 0: the rest is 0).
+ * ``out`` holds 32 values.  SG_ERR_ARG for invalid sizes. */
+int sg_tune_plan(int n, int M, int p, int q, int precision, long long smem_max, long long* out);
+
 /* Count of kernel launches this library has queued since load (all handles, all threads). */
 long long sg_launch_count(void);
 

@@ -315,9 +315,9 @@ __global__ void tile_stack_kernel(int m, int tiles_per_line, int ntiles, int Lu,
 
 // ------------------------------------------------------------------ host: tables and launch
 
-int build_tile_op(System& s, TileOp& op, int kappa, int elem, size_t smem_max, cudaStream_t st) {
+int plan_tile_op(const System& s, int kappa, int elem, size_t smem_max, TilePlan& op) {
   const int P = s.P, L = s.L, m = s.pat.m;
-  op = TileOp();
+  op = TilePlan();
   op.kappa = kappa;
   op.elem = elem;
   if (m < 3 || kappa < 1 || kappa > 4 || P > 256) return fail(SG_ERR_ARG, "tile operator: unsupported sizes");
@@ -451,28 +451,60 @@ int build_tile_op(System& s, TileOp& op, int kappa, int elem, size_t smem_max, c
   op.smem = 128 + (size_t)elem * (2 * (size_t)op.abuf_elems + op.tbuf_elems + op.xslab_elems);
   if (op.smem > smem_max) return fail(SG_ERR_ARG, "tile operator: shared memory budget exceeded");
   op.apw = (P + kWarps - 1) / kWarps;
-  SG_TRY(op.chunk.alloc(cdesc.size()));
-  SG_TRY(op.chunk.upload(cdesc, st));
-  SG_TRY(op.group.alloc(gdesc.size()));
-  SG_TRY(op.group.upload(gdesc, st));
-  SG_TRY(op.ulist.alloc(ul.size()));
-  SG_TRY(op.ulist.upload(ul, st));
-  SG_TRY(op.ent_ptr.alloc(eptr.size()));
-  SG_TRY(op.ent_ptr.upload(eptr, st));
-  SG_TRY(op.ent_slot.alloc(eslot.size()));
-  SG_TRY(op.ent_slot.upload(eslot, st));
+  op.pairs = (long long)std::count_if(pair_slot.begin(), pair_slot.end(), [](int v) { return v >= 0; });
+  op.entries = (long long)eslot.size();
+  op.cdesc.swap(cdesc);
+  op.gdesc.swap(gdesc);
+  op.ul.swap(ul);
+  op.kperm.swap(kperm);
+  op.eptr.swap(eptr);
+  op.eslot.swap(eslot);
+  op.eg.swap(eg);
+  return SG_OK;
+}
+
+int build_tile_op(System& s, TileOp& op, int kappa, int elem, size_t smem_max, cudaStream_t st) {
+  TilePlan pl;
+  op = TileOp();
+  SG_TRY(plan_tile_op(s, kappa, elem, smem_max, pl));
+  const int m = s.pat.m, L = s.L;
+  op.kappa = pl.kappa;
+  op.elem = pl.elem;
+  op.tiles_per_line = pl.tiles_per_line;
+  op.ntiles = pl.ntiles;
+  op.Pp = pl.Pp;
+  op.Lu = pl.Lu;
+  op.nchunks = pl.nchunks;
+  op.ngroups = pl.ngroups;
+  op.max_chunk_k = pl.max_chunk_k;
+  op.max_slots = pl.max_slots;
+  op.apw = pl.apw;
+  op.abuf_elems = pl.abuf_elems;
+  op.tbuf_elems = pl.tbuf_elems;
+  op.xslab_elems = pl.xslab_elems;
+  op.smem = pl.smem;
+  SG_TRY(op.chunk.alloc(pl.cdesc.size()));
+  SG_TRY(op.chunk.upload(pl.cdesc, st));
+  SG_TRY(op.group.alloc(pl.gdesc.size()));
+  SG_TRY(op.group.upload(pl.gdesc, st));
+  SG_TRY(op.ulist.alloc(pl.ul.size()));
+  SG_TRY(op.ulist.upload(pl.ul, st));
+  SG_TRY(op.ent_ptr.alloc(pl.eptr.size()));
+  SG_TRY(op.ent_ptr.upload(pl.eptr, st));
+  SG_TRY(op.ent_slot.alloc(pl.eslot.size()));
+  SG_TRY(op.ent_slot.upload(pl.eslot, st));
   if (elem == 8) {
-    SG_TRY(op.ent_g.alloc(eg.size()));
-    SG_TRY(op.ent_g.upload(eg, st));
+    SG_TRY(op.ent_g.alloc(pl.eg.size()));
+    SG_TRY(op.ent_g.upload(pl.eg, st));
   } else {
-    std::vector<float> ef(eg.begin(), eg.end());
+    std::vector<float> ef(pl.eg.begin(), pl.eg.end());
     SG_TRY(op.ent_g32.alloc(ef.size()));
     SG_TRY(op.ent_g32.upload(ef, st));
   }
   // the tiled stack
   DBuf<int> dperm;
-  SG_TRY(dperm.alloc(kperm.size()));
-  SG_TRY(dperm.upload(kperm, st));
+  SG_TRY(dperm.alloc(pl.kperm.size()));
+  SG_TRY(dperm.upload(pl.kperm, st));
   const size_t total = (size_t)op.ntiles * op.Lu * 9 * kTW;
   const int grid = (int)std::min<size_t>((total + 255) / 256, 152 * 64);
   if (elem == 8) {

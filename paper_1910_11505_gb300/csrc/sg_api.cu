@@ -219,6 +219,16 @@ static int build_tables(System& s) {
   return SG_OK;
 }
 
+int host_tables(System& s) {
+  sg_params& p = s.prm;
+  if (p.q <= 0) p.q = 2 * p.p;
+  s.n = p.n;
+  s.M = p.M;
+  s.pat = make_pattern(p.n);
+  s.N = s.pat.N;
+  return build_tables(s);
+}
+
 static int upload_i(DBuf<int>& d, const std::vector<int>& h, cudaStream_t st) {
   SG_TRY(d.alloc(h.size()));
   return d.upload(h, st);
@@ -418,10 +428,12 @@ static int setup_system(System& s, cudaStream_t st, bool krylov = true) {
   {
     const size_t smax = smem_optin_max();
     if (build_tile_op(s, s.tile64, 2, 8, smax, st) != SG_OK) {
+      s.tile_msg = "fp64: " + g_last_error;
       free_tile_op(s.tile64);
       set_error("");
     }
     if (p.precision == SG_MIXED_FP32 && build_tile_op(s, s.tile32, 4, 4, smax, st) != SG_OK) {
+      s.tile_msg += " fp32: " + g_last_error;
       free_tile_op(s.tile32);
       set_error("");
     }
@@ -851,6 +863,56 @@ int sg_export(const sg_handle* h, int sys, int what, void* dst, size_t bytes) {
 }
 
 long long sg_launch_count(void) { return g_launches.load(); }
+
+int sg_op_info(const sg_handle* h, int sys, long long* info, char* msg, int msg_len) {
+  System* s = get_sys(h, sys);
+  if (!s || !info) return fail(SG_ERR_ARG, "bad handle, system index or pointer");
+  const TileOp* ops[2] = {&s->tile64, &s->tile32};
+  for (int i = 0; i < 2; ++i) {
+    info[4 * i + 0] = ops[i]->ready ? 2 : 1;
+    info[4 * i + 1] = ops[i]->ready ? ops[i]->kappa : 0;
+    info[4 * i + 2] = ops[i]->ready ? (long long)ops[i]->smem : 0;
+    info[4 * i + 3] = ops[i]->ready ? ops[i]->nchunks : 0;
+  }
+  if (s->prm.precision == SG_FP64) info[4] = 0;
+  if (msg && msg_len > 0) {
+    std::strncpy(msg, s->tile_msg.c_str(), (size_t)msg_len - 1);
+    msg[msg_len - 1] = 0;
+  }
+  return SG_OK;
+}
+
+int sg_tune_plan(int n, int M, int p, int q, int precision, long long smem_max, long long* out) {
+  if (!out) return fail(SG_ERR_ARG, "out is NULL");
+  sg_params prm;
+  sg_default_params(&prm);
+  prm.n = n;
+  prm.M = M;
+  prm.p = p;
+  prm.q = q;
+  SG_TRY(validate(prm));
+  System s;
+  s.prm = prm;
+  SG_TRY(host_tables(s));
+  const int elem = precision == SG_FP64 ? 8 : 4;
+  for (int kappa = 1; kappa <= 4; ++kappa) {
+    long long* o = out + 8 * (kappa - 1);
+    for (int i = 0; i < 8; ++i) o[i] = 0;
+    TilePlan pl;
+    const int rc = plan_tile_op(s, kappa, elem, (size_t)smem_max, pl);
+    set_error("");
+    o[0] = rc == SG_OK;
+    if (rc != SG_OK) continue;
+    o[1] = (long long)pl.smem;
+    o[2] = pl.nchunks;
+    o[3] = pl.max_slots;
+    o[4] = pl.pairs;
+    o[5] = pl.entries;
+    o[6] = pl.Lu;
+    o[7] = pl.ngroups;
+  }
+  return SG_OK;
+}
 
 int sg_timing_start(sg_handle* h, int stride) {
   if (!h || stride < 1) return fail(SG_ERR_ARG, "bad handle or stride");

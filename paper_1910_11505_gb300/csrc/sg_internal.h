@@ -168,6 +168,19 @@ struct TileOp {
   DBuf<float> ent_g32, stack32;
 };
 
+// Host-side plan of the row-tiled operator (tables before upload).
+struct TilePlan {
+  int kappa = 0, elem = 0, tiles_per_line = 0, ntiles = 0, Pp = 0, Lu = 0;
+  int nchunks = 0, ngroups = 0, max_chunk_k = 0, max_slots = 0, apw = 0;
+  int abuf_elems = 0, tbuf_elems = 0, xslab_elems = 0;
+  size_t smem = 0;
+  long long pairs = 0, entries = 0;
+  std::vector<int4> cdesc, gdesc;
+  std::vector<int2> ul;
+  std::vector<int> kperm, eptr, eslot;
+  std::vector<double> eg;
+};
+
 // ------------------------------------------------------------------ per-system state
 
 struct System {
@@ -196,6 +209,7 @@ struct System {
   DBuf<double> ent_g;
   DBuf<float> ent_g_f32;
   TileOp tile64, tile32;       // row-tiled operator in FP64 / FP32 (when built)
+  std::string tile_msg;        // why a row-tiled operator was not built (empty if it was)
   // device: preconditioner
   int nfac = 0;                // number of factor sets (1 for mean, P for field split)
   DBuf<double> blk;            // nfac x nnz block matrices (A_0 or K_aa) before factorisation
@@ -315,7 +329,11 @@ void free_system_public(System* s);
 int setup_system_public(System& s, cudaStream_t st, bool krylov);
 
 // Row-tiled operator (k_apply_tile.cu)
+int plan_tile_op(const System& s, int kappa, int elem, size_t smem_max, TilePlan& plan);
 int build_tile_op(System& s, TileOp& op, int kappa, int elem, size_t smem_max, cudaStream_t st);
+// Host-only setup pieces used by the planner entry point: the mesh pattern, the chaos index sets
+// and the triple products of a parameter set.
+int host_tables(System& s);
 void free_tile_op(TileOp& op);
 template <typename T>
 int launch_tile_op(const System& s, const TileOp& op, const T* X, T* Y, T alpha, const T* B,

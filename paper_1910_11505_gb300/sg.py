@@ -30,7 +30,7 @@ PRECISIONS = {"fp64": SG_FP64, "fp32": SG_MIXED_FP32, "bf16": SG_MIXED_BF16}
 EXPORTED = ["sg_default_params", "sg_setup", "sg_dims", "sg_nnz", "sg_matvec", "sg_matvec_lowp",
             "sg_precond_apply", "sg_precond_apply_lowp", "sg_precond_apply_noalloc", "sg_rhs",
             "sg_gmres_solve",
-            "sg_export", "sg_launch_count",
+            "sg_export", "sg_launch_count", "sg_tune_plan", "sg_op_info",
             "sg_timing_start", "sg_timing_stop", "sg_free", "sg_last_error",
             "sgnet_create", "sgnet_set_stats", "sgnet_forward", "sgnet_predict", "sgnet_loss_grad",
             "sgnet_adam_step", "sgnet_train_step", "sgnet_num_params", "sgnet_get", "sgnet_set",
@@ -91,6 +91,11 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.sg_gmres_solve.argtypes = [vp, ctypes.POINTER(vp), ctypes.POINTER(vp),
                                    ctypes.POINTER(sg_solve_info), vp]
     lib.sg_export.argtypes = [vp, c_int, c_int, vp, ctypes.c_size_t]
+    lib.sg_tune_plan.argtypes = [c_int, c_int, c_int, c_int, c_int, ctypes.c_longlong,
+                                 ctypes.POINTER(ctypes.c_longlong)]
+    lib.sg_tune_plan.restype = c_int
+    lib.sg_op_info.argtypes = [vp, c_int, ctypes.POINTER(ctypes.c_longlong), ctypes.c_char_p, c_int]
+    lib.sg_op_info.restype = c_int
     lib.sg_launch_count.argtypes = []
     lib.sg_launch_count.restype = ctypes.c_longlong
     lib.sg_timing_start.argtypes = [vp, c_int]
@@ -222,6 +227,31 @@ def sg_matvec_lowp(h: SGHandle, sys: int, X, Y, stream=None):
 def sg_precond_apply(h: SGHandle, sys: int, R, Z, stream=None):
     _check(load_library().sg_precond_apply(h.raw, sys, _ptr(R, "f64"), _ptr(Z, "f64"),
                                            _stream_ptr(stream)))
+
+
+def sg_op_info(h: SGHandle, sys: int = 0):
+    """Operator kernels of a system: {"fp64": {...}, "fp32": {...}, "msg": str}."""
+    info = (ctypes.c_longlong * 8)()
+    msg = ctypes.create_string_buffer(512)
+    _check(load_library().sg_op_info(h.raw, sys, info, msg, 512))
+    names = {0: "none", 1: "pairs", 2: "tile"}
+    out = {}
+    for i, key in enumerate(("fp64", "fp32")):
+        out[key] = {"kernel": names[int(info[4 * i])], "kappa": int(info[4 * i + 1]),
+                    "smem": int(info[4 * i + 2]), "chunks": int(info[4 * i + 3])}
+    out["msg"] = msg.value.decode()
+    return out
+
+
+def sg_tune_plan(n, M, p, q=0, precision="fp64", smem_max=232448):
+    """Host-only plan of the row-tiled operator for kappa = 1..4 (see include/sg.h): a list of
+    dicts with keys fits, smem, chunks, max_slots, pairs, entries, k_kept, groups."""
+    if isinstance(precision, str):
+        precision = PRECISIONS[precision]
+    out = (ctypes.c_longlong * 32)()
+    _check(load_library().sg_tune_plan(n, M, p, q, precision, smem_max, out))
+    keys = ["fits", "smem", "chunks", "max_slots", "pairs", "entries", "k_kept", "groups"]
+    return [dict(zip(keys, out[8 * i:8 * i + 8])) for i in range(4)]
 
 
 def sg_precond_apply_lowp(h: SGHandle, sys: int, R, Z, stream=None):
