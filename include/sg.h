@@ -79,7 +79,16 @@ typedef struct {
   int mg_coarse;     /* SG_PC_MG: cells per side of the coarsest mesh (the paper: 2); n must be  */
                      /* mg_coarse times a power of two, and the coarsest interior system of     */
                      /* (mg_coarse - 1)^2 P unknowns is solved with its dense inverse (<= 4096)  */
+  int op_kernel;     /* SG operator kernel: SG_OP_AUTO (time the candidates on this system at   */
+                     /* setup, keep the fastest; the choice is cached per N, P, L and precision */
+                     /* for the process), SG_OP_PAIRS or SG_OP_TILE                             */
+  int op_kappa;      /* SG_OP_TILE: k per register group, 1, 2 or 4 (0: 2 in FP64, 4 in FP32)   */
+  int op_ctas;       /* SG_OP_TILE: CTAs per SM the shared memory is planned for, 1 or 2 (0: 1) */
 } sg_params;
+
+#define SG_OP_AUTO 0   /* choose by timing (see op_kernel)                                      */
+#define SG_OP_PAIRS 1  /* one CTA per 4 rows, (k, b) pairs over threads, operands in shared mem */
+#define SG_OP_TILE 2   /* 32 rows of a grid line per CTA, one per lane, k groups in registers  */
 
 typedef struct {
   int iters;         /* GMRES iterations (all cycles; inner FGMRES iterations in mixed mode)  */
@@ -91,7 +100,8 @@ typedef struct {
 
 /* Fill ``prm`` with defaults: n=16, M=2, p=2, q=2p, sigma=0.5, ell=1, a_min=0, mu=0, f=1,
  * mean preconditioner, 1 inner / 1 outer step, restart 30, max_iters 2000, rtol 1e-10,
- * atol 0, FP64, inner_rtol 1e-4, graphs 0, mg_smoother SG_PC_FS_GS, mg_coarse 2. */
+ * atol 0, FP64, inner_rtol 1e-4, graphs 0, mg_smoother SG_PC_FS_GS, mg_coarse 2,
+ * op_kernel SG_OP_AUTO, op_kappa 0, op_ctas 0. */
 void sg_default_params(sg_params* prm);
 
 /* Build ``nsys`` independent SG systems (Sec. 2: KL modes of Eq. gen_eigen in closed form,
@@ -172,12 +182,13 @@ int sg_export(const sg_handle* h, int sys, int what, void* dst, size_t bytes);
  * was not built ("" if it was). */
 int sg_op_info(const sg_handle* h, int sys, long long* info, char* msg, int msg_len);
 
-/* For tests and the operator tuner, host only (no device work): plan the row-tiled operator of a
- * system with these sizes for kappa = 1..4 k per register group, in FP64 (precision SG_FP64) or
- * FP32 (any other precision), under a shared-memory budget of smem_max bytes per CTA.  For each
- * kappa, out[8 (kappa - 1) + i] is {fits, shared-memory bytes, chunks, largest chunk's T slots,
- * (k, b) pairs placed, stage-2 entries placed, k kept, k groups} (fits = 0: the rest is 0).
- * ``out`` holds 32 values.  SG_ERR_ARG for invalid sizes. */
+/* For tests, host only (no device work): plan the row-tiled operator of a system with these sizes
+ * in FP64 (precision SG_FP64) or FP32 (any other precision) for the six variants kappa in {1, 2, 4}
+ * k per register group x 1 or 2 CTAs per SM (rows 0..5, CTAs outer), under a shared-memory budget
+ * of smem_max bytes per SM (halved per CTA for two CTAs).  Row r is out[12 r .. 12 r + 11] =
+ * {kappa, CTAs, fits, shared-memory bytes, chunks, largest chunk's T slots, (k, b) pairs placed,
+ * stage-2 entries placed, k kept, k groups, tables verified by decoding them as the kernel does,
+ * budget}; ``out`` holds 72 values.  SG_ERR_ARG for invalid sizes. */
 int sg_tune_plan(int n, int M, int p, int q, int precision, long long smem_max, long long* out);
 
 /* Count of kernel launches this library has queued since load (all handles, all threads). */

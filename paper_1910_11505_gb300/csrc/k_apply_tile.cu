@@ -24,266 +24,17 @@
 // Every wait on an mbarrier is bounded: after kWaitLimit polls the kernel raises the error word,
 // waits (bounded again) for its own copies in flight and returns with NaN in the rows it owns.
 #include <algorithm>
+#include <array>
 #include <cmath>
 #include <cstring>
+#include <map>
 #include <numeric>
 
-#include "sg_internal.h"
+#include "k_apply_tile.cuh"
 
 namespace sg {
 
 namespace {
-
-constexpr int kTW = 32;       // rows per tile
-constexpr int kWarps = 8;     // warps per CTA: groups per chunk and a-strides of stage 2
-constexpr int kSlab = kTW + 2;
-constexpr long long kWaitLimit = 1LL << 22;
-
-struct TileDims {
-  int m, tiles_per_line, ntiles, P, Pp, nchunks;
-  int abuf_elems, tbuf_elems, xslab_elems;
-};
-
-__device__ __forceinline__ unsigned smem_u32(const void* p) {
-  return (unsigned)__cvta_generic_to_shared(p);
-}
-
-__device__ __forceinline__ void mbar_init(unsigned long long* bar, unsigned count) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(smem_u32(bar)), "r"(count) : "memory");
-}
-
-__device__ __forceinline__ void mbar_expect_tx(unsigned long long* bar, unsigned bytes) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(smem_u32(bar)),
-               "r"(bytes)
-               : "memory");
-}
-
-__device__ __forceinline__ bool mbar_try_wait(unsigned long long* bar, unsigned parity) {
-  unsigned ok;
-  asm volatile(
-      "{\n"
-      ".reg .pred p;\n"
-      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
-      "selp.u32 %0, 1, 0, p;\n"
-      "}\n"
-      : "=r"(ok)
-      : "r"(smem_u32(bar)), "r"(parity)
-      : "memory");
-  return ok != 0;
-}
-
-// Bounded wait for the given phase parity of an mbarrier.
-__device__ __forceinline__ bool mbar_wait_bounded(unsigned long long* bar, unsigned parity) {
-  for (long long it = 0; it < kWaitLimit; ++it)
-    if (mbar_try_wait(bar, parity)) return true;
-  return false;
-}
-
-__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, unsigned bytes,
-                                         unsigned long long* bar) {
-  asm volatile(
-      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n" ::"r"(
-          smem_u32(dst)),
-      "l"(src), "r"(bytes), "r"(smem_u32(bar))
-      : "memory");
-}
-
-template <typename T>
-__device__ __forceinline__ T nan_of();
-template <>
-__device__ __forceinline__ double nan_of<double>() { return __longlong_as_double(0x7ff8000000000000LL); }
-template <>
-__device__ __forceinline__ float nan_of<float>() { return __int_as_float(0x7fc00000); }
-
-template <typename T, int KAPPA, int APW>
-__global__ void __launch_bounds__(kWarps * 32, 1) sg_apply_tile_kernel(
-    TileDims d, const int4* __restrict__ chunk, const int4* __restrict__ group,
-    const int2* __restrict__ ulist, const int* __restrict__ ent_ptr,
-    const int* __restrict__ ent_slot, const T* __restrict__ ent_g, const T* __restrict__ stack,
-    const T* __restrict__ X, T* __restrict__ Y, T alpha, const T* __restrict__ B, T beta,
-    const int* __restrict__ done, int* __restrict__ err) {
-  if (done != nullptr && *done) return;
-  extern __shared__ __align__(128) unsigned char smem_raw[];
-  unsigned long long* bar = reinterpret_cast<unsigned long long*>(smem_raw);  // 2 barriers
-  int* s_fail = reinterpret_cast<int*>(smem_raw + 16);
-  T* Abuf0 = reinterpret_cast<T*>(smem_raw + 128);
-  T* Abuf1 = Abuf0 + d.abuf_elems;
-  T* Ts = Abuf1 + d.abuf_elems;
-  T* Xs = Ts + d.tbuf_elems;
-  const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
-  const int P = d.P, Pp = d.Pp, m = d.m;
-
-  if (tid == 0) {
-    mbar_init(&bar[0], 1);
-    mbar_init(&bar[1], 1);
-    *s_fail = 0;
-    asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
-    asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
-  }
-  __syncthreads();
-
-  // the stack of tile t starts at t * kstride elements; chunk c at chunk[c].x * 9 * 32 within it
-  const size_t kstride = (size_t)chunk[d.nchunks - 1].x * 9 * kTW + (size_t)chunk[d.nchunks - 1].y * 9 * kTW;
-  auto issue = [&](int t, int c, int slot) {
-    const int4 cd = chunk[c];
-    const unsigned bytes = (unsigned)((size_t)cd.y * 9 * kTW * sizeof(T));
-    T* dst = slot ? Abuf1 : Abuf0;
-    const T* src = stack + (size_t)t * kstride + (size_t)cd.x * 9 * kTW;
-    mbar_expect_tx(&bar[slot], bytes);
-    bulk_g2s(dst, src, bytes, &bar[slot]);
-  };
-
-  T acc[APW];
-  long long it = 0;  // work items (tile, chunk) of this CTA so far
-  bool next_issued = false;  // whether the copy of item it + 1 is in flight
-  if (blockIdx.x < d.ntiles && tid == 0) issue(blockIdx.x, 0, 0);
-  bool failed = false;
-
-  for (int t = blockIdx.x; t < d.ntiles && !failed; t += gridDim.x) {
-    const int y = 1 + t / d.tiles_per_line;
-    const int x0 = 1 + (t % d.tiles_per_line) * kTW;
-    const int nrows = min(kTW, m - 1 - x0);
-    // X on lines y-1, y, y+1 for nodes x0-1 .. x0+32 (zero beyond the mesh)
-    for (int idx = tid; idx < 3 * kSlab * P; idx += blockDim.x) {
-      const int dy = idx / (kSlab * P);
-      const int rem = idx - dy * kSlab * P;
-      const int xi = rem / P, b = rem - xi * P;
-      const int x = x0 - 1 + xi;
-      T v = T(0);
-      if (x < m) v = X[((size_t)(y - 1 + dy) * m + x) * P + b];
-      Xs[(dy * kSlab + xi) * Pp + b] = v;
-    }
-#pragma unroll
-    for (int j = 0; j < APW; ++j) acc[j] = T(0);
-
-    for (int c = 0; c < d.nchunks; ++c, ++it) {
-      // prefetch the next work item into the other slot (its last reader finished before the
-      // barrier that closed the previous item)
-      if (tid == 0) {
-        int tn = t, cn = c + 1;
-        if (cn == d.nchunks) {
-          tn = t + gridDim.x;
-          cn = 0;
-        }
-        if (tn < d.ntiles) {
-          issue(tn, cn, (int)((it + 1) & 1));
-          next_issued = true;
-        } else {
-          next_issued = false;
-        }
-      }
-      const int slot = (int)(it & 1);
-      if (!mbar_wait_bounded(&bar[slot], (unsigned)((it >> 1) & 1))) *s_fail = 1;
-      __syncthreads();
-      if (*s_fail) {
-        failed = true;
-        break;
-      }
-      const T* Ab = slot ? Abuf1 : Abuf0;
-      const int4 cd = chunk[c];
-      // ---- stage 1: T for the pairs of this warp's group
-      if (w < cd.w) {
-        const int4 gd = group[cd.z + w];  // ulist start, length, first k position, k count
-        T a[KAPPA][9];
-#pragma unroll
-        for (int j = 0; j < KAPPA; ++j) {
-          if (j < gd.w) {
-#pragma unroll
-            for (int e = 0; e < 9; ++e) a[j][e] = Ab[((size_t)(gd.z + j) * 9 + e) * kTW + lane];
-          } else {
-#pragma unroll
-            for (int e = 0; e < 9; ++e) a[j][e] = T(0);
-          }
-        }
-        const int2* ul = ulist + gd.x;
-        for (int u = 0; u < gd.y; ++u) {
-          const int2 ue = ul[u];
-          const int b = ue.x & 0xffff, mask = ue.x >> 16;
-          int sl = ue.y;
-          T xv[9];
-#pragma unroll
-          for (int dy = 0; dy < 3; ++dy)
-#pragma unroll
-            for (int dx = 0; dx < 3; ++dx) xv[dy * 3 + dx] = Xs[(dy * kSlab + lane + dx) * Pp + b];
-#pragma unroll
-          for (int j = 0; j < KAPPA; ++j) {
-            if (mask & (1 << j)) {
-              T s = a[j][0] * xv[0];
-#pragma unroll
-              for (int e = 1; e < 9; ++e) s = fma(a[j][e], xv[e], s);
-              Ts[(size_t)sl * kTW + lane] = s;
-              ++sl;
-            }
-          }
-        }
-      }
-      __syncthreads();
-      // ---- stage 2: Y[row, a] += sum G T over this chunk's entries of the warp's outputs
-      const int* ep = ent_ptr + (size_t)c * (P + 1);
-#pragma unroll
-      for (int j = 0; j < APW; ++j) {
-        const int a = w + kWarps * j;
-        if (a < P) {
-          T s = T(0);
-          const int q1 = ep[a + 1];
-          for (int q = ep[a]; q < q1; ++q) s = fma(ent_g[q], Ts[(size_t)ent_slot[q] * kTW + lane], s);
-          acc[j] += s;
-        }
-      }
-      __syncthreads();
-    }
-    if (failed) break;
-    // ---- epilogue: Y rows of the tile through shared memory (coalesced)
-#pragma unroll
-    for (int j = 0; j < APW; ++j) {
-      const int a = w + kWarps * j;
-      if (a < P) Ts[(size_t)a * kTW + lane] = acc[j];
-    }
-    __syncthreads();
-    const size_t row0 = (size_t)y * m + x0;
-    for (int idx = tid; idx < nrows * P; idx += blockDim.x) {
-      const int r = idx / P, a = idx - r * P;
-      const size_t o = row0 * P + idx;
-      T v = alpha * Ts[(size_t)a * kTW + r];
-      if (B != nullptr) v = fma(beta, B[o], v);
-      Y[o] = v;
-    }
-    __syncthreads();
-  }
-  if (failed) {
-    // a bulk copy did not complete in time: record it, let the copies this CTA issued land
-    // (bounded), and leave NaN in every row of the CTA's tiles so no caller takes them as results
-    if (tid == 0) {
-      atomicExch(err, 1);
-      mbar_wait_bounded(&bar[it & 1], (unsigned)((it >> 1) & 1));
-      if (next_issued) mbar_wait_bounded(&bar[(it + 1) & 1], (unsigned)(((it + 1) >> 1) & 1));
-    }
-    __syncthreads();
-    for (int t = blockIdx.x; t < d.ntiles; t += gridDim.x) {
-      const int y = 1 + t / d.tiles_per_line;
-      const int x0 = 1 + (t % d.tiles_per_line) * kTW;
-      const int nrows = min(kTW, m - 1 - x0);
-      for (int idx = tid; idx < nrows * P; idx += blockDim.x)
-        Y[((size_t)y * m + x0) * P + idx] = nan_of<T>();
-    }
-    return;
-  }
-  // ---- boundary rows: identity rows of K
-  const int nb = 4 * (m - 1);
-  for (long long idx = (long long)blockIdx.x * blockDim.x + tid; idx < (long long)nb * P;
-       idx += (long long)gridDim.x * blockDim.x) {
-    const int q = (int)(idx / P), a = (int)(idx - (long long)q * P);
-    int x, y;
-    if (q < m) { x = q; y = 0; }
-    else if (q < 2 * m) { x = q - m; y = m - 1; }
-    else if (q < 3 * m - 2) { x = 0; y = q - 2 * m + 1; }
-    else { x = m - 1; y = q - (3 * m - 2) + 1; }
-    const size_t o = ((size_t)y * m + x) * P + a;
-    T v = alpha * X[o];
-    if (B != nullptr) v = fma(beta, B[o], v);
-    Y[o] = v;
-  }
-}
 
 // Tiled stack from the nnz x L stack: for tile t, permuted k position kp, entry e, row r:
 // value of A_{kperm[kp]} at entry e of node (x0 + r, y), 0 for rows beyond the line.
@@ -315,19 +66,30 @@ __global__ void tile_stack_kernel(int m, int tiles_per_line, int ntiles, int Lu,
 
 // ------------------------------------------------------------------ host: tables and launch
 
-int plan_tile_op(const System& s, int kappa, int elem, size_t smem_max, TilePlan& op) {
+static size_t round16(size_t v) { return (v + 15) / 16 * 16; }
+static size_t round128(size_t v) { return (v + 127) / 128 * 128; }
+
+// Plan of the row-tiled operator for kappa k per group and ``ctas`` CTAs per SM, whose shared
+// memory must fit smem_max bytes per CTA.  Groups: seeds in order of total degree, each grown by
+// the k whose b list overlaps the group's union most (Jaccard).  Chunks: consecutive groups, at
+// most one per warp, cut so that T slots, stack values and side table fit the budget.
+int plan_tile_op(const System& s, int kappa, int elem, size_t smem_max, TilePlan& op, int ctas) {
   const int P = s.P, L = s.L, m = s.pat.m;
   op = TilePlan();
   op.kappa = kappa;
   op.elem = elem;
-  if (m < 3 || kappa < 1 || kappa > 4 || P > 256) return fail(SG_ERR_ARG, "tile operator: unsupported sizes");
+  op.ctas = ctas;
+  if (m < 3 || kappa < 1 || kappa > 4 || P > 256 || ctas < 1 || ctas > 2)
+    return fail(SG_ERR_ARG, "tile operator: unsupported sizes");
+  if (!tile_variant_ok(elem, kappa, (P + kWarps - 1) / kWarps, ctas))
+    return fail(SG_ERR_ARG, "tile operator: no kernel variant for these sizes");
   op.tiles_per_line = (m - 2 + kTW - 1) / kTW;
   op.ntiles = op.tiles_per_line * (m - 2);
   op.Pp = P | 1;
-  // b lists per k as bit sets
   const int words = (P + 63) / 64;
   std::vector<unsigned long long> bset((size_t)L * words, 0ULL);
   std::vector<int> bcount(L, 0);
+  std::vector<std::vector<int>> nA((size_t)L * P);  // a of each (k, b)
   for (const Triple& t : s.triples) {
     unsigned long long& wd = bset[(size_t)t.k * words + t.b / 64];
     const unsigned long long bit = 1ULL << (t.b % 64);
@@ -336,7 +98,6 @@ int plan_tile_op(const System& s, int kappa, int elem, size_t smem_max, TilePlan
       bcount[t.k]++;
     }
   }
-  // greedy groups of kappa k with similar b lists, seeds in order of total degree
   std::vector<int> Jq = total_degree_set(s.M, s.prm.q);
   std::vector<int> deg(L, 0), order;
   for (int k = 0; k < L; ++k)
@@ -375,101 +136,202 @@ int plan_tile_op(const System& s, int kappa, int elem, size_t smem_max, TilePlan
     }
     groups.push_back(g);
   }
-  // group union lists and pair slots; chunks of at most kWarps groups and slot capacity
+  // entries (a, G) per (k, b), a ascending
+  std::vector<std::vector<std::pair<int, double>>> pe((size_t)L * P);
+  for (const Triple& t : s.triples) pe[(size_t)t.k * P + t.b].push_back({t.a, t.g});
+  const size_t esize = elem == 8 ? 16 : 8;
   const size_t xslab = (size_t)3 * kSlab * op.Pp;
-  const size_t fixed = 128 + elem * (xslab + 2 * (size_t)kWarps * kappa * 9 * kTW);
-  if (fixed + (size_t)elem * P * kTW > smem_max) return fail(SG_ERR_ARG, "tile operator: P too large for shared memory");
-  const int slot_cap = (int)std::min<size_t>(16384, (smem_max - fixed) / ((size_t)elem * kTW));
-  std::vector<int4> gdesc, cdesc;
-  std::vector<int2> ul;
-  std::vector<int> kperm;
-  std::vector<int> pair_slot((size_t)L * P, -1), pair_chunk((size_t)L * P, -1);
-  int cur_groups = 0, cur_slots = 0, cur_k0 = 0;
-  auto close_chunk = [&]() {
-    if (cur_groups == 0) return;
-    const int k1 = (int)kperm.size();
-    cdesc.push_back(make_int4(cur_k0, k1 - cur_k0, (int)gdesc.size() - cur_groups, cur_groups));
-    op.max_chunk_k = std::max(op.max_chunk_k, k1 - cur_k0);
-    op.max_slots = std::max(op.max_slots, cur_slots);
-    cur_groups = 0;
-    cur_slots = 0;
-    cur_k0 = k1;
-  };
-  for (auto& g : groups) {
-    int gslots = 0;
-    for (int k : g) gslots += bcount[k];
-    if (gslots > slot_cap) return fail(SG_ERR_ARG, "tile operator: a k group exceeds the slot capacity");
-    if (cur_groups == kWarps || cur_slots + gslots > slot_cap) close_chunk();
-    const int kloc = (int)kperm.size() - cur_k0;
-    const int ul0 = (int)ul.size();
-    int sl = cur_slots;
-    const int c = (int)cdesc.size();
-    for (int b = 0; b < P; ++b) {
-      unsigned mask = 0;
-      for (int j = 0; j < (int)g.size(); ++j)
-        if (bset[(size_t)g[j] * words + b / 64] >> (b % 64) & 1ULL) mask |= 1u << j;
-      if (!mask) continue;
-      ul.push_back(make_int2(b | (int)(mask << 16), sl));
-      for (int j = 0; j < (int)g.size(); ++j)
-        if (mask >> j & 1u) {
-          pair_slot[(size_t)g[j] * P + b] = sl++;
-          pair_chunk[(size_t)g[j] * P + b] = c;
+  const size_t abytes_max = round128((size_t)kWarps * kappa * 9 * kTW * elem);
+  const size_t fixed = 128 + 2 * abytes_max + round128(elem * xslab);
+  if (fixed + (size_t)elem * P * kTW > smem_max)
+    return fail(SG_ERR_ARG, "tile operator: P too large for shared memory");
+  int slot_cap = (int)std::min<size_t>(16384, (smem_max - fixed) / ((size_t)elem * kTW));
+  for (int attempt = 0; attempt < 40; ++attempt) {
+    // cut the chunks for this slot capacity
+    op.cdesc.clear();
+    op.cxdesc.clear();
+    op.gdesc.clear();
+    op.kperm.clear();
+    op.side.clear();
+    op.max_chunk_k = op.max_slots = 0;
+    op.max_side = 0;
+    op.pairs = op.entries = 0;
+    bool ok = true;
+    size_t gi = 0;
+    while (gi < groups.size() && ok) {
+      const int k0 = (int)op.kperm.size();
+      const int g0 = (int)op.gdesc.size();
+      int slots = 0;
+      std::vector<int2> ul;
+      std::vector<std::vector<std::pair<int, double>>> perA(P);  // (slot, G) per a
+      while (gi < groups.size() && (int)op.gdesc.size() - g0 < kWarps) {
+        const auto& g = groups[gi];
+        int gslots = 0;
+        for (int k : g) gslots += bcount[k];
+        if (gslots > slot_cap) {
+          ok = false;
+          break;
         }
-    }
-    gdesc.push_back(make_int4(ul0, (int)ul.size() - ul0, kloc, (int)g.size()));
-    for (int k : g) kperm.push_back(k);
-    cur_slots = sl;
-    ++cur_groups;
-  }
-  close_chunk();
-  op.nchunks = (int)cdesc.size();
-  op.Lu = (int)kperm.size();
-  op.ngroups = (int)gdesc.size();
-  // stage 2 entries per (chunk, a), sorted by slot
-  std::vector<std::vector<std::pair<int, double>>> per((size_t)op.nchunks * P);
-  for (const Triple& t : s.triples) {
-    const size_t pk = (size_t)t.k * P + t.b;
-    per[(size_t)pair_chunk[pk] * P + t.a].push_back({pair_slot[pk], t.g});
-  }
-  std::vector<int> eptr((size_t)op.nchunks * (P + 1)), eslot;
-  std::vector<double> eg;
-  for (int c = 0; c < op.nchunks; ++c) {
-    for (int a = 0; a < P; ++a) {
-      auto& v = per[(size_t)c * P + a];
-      std::sort(v.begin(), v.end());
-      eptr[(size_t)c * (P + 1) + a] = (int)eslot.size();
-      for (auto& pr : v) {
-        eslot.push_back(pr.first);
-        eg.push_back(pr.second);
+        if (slots + gslots > slot_cap) break;
+        const int kloc = (int)op.kperm.size() - k0;
+        const int ul0 = (int)ul.size();
+        for (int b = 0; b < P; ++b) {
+          unsigned mask = 0;
+          for (int j = 0; j < (int)g.size(); ++j)
+            if (bset[(size_t)g[j] * words + b / 64] >> (b % 64) & 1ULL) mask |= 1u << j;
+          if (!mask) continue;
+          ul.push_back(make_int2(b | (int)(mask << 16), slots));
+          for (int j = 0; j < (int)g.size(); ++j)
+            if (mask >> j & 1u) {
+              for (auto& ae : pe[(size_t)g[j] * P + b]) perA[ae.first].push_back({slots, ae.second});
+              ++slots;
+              ++op.pairs;
+            }
+        }
+        op.gdesc.push_back(make_int4(ul0, (int)ul.size() - ul0, kloc, (int)g.size()));
+        for (int k : g) op.kperm.push_back(k);
+        ++gi;
       }
+      if (!ok) break;
+      // side table of the chunk: union lists, entry offsets per a, entries
+      const size_t off_eptr = round16(8 * ul.size());
+      const size_t off_ent = round16(off_eptr + 4 * (size_t)(P + 1));
+      size_t nent = 0;
+      for (int a = 0; a < P; ++a) nent += perA[a].size();
+      const size_t bytes = round16(off_ent + esize * nent);
+      const size_t base = op.side.size();
+      op.side.resize(base + bytes, 0);
+      unsigned char* sb = op.side.data() + base;
+      std::memcpy(sb, ul.data(), 8 * ul.size());
+      int* ep = reinterpret_cast<int*>(sb + off_eptr);
+      size_t q = 0;
+      for (int a = 0; a < P; ++a) {
+        ep[a] = (int)q;
+        std::sort(perA[a].begin(), perA[a].end());
+        for (auto& e : perA[a]) {
+          unsigned char* dst = sb + off_ent + esize * q;
+          if (elem == 8) {
+            std::memcpy(dst, &e.first, 4);
+            std::memcpy(dst + 8, &e.second, 8);
+          } else {
+            const float gf = (float)e.second;
+            std::memcpy(dst, &e.first, 4);
+            std::memcpy(dst + 4, &gf, 4);
+          }
+          ++q;
+        }
+      }
+      ep[P] = (int)q;
+      op.entries += (long long)nent;
+      const int nk = (int)op.kperm.size() - k0;
+      op.cdesc.push_back(make_int4(k0, nk, g0, (int)op.gdesc.size() - g0));
+      op.cxdesc.push_back(make_int4((int)(base / 16), (int)bytes, (int)off_eptr, (int)off_ent));
+      op.max_chunk_k = std::max(op.max_chunk_k, nk);
+      op.max_slots = std::max(op.max_slots, slots);
+      op.max_side = std::max(op.max_side, bytes);
     }
-    eptr[(size_t)c * (P + 1) + P] = (int)eslot.size();
+    if (!ok) return fail(SG_ERR_ARG, "tile operator: a k group exceeds the slot capacity");
+    op.abytes_slot = (int)round128((size_t)op.max_chunk_k * 9 * kTW * elem);
+    op.sbytes_slot = (int)round128(op.max_side);
+    op.tbuf_elems = std::max(op.max_slots, P) * kTW;
+    op.xslab_elems = (int)xslab;
+    op.smem = 128 + 2 * (size_t)op.abytes_slot + 2 * (size_t)op.sbytes_slot +
+              (size_t)elem * (op.tbuf_elems + op.xslab_elems);
+    if (op.smem <= smem_max) break;
+    slot_cap = std::max(1, (int)(slot_cap * 0.85));
   }
-  op.abuf_elems = op.max_chunk_k * 9 * kTW;
-  op.tbuf_elems = std::max(op.max_slots, P) * kTW;
-  op.xslab_elems = (int)xslab;
-  op.smem = 128 + (size_t)elem * (2 * (size_t)op.abuf_elems + op.tbuf_elems + op.xslab_elems);
   if (op.smem > smem_max) return fail(SG_ERR_ARG, "tile operator: shared memory budget exceeded");
+  op.nchunks = (int)op.cdesc.size();
+  op.ngroups = (int)op.gdesc.size();
+  op.Lu = (int)op.kperm.size();
   op.apw = (P + kWarps - 1) / kWarps;
-  op.pairs = (long long)std::count_if(pair_slot.begin(), pair_slot.end(), [](int v) { return v >= 0; });
-  op.entries = (long long)eslot.size();
-  op.cdesc.swap(cdesc);
-  op.gdesc.swap(gdesc);
-  op.ul.swap(ul);
-  op.kperm.swap(kperm);
-  op.eptr.swap(eptr);
-  op.eslot.swap(eslot);
-  op.eg.swap(eg);
   return SG_OK;
 }
 
-int build_tile_op(System& s, TileOp& op, int kappa, int elem, size_t smem_max, cudaStream_t st) {
+// Decode a plan's tables the way the kernel reads them and check them against the triple
+// products: every (k, b) pair of a nonzero G_k[a, b] gets exactly one T slot, every nonzero
+// G_k[a, b] exactly one stage-2 entry with its value, and every read stays inside its chunk's
+// side table, stack slot and T buffer.  Host only.
+int verify_tile_plan(const System& s, const TilePlan& pl) {
+  const int P = s.P;
+  const size_t esize = pl.elem == 8 ? 16 : 8;
+  std::map<std::array<int, 3>, double> want;
+  for (const Triple& t : s.triples) want[{t.k, t.a, t.b}] = t.g;
+  std::map<std::array<int, 3>, double> got;
+  std::vector<char> seen((size_t)s.L * P, 0);
+  for (int c = 0; c < pl.nchunks; ++c) {
+    const int4 cd = pl.cdesc[c], cx = pl.cxdesc[c];
+    if ((size_t)cx.x * 16 + cx.y > pl.side.size() || cx.y % 16 || cx.y > pl.sbytes_slot)
+      return fail(SG_ERR_ARG, "plan: side table out of range");
+    if ((size_t)cd.y * 9 * 32 * pl.elem > (size_t)pl.abytes_slot) return fail(SG_ERR_ARG, "plan: stack slot");
+    const unsigned char* sb = pl.side.data() + (size_t)cx.x * 16;
+    std::vector<std::array<int, 2>> slot_kb;  // (k, b) of each slot
+    for (int g = cd.z; g < cd.z + cd.w; ++g) {
+      const int4 gd = pl.gdesc[g];
+      if (gd.z + gd.w > cd.y || (size_t)(gd.x + gd.y) * 8 > (size_t)cx.z)
+        return fail(SG_ERR_ARG, "plan: group out of range");
+      for (int u = 0; u < gd.y; ++u) {
+        int2 e;
+        std::memcpy(&e, sb + 8 * (size_t)(gd.x + u), 8);
+        const int b = e.x & 0xffff, mask = e.x >> 16;
+        int sl = e.y;
+        for (int j = 0; j < gd.w; ++j)
+          if (mask >> j & 1) {
+            const int k = pl.kperm[cd.x + gd.z + j];
+            if (sl != (int)slot_kb.size()) return fail(SG_ERR_ARG, "plan: slots not consecutive");
+            if (seen[(size_t)k * P + b]++) return fail(SG_ERR_ARG, "plan: pair placed twice");
+            slot_kb.push_back({k, b});
+            ++sl;
+          }
+        if (mask >> gd.w) return fail(SG_ERR_ARG, "plan: mask beyond the group");
+      }
+    }
+    if ((int)slot_kb.size() > pl.max_slots || (size_t)pl.max_slots * 32 > (size_t)pl.tbuf_elems)
+      return fail(SG_ERR_ARG, "plan: T buffer");
+    const int* ep = reinterpret_cast<const int*>(sb + cx.z);
+    for (int a = 0; a < P; ++a) {
+      if (ep[a] > ep[a + 1]) return fail(SG_ERR_ARG, "plan: entry offsets");
+      for (int q = ep[a]; q < ep[a + 1]; ++q) {
+        if ((size_t)cx.w + esize * (q + 1) > (size_t)cx.y) return fail(SG_ERR_ARG, "plan: entry out of range");
+        int slot;
+        double g;
+        std::memcpy(&slot, sb + cx.w + esize * q, 4);
+        if (pl.elem == 8) {
+          std::memcpy(&g, sb + cx.w + esize * q + 8, 8);
+        } else {
+          float gf;
+          std::memcpy(&gf, sb + cx.w + esize * q + 4, 4);
+          g = gf;
+        }
+        if (slot < 0 || slot >= (int)slot_kb.size()) return fail(SG_ERR_ARG, "plan: entry slot");
+        auto key = std::array<int, 3>{slot_kb[slot][0], a, slot_kb[slot][1]};
+        if (got.count(key)) return fail(SG_ERR_ARG, "plan: entry placed twice");
+        got[key] = g;
+      }
+    }
+  }
+  if (got.size() != want.size()) return fail(SG_ERR_ARG, "plan: entries missing");
+  for (auto& kv : want) {
+    auto it = got.find(kv.first);
+    if (it == got.end()) return fail(SG_ERR_ARG, "plan: entry missing");
+    const double tol = pl.elem == 8 ? 0.0 : 1e-7 * std::fabs(kv.second);
+    if (std::fabs(it->second - kv.second) > tol) return fail(SG_ERR_ARG, "plan: entry value");
+  }
+  const size_t smem = 128 + 2 * (size_t)pl.abytes_slot + 2 * (size_t)pl.sbytes_slot +
+                      (size_t)pl.elem * (pl.tbuf_elems + pl.xslab_elems);
+  if (smem != pl.smem || pl.abytes_slot % 128 || pl.sbytes_slot % 128) return fail(SG_ERR_ARG, "plan: layout");
+  return SG_OK;
+}
+
+int build_tile_op(System& s, TileOp& op, int kappa, int elem, size_t smem_max, cudaStream_t st,
+                  int ctas) {
   TilePlan pl;
   op = TileOp();
-  SG_TRY(plan_tile_op(s, kappa, elem, smem_max, pl));
+  SG_TRY(plan_tile_op(s, kappa, elem, smem_max, pl, ctas));
   const int m = s.pat.m, L = s.L;
   op.kappa = pl.kappa;
   op.elem = pl.elem;
+  op.ctas = pl.ctas;
   op.tiles_per_line = pl.tiles_per_line;
   op.ntiles = pl.ntiles;
   op.Pp = pl.Pp;
@@ -479,28 +341,19 @@ int build_tile_op(System& s, TileOp& op, int kappa, int elem, size_t smem_max, c
   op.max_chunk_k = pl.max_chunk_k;
   op.max_slots = pl.max_slots;
   op.apw = pl.apw;
-  op.abuf_elems = pl.abuf_elems;
+  op.abytes_slot = pl.abytes_slot;
+  op.sbytes_slot = pl.sbytes_slot;
   op.tbuf_elems = pl.tbuf_elems;
   op.xslab_elems = pl.xslab_elems;
   op.smem = pl.smem;
   SG_TRY(op.chunk.alloc(pl.cdesc.size()));
   SG_TRY(op.chunk.upload(pl.cdesc, st));
+  SG_TRY(op.chunkx.alloc(pl.cxdesc.size()));
+  SG_TRY(op.chunkx.upload(pl.cxdesc, st));
   SG_TRY(op.group.alloc(pl.gdesc.size()));
   SG_TRY(op.group.upload(pl.gdesc, st));
-  SG_TRY(op.ulist.alloc(pl.ul.size()));
-  SG_TRY(op.ulist.upload(pl.ul, st));
-  SG_TRY(op.ent_ptr.alloc(pl.eptr.size()));
-  SG_TRY(op.ent_ptr.upload(pl.eptr, st));
-  SG_TRY(op.ent_slot.alloc(pl.eslot.size()));
-  SG_TRY(op.ent_slot.upload(pl.eslot, st));
-  if (elem == 8) {
-    SG_TRY(op.ent_g.alloc(pl.eg.size()));
-    SG_TRY(op.ent_g.upload(pl.eg, st));
-  } else {
-    std::vector<float> ef(pl.eg.begin(), pl.eg.end());
-    SG_TRY(op.ent_g32.alloc(ef.size()));
-    SG_TRY(op.ent_g32.upload(ef, st));
-  }
+  SG_TRY(op.side.alloc(pl.side.size()));
+  SG_TRY(op.side.upload(pl.side, st));
   // the tiled stack
   DBuf<int> dperm;
   SG_TRY(dperm.alloc(pl.kperm.size()));
@@ -528,67 +381,26 @@ int build_tile_op(System& s, TileOp& op, int kappa, int elem, size_t smem_max, c
 
 void free_tile_op(TileOp& op) {
   op.chunk.release();
+  op.chunkx.release();
   op.group.release();
-  op.ulist.release();
-  op.ent_ptr.release();
-  op.ent_slot.release();
-  op.ent_g.release();
-  op.ent_g32.release();
+  op.side.release();
   op.stack.release();
   op.stack32.release();
   op.err.release();
   op.ready = false;
 }
 
-template <typename T, int KAPPA, int APW>
-static int launch_tile_k(const System& s, const TileOp& op, const T* X, T* Y, T alpha, const T* B,
-                         T beta, cudaStream_t st, const int* done) {
-  auto kern = sg_apply_tile_kernel<T, KAPPA, APW>;
-  SG_TRY(ensure_smem((const void*)kern, op.smem));
-  TileDims d{s.pat.m, op.tiles_per_line, op.ntiles, s.P, op.Pp, op.nchunks,
-             op.abuf_elems, op.tbuf_elems, op.xslab_elems};
-  int sms = 152;
-  {
-    int dev = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  }
-  const int grid = std::max(1, std::min(op.ntiles, sms));
-  const T* eg;
-  const T* stack;
-  if constexpr (sizeof(T) == 8) {
-    eg = op.ent_g.p;
-    stack = op.stack.p;
-  } else {
-    eg = op.ent_g32.p;
-    stack = op.stack32.p;
-  }
-  TimeScope ts(s.timer, sizeof(T) == 8 ? K_APPLY_F64 : K_APPLY_LOWP, st);
-  kern<<<grid, kWarps * 32, op.smem, st>>>(d, op.chunk.p, op.group.p, op.ulist.p, op.ent_ptr.p,
-                                           op.ent_slot.p, eg, stack, X, Y, alpha, B, beta, done,
-                                           op.err.p);
-  return check_launch("sg_apply_tile");
-}
-
-template <typename T, int KAPPA>
-static int launch_tile_apw(const System& s, const TileOp& op, const T* X, T* Y, T alpha,
-                           const T* B, T beta, cudaStream_t st, const int* done) {
-  if (op.apw <= 4) return launch_tile_k<T, KAPPA, 4>(s, op, X, Y, alpha, B, beta, st, done);
-  if (op.apw <= 8) return launch_tile_k<T, KAPPA, 8>(s, op, X, Y, alpha, B, beta, st, done);
-  if (op.apw <= 16) return launch_tile_k<T, KAPPA, 16>(s, op, X, Y, alpha, B, beta, st, done);
-  return launch_tile_k<T, KAPPA, 32>(s, op, X, Y, alpha, B, beta, st, done);
-}
+int launch_tile_op_f64(const System& s, const TileOp& op, const double* X, double* Y, double alpha,
+                      const double* B, double beta, cudaStream_t st, const int* done);
+int launch_tile_op_f32(const System& s, const TileOp& op, const float* X, float* Y, float alpha,
+                      const float* B, float beta, cudaStream_t st, const int* done);
 
 template <typename T>
 int launch_tile_op(const System& s, const TileOp& op, const T* X, T* Y, T alpha, const T* B,
                    T beta, cudaStream_t st, const int* done) {
   if (!op.ready) return fail(SG_ERR_ARG, "tile operator not built");
-  switch (op.kappa) {
-    case 1: return launch_tile_apw<T, 1>(s, op, X, Y, alpha, B, beta, st, done);
-    case 2: return launch_tile_apw<T, 2>(s, op, X, Y, alpha, B, beta, st, done);
-    case 3: return launch_tile_apw<T, 3>(s, op, X, Y, alpha, B, beta, st, done);
-    default: return launch_tile_apw<T, 4>(s, op, X, Y, alpha, B, beta, st, done);
-  }
+  if constexpr (sizeof(T) == 8) return launch_tile_op_f64(s, op, X, Y, alpha, B, beta, st, done);
+  else return launch_tile_op_f32(s, op, X, Y, alpha, B, beta, st, done);
 }
 
 template int launch_tile_op<double>(const System&, const TileOp&, const double*, double*, double,

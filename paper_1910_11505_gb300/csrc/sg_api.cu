@@ -2,6 +2,7 @@
 // right-hand-side entry points, and the restarted GMRES driver (Sec. 3) that queues whole Arnoldi
 // cycles per system on the system's own stream and synchronises once per cycle.
 #include <algorithm>
+#include <array>
 #include <atomic>
 #include <chrono>
 #include <cmath>
@@ -105,6 +106,7 @@ template struct DBuf<float>;
 template struct DBuf<int>;
 template struct DBuf<int2>;
 template struct DBuf<int4>;
+template struct DBuf<unsigned char>;
 template struct DBuf<unsigned int>;
 template struct DBuf<__nv_bfloat16>;
 
@@ -136,6 +138,10 @@ static int validate(const sg_params& p) {
   if (p.precision != SG_FP64 && !(p.inner_rtol > 0.0 && p.inner_rtol < 1.0))
     return fail(SG_ERR_ARG, "inner_rtol must be in (0, 1)");
   if (p.graphs != 0 && p.graphs != 1) return fail(SG_ERR_ARG, "graphs must be 0 or 1");
+  if (p.op_kernel < SG_OP_AUTO || p.op_kernel > SG_OP_TILE) return fail(SG_ERR_ARG, "unknown op_kernel");
+  if (p.op_kappa != 0 && p.op_kappa != 1 && p.op_kappa != 2 && p.op_kappa != 4)
+    return fail(SG_ERR_ARG, "op_kappa must be 0, 1, 2 or 4");
+  if (p.op_ctas < 0 || p.op_ctas > 2) return fail(SG_ERR_ARG, "op_ctas must be 0, 1 or 2");
   if (p.precond == SG_PC_MEAN || p.precond == SG_PC_FS_GS || p.precond == SG_PC_FS_JACOBI ||
       p.precond == SG_PC_MG) {
     // the wavefront solve: 2 wc compute and some staging threads; shared memory for its level
@@ -227,6 +233,136 @@ int host_tables(System& s) {
   s.pat = make_pattern(p.n);
   s.N = s.pat.N;
   return build_tables(s);
+}
+
+// ------------------------------------------------------------------ operator kernel tuner
+
+// The choice for one system shape and operator precision: the pair kernel, or the row-tiled kernel
+// with kappa k per register group and shared memory planned for ``ctas`` CTAs per SM.
+struct TuneChoice {
+  int kernel = SG_OP_PAIRS, kappa = 0, ctas = 1;
+  double ms = 0.0;
+};
+static std::mutex g_tune_mu;
+static std::map<std::array<long long, 5>, TuneChoice> g_tune;
+
+static std::string describe(const TuneChoice& c) {
+  if (c.kernel == SG_OP_PAIRS) return "pairs";
+  return "tile k" + std::to_string(c.kappa) + " x" + std::to_string(c.ctas);
+}
+
+// Shared memory one CTA may plan for when ``ctas`` CTAs share an SM.
+static size_t smem_budget(int ctas) {
+  const size_t opt = smem_optin_max();
+  if (ctas <= 1) return opt;
+  int dev = 0, per_sm = 0;
+  cudaGetDevice(&dev);
+  if (cudaDeviceGetAttribute(&per_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev) != cudaSuccess)
+    per_sm = 0;
+  const size_t each = per_sm > 0 ? (size_t)per_sm / ctas : opt / ctas;
+  return std::min(opt, each > 1024 ? each - 1024 : each);
+}
+
+template <typename T>
+static int time_operator(const System& s, const T* X, T* Y, cudaStream_t st, double* ms) {
+  auto run = [&]() {
+    if constexpr (sizeof(T) == 8) return launch_matvec_f64(s, X, Y, 1.0, nullptr, 0.0, st);
+    else return launch_matvec_f32(s, X, Y, 1.0f, nullptr, 0.0f, st);
+  };
+  cudaEvent_t a, b;
+  SG_CUDA(cudaEventCreate(&a));
+  SG_CUDA(cudaEventCreate(&b));
+  int rc = run();
+  if (rc == SG_OK) rc = cudaEventRecord(a, st) == cudaSuccess ? SG_OK : SG_ERR_CUDA;
+  for (int r = 0; r < 3 && rc == SG_OK; ++r) rc = run();
+  if (rc == SG_OK) rc = cudaEventRecord(b, st) == cudaSuccess ? SG_OK : SG_ERR_CUDA;
+  float t = 0.f;
+  if (rc == SG_OK && cudaEventSynchronize(b) == cudaSuccess && cudaEventElapsedTime(&t, a, b) == cudaSuccess)
+    *ms = t / 3.0;
+  else if (rc == SG_OK)
+    rc = fail(SG_ERR_CUDA, "timing the operator failed");
+  cudaEventDestroy(a);
+  cudaEventDestroy(b);
+  return rc;
+}
+
+// Build the operator kernel of precision ``elem`` (8: FP64, 4: FP32) that op_kernel asks for.
+// SG_OP_AUTO times the pair kernel and every row-tiled variant that fits (kappa 1, 2, 4; one or
+// two CTAs per SM) on this system, keeps the fastest and caches the choice for the system's
+// (N, P, L, q, element size).
+static int choose_operator(System& s, int elem, cudaStream_t st) {
+  TileOp& op = elem == 8 ? s.tile64 : s.tile32;
+  const sg_params& p = s.prm;
+  std::string& note = s.tile_msg;
+  if (p.op_kernel == SG_OP_PAIRS) return SG_OK;
+  if (p.op_kernel == SG_OP_TILE) {
+    const int kappa = p.op_kappa ? p.op_kappa : (elem == 8 ? 2 : 4);
+    const int ctas = p.op_ctas ? p.op_ctas : 1;
+    if (build_tile_op(s, op, kappa, elem, smem_budget(ctas), st, ctas) != SG_OK) {
+      note += (elem == 8 ? "fp64: " : "fp32: ") + g_last_error + "; ";
+      free_tile_op(op);
+      set_error("");
+    }
+    return SG_OK;
+  }
+  const std::array<long long, 5> key{s.N, s.P, s.L, p.q, elem};
+  {
+    std::lock_guard<std::mutex> lock(g_tune_mu);
+    auto itc = g_tune.find(key);
+    if (itc != g_tune.end()) {
+      const TuneChoice c = itc->second;
+      note += std::string(elem == 8 ? "fp64: " : "fp32: ") + describe(c) + " (cached); ";
+      if (c.kernel == SG_OP_PAIRS) return SG_OK;
+      if (build_tile_op(s, op, c.kappa, elem, smem_budget(c.ctas), st, c.ctas) != SG_OK) {
+        free_tile_op(op);
+        set_error("");
+      }
+      return SG_OK;
+    }
+  }
+  const size_t NP = (size_t)s.N * s.P;
+  DBuf<unsigned char> xb, yb;
+  SG_TRY(xb.alloc(NP * elem));
+  SG_TRY(yb.alloc(NP * elem));
+  SG_CUDA(cudaMemsetAsync(xb.p, 0, NP * elem, st));
+  auto timed = [&](double* ms) {
+    if (elem == 8)
+      return time_operator<double>(s, (const double*)xb.p, (double*)yb.p, st, ms);
+    return time_operator<float>(s, (const float*)xb.p, (float*)yb.p, st, ms);
+  };
+  TuneChoice best;
+  std::string log = std::string(elem == 8 ? "fp64:" : "fp32:");
+  SG_TRY(timed(&best.ms));  // the pair kernel (no row-tiled operator built yet)
+  log += " pairs " + std::to_string(best.ms) + " ms";
+  for (int ctas : {1, 2})
+    for (int kappa : {1, 2, 4}) {
+      TileOp cand;
+      if (build_tile_op(s, cand, kappa, elem, smem_budget(ctas), st, ctas) != SG_OK) {
+        free_tile_op(cand);
+        set_error("");
+        continue;
+      }
+      std::swap(op, cand);
+      double ms = 0.0;
+      const int rc = timed(&ms);
+      std::swap(op, cand);
+      TuneChoice c{SG_OP_TILE, kappa, ctas, ms};
+      if (rc == SG_OK) log += ", " + describe(c) + " " + std::to_string(ms) + " ms";
+      if (rc == SG_OK && ms < best.ms) {
+        best = c;
+        free_tile_op(op);
+        op = std::move(cand);
+        cand = TileOp();
+      }
+      free_tile_op(cand);
+      set_error("");
+    }
+  xb.release();
+  yb.release();
+  note += log + "; chose " + describe(best) + "; ";
+  std::lock_guard<std::mutex> lock(g_tune_mu);
+  g_tune[key] = best;
+  return SG_OK;
 }
 
 static int upload_i(DBuf<int>& d, const std::vector<int>& h, cudaStream_t st) {
@@ -424,20 +560,9 @@ static int setup_system(System& s, cudaStream_t st, bool krylov = true) {
     SG_TRY(s.stack_bf16.alloc(nnzL));
     SG_TRY(launch_cast_bf16(s.stack.p, s.stack_bf16.p, nnzL, st));
   }
-  // the row-tiled operator where its shared-memory budget allows (else the pair kernel serves)
-  {
-    const size_t smax = smem_optin_max();
-    if (build_tile_op(s, s.tile64, 2, 8, smax, st) != SG_OK) {
-      s.tile_msg = "fp64: " + g_last_error;
-      free_tile_op(s.tile64);
-      set_error("");
-    }
-    if (p.precision == SG_MIXED_FP32 && build_tile_op(s, s.tile32, 4, 4, smax, st) != SG_OK) {
-      s.tile_msg += " fp32: " + g_last_error;
-      free_tile_op(s.tile32);
-      set_error("");
-    }
-  }
+  // the SG operator kernels, chosen by op_kernel (timed per system shape when automatic)
+  SG_TRY(choose_operator(s, 8, st));
+  if (p.precision == SG_MIXED_FP32) SG_TRY(choose_operator(s, 4, st));
 
   // preconditioner blocks and factors
   const size_t NP = (size_t)s.N * s.P;
@@ -737,6 +862,9 @@ void sg_default_params(sg_params* p) {
   p->graphs = 0;
   p->mg_smoother = SG_PC_FS_GS;
   p->mg_coarse = 2;
+  p->op_kernel = SG_OP_AUTO;
+  p->op_kappa = 0;
+  p->op_ctas = 0;
 }
 
 int sg_setup(const sg_params* prm, int nsys, void* stream, sg_handle** out) {
@@ -895,22 +1023,30 @@ int sg_tune_plan(int n, int M, int p, int q, int precision, long long smem_max, 
   s.prm = prm;
   SG_TRY(host_tables(s));
   const int elem = precision == SG_FP64 ? 8 : 4;
-  for (int kappa = 1; kappa <= 4; ++kappa) {
-    long long* o = out + 8 * (kappa - 1);
-    for (int i = 0; i < 8; ++i) o[i] = 0;
-    TilePlan pl;
-    const int rc = plan_tile_op(s, kappa, elem, (size_t)smem_max, pl);
-    set_error("");
-    o[0] = rc == SG_OK;
-    if (rc != SG_OK) continue;
-    o[1] = (long long)pl.smem;
-    o[2] = pl.nchunks;
-    o[3] = pl.max_slots;
-    o[4] = pl.pairs;
-    o[5] = pl.entries;
-    o[6] = pl.Lu;
-    o[7] = pl.ngroups;
-  }
+  int row = 0;
+  for (int ctas = 1; ctas <= 2; ++ctas)
+    for (int kappa : {1, 2, 4}) {
+      long long* o = out + 12 * row++;
+      for (int i = 0; i < 12; ++i) o[i] = 0;
+      o[0] = kappa;
+      o[1] = ctas;
+      TilePlan pl;
+      const size_t budget = ctas == 1 ? (size_t)smem_max : (size_t)smem_max / 2;
+      const int rc = plan_tile_op(s, kappa, elem, budget, pl, ctas);
+      set_error("");
+      o[2] = rc == SG_OK;
+      if (rc != SG_OK) continue;
+      o[3] = (long long)pl.smem;
+      o[4] = pl.nchunks;
+      o[5] = pl.max_slots;
+      o[6] = pl.pairs;
+      o[7] = pl.entries;
+      o[8] = pl.Lu;
+      o[9] = pl.ngroups;
+      o[10] = verify_tile_plan(s, pl) == SG_OK;
+      o[11] = (long long)budget;
+      set_error("");
+    }
   return SG_OK;
 }
 

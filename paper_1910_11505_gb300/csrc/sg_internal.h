@@ -157,28 +157,30 @@ struct Triple {
 // one grid line as [k position][entry][row].
 struct TileOp {
   bool ready = false;
-  int kappa = 0, elem = 0, tiles_per_line = 0, ntiles = 0, Pp = 0, Lu = 0;
+  int kappa = 0, elem = 0, ctas = 1, tiles_per_line = 0, ntiles = 0, Pp = 0, Lu = 0;
   int nchunks = 0, ngroups = 0, max_chunk_k = 0, max_slots = 0, apw = 0;
-  int abuf_elems = 0, tbuf_elems = 0, xslab_elems = 0;
+  int abytes_slot = 0, sbytes_slot = 0, tbuf_elems = 0, xslab_elems = 0;
   size_t smem = 0;
-  DBuf<int4> chunk, group;
-  DBuf<int2> ulist;
-  DBuf<int> ent_ptr, ent_slot, err;
-  DBuf<double> ent_g, stack;
-  DBuf<float> ent_g32, stack32;
+  DBuf<int4> chunk, chunkx, group;
+  DBuf<unsigned char> side;
+  DBuf<int> err;
+  DBuf<double> stack;
+  DBuf<float> stack32;
 };
 
-// Host-side plan of the row-tiled operator (tables before upload).
+// Host-side plan of the row-tiled operator (tables before upload).  Per chunk: {first k position,
+// k count, first group, groups} and {side table offset in 16-byte units, bytes, offset of the
+// per-a entry offsets, offset of the entries}; per group {union list start within the chunk,
+// length, first k position within the chunk, k count}; the side tables of all chunks.
 struct TilePlan {
-  int kappa = 0, elem = 0, tiles_per_line = 0, ntiles = 0, Pp = 0, Lu = 0;
+  int kappa = 0, elem = 0, ctas = 1, tiles_per_line = 0, ntiles = 0, Pp = 0, Lu = 0;
   int nchunks = 0, ngroups = 0, max_chunk_k = 0, max_slots = 0, apw = 0;
-  int abuf_elems = 0, tbuf_elems = 0, xslab_elems = 0;
-  size_t smem = 0;
+  int abytes_slot = 0, sbytes_slot = 0, tbuf_elems = 0, xslab_elems = 0;
+  size_t smem = 0, max_side = 0;
   long long pairs = 0, entries = 0;
-  std::vector<int4> cdesc, gdesc;
-  std::vector<int2> ul;
-  std::vector<int> kperm, eptr, eslot;
-  std::vector<double> eg;
+  std::vector<int4> cdesc, cxdesc, gdesc;
+  std::vector<int> kperm;
+  std::vector<unsigned char> side;
 };
 
 // ------------------------------------------------------------------ per-system state
@@ -329,8 +331,10 @@ void free_system_public(System* s);
 int setup_system_public(System& s, cudaStream_t st, bool krylov);
 
 // Row-tiled operator (k_apply_tile.cu)
-int plan_tile_op(const System& s, int kappa, int elem, size_t smem_max, TilePlan& plan);
-int build_tile_op(System& s, TileOp& op, int kappa, int elem, size_t smem_max, cudaStream_t st);
+int plan_tile_op(const System& s, int kappa, int elem, size_t smem_max, TilePlan& plan, int ctas);
+int build_tile_op(System& s, TileOp& op, int kappa, int elem, size_t smem_max, cudaStream_t st,
+                  int ctas);
+int verify_tile_plan(const System& s, const TilePlan& plan);
 // Host-only setup pieces used by the planner entry point: the mesh pattern, the chaos index sets
 // and the triple products of a parameter set.
 int host_tables(System& s);

@@ -26,6 +26,7 @@ SG_FP64, SG_MIXED_FP32, SG_MIXED_BF16 = 0, 1, 2
 PRECONDS = {"none": SG_PC_NONE, "mean": SG_PC_MEAN, "fs_gs": SG_PC_FS_GS,
             "fs_jacobi": SG_PC_FS_JACOBI, "mg": SG_PC_MG}
 PRECISIONS = {"fp64": SG_FP64, "fp32": SG_MIXED_FP32, "bf16": SG_MIXED_BF16}
+OP_KERNELS = {"auto": 0, "pairs": 1, "tile": 2}
 
 EXPORTED = ["sg_default_params", "sg_setup", "sg_dims", "sg_nnz", "sg_matvec", "sg_matvec_lowp",
             "sg_precond_apply", "sg_precond_apply_lowp", "sg_precond_apply_noalloc", "sg_rhs",
@@ -53,7 +54,8 @@ class sg_params(ctypes.Structure):
                 ("restart", ctypes.c_int), ("max_iters", ctypes.c_int), ("rtol", ctypes.c_double),
                 ("atol", ctypes.c_double), ("precision", ctypes.c_int),
                 ("inner_rtol", ctypes.c_double), ("graphs", ctypes.c_int),
-                ("mg_smoother", ctypes.c_int), ("mg_coarse", ctypes.c_int)]
+                ("mg_smoother", ctypes.c_int), ("mg_coarse", ctypes.c_int),
+                ("op_kernel", ctypes.c_int), ("op_kappa", ctypes.c_int), ("op_ctas", ctypes.c_int)]
 
 
 class sg_solve_info(ctypes.Structure):
@@ -165,6 +167,8 @@ def sg_default_params(**overrides) -> sg_params:
     for k, v in overrides.items():
         if k in ("precond", "mg_smoother") and isinstance(v, str):
             v = PRECONDS[v]
+        if k == "op_kernel" and isinstance(v, str):
+            v = OP_KERNELS[v]
         if k == "precision" and isinstance(v, str):
             v = PRECISIONS[v]
         setattr(p, k, v)
@@ -244,14 +248,15 @@ def sg_op_info(h: SGHandle, sys: int = 0):
 
 
 def sg_tune_plan(n, M, p, q=0, precision="fp64", smem_max=232448):
-    """Host-only plan of the row-tiled operator for kappa = 1..4 (see include/sg.h): a list of
-    dicts with keys fits, smem, chunks, max_slots, pairs, entries, k_kept, groups."""
+    """Host-only plans of the row-tiled operator (see include/sg.h): a list of six dicts with keys
+    kappa, ctas, fits, smem, chunks, max_slots, pairs, entries, k_kept, groups, verified, budget."""
     if isinstance(precision, str):
         precision = PRECISIONS[precision]
-    out = (ctypes.c_longlong * 32)()
+    out = (ctypes.c_longlong * 72)()
     _check(load_library().sg_tune_plan(n, M, p, q, precision, smem_max, out))
-    keys = ["fits", "smem", "chunks", "max_slots", "pairs", "entries", "k_kept", "groups"]
-    return [dict(zip(keys, out[8 * i:8 * i + 8])) for i in range(4)]
+    keys = ["kappa", "ctas", "fits", "smem", "chunks", "max_slots", "pairs", "entries", "k_kept",
+            "groups", "verified", "budget"]
+    return [dict(zip(keys, out[12 * i:12 * i + 12])) for i in range(6)]
 
 
 def sg_precond_apply_lowp(h: SGHandle, sys: int, R, Z, stream=None):

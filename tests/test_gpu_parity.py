@@ -289,3 +289,55 @@ def test_graph_replay_equals_plain_launches(pc, prec):
         assert outs[0][rep][1] == outs[1][rep][1]
         for a, b in zip(outs[0][rep][0], outs[1][rep][0]):
             assert torch.equal(a, b)
+
+
+OP_VARIANTS = [dict(op_kernel="pairs"), dict(op_kernel="tile", op_kappa=1),
+               dict(op_kernel="tile", op_kappa=2), dict(op_kernel="tile", op_kappa=1, op_ctas=2),
+               dict(op_kernel="tile", op_kappa=2, op_ctas=2)]
+
+
+@pytest.mark.parametrize("variant", OP_VARIANTS)
+@pytest.mark.parametrize("case", [CASES[0], CASES[1], CASES[3], dict(n=40, M=3, p=3, sigma=0.9, ell=0.5)])
+def test_matvec_parity_every_operator_kernel(case, variant):
+    # each kernel the tuner may choose, forced, against the oracle (n = 40: lines of 39 interior
+    # nodes, one full tile of 32 rows and a ragged one of 7)
+    h = sg.sg_setup(_params(case, **variant))
+    info = sg.sg_op_info(h)
+    want = "pairs" if variant["op_kernel"] == "pairs" else "tile"
+    assert info["fp64"]["kernel"] == want, info
+    prob = _oracle(case)
+    X = W.random_field(prob.N, prob.P, seed=13)
+    Y = torch.empty(prob.N, prob.P, dtype=torch.float64, device="cuda")
+    sg.sg_matvec(h, 0, _dev(X), Y)
+    torch.cuda.synchronize()
+    ref = O.sg_matvec(prob, X)
+    assert _relerr(Y.cpu().numpy(), ref) <= 1e-12
+    h.close()
+
+
+@pytest.mark.parametrize("variant", [dict(op_kernel="pairs"), dict(op_kernel="tile", op_kappa=4),
+                                     dict(op_kernel="tile", op_kappa=2, op_ctas=2)])
+def test_fp32_operator_every_kernel(variant):
+    case = dict(n=40, M=3, p=3, sigma=0.9, ell=0.5)
+    h = sg.sg_setup(_params(case, precision="fp32", **variant))
+    assert sg.sg_op_info(h)["fp32"]["kernel"] == ("pairs" if variant["op_kernel"] == "pairs" else "tile")
+    prob = _oracle(case)
+    X = W.random_field(prob.N, prob.P, seed=15)
+    Y = torch.empty(prob.N, prob.P, dtype=torch.float32, device="cuda")
+    sg.sg_matvec_lowp(h, 0, _dev(X).float(), Y)
+    ref = O.sg_matvec(prob, X.astype(np.float32).astype(np.float64))
+    assert _relerr(Y.double().cpu().numpy(), ref) <= 2e-5
+    h.close()
+
+
+def test_operator_tuner_choice_is_cached_and_reported():
+    case = dict(n=24, M=2, p=2, sigma=0.5, ell=1.0)
+    h1 = sg.sg_setup(_params(case, op_kernel="auto"))
+    m1 = sg.sg_op_info(h1)["msg"]
+    h2 = sg.sg_setup(_params(case, op_kernel="auto"))
+    info = sg.sg_op_info(h2)
+    assert "chose" in m1 or "cached" in m1, m1
+    assert "cached" in info["msg"], info
+    assert info["fp64"]["kernel"] == sg.sg_op_info(h1)["fp64"]["kernel"]
+    h1.close()
+    h2.close()

@@ -32,14 +32,15 @@ def test_plan_places_every_pair_and_entry_once(sg, M, p, precision):
     plan = sg.sg_tune_plan(64, M, p, 0, precision)
     elem = 8 if precision == "fp64" else 4
     P = G.shape[1]
-    for kappa, pl in enumerate(plan, start=1):
+    for pl in plan:
         if not pl["fits"]:
             continue
+        assert pl["verified"], pl
         assert pl["pairs"] == pairs and pl["entries"] == entries and pl["k_kept"] == ks
-        assert pl["groups"] >= math.ceil(ks / kappa)
-        assert pl["smem"] <= 232448
-        # the stated layout: barriers, two stack chunk slots, T slots (or the Y staging of P
-        # outputs), the three grid lines of X with an odd stride
+        assert pl["groups"] >= math.ceil(ks / pl["kappa"])
+        assert pl["smem"] <= pl["budget"]
+        # the stated layout: barriers, two stack chunk slots and two side-table slots, T slots (or
+        # the Y staging of P outputs), the three grid lines of X with an odd stride
         slab = 3 * 34 * (P | 1)
         assert pl["smem"] >= 128 + elem * (slab + 32 * max(pl["max_slots"], P))
     assert plan[0]["fits"]
@@ -50,9 +51,20 @@ def test_plan_respects_the_shared_memory_budget(sg):
     for pl in big:
         if pl["fits"]:
             small = sg.sg_tune_plan(128, 4, 3, 0, "fp64", smem_max=pl["smem"] - 1)
-            assert all(q["smem"] <= pl["smem"] - 1 for q in small if q["fits"])
+            assert all(q["smem"] <= q["budget"] for q in small if q["fits"])
     tiny = sg.sg_tune_plan(128, 4, 3, 0, "fp64", smem_max=16 * 1024)
     assert not any(q["fits"] for q in tiny)
+
+
+@pytest.mark.parametrize("n,M,p,precision", [(128, 4, 3, "fp64"), (128, 4, 3, "fp32"),
+                                             (256, 6, 3, "fp32"), (256, 6, 3, "fp64"),
+                                             (16, 8, 2, "fp32")])
+def test_plans_at_solver_sizes_decode_to_the_triple_products(sg, n, M, p, precision):
+    plan = sg.sg_tune_plan(n, M, p, 0, precision)
+    assert any(pl["fits"] for pl in plan)
+    for pl in plan:
+        if pl["fits"]:
+            assert pl["verified"], pl
 
 
 def test_plan_refuses_invalid_sizes(sg):
