@@ -72,6 +72,7 @@ def run_c5(ntrain=4096, ntest=256, steps=3000):
     Z, T, gen = learned.generate(tr, chunk=64, precision="fp32", rtol=1e-6)
     net = sg.SGNet(Z.shape[1], 64, 64, T.shape[1], max_batch=256, bf16=True, seed=1910)
     net.set_stats(Z, T)
+    net.set_basis(T)
     torch.cuda.synchronize()
     t0 = time.time()
     losses = learned.train(net, Z, T, steps=steps, batch=256, lr=1e-3, log_every=max(1, steps // 10))

@@ -191,6 +191,11 @@ int sg_op_info(const sg_handle* h, int sys, long long* info, char* msg, int msg_
  * budget}; ``out`` holds 72 values.  SG_ERR_ARG for invalid sizes. */
 int sg_tune_plan(int n, int M, int p, int q, int precision, long long smem_max, long long* out);
 
+/* Measure the device's FMA throughput (independent FMA chains on every SM, CUDA events) in FP64
+ * (precision SG_FP64) or FP32 (any other), in GFLOP/s (2 flops per FMA), on the legacy default
+ * stream of the current device; synchronous.  The ALU roofline of the FP64 operator divides by it. */
+int sg_probe_fma(int precision, double* gflops);
+
 /* Count of kernel launches this library has queued since load (all handles, all threads). */
 long long sg_launch_count(void);
 

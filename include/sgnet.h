@@ -37,6 +37,15 @@ int sgnet_create(int in_dim, int h1, int h2, int out_dim, int max_batch, int bf1
  * standard deviation of Z (sd floored at 1e-6), b3 := per-output mean of T. */
 int sgnet_set_stats(sgnet* net, const float* Z, const float* T, int n, void* stream);
 
+/* Output basis from the training targets (call after sgnet_set_stats with the same T): the
+ * first min(n, h2) centred targets T_r - b3 are orthonormalised (classical Gram-Schmidt applied
+ * twice, FP64 sums), each basis vector q_j is scaled by s_j = max_r |q_j . (T_r - b3)| / 0.9, and
+ * W3 := [s_j q_j] with the remaining columns 0; Adam then leaves W3 and b3 fixed.  Every
+ * prediction lies in the span of training solutions around their mean, so its error is a smooth
+ * combination of solutions rather than unstructured noise, which K would amplify in the initial
+ * residual.  Synchronous. */
+int sgnet_set_basis(sgnet* net, const float* T, int n, void* stream);
+
 /* Forward pass for B <= max_batch inputs; Y: B x out FP32 (device). */
 int sgnet_forward(sgnet* net, const float* Z, int B, float* Y, void* stream);
 

@@ -5,6 +5,7 @@
 // over the batch.  The back-propagation into the hidden layer is a split-K product over D with a
 // deterministic second-stage sum.  Small layers run one CTA per sample.  No atomics: results do
 // not depend on scheduling.
+#include <algorithm>
 #include <cmath>
 #include <cstring>
 #include <vector>
@@ -282,6 +283,87 @@ __global__ void out_mean_kernel(int n, int out, const float* __restrict__ T, flo
   b3[j] = s / n;
 }
 
+// ---- output basis from the training targets (sgnet_set_basis)
+// V[j] = T[j] - b3 for the first nb training rows (j-major, D entries each).
+__global__ void center_rows_kernel(int nb, int out, const float* __restrict__ T,
+                                   const float* __restrict__ b3, float* __restrict__ V) {
+  const size_t total = (size_t)nb * out;
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < total;
+       i += (size_t)gridDim.x * blockDim.x)
+    V[i] = T[i] - b3[i % out];
+}
+
+// d[i] = V[i] . V[j] for i < ni (one CTA per i, FP64 accumulation, fixed-order tree).
+__global__ void basis_dots_kernel(int out, const float* __restrict__ V, int j, double* __restrict__ d) {
+  __shared__ double red[256];
+  const int i = blockIdx.x;
+  const float* a = V + (size_t)i * out;
+  const float* b = V + (size_t)j * out;
+  double s = 0.0;
+  for (int u = threadIdx.x; u < out; u += blockDim.x) s += (double)a[u] * (double)b[u];
+  red[threadIdx.x] = s;
+  __syncthreads();
+  for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+    if (threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) d[i] = red[0];
+}
+
+// V[j] -= sum_{i<j} d[i] V[i]   (one classical Gram-Schmidt pass)
+__global__ void basis_update_kernel(int out, float* __restrict__ V, int j, const double* __restrict__ d) {
+  for (int u = blockIdx.x * blockDim.x + threadIdx.x; u < out; u += gridDim.x * blockDim.x) {
+    double v = V[(size_t)j * out + u];
+    for (int i = 0; i < j; ++i) v -= d[i] * (double)V[(size_t)i * out + u];
+    V[(size_t)j * out + u] = (float)v;
+  }
+}
+
+// V[j] /= ||V[j]|| (d[j] holds the squared norm); a vector that vanished becomes 0
+__global__ void basis_scale_kernel(int out, float* __restrict__ V, int j, const double* __restrict__ d) {
+  const double nrm = sqrt(d[j]);
+  const float f = nrm > 1e-30 ? (float)(1.0 / nrm) : 0.f;
+  for (int u = blockIdx.x * blockDim.x + threadIdx.x; u < out; u += gridDim.x * blockDim.x)
+    V[(size_t)j * out + u] *= f;
+}
+
+// c[r, j] = Q[j] . (T[r] - b3) for every training row r (one CTA per (r, j), FP64 accumulation)
+__global__ void basis_coef_kernel(int rows, int nb, int out, const float* __restrict__ Q,
+                                  const float* __restrict__ T, const float* __restrict__ b3,
+                                  double* __restrict__ c) {
+  __shared__ double red[256];
+  const int r = blockIdx.x, j = blockIdx.y;
+  const float* q = Q + (size_t)j * out;
+  const float* t = T + (size_t)r * out;
+  double s = 0.0;
+  for (int u = threadIdx.x; u < out; u += blockDim.x) s += (double)q[u] * ((double)t[u] - (double)b3[u]);
+  red[threadIdx.x] = s;
+  __syncthreads();
+  for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+    if (threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) c[(size_t)r * nb + j] = red[0];
+}
+
+// W3[u, j] = Q[j, u] * s_j with s_j = max_r |c[r, j]| / 0.9 (the hidden layer's tanh then reaches
+// every training coefficient), columns beyond nb zero
+__global__ void basis_w3_kernel(int rows, int nb, int h2, int out, const float* __restrict__ Q,
+                                const double* __restrict__ c, float* __restrict__ W3) {
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < (size_t)out * h2;
+       i += (size_t)gridDim.x * blockDim.x) {
+    const int j = (int)(i % h2);
+    const size_t u = i / h2;
+    float v = 0.f;
+    if (j < nb) {
+      double mx = 0.0;
+      for (int r = 0; r < rows; ++r) mx = fmax(mx, fabs(c[(size_t)r * nb + j]));
+      v = Q[(size_t)j * out + u] * (float)(mx / 0.9);
+    }
+    W3[i] = v;
+  }
+}
+
 }  // namespace
 }  // namespace sg
 
@@ -289,6 +371,7 @@ struct sgnet {
   int in = 0, h1 = 0, h2 = 0, out = 0, maxb = 0, bf16 = 0;
   int oW1 = 0, ob1 = 0, oW2 = 0, ob2 = 0, oW3 = 0, ob3 = 0;
   long long np = 0, step = 0;
+  int frozen_out = 0;        // 1: Adam leaves the output layer (W3, b3) as set_basis left it
   sg::DBuf<float> P, G, M, V, mu, sd, Zh, H1, H2, dY, dH2, dA2, dA1, part, lpart, loss, Ytmp;
   sg::DBuf<__nv_bfloat16> W3h;
 };
@@ -414,6 +497,43 @@ int sgnet_set_stats(sgnet* n, const float* Z, const float* T, int rows, void* st
   return check_launch("out_mean");
 }
 
+int sgnet_set_basis(sgnet* n, const float* T, int rows, void* stream) {
+  if (!n || !T || rows < 1) return fail(SG_ERR_ARG, "bad arguments");
+  cudaStream_t st = (cudaStream_t)stream;
+  const int nb = std::min(rows, n->h2);
+  DBuf<float> Q;
+  DBuf<double> d, c;
+  SG_TRY(Q.alloc((size_t)nb * n->out));
+  SG_TRY(d.alloc(n->h2));
+  SG_TRY(c.alloc((size_t)rows * nb));
+  const int g = std::min(608, (n->out + 255) / 256);
+  center_rows_kernel<<<608, 256, 0, st>>>(nb, n->out, T, n->P.p + n->ob3, Q.p);
+  SG_TRY(check_launch("center_rows"));
+  for (int j = 0; j < nb; ++j) {
+    for (int pass = 0; pass < 2 && j > 0; ++pass) {  // CGS2
+      basis_dots_kernel<<<j, 256, 0, st>>>(n->out, Q.p, j, d.p);
+      SG_TRY(check_launch("basis_dots"));
+      basis_update_kernel<<<g, 256, 0, st>>>(n->out, Q.p, j, d.p);
+      SG_TRY(check_launch("basis_update"));
+    }
+    basis_dots_kernel<<<1, 256, 0, st>>>(n->out, Q.p + (size_t)j * n->out, 0, d.p + j);
+    SG_TRY(check_launch("basis_norm"));
+    basis_scale_kernel<<<g, 256, 0, st>>>(n->out, Q.p, j, d.p);
+    SG_TRY(check_launch("basis_scale"));
+  }
+  basis_coef_kernel<<<dim3(rows, nb), 256, 0, st>>>(rows, nb, n->out, Q.p, T, n->P.p + n->ob3, c.p);
+  SG_TRY(check_launch("basis_coef"));
+  basis_w3_kernel<<<608, 256, 0, st>>>(rows, nb, n->h2, n->out, Q.p, c.p, n->P.p + n->oW3);
+  SG_TRY(check_launch("basis_w3"));
+  SG_TRY(refresh_bf16(n, st));
+  SG_CUDA(cudaStreamSynchronize(st));
+  Q.release();
+  d.release();
+  c.release();
+  n->frozen_out = 1;
+  return SG_OK;
+}
+
 int sgnet_forward(sgnet* n, const float* Z, int B, float* Y, void* stream) {
   SG_TRY(check_batch(n, B));
   if (!Z || !Y) return fail(SG_ERR_ARG, "NULL pointer");
@@ -475,7 +595,8 @@ int sgnet_adam_step(sgnet* n, float lr, void* stream) {
   n->step += 1;
   float c1 = (float)(1.0 - std::pow(0.9, (double)n->step));
   float c2 = (float)(1.0 - std::pow(0.999, (double)n->step));
-  adam_kernel<<<608, 256, 0, st>>>((size_t)n->np, n->P.p, n->G.p, n->M.p, n->V.p, lr, c1, c2);
+  const size_t nupd = n->frozen_out ? (size_t)n->oW3 : (size_t)n->np;  // W3, b3 come last
+  adam_kernel<<<608, 256, 0, st>>>(nupd, n->P.p, n->G.p, n->M.p, n->V.p, lr, c1, c2);
   SG_TRY(check_launch("adam"));
   return refresh_bf16(n, st);
 }

@@ -31,9 +31,9 @@ OP_KERNELS = {"auto": 0, "pairs": 1, "tile": 2}
 EXPORTED = ["sg_default_params", "sg_setup", "sg_dims", "sg_nnz", "sg_matvec", "sg_matvec_lowp",
             "sg_precond_apply", "sg_precond_apply_lowp", "sg_precond_apply_noalloc", "sg_rhs",
             "sg_gmres_solve",
-            "sg_export", "sg_launch_count", "sg_tune_plan", "sg_op_info",
+            "sg_export", "sg_launch_count", "sg_tune_plan", "sg_op_info", "sg_probe_fma",
             "sg_timing_start", "sg_timing_stop", "sg_free", "sg_last_error",
-            "sgnet_create", "sgnet_set_stats", "sgnet_forward", "sgnet_predict", "sgnet_loss_grad",
+            "sgnet_create", "sgnet_set_stats", "sgnet_set_basis", "sgnet_forward", "sgnet_predict", "sgnet_loss_grad",
             "sgnet_adam_step", "sgnet_train_step", "sgnet_num_params", "sgnet_get", "sgnet_set",
             "sgnet_free"]
 
@@ -98,6 +98,8 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.sg_tune_plan.restype = c_int
     lib.sg_op_info.argtypes = [vp, c_int, ctypes.POINTER(ctypes.c_longlong), ctypes.c_char_p, c_int]
     lib.sg_op_info.restype = c_int
+    lib.sg_probe_fma.argtypes = [c_int, ctypes.POINTER(ctypes.c_double)]
+    lib.sg_probe_fma.restype = c_int
     lib.sg_launch_count.argtypes = []
     lib.sg_launch_count.restype = ctypes.c_longlong
     lib.sg_timing_start.argtypes = [vp, c_int]
@@ -109,6 +111,7 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.sgnet_create.argtypes = [c_int, c_int, c_int, c_int, c_int, c_int, ctypes.c_ulonglong,
                                  ctypes.POINTER(vp)]
     lib.sgnet_set_stats.argtypes = [vp, vp, vp, c_int, vp]
+    lib.sgnet_set_basis.argtypes = [vp, vp, c_int, vp]
     lib.sgnet_forward.argtypes = [vp, vp, c_int, vp, vp]
     lib.sgnet_predict.argtypes = [vp, vp, c_int, vp, vp]
     lib.sgnet_loss_grad.argtypes = [vp, vp, vp, c_int, fp, vp]
@@ -120,7 +123,7 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.sgnet_set.argtypes = [vp, c_int, fp, ctypes.c_size_t]
     lib.sgnet_free.argtypes = [vp]
     lib.sgnet_free.restype = None
-    for name in ("sgnet_create", "sgnet_set_stats", "sgnet_forward", "sgnet_predict",
+    for name in ("sgnet_create", "sgnet_set_stats", "sgnet_set_basis", "sgnet_forward", "sgnet_predict",
                  "sgnet_loss_grad", "sgnet_adam_step", "sgnet_train_step", "sgnet_get", "sgnet_set"):
         getattr(lib, name).restype = c_int
     lib.sg_last_error.argtypes = []
@@ -231,6 +234,15 @@ def sg_matvec_lowp(h: SGHandle, sys: int, X, Y, stream=None):
 def sg_precond_apply(h: SGHandle, sys: int, R, Z, stream=None):
     _check(load_library().sg_precond_apply(h.raw, sys, _ptr(R, "f64"), _ptr(Z, "f64"),
                                            _stream_ptr(stream)))
+
+
+def sg_probe_fma(precision="fp64") -> float:
+    """Measured FMA throughput of the current device in GFLOP/s (see include/sg.h)."""
+    if isinstance(precision, str):
+        precision = PRECISIONS[precision]
+    v = ctypes.c_double()
+    _check(load_library().sg_probe_fma(precision, ctypes.byref(v)))
+    return v.value
 
 
 def sg_op_info(h: SGHandle, sys: int = 0):
@@ -345,6 +357,11 @@ class SGNet:
     @property
     def num_params(self):
         return int(load_library().sgnet_num_params(self.raw))
+
+    def set_basis(self, T, stream=None):
+        """Output layer from the training targets' span, then kept fixed (include/sgnet.h)."""
+        _check(load_library().sgnet_set_basis(self.raw, _ptr(T, "f32"), T.shape[0],
+                                              _stream_ptr(stream)))
 
     def set_stats(self, Z, T, stream=None):
         _check(load_library().sgnet_set_stats(self.raw, _ptr(Z, "f32"), _ptr(T, "f32"), Z.shape[0],

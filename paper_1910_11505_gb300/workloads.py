@@ -61,6 +61,13 @@ def c2_params(sigma=None):
                  max_iters=4000) for s in sig]
 
 
+def c3_mg_params(precision="fp64"):
+    """c3 with the multigrid V-cycle preconditioner of the paper's G-M-F-I (field-split
+    Gauss-Seidel + ILU(0) smoothing, one pre- and one post-step, 2 x 2 coarsest mesh)."""
+    return dict(n=256, M=6, p=3, sigma=1.0, ell=0.5, precond="mg", mg_smoother="fs_gs",
+                rtol=1e-8, restart=50, max_iters=400, precision=precision, graphs=1)
+
+
 def c3_params(precision="fp64"):
     return dict(n=256, M=6, p=3, sigma=1.0, ell=0.5, precond="mean", rtol=1e-8, restart=100,
                 max_iters=6000, precision=precision)

@@ -107,13 +107,42 @@ def test_trained_network_reduces_gmres_iterations():
     train_p = [dict(base, sigma=s, ell=l) for s, l in draws[:256]]
     test_p = [dict(base, sigma=s, ell=l) for s, l in draws[256:288]]
     Z, T, gen = learned.generate(train_p, chunk=64)
-    net = sg.SGNet(Z.shape[1], 32, 32, T.shape[1], max_batch=64, bf16=True, seed=9)
+    net = sg.SGNet(Z.shape[1], 64, 64, T.shape[1], max_batch=64, bf16=True, seed=9)
     net.set_stats(Z, T)
-    learned.train(net, Z, T, steps=2000, batch=64, lr=1e-3)
+    net.set_basis(T)
+    learned.train(net, Z, T, steps=4000, batch=64, lr=2e-3)
     ev = learned.warm_start_eval(net, test_p)
     assert ev["rc"] == (sg.SG_OK, sg.SG_OK)
     assert max(ev["warm_resid"]) <= 1e-8  # the final FP64 residual still decides
     zero, warm = np.array(ev["zero_iters"]), np.array(ev["warm_iters"])
     assert warm.mean() < 0.9 * zero.mean(), ev
     assert (warm <= zero).mean() >= 0.75, ev
+    net.close()
+
+
+def test_output_basis_is_orthogonal_and_fixed_by_adam():
+    # the output layer spans the centred training targets (scaled orthonormal columns) and Adam
+    # leaves it unchanged while the hidden layers train
+    rng = np.random.default_rng(7)
+    D = 300
+    T = torch.from_numpy(rng.normal(size=(24, D)).astype(np.float32)).cuda()
+    Z = torch.from_numpy(rng.normal(size=(24, 6)).astype(np.float32)).cuda()
+    net = sg.SGNet(6, 16, 8, D, max_batch=32, bf16=False, seed=2)
+    net.set_stats(Z, T)
+    net.set_basis(T)
+    p0 = net.get(0).astype(np.float64)
+    dims = (6, 16, 8, D)
+    W3 = _unflatten(p0.astype(np.float32), dims)[4]
+    g = W3.T @ W3
+    assert np.abs(g - np.diag(np.diag(g))).max() <= 1e-5 * np.diag(g).max()
+    Tc = T.cpu().numpy().astype(np.float64) - T.cpu().numpy().astype(np.float64).mean(0)
+    # the first 8 centred targets lie in the span of the columns
+    Q = W3 / np.linalg.norm(W3, axis=0)
+    resid = Tc[:8].T - Q @ (Q.T @ Tc[:8].T)
+    assert np.abs(resid).max() <= 1e-4 * np.abs(Tc).max()
+    net.train_step(Z[:16], T[:16], 1e-2)
+    p1 = net.get(0).astype(np.float64)
+    nsmall = 16 * 6 + 16 + 8 * 16 + 8
+    assert np.array_equal(p1[nsmall:], p0[nsmall:])
+    assert not np.array_equal(p1[:nsmall], p0[:nsmall])
     net.close()
