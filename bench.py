@@ -1,15 +1,21 @@
 """Benchmark of the SG-GMRES hot path on GB300.
 
-Workload (one step): solve the four field-split Gauss-Seidel SG systems of the 128 x 128 Q1 mesh,
-M = 4 KL terms, p = 3 (P = 35, L = 210), ell = 0.5, sigma in {0.25, 0.5, 1.0, 1.5}, FP64,
-relative residual 1e-10, from a zero initial guess.  value = solved systems per second over all
-ranks (each rank solves its own copy of the four systems: weak scaling, no collective on the
-data path).
+Workload (c3): the stochastic Galerkin system of -div(a grad u) = 1 on the unit square, 256 x 256
+Q1 mesh, M = 6 KL terms of the exponential covariance (sigma = 1, ell = 0.5), chaos degree p = 3
+(P = 84 solution terms, L = 924 coefficient terms; 5.5 M unknowns), relative residual 1e-8 from a
+zero initial guess, GMRES(50) preconditioned by the multigrid V-cycle of the paper's G-M-F-I
+(field-split Gauss-Seidel with ILU(0) blocks as the level solver, one pre- and one post-smoothing
+step, 2 x 2 coarsest mesh solved directly).  One step = one solve in the mixed-precision form
+(FP32 operator, preconditioner and inner basis inside FP64 flexible GMRES with FP64 iterative
+refinement).  value = solves per second over all ranks (each rank solves its own copy: weak
+scaling, no collective on the data path).
 
-Also reported: the roofline of the dominant kernel (live CUDA-event timing inside the library on
-the stream each kernel is launched on), the SG operator's own throughput, the end-to-end rate
-through the C ABI with host buffers, SM clocks sampled during the timed region, and the FP64
-CPU oracle timed on the host cores on a bounded sample (``cpu_baseline``).
+Also in the JSON line: the FP64 GPU solve of the same system (rate, iterations, and the mixed
+solution's distance from it), the SG operator alone in FP64 and FP32 (HBM GB/s and, for FP64,
+FLOP/s against the FP64 FMA peak measured here by the library's probe), the roofline of the
+dominant kernel from a separate per-kernel timing pass, the end-to-end rate through the C ABI
+with host buffers, SM clocks sampled during the timed region, and the FP64 CPU oracle on the
+host cores (``cpu_baseline``).
 
 ``--impl reference`` times the oracle alone (the CPU reference of this project) on a bounded
 sample of the same workload and prints the same JSON line with "impl": "reference".
@@ -20,6 +26,7 @@ from __future__ import annotations
 import argparse
 import json
 import os
+import platform
 import statistics
 import subprocess
 import sys
@@ -29,14 +36,11 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "SG solves/sec & matvec HBM GB/s, mixed/learned vs FP64 GMRES at 1e-8 residual"
-WORKLOAD = ("c2: 128x128 Q1 mesh, M=4, p=3 (P=35, L=210), ell=0.5, sigma in {0.25,0.5,1.0,1.5}, "
-            "FP64 GMRES(300) with field-split Gauss-Seidel + ILU(0), rel. residual 1e-10, x0 = 0")
+WORKLOAD = ("c3: 256x256 Q1 mesh, M=6, p=3 (P=84, L=924, 5.5M unknowns), sigma=1, ell=0.5, "
+            "GMRES(50) + multigrid V-cycle (field-split Gauss-Seidel + ILU(0) smoother, 1/1, "
+            "2x2 coarsest), rel. residual 1e-8, x0 = 0; mixed FP32/FP64 FGMRES + refinement")
 PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
-DFMA_PEAK_GFLOPS = 1192.0   # measured FP64 FMA loop on GB300 (2 DFMA per clock per SM, 2 flops each)
-ITERS_FILE = os.path.join(ROOT, "oracle", "c2_iterations.json")
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "traffic.json")
-KERNEL_SOURCES = {"ilu_solve": "paper_1910_11505_gb300/csrc/k_precond.cu",
-                  "apply_f64": "paper_1910_11505_gb300/csrc/k_matvec.cu"}
 
 
 def measured_traffic(kernel):
@@ -46,9 +50,11 @@ def measured_traffic(kernel):
     try:
         with open(TRAFFIC_FILE) as f:
             rec = json.load(f)[kernel]
-        with open(os.path.join(ROOT, rec["source"]), "rb") as f:
-            sha = hashlib.sha256(f.read()).hexdigest()
-        return rec["bytes_per_launch"] if sha == rec["sha256"] else None
+        h = hashlib.sha256()
+        for src in rec["sources"]:
+            with open(os.path.join(ROOT, src), "rb") as f:
+                h.update(f.read())
+        return rec["bytes_per_launch"] if h.hexdigest() == rec["sha256"] else None
     except Exception:
         return None
 
@@ -60,6 +66,20 @@ def _peaks():
         return float(p["hbm_gbs"]), "measured"
     except Exception:
         return 6800.0, "fallback"
+
+
+def cpu_info():
+    model = platform.processor() or platform.machine()
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                key = line.split(":")[0].strip().lower()
+                if key in ("model name", "cpu part", "hardware"):
+                    model = line.split(":", 1)[1].strip()
+                    break
+    except Exception:
+        pass
+    return {"nproc": os.cpu_count(), "model": model, "machine": platform.machine()}
 
 
 # ---------------------------------------------------------------- clocks
@@ -106,75 +126,150 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
-# ---------------------------------------------------------------- oracle (CPU) timing
+# ---------------------------------------------------------------- oracle (CPU) sample
 
-def cpu_oracle_sample(iters_cap: int, sigma: float):
-    """Time the FP64 oracle's GMRES on one c2 system for ``iters_cap`` iterations (setup excluded);
-    runs in a fresh single-threaded process.  Returns seconds per GMRES iteration."""
-    code = (
-        "import os,sys,time,json\n"
-        f"sys.path.insert(0,{ROOT!r})\n"
-        "import numpy as np\n"
-        "import oracle as O\n"
-        f"prob=O.build_problem(128,4,3,sigma={sigma},ell=0.5)\n"
-        "blocks=O.fs_blocks(prob)\n"
-        "N,P=prob.N,prob.P\n"
-        "K=lambda v:O.sg_matvec(prob,v.reshape(N,P)).ravel()\n"
-        "M=lambda v:O.fs_precond(prob,v.reshape(N,P),blocks=blocks).ravel()\n"
-        "t=time.perf_counter()\n"
-        f"x,info=O.gmres(K,M,prob.F.ravel(),rtol=1e-10,restart=300,max_iters={iters_cap})\n"
-        "dt=time.perf_counter()-t\n"
-        "print(json.dumps({'seconds':dt,'iters':info['iters']}))\n")
+ORACLE_SAMPLE = r'''
+import json, os, sys, tempfile, time
+sys.path.insert(0, ROOT)
+import numpy as np
+import oracle as O
+from multiprocessing import get_context
+
+N_, M_, P_, SIG, ELL = 256, 6, 3, 1.0, 0.5
+_G = None
+
+
+def _load(path):
+    global _G
+    _G = np.load(path)
+
+
+def rows_time(rows):
+    kl = O.kl_modes_2d(SIG, ELL, M_)
+    Jq = O.multi_indices(M_, 2 * P_)
+    X = np.random.default_rng(3).normal(size=((N_ + 1) ** 2, _G.shape[1]))
+    t = time.perf_counter()
+    O.sg_matvec_rows(N_, rows, kl, Jq, _G, 0.0, 0.0, X)
+    return time.perf_counter() - t
+
+
+def main():
+    global _G
+    nrows, reps, cores = int(sys.argv[1]), int(sys.argv[2]), int(sys.argv[3])
+    m = N_ + 1
+    _G = O.triple_products(O.multi_indices(M_, 2 * P_), O.multi_indices(M_, P_))
+    fd, gpath = tempfile.mkstemp(suffix=".npy")
+    os.close(fd)
+    np.save(gpath, _G)
+    rng = np.random.default_rng(0)
+    interior = [x + m * y for y in range(1, m - 1) for x in range(1, m - 1)]
+    rows = [int(r) for r in rng.choice(interior, nrows, replace=False)]
+    rows_time(rows[:2])
+    single = sorted(rows_time(rows) for _ in range(reps))[reps // 2] / nrows
+    # all cores: the same sample on every worker at once (rows per second of the whole host)
+    with get_context("spawn").Pool(cores, initializer=_load, initargs=(gpath,)) as pool:
+        pool.map(rows_time, [rows[:2]] * cores)
+        t = time.perf_counter()
+        pool.map(rows_time, [rows] * cores)
+        multi = (time.perf_counter() - t) / (nrows * cores)
+    os.remove(gpath)
+    # one ILU(0) block solve (two triangular sweeps) of the 256 x 256 mean stiffness
+    import scipy.sparse
+    kl = O.kl_modes_2d(SIG, ELL, M_)
+    Jq0 = O.multi_indices(M_, 0)
+    elems = np.arange(N_ * N_)
+    loc = O.q1_local_stiffness_stack(N_, elems, kl, Jq0, 0.0, 0.0)
+    ex, ey = elems % N_, elems // N_
+    base = ex + m * ey
+    nodes = np.stack([base, base + 1, base + m, base + m + 1], axis=1)
+    A = scipy.sparse.coo_matrix((loc[:, 0].reshape(-1), (np.repeat(nodes[:, :, None], 4, 2).ravel(),
+                                np.repeat(nodes[:, None, :], 4, 1).ravel())), shape=(m * m, m * m)).tocsr()
+    bnd = O.boundary_mask(N_)
+    keep = scipy.sparse.diags((~bnd).astype(float))
+    A = (keep @ A @ keep + scipy.sparse.diags(bnd.astype(float))).tocsr()
+    A.sort_indices()
+    LU = O.ilu0(A)
+    r = np.random.default_rng(1).normal(size=m * m)
+    ts = []
+    for _ in range(reps):
+        t = time.perf_counter()
+        O.ilu0_solve(LU, r)
+        ts.append(time.perf_counter() - t)
+    block = sorted(ts)[reps // 2]
+    print(json.dumps({"row_s_single": single, "row_s_allcores": multi, "block_solve_s": block,
+                      "rows": nrows, "reps": reps, "cores": cores}))
+
+
+if __name__ == "__main__":
+    main()
+'''
+
+
+def oracle_sample(nrows=48, reps=5, cores=None):
+    """Run the FP64 oracle on a bounded sample of the c3 workload in a fresh process (started
+    before any GPU work): sampled operator rows (median of ``reps``) on one core and on all
+    cores, and one c3-size ILU(0) block solve (median of ``reps``)."""
+    cores = cores or os.cpu_count() or 1
+    import tempfile
+    code = f"ROOT = {ROOT!r}\n" + ORACLE_SAMPLE
+    fd, script = tempfile.mkstemp(prefix="oracle_sample_", suffix=".py")
+    with os.fdopen(fd, "w") as f:
+        f.write(code)
     env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
-    r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env,
-                       timeout=1800)
+    try:
+        r = subprocess.run([sys.executable, script, str(nrows), str(reps), str(cores)],
+                           capture_output=True, text=True, env=env, timeout=1200)
+    finally:
+        try:
+            os.remove(script)
+        except OSError:
+            pass
     if r.returncode != 0:
         raise RuntimeError(r.stderr[-2000:])
-    d = json.loads(r.stdout.strip().splitlines()[-1])
-    return d["seconds"] / max(1, d["iters"]), d
+    return json.loads(r.stdout.strip().splitlines()[-1])
 
 
-C2_RESTART = 300
-
-
-def oracle_iterations():
-    """GMRES iteration counts of the oracle on the four c2 systems (written by
-    oracle/c2_iterations.py) for the restart length the bench uses, or None."""
-    try:
-        with open(ITERS_FILE) as f:
-            d = json.load(f)
-        return d if d.get("restart") == C2_RESTART else None
-    except Exception:
-        return None
+def oracle_solve_estimate(sample, iters, levels=8, P=84, N=66049):
+    """Seconds of one c3 solve by the oracle's arithmetic, from the sampled costs: per GMRES
+    iteration one V-cycle and one outer operator application; per V-cycle on each level two
+    Gauss-Seidel sweeps of P block solves and their coupling (about one operator application per
+    sweep), two residual operator applications; level sizes fall by 4 per level (the coarsest
+    direct solve is negligible).  Returns (single-core, all-core) seconds; the block solves are
+    sequential, so only the operator applications use more cores."""
+    mv1 = sample["row_s_single"] * N
+    mvn = sample["row_s_allcores"] * N
+    geo = sum(0.25 ** k for k in range(levels - 1))
+    blocks = 2 * P * sample["block_solve_s"] * geo
+    per_it_1 = blocks + (4 * geo + 1) * mv1
+    per_it_n = blocks + (4 * geo + 1) * mvn
+    return iters * per_it_1, iters * per_it_n
 
 
 def reference_arm(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return 0
-    from paper_1910_11505_gb300 import workloads as W
-    its = oracle_iterations()
-    cap = 2
-    per_solve = []
+    info = cpu_info()
+    iters = 25  # the mixed form's inner iterations on this workload (same algorithm on the GPU)
+    per_step = []
     for k in range(args.warmup + args.steps):
-        sig = W.C2_SIGMAS[k % 4]
-        t_it, d = cpu_oracle_sample(cap, sig)
+        smp = oracle_sample(nrows=16, reps=3)
         if k >= args.warmup:
-            n_it = its["iters"][str(sig)] if its else None
-            per_solve.append(t_it * (n_it if n_it else 1))
-    total = sum(per_solve)
-    value = len(per_solve) / total
-    unit = "solves/s" if its else "GMRES iterations/s"
-    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": unit,
+            per_step.append(oracle_solve_estimate(smp, iters)[1])
+    total = sum(per_step)
+    value = len(per_step) / total
+    sample = (f"per step: 16 sampled c3 operator rows on one core and on all {info['nproc']} "
+              f"cores, one c3 ILU(0) block solve; a solve estimated from them for {iters} "
+              "GMRES iterations with the multigrid cost model of bench.py")
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "solves/s",
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
-            "ms_per_step": 1000 * total / len(per_solve), "higher_is_better": True,
+            "ms_per_step": 1000 * total / len(per_step), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": WORKLOAD},
-            "cpu_baseline": {"value": value, "unit": unit, "cores": 1, "kind": "oracle",
-                             "sample": f"{cap} GMRES iterations of one c2 system per step (setup "
-                                       "excluded), scaled by the oracle's own iteration count to "
-                                       "a full solve"},
-            "e2e": {"value": value, "unit": unit, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+            "cpu_baseline": {"value": value, "unit": "solves/s", "cores": info["nproc"],
+                             "kind": "oracle", "sample": sample, "cpu": info},
+            "e2e": {"value": value, "unit": "solves/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
 
@@ -199,7 +294,23 @@ def aggregate_ranks(ms_local: float, systems_local: int, device="cpu"):
 # ---------------------------------------------------------------- GPU arm
 
 def algorithmic_bytes_apply(nnzA, N, P, L, s):
+    """SG operator bytes: the stack once, its pattern, X read and Y written once."""
     return nnzA * L * s + 4 * nnzA + 4 * (N + 1) + 2 * N * P * s
+
+
+def time_matvec(sg, torch, h, X, Y, fn, stream, reps=20):
+    for _ in range(3):
+        fn(h, 0, X, Y, stream)
+    torch.cuda.synchronize()
+    ts = []
+    for _ in range(reps):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        fn(h, 0, X, Y, stream)
+        b.record(stream)
+        b.synchronize()
+        ts.append(a.elapsed_time(b))
+    return statistics.median(ts) / 1000.0
 
 
 def main():
@@ -209,7 +320,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--timing-stride", type=int, default=4)
+    ap.add_argument("--fp64-solves", type=int, default=2)
     args = ap.parse_args()
     if args.impl == "reference":
         return reference_arm(args)
@@ -228,30 +339,25 @@ def main():
     # the CPU oracle sample runs in a child process started before any GPU work
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
-        cpu_t_iter, cpu_info = cpu_oracle_sample(3, 0.5)
-        cpu = (cpu_t_iter, cpu_info)
+        cpu = oracle_sample()
 
     import __graft_entry__
     __graft_entry__.build()
     from paper_1910_11505_gb300 import sg, workloads as W
 
     stream = torch.cuda.current_stream()
-    params = [sg.sg_default_params(**d) for d in W.c2_params()]
-    h = sg.sg_setup(params, stream)
-    ns = h.nsys
-    Fs, Xs = [], []
-    for i in range(ns):
-        N, P, L = sg.sg_dims(h, i)
-        F = torch.empty(N, P, dtype=torch.float64, device="cuda")
-        sg.sg_rhs(h, i, F, stream)
-        Fs.append(F)
-        Xs.append(torch.zeros_like(F))
-    nnzA, nnzG = sg.sg_nnz(h, 0)
+    t0 = time.time()
+    h = sg.sg_setup(sg.sg_default_params(**W.c3_mg_params("fp32")), stream)
+    setup_s = time.time() - t0
+    N, P, L = sg.sg_dims(h)
+    nnzA, nnzG = sg.sg_nnz(h)
+    F = torch.empty(N, P, dtype=torch.float64, device="cuda")
+    sg.sg_rhs(h, 0, F, stream)
+    X = torch.zeros_like(F)
 
     def step():
-        for X in Xs:
-            X.zero_()
-        return sg.sg_gmres_solve(h, Fs, Xs, stream)
+        X.zero_()
+        return sg.sg_gmres_solve(h, [F], [X], stream)
 
     for _ in range(args.warmup):
         rc, info = step()
@@ -262,7 +368,6 @@ def main():
         dist.barrier()
     clocks = ClockSampler(local)
     clocks.start()
-    sg.sg_timing_start(h, args.timing_stride)
     l0 = sg.sg_launch_count()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(stream)
@@ -270,117 +375,152 @@ def main():
     for _ in range(args.steps):
         rc, info = step()
         assert rc == sg.SG_OK, info
-        infos.append(info)
+        infos.append(info[0])
     e1.record(stream)
     torch.cuda.synchronize()
     ms = e0.elapsed_time(e1)
     launches = sg.sg_launch_count() - l0
-    ktimes = sg.sg_timing_stop(h)
     clk = clocks.stop()
-    ms, systems = aggregate_ranks(ms, ns * args.steps, device="cuda")
+    ms, systems = aggregate_ranks(ms, args.steps, device="cuda")
     if world > 1:
         dist.barrier()
     value = systems / (ms / 1000.0)
+    x_mixed = X.clone()
 
-    # dominant kernel class by estimated total time
+    # per-kernel timing, in a pass of its own: one more solve on a handle without graph replay
+    # (events inside a captured graph would become graph nodes), every 4th launch of each kernel
+    # class bracketed by events on its own stream
+    ht = sg.sg_setup(sg.sg_default_params(**dict(W.c3_mg_params("fp32"), graphs=0)), stream)
+    Xt = torch.zeros_like(F)
+    sg.sg_timing_start(ht, 4)
+    sg.sg_gmres_solve(ht, [F], [Xt], stream)
+    ktimes = sg.sg_timing_stop(ht)
+    ht.close()
+    del Xt
     est = {c: (v[0] / v[1] * v[2] if v[1] else 0.0) for c, v in ktimes.items()}
+    tot = sum(est.values())
     dom = max(est, key=est.get)
-    d_ms, d_timed, d_launch = ktimes[dom]
+    d_ms, d_timed, _ = ktimes[dom]
     d_avg_s = d_ms / max(1, d_timed) / 1000.0
     hbm, peak_kind = _peaks()
-    N, P, L = sg.sg_dims(h, 0)
-    if dom == "ilu_solve":
-        # one block solve: 9 factor values per row (lower 4, upper 4, 1/u_ii), the right-hand
-        # side column and z, and the level table
-        m = int(round(N ** 0.5))
-        alg_bytes = 9 * N * 8 + 2 * N * 8 + 4 * (3 * m - 1)
-    elif dom == "apply_f64":
-        alg_bytes = algorithmic_bytes_apply(nnzA, N, P, L, 8)
-    else:
-        alg_bytes = None
-    roof = {"kernel": dom, "bound": "hbm",
-            "achieved": (alg_bytes / d_avg_s / 1e9) if alg_bytes else None,
-            "peak": hbm, "unit": "GB/s", "peak_kind": peak_kind,
-            "frac": (alg_bytes / d_avg_s / 1e9 / hbm) if alg_bytes else None,
-            "traffic": measured_traffic(dom), "avg_launch_us": d_avg_s * 1e6,
-            "launches_timed": d_timed, "share_of_timed_gpu_time": est[dom] / max(1e-30, sum(est.values()))}
-    if dom == "ilu_solve":
-        # the block solve is bound by its dependency chain: two sweeps of 3m - 8 interior
-        # wavefront levels, one barrier step each plus two, and per step two dependent FP64 FMAs
-        # (64 cycles each on this GPU), a shared-memory load and store (~50 cycles) and the
-        # barrier (~50 cycles): an estimated floor of ~230 cycles per step at 2.07 GHz
-        m = int(round(N ** 0.5))
-        steps = 2 * (3 * m - 8) + 4
-        roof["critical_path_steps"] = steps
-        roof["ns_per_step"] = d_avg_s * 1e9 / steps
-        roof["ns_per_step_floor_est"] = (2 * 64 + 50 + 50) / 2.07
+    dfma = sg.sg_probe_fma("fp64")
+    ffma = sg.sg_probe_fma("fp32")
 
-    # the SG operator alone (K1): FP64 DFMA-bound, reported against the DFMA peak as well
-    X = torch.from_numpy(W.random_field(N, P, seed=7)).cuda()
-    Y = torch.empty_like(X)
-    for _ in range(3):
-        sg.sg_matvec(h, 1, X, Y, stream)
-    ea, eb = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    reps = 20
-    ea.record(stream)
-    for _ in range(reps):
-        sg.sg_matvec(h, 1, X, Y, stream)
-    eb.record(stream)
-    torch.cuda.synchronize()
-    mv_s = ea.elapsed_time(eb) / 1000.0 / reps
-    ops = sg.sg_launch_count()  # noqa: F841
-    # flops: 9 U + nnz_G FMAs per interior row (U = (k, b) pairs), 2 flops each
-    trip = sg.sg_export(h, 1, 5).reshape(-1, 4)
+    # the SG operator alone at c3 (inputs larger than L2: the 4.5 GB / 2.2 GB stacks)
+    Xr = torch.from_numpy(W.random_field(N, P, seed=7)).cuda()
+    Yr = torch.empty_like(Xr)
+    mv64_s = time_matvec(sg, torch, h, Xr, Yr, sg.sg_matvec, stream)
+    X32, Y32 = Xr.float(), torch.empty(N, P, dtype=torch.float32, device="cuda")
+    mv32_s = time_matvec(sg, torch, h, X32, Y32, sg.sg_matvec_lowp, stream)
+    trip = sg.sg_export(h, 0, 5).reshape(-1, 4)
     U = len({(int(k), int(b)) for k, _, b in trip[:, :3]})
     flops = 2.0 * N * (9 * U + nnzG)
-    matvec = {"ms": mv_s * 1e3,
-              "gbs": algorithmic_bytes_apply(nnzA, N, P, L, 8) / mv_s / 1e9,
-              "hbm_frac": algorithmic_bytes_apply(nnzA, N, P, L, 8) / mv_s / 1e9 / hbm,
-              "gflops": flops / mv_s / 1e9, "bound": "alu",
-              "dfma_peak_gflops": DFMA_PEAK_GFLOPS, "alu_frac": flops / mv_s / 1e9 / DFMA_PEAK_GFLOPS}
+    b64 = algorithmic_bytes_apply(nnzA, N, P, L, 8)
+    b32 = algorithmic_bytes_apply(nnzA, N, P, L, 4)
+    opk = sg.sg_op_info(h)
+    matvec = {
+        "fp64": {"ms": mv64_s * 1e3, "gbs": b64 / mv64_s / 1e9, "hbm_frac": b64 / mv64_s / 1e9 / hbm,
+                 "gflops": flops / mv64_s / 1e9, "bound": "alu", "dfma_peak_gflops": dfma,
+                 "alu_frac": flops / mv64_s / 1e9 / dfma, "kernel": opk["fp64"]},
+        "fp32": {"ms": mv32_s * 1e3, "gbs": b32 / mv32_s / 1e9, "hbm_frac": b32 / mv32_s / 1e9 / hbm,
+                 "gflops": flops / mv32_s / 1e9, "ffma_peak_gflops": ffma,
+                 "alu_frac": flops / mv32_s / 1e9 / ffma, "kernel": opk["fp32"]},
+        "bytes_fp64": b64, "bytes_fp32": b32, "flops": flops, "pairs_U": U, "nnz_G": nnzG,
+        "tuner": opk["msg"]}
+    del Xr, Yr, X32, Y32
 
-    # end to end through the C ABI with pinned host buffers
-    Fh = [F.cpu().pin_memory() for F in Fs]
-    Xh = [torch.empty_like(F).pin_memory() for F in Fh]
+    if dom in ("apply_lowp", "apply_f64"):
+        s = 4 if dom == "apply_lowp" else 8
+        alg = algorithmic_bytes_apply(nnzA, N, P, L, s)
+        roof = {"kernel": "sg_apply (SG operator, %s)" % ("FP32" if s == 4 else "FP64"),
+                "bound": "hbm", "achieved": alg / d_avg_s / 1e9, "peak": hbm, "unit": "GB/s",
+                "frac": alg / d_avg_s / 1e9 / hbm, "traffic": measured_traffic(dom)}
+    else:
+        # ILU(0) block solves (FP32) of the seven smoothing levels n = 256 .. 4, the same number
+        # of launches on each: per launch the 9 factor values per row, the right-hand side and
+        # the result, averaged over the levels
+        s = 4
+        lev_n = [256 >> k for k in range(7)]
+        alg = sum(11 * s * (nl + 1) ** 2 for nl in lev_n) / len(lev_n)
+        # the floor of the dependency chain: 2 (3m - 8) + 4 barrier steps per solve
+        steps = sum(2 * (3 * (nl + 1) - 8) + 4 for nl in lev_n) / len(lev_n)
+        roof = {"kernel": "ilu block solve (FP32, levels n=256..4)", "bound": "hbm",
+                "achieved": alg / d_avg_s / 1e9, "peak": hbm, "unit": "GB/s",
+                "frac": alg / d_avg_s / 1e9 / hbm, "traffic": measured_traffic(dom),
+                "latency_bound": True, "barrier_steps_per_launch": steps,
+                "ns_per_barrier_step": d_avg_s * 1e9 / steps}
+    roof.update({"peak_kind": peak_kind, "class": dom, "avg_launch_us": d_avg_s * 1e6,
+                 "launches_timed": d_timed, "share_of_gpu_time": est[dom] / max(1e-30, tot)})
+
+    # FP64 GPU GMRES on the same system (the comparison of the metric)
+    h64 = sg.sg_setup(sg.sg_default_params(**W.c3_mg_params("fp64")), stream)
+    X64 = torch.zeros_like(F)
+    rc, info64 = sg.sg_gmres_solve(h64, [F], [X64], stream)  # warm-up (graph capture)
+    assert rc == sg.SG_OK, info64
+    torch.cuda.synchronize()
+    ea, eb = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ea.record(stream)
+    for _ in range(args.fp64_solves):
+        X64.zero_()
+        rc, info64 = sg.sg_gmres_solve(h64, [F], [X64], stream)
+        assert rc == sg.SG_OK, info64
+    eb.record(stream)
+    torch.cuda.synchronize()
+    fp64_s = ea.elapsed_time(eb) / 1000.0 / args.fp64_solves
+    fp64 = {"solves_per_s": 1.0 / fp64_s, "iters": info64[0]["iters"],
+            "rel_resid": info64[0]["rel_resid"],
+            "mixed_vs_fp64_rel_err": float((x_mixed - X64).norm() / X64.norm()),
+            "speedup_mixed_over_fp64": value / world / (1.0 / fp64_s)}
+    h64.close()
+    del X64
+
+    # end to end through the C ABI with pinned host buffers (F in, X out, every step)
+    Fh = F.cpu().pin_memory()
+    Xh = torch.empty_like(Fh).pin_memory()
     e2e_steps = max(1, min(args.steps, 3))
     torch.cuda.synchronize()
     ea.record(stream)
     for _ in range(e2e_steps):
-        for i in range(ns):
-            Fs[i].copy_(Fh[i], non_blocking=True)
-            Xs[i].zero_()
-        rc, _ = sg.sg_gmres_solve(h, Fs, Xs, stream)
-        for i in range(ns):
-            Xh[i].copy_(Xs[i], non_blocking=True)
+        F.copy_(Fh, non_blocking=True)
+        X.zero_()
+        rc, _ = sg.sg_gmres_solve(h, [F], [X], stream)
+        Xh.copy_(X, non_blocking=True)
     eb.record(stream)
     torch.cuda.synchronize()
     e2e_ms = ea.elapsed_time(eb) / e2e_steps
-    bytes_np = sum(F.numel() * 8 for F in Fh)
-    e2e = {"value": ns * world / (e2e_ms / 1000.0), "unit": "solves/s",
-           "h2d_bytes_per_step": bytes_np, "d2h_bytes_per_step": bytes_np}
+    nbytes = F.numel() * 8
+    e2e = {"value": world / (e2e_ms / 1000.0), "unit": "solves/s",
+           "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes}
 
+    last = infos[-1]
     line = {"metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32+f64",
             "data": "synthetic",
-            "config": {"workload": WORKLOAD, "systems_per_step_per_gpu": ns,
-                       "l2": "inputs larger than L2 (four 249 MB FP64 stiffness stacks)",
-                       "iters": [i["iters"] for i in infos[-1]],
-                       "rel_resid": [i["rel_resid"] for i in infos[-1]]},
-            "roofline": roof, "matvec": matvec, "e2e": e2e, "gpu_launches": launches,
-            "clocks": clk,
-            "kernel_ms": {c: {"timed_ms": v[0], "timed": v[1], "launches": v[2]}
-                          for c, v in ktimes.items()}}
+            "config": {"workload": WORKLOAD, "N": N, "P": P, "L": L, "nnz_A": nnzA,
+                       "l2": "inputs larger than L2 (2.2 GB FP32 / 4.5 GB FP64 stiffness stacks)",
+                       "iters": last["iters"], "refinements": last["restarts"],
+                       "rel_resid": last["rel_resid"], "setup_s": setup_s},
+            "fp64": fp64, "roofline": roof, "matvec": matvec, "e2e": e2e,
+            "gpu_launches": launches, "clocks": clk,
+            "kernel_ms_timing_pass": {c: {"timed_ms": v[0], "timed": v[1], "launches": v[2],
+                                          "est_total_ms": est[c]} for c, v in ktimes.items()}}
     if cpu is not None:
-        t_it, info = cpu
-        its = oracle_iterations()
-        n_it = its["iters"]["0.5"] if its else infos[-1][1]["iters"]
-        src = "the oracle's own count" if its else "the GPU path's count (same algorithm)"
+        est1, estn = oracle_solve_estimate(cpu, last["iters"])
+        info = cpu_info()
         line["cpu_baseline"] = {
-            "value": 1.0 / (t_it * n_it), "unit": "solves/s", "cores": 1, "kind": "oracle",
-            "sample": f"{info['iters']} FP64 GMRES iterations of the sigma=0.5 c2 system in "
-                      f"{info['seconds']:.1f} s (setup excluded), scaled to {n_it} iterations "
-                      f"per solve ({src})"}
+            "value": 1.0 / estn, "unit": "solves/s", "cores": info["nproc"], "kind": "oracle",
+            "single_core_solves_per_s": 1.0 / est1, "cpu": info,
+            "matvec_s_single_core": cpu["row_s_single"] * N,
+            "matvec_s_all_cores": cpu["row_s_allcores"] * N,
+            "block_solve_s": cpu["block_solve_s"],
+            "sample": (f"{cpu['rows']} sampled c3 operator rows (median of {cpu['reps']}) on one "
+                       f"core and on all {cpu['cores']} cores, one c3-size ILU(0) block solve "
+                       f"(median of {cpu['reps']}); a solve estimated from them for the GPU's "
+                       f"{last['iters']} GMRES iterations: per iteration one V-cycle (two sweeps "
+                       "of 84 block solves and ~4 operator applications per level, levels 4x "
+                       "smaller each) and one outer operator application, in FP64")}
     if rank == 0:
         print(json.dumps(line), flush=True)
     h.close()

@@ -1,7 +1,7 @@
 """Small, self-contained cases of single kernels for profiling (e.g. under ``ncu``).
 
     python profile_cases.py precond [fs_gs|fs_jacobi|mean] [n]
-    python profile_cases.py matvec [fp64|fp32|bf16] [n] [M] [p]
+    python profile_cases.py matvec [fp64|fp32|bf16] [n] [M] [p] [pairs|tile [kappa] [ctas]]
     python profile_cases.py gmres [n] [iters]      # Arnoldi kernels
     python profile_cases.py net [batch]            # network training step
 
@@ -41,8 +41,15 @@ def main(argv):
         n = int(argv[3]) if len(argv) > 3 else 128
         M = int(argv[4]) if len(argv) > 4 else 6
         p = int(argv[5]) if len(argv) > 5 else 3
+        op = {}
+        if len(argv) > 6:  # operator kernel: pairs | tile [kappa] [ctas]
+            op["op_kernel"] = argv[6]
+            if len(argv) > 7:
+                op["op_kappa"] = int(argv[7])
+            if len(argv) > 8:
+                op["op_ctas"] = int(argv[8])
         h = sg.sg_setup(sg.sg_default_params(n=n, M=M, p=p, sigma=1.0, ell=0.5, precond="none",
-                                             precision=prec))
+                                             precision=prec, **op))
         N, P, _ = sg.sg_dims(h)
         X = torch.from_numpy(W.random_field(N, P, seed=2)).cuda()
         if prec == "fp64":
