@@ -81,7 +81,7 @@ int plan_tile_op(const System& s, int kappa, int elem, size_t smem_max, TilePlan
   op.ctas = ctas;
   if (m < 3 || kappa < 1 || kappa > 4 || P > 256 || ctas < 1 || ctas > 2)
     return fail(SG_ERR_ARG, "tile operator: unsupported sizes");
-  if (!tile_variant_ok(elem, kappa, (P + kWarps - 1) / kWarps, ctas))
+  if (!tile_variant_ok(elem, kappa, ctas))
     return fail(SG_ERR_ARG, "tile operator: no kernel variant for these sizes");
   op.tiles_per_line = (m - 2 + kTW - 1) / kTW;
   op.ntiles = op.tiles_per_line * (m - 2);
@@ -142,8 +142,8 @@ int plan_tile_op(const System& s, int kappa, int elem, size_t smem_max, TilePlan
   const size_t esize = elem == 8 ? 16 : 8;
   const size_t xslab = (size_t)3 * kSlab * op.Pp;
   const size_t abytes_max = round128((size_t)kWarps * kappa * 9 * kTW * elem);
-  const size_t fixed = 128 + 2 * abytes_max + round128(elem * xslab);
-  if (fixed + (size_t)elem * P * kTW > smem_max)
+  const size_t fixed = 128 + 2 * abytes_max + round128(elem * xslab) + (size_t)elem * P * kTW;
+  if (fixed + (size_t)elem * kTW > smem_max)
     return fail(SG_ERR_ARG, "tile operator: P too large for shared memory");
   int slot_cap = (int)std::min<size_t>(16384, (smem_max - fixed) / ((size_t)elem * kTW));
   for (int attempt = 0; attempt < 40; ++attempt) {
@@ -193,21 +193,88 @@ int plan_tile_op(const System& s, int kappa, int elem, size_t smem_max, TilePlan
         ++gi;
       }
       if (!ok) break;
-      // side table of the chunk: union lists, entry offsets per a, entries
-      const size_t off_eptr = round16(8 * ul.size());
-      const size_t off_ent = round16(off_eptr + 4 * (size_t)(P + 1));
+      // side table of the chunk (layout in k_apply_tile.cuh): union lists, the stage-1 pieces
+      // and stage-2 runs of each warp, the entries sorted by a
+      const int ng = (int)op.gdesc.size() - g0;
+      // stage 1: split the groups' union lists into pieces of about equal cost per warp (cost of
+      // a union entry: its 9 X loads plus 10 per pair it forms)
+      std::vector<std::vector<int4>> pw(kWarps);
+      {
+        double total = 0.0;
+        std::vector<double> cost(ul.size());
+        for (size_t u = 0; u < ul.size(); ++u) {
+          cost[u] = 9.0 + 10.0 * __builtin_popcount((unsigned)ul[u].x >> 16);
+          total += cost[u];
+        }
+        const double per = total / kWarps;
+        int wk = 0;
+        double acc = 0.0;
+        for (int g = 0; g < ng; ++g) {
+          const int4 gd = op.gdesc[g0 + g];
+          int u0 = 0;
+          for (int u = 0; u < gd.y; ++u) {
+            acc += cost[gd.x + u];
+            if (acc >= per * (wk + 1) && wk < kWarps - 1 && u + 1 < gd.y) {
+              pw[wk].push_back(make_int4(g, u0, u + 1 - u0, 0));
+              u0 = u + 1;
+              ++wk;
+            }
+          }
+          if (gd.y > u0) pw[wk].push_back(make_int4(g, u0, gd.y - u0, 0));
+          while (wk < kWarps - 1 && acc >= per * (wk + 1)) ++wk;
+        }
+      }
+      // stage 2: runs (one per a with entries), entries sorted by a, split over the warps at run
+      // boundaries with about equal entry counts
+      std::vector<int4> runs;
       size_t nent = 0;
-      for (int a = 0; a < P; ++a) nent += perA[a].size();
+      for (int a = 0; a < P; ++a) {
+        std::sort(perA[a].begin(), perA[a].end());
+        if (!perA[a].empty()) {
+          runs.push_back(make_int4(a, (int)nent, (int)(nent + perA[a].size()), 0));
+          nent += perA[a].size();
+        }
+      }
+      std::vector<int> s2ptr(kWarps + 1, (int)runs.size());
+      {
+        const double per = (double)(nent + runs.size()) / kWarps;
+        double acc = 0.0;
+        int wk = 0;
+        s2ptr[0] = 0;
+        for (size_t r = 0; r < runs.size(); ++r) {
+          while (wk < kWarps - 1 && acc >= per * (wk + 1)) s2ptr[++wk] = (int)r;
+          acc += 1.0 + (runs[r].z - runs[r].y);
+        }
+        while (wk < kWarps - 1) s2ptr[++wk] = (int)runs.size();
+        s2ptr[kWarps] = (int)runs.size();
+      }
+      std::vector<int> s1ptr(kWarps + 1, 0);
+      std::vector<int4> s1;
+      for (int wk = 0; wk < kWarps; ++wk) {
+        s1ptr[wk] = (int)s1.size();
+        s1.insert(s1.end(), pw[wk].begin(), pw[wk].end());
+      }
+      s1ptr[kWarps] = (int)s1.size();
+      const size_t off_ul = 32;
+      const size_t off_s1ptr = round16(off_ul + 8 * ul.size());
+      const size_t off_s1 = round16(off_s1ptr + 4 * (kWarps + 1));
+      const size_t off_s2ptr = round16(off_s1 + 16 * s1.size());
+      const size_t off_s2 = round16(off_s2ptr + 4 * (kWarps + 1));
+      const size_t off_ent = round16(off_s2 + 16 * runs.size());
       const size_t bytes = round16(off_ent + esize * nent);
       const size_t base = op.side.size();
       op.side.resize(base + bytes, 0);
       unsigned char* sb = op.side.data() + base;
-      std::memcpy(sb, ul.data(), 8 * ul.size());
-      int* ep = reinterpret_cast<int*>(sb + off_eptr);
+      const int hdr[8] = {(int)off_ul, (int)off_s1ptr, (int)off_s1, (int)off_s2ptr, (int)off_s2,
+                          (int)off_ent, 0, 0};
+      std::memcpy(sb, hdr, sizeof(hdr));
+      std::memcpy(sb + off_ul, ul.data(), 8 * ul.size());
+      std::memcpy(sb + off_s1ptr, s1ptr.data(), 4 * s1ptr.size());
+      std::memcpy(sb + off_s1, s1.data(), 16 * s1.size());
+      std::memcpy(sb + off_s2ptr, s2ptr.data(), 4 * s2ptr.size());
+      std::memcpy(sb + off_s2, runs.data(), 16 * runs.size());
       size_t q = 0;
-      for (int a = 0; a < P; ++a) {
-        ep[a] = (int)q;
-        std::sort(perA[a].begin(), perA[a].end());
+      for (int a = 0; a < P; ++a)
         for (auto& e : perA[a]) {
           unsigned char* dst = sb + off_ent + esize * q;
           if (elem == 8) {
@@ -220,12 +287,10 @@ int plan_tile_op(const System& s, int kappa, int elem, size_t smem_max, TilePlan
           }
           ++q;
         }
-      }
-      ep[P] = (int)q;
       op.entries += (long long)nent;
       const int nk = (int)op.kperm.size() - k0;
       op.cdesc.push_back(make_int4(k0, nk, g0, (int)op.gdesc.size() - g0));
-      op.cxdesc.push_back(make_int4((int)(base / 16), (int)bytes, (int)off_eptr, (int)off_ent));
+      op.cxdesc.push_back(make_int4((int)(base / 16), (int)bytes, (int)off_s2, (int)off_ent));
       op.max_chunk_k = std::max(op.max_chunk_k, nk);
       op.max_slots = std::max(op.max_slots, slots);
       op.max_side = std::max(op.max_side, bytes);
@@ -233,10 +298,10 @@ int plan_tile_op(const System& s, int kappa, int elem, size_t smem_max, TilePlan
     if (!ok) return fail(SG_ERR_ARG, "tile operator: a k group exceeds the slot capacity");
     op.abytes_slot = (int)round128((size_t)op.max_chunk_k * 9 * kTW * elem);
     op.sbytes_slot = (int)round128(op.max_side);
-    op.tbuf_elems = std::max(op.max_slots, P) * kTW;
+    op.tbuf_elems = std::max(op.max_slots, 1) * kTW;
     op.xslab_elems = (int)xslab;
     op.smem = 128 + 2 * (size_t)op.abytes_slot + 2 * (size_t)op.sbytes_slot +
-              (size_t)elem * (op.tbuf_elems + op.xslab_elems);
+              (size_t)elem * (op.tbuf_elems + (size_t)P * kTW + op.xslab_elems);
     if (op.smem <= smem_max) break;
     slot_cap = std::max(1, (int)(slot_cap * 0.85));
   }
@@ -259,20 +324,46 @@ int verify_tile_plan(const System& s, const TilePlan& pl) {
   for (const Triple& t : s.triples) want[{t.k, t.a, t.b}] = t.g;
   std::map<std::array<int, 3>, double> got;
   std::vector<char> seen((size_t)s.L * P, 0);
+  auto rd = [](const unsigned char* p, size_t off, void* dst, size_t n) { std::memcpy(dst, p + off, n); };
   for (int c = 0; c < pl.nchunks; ++c) {
     const int4 cd = pl.cdesc[c], cx = pl.cxdesc[c];
     if ((size_t)cx.x * 16 + cx.y > pl.side.size() || cx.y % 16 || cx.y > pl.sbytes_slot)
       return fail(SG_ERR_ARG, "plan: side table out of range");
     if ((size_t)cd.y * 9 * 32 * pl.elem > (size_t)pl.abytes_slot) return fail(SG_ERR_ARG, "plan: stack slot");
     const unsigned char* sb = pl.side.data() + (size_t)cx.x * 16;
+    int hdr[8];
+    rd(sb, 0, hdr, sizeof(hdr));
+    for (int i = 0; i < 6; ++i)
+      if (hdr[i] % 16 || hdr[i] > cx.y) return fail(SG_ERR_ARG, "plan: header");
+    // union lists: every entry of every group exactly once in the warps' pieces
+    std::vector<std::vector<char>> covered(cd.w);
+    for (int g = 0; g < cd.w; ++g) covered[g].assign(pl.gdesc[cd.z + g].y, 0);
+    int s1ptr[9];
+    rd(sb, hdr[1], s1ptr, sizeof(s1ptr));
+    if (s1ptr[0] != 0) return fail(SG_ERR_ARG, "plan: stage-1 lists");
+    for (int w = 0; w < 8; ++w) {
+      if (s1ptr[w + 1] < s1ptr[w]) return fail(SG_ERR_ARG, "plan: stage-1 lists");
+      for (int pc = s1ptr[w]; pc < s1ptr[w + 1]; ++pc) {
+        int4 piece;
+        rd(sb, hdr[2] + 16 * (size_t)pc, &piece, 16);
+        if (hdr[2] + 16 * (size_t)(pc + 1) > (size_t)hdr[3]) return fail(SG_ERR_ARG, "plan: piece range");
+        if (piece.x < 0 || piece.x >= cd.w) return fail(SG_ERR_ARG, "plan: piece group");
+        const int4 gd = pl.gdesc[cd.z + piece.x];
+        if (piece.y < 0 || piece.z < 1 || piece.y + piece.z > gd.y) return fail(SG_ERR_ARG, "plan: piece");
+        for (int u = piece.y; u < piece.y + piece.z; ++u) {
+          if (covered[piece.x][u]++) return fail(SG_ERR_ARG, "plan: union entry twice");
+        }
+      }
+    }
     std::vector<std::array<int, 2>> slot_kb;  // (k, b) of each slot
-    for (int g = cd.z; g < cd.z + cd.w; ++g) {
-      const int4 gd = pl.gdesc[g];
-      if (gd.z + gd.w > cd.y || (size_t)(gd.x + gd.y) * 8 > (size_t)cx.z)
+    for (int g = 0; g < cd.w; ++g) {
+      const int4 gd = pl.gdesc[cd.z + g];
+      if (gd.z + gd.w > cd.y || hdr[0] + 8 * (size_t)(gd.x + gd.y) > (size_t)hdr[1])
         return fail(SG_ERR_ARG, "plan: group out of range");
       for (int u = 0; u < gd.y; ++u) {
+        if (!covered[g][u]) return fail(SG_ERR_ARG, "plan: union entry not covered");
         int2 e;
-        std::memcpy(&e, sb + 8 * (size_t)(gd.x + u), 8);
+        rd(sb, hdr[0] + 8 * (size_t)(gd.x + u), &e, 8);
         const int b = e.x & 0xffff, mask = e.x >> 16;
         int sl = e.y;
         for (int j = 0; j < gd.w; ++j)
@@ -288,25 +379,35 @@ int verify_tile_plan(const System& s, const TilePlan& pl) {
     }
     if ((int)slot_kb.size() > pl.max_slots || (size_t)pl.max_slots * 32 > (size_t)pl.tbuf_elems)
       return fail(SG_ERR_ARG, "plan: T buffer");
-    const int* ep = reinterpret_cast<const int*>(sb + cx.z);
-    for (int a = 0; a < P; ++a) {
-      if (ep[a] > ep[a + 1]) return fail(SG_ERR_ARG, "plan: entry offsets");
-      for (int q = ep[a]; q < ep[a + 1]; ++q) {
-        if ((size_t)cx.w + esize * (q + 1) > (size_t)cx.y) return fail(SG_ERR_ARG, "plan: entry out of range");
-        int slot;
-        double g;
-        std::memcpy(&slot, sb + cx.w + esize * q, 4);
-        if (pl.elem == 8) {
-          std::memcpy(&g, sb + cx.w + esize * q + 8, 8);
-        } else {
-          float gf;
-          std::memcpy(&gf, sb + cx.w + esize * q + 4, 4);
-          g = gf;
+    // stage-2 runs: one per a at most, covering the entries once
+    int s2ptr[9];
+    rd(sb, hdr[3], s2ptr, sizeof(s2ptr));
+    std::vector<char> a_seen(P, 0);
+    if (s2ptr[0] != 0) return fail(SG_ERR_ARG, "plan: stage-2 lists");
+    for (int w = 0; w < 8; ++w) {
+      if (s2ptr[w + 1] < s2ptr[w]) return fail(SG_ERR_ARG, "plan: stage-2 lists");
+      for (int rn = s2ptr[w]; rn < s2ptr[w + 1]; ++rn) {
+        int4 run;
+        rd(sb, hdr[4] + 16 * (size_t)rn, &run, 16);
+        if (hdr[4] + 16 * (size_t)(rn + 1) > (size_t)hdr[5]) return fail(SG_ERR_ARG, "plan: run range");
+        if (run.x < 0 || run.x >= P || a_seen[run.x]++) return fail(SG_ERR_ARG, "plan: run output");
+        for (int q = run.y; q < run.z; ++q) {
+          if ((size_t)hdr[5] + esize * (q + 1) > (size_t)cx.y) return fail(SG_ERR_ARG, "plan: entry out of range");
+          int slot;
+          double g;
+          rd(sb, hdr[5] + esize * q, &slot, 4);
+          if (pl.elem == 8) {
+            rd(sb, hdr[5] + esize * q + 8, &g, 8);
+          } else {
+            float gf;
+            rd(sb, hdr[5] + esize * q + 4, &gf, 4);
+            g = gf;
+          }
+          if (slot < 0 || slot >= (int)slot_kb.size()) return fail(SG_ERR_ARG, "plan: entry slot");
+          auto key = std::array<int, 3>{slot_kb[slot][0], run.x, slot_kb[slot][1]};
+          if (got.count(key)) return fail(SG_ERR_ARG, "plan: entry placed twice");
+          got[key] = g;
         }
-        if (slot < 0 || slot >= (int)slot_kb.size()) return fail(SG_ERR_ARG, "plan: entry slot");
-        auto key = std::array<int, 3>{slot_kb[slot][0], a, slot_kb[slot][1]};
-        if (got.count(key)) return fail(SG_ERR_ARG, "plan: entry placed twice");
-        got[key] = g;
       }
     }
   }
@@ -318,7 +419,7 @@ int verify_tile_plan(const System& s, const TilePlan& pl) {
     if (std::fabs(it->second - kv.second) > tol) return fail(SG_ERR_ARG, "plan: entry value");
   }
   const size_t smem = 128 + 2 * (size_t)pl.abytes_slot + 2 * (size_t)pl.sbytes_slot +
-                      (size_t)pl.elem * (pl.tbuf_elems + pl.xslab_elems);
+                      (size_t)pl.elem * (pl.tbuf_elems + (size_t)P * 32 + pl.xslab_elems);
   if (smem != pl.smem || pl.abytes_slot % 128 || pl.sbytes_slot % 128) return fail(SG_ERR_ARG, "plan: layout");
   return SG_OK;
 }

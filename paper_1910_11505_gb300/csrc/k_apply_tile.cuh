@@ -110,7 +110,15 @@ struct TileArgs {
   int abytes_slot, sbytes_slot, tbuf_elems;
 };
 
-template <typename T, int KAPPA, int APW, int MINB>
+// Side table of one chunk (16-byte aligned sections, offsets in the header, bytes):
+//   int hdr[8]   = {off_ul, off_s1ptr, off_s1, off_s2ptr, off_s2, off_ent, 0, 0}
+//   int2 ul[]    union lists of the chunk's groups: (b | mask << 16, first T slot)
+//   int s1ptr[9] per-warp ranges of stage-1 pieces; int4 s1[] = {group, first entry, count, 0}
+//   int s2ptr[9] per-warp ranges of stage-2 runs;   int4 s2[] = {a, first entry, end entry, 0}
+//   TEnt ent[]   stage-2 entries (T slot, G_k[a,b]) sorted by a
+// The pieces and runs are split over the warps at setup so every warp gets about the same work,
+// and each output a of a chunk belongs to one warp's run, so Y accumulates without conflicts.
+template <typename T, int KAPPA, int MINB>
 __global__ void __launch_bounds__(kWarps * 32, MINB) sg_apply_tile_kernel(
     TileArgs d, const int4* __restrict__ chunk, const int4* __restrict__ chunkx,
     const int4* __restrict__ group, const unsigned char* __restrict__ side,
@@ -124,7 +132,8 @@ __global__ void __launch_bounds__(kWarps * 32, MINB) sg_apply_tile_kernel(
   unsigned char* Sslot[2] = {smem_raw + 128 + 2 * (size_t)d.abytes_slot,
                              smem_raw + 128 + 2 * (size_t)d.abytes_slot + d.sbytes_slot};
   T* Ts = reinterpret_cast<T*>(smem_raw + 128 + 2 * (size_t)d.abytes_slot + 2 * (size_t)d.sbytes_slot);
-  T* Xs = Ts + d.tbuf_elems;
+  T* Ys = Ts + d.tbuf_elems;              // P x 32 accumulators of the tile
+  T* Xs = Ys + (size_t)d.P * kTW;
   const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
   const int P = d.P, Pp = d.Pp, m = d.m;
 
@@ -137,8 +146,8 @@ __global__ void __launch_bounds__(kWarps * 32, MINB) sg_apply_tile_kernel(
   }
   __syncthreads();
 
-  // one work item = (tile, chunk): the chunk's stack values of the tile and its side table (union
-  // lists and stage-2 entries), two bulk copies completing on the slot's barrier
+  // one work item = (tile, chunk): the chunk's stack values of the tile and its side table,
+  // two bulk copies completing on the slot's barrier
   auto issue = [&](int t, int c, int slot) {
     const int4 cd = chunk[c], cx = chunkx[c];
     const unsigned abytes = (unsigned)((size_t)cd.y * 9 * kTW * sizeof(T));
@@ -147,7 +156,6 @@ __global__ void __launch_bounds__(kWarps * 32, MINB) sg_apply_tile_kernel(
     bulk_g2s(Sslot[slot], side + (size_t)cx.x * 16, (unsigned)cx.y, &bar[slot]);
   };
 
-  T acc[APW];
   long long it = 0;          // work items of this CTA so far
   bool next_issued = false;  // whether the copies of item it + 1 are in flight
   if (blockIdx.x < d.ntiles && tid == 0) issue(blockIdx.x, 0, 0);
@@ -165,8 +173,7 @@ __global__ void __launch_bounds__(kWarps * 32, MINB) sg_apply_tile_kernel(
       T* dst = Xs + (size_t)nd * Pp;
       for (int b = lane; b < P; b += 32) dst[b] = x < m ? src[b] : T(0);
     }
-#pragma unroll
-    for (int j = 0; j < APW; ++j) acc[j] = T(0);
+    for (int i = tid; i < P * kTW; i += blockDim.x) Ys[i] = T(0);
 
     for (int c = 0; c < d.nchunks; ++c, ++it) {
       // prefetch the next work item into the other slot (its last readers finished before the
@@ -189,103 +196,100 @@ __global__ void __launch_bounds__(kWarps * 32, MINB) sg_apply_tile_kernel(
       }
       const T* Ab = reinterpret_cast<const T*>(Aslot[slot]);
       const unsigned char* Sb = Sslot[slot];
+      const int* hdr = reinterpret_cast<const int*>(Sb);
       const int4 cd = chunk[c];
-      // ---- stage 1: T for the pairs of this warp's group, two b per step
-      if (w < cd.w) {
-        const int4 gd = group[cd.z + w];  // union list start (in the chunk), length, k position, k count
-        T a[KAPPA][9];
-#pragma unroll
-        for (int j = 0; j < KAPPA; ++j) {
-          if (j < gd.w) {
-#pragma unroll
-            for (int e = 0; e < 9; ++e) a[j][e] = Ab[((size_t)(gd.z + j) * 9 + e) * kTW + lane];
-          } else {
-#pragma unroll
-            for (int e = 0; e < 9; ++e) a[j][e] = T(0);
-          }
-        }
-        const int2* ul = reinterpret_cast<const int2*>(Sb) + gd.x;
-        auto pairs_of = [&](int bm, int sl, const T* xv) {
-          const int mask = bm >> 16;
+      // ---- stage 1: this warp's pieces of the groups' union lists, two b per step
+      {
+        const int2* ul = reinterpret_cast<const int2*>(Sb + hdr[0]);
+        const int* s1ptr = reinterpret_cast<const int*>(Sb + hdr[1]);
+        const int4* s1 = reinterpret_cast<const int4*>(Sb + hdr[2]);
+        for (int pc = s1ptr[w]; pc < s1ptr[w + 1]; ++pc) {
+          const int4 piece = s1[pc];
+          const int4 gd = group[cd.z + piece.x];  // union start, length, first k position, k count
+          T a[KAPPA][9];
 #pragma unroll
           for (int j = 0; j < KAPPA; ++j) {
-            if (mask & (1 << j)) {
-              T s = a[j][0] * xv[0];
+            if (j < gd.w) {
 #pragma unroll
-              for (int e = 1; e < 9; ++e) s = fma(a[j][e], xv[e], s);
-              Ts[(size_t)sl * kTW + lane] = s;
-              ++sl;
+              for (int e = 0; e < 9; ++e) a[j][e] = Ab[((size_t)(gd.z + j) * 9 + e) * kTW + lane];
+            } else {
+#pragma unroll
+              for (int e = 0; e < 9; ++e) a[j][e] = T(0);
             }
           }
-        };
-        int u = 0;
-        for (; u + 1 < gd.y; u += 2) {
-          const int2 e0 = ul[u], e1 = ul[u + 1];
-          const int b0 = e0.x & 0xffff, b1 = e1.x & 0xffff;
-          T x0v[9], x1v[9];
+          const int2* gl = ul + gd.x + piece.y;
+          auto pairs_of = [&](int bm, int sl, const T* xv) {
+            const int mask = bm >> 16;
 #pragma unroll
-          for (int dy = 0; dy < 3; ++dy)
+            for (int j = 0; j < KAPPA; ++j) {
+              if (mask & (1 << j)) {
+                T s = a[j][0] * xv[0];
 #pragma unroll
-            for (int dx = 0; dx < 3; ++dx) {
-              const int base = (dy * kSlab + lane + dx) * Pp;
-              x0v[dy * 3 + dx] = Xs[base + b0];
-              x1v[dy * 3 + dx] = Xs[base + b1];
+                for (int e = 1; e < 9; ++e) s = fma(a[j][e], xv[e], s);
+                Ts[(size_t)sl * kTW + lane] = s;
+                ++sl;
+              }
             }
-          pairs_of(e0.x, e0.y, x0v);
-          pairs_of(e1.x, e1.y, x1v);
-        }
-        if (u < gd.y) {
-          const int2 e0 = ul[u];
-          const int b0 = e0.x & 0xffff;
-          T x0v[9];
+          };
+          int u = 0;
+          for (; u + 1 < piece.z; u += 2) {
+            const int2 e0 = gl[u], e1 = gl[u + 1];
+            const int b0 = e0.x & 0xffff, b1 = e1.x & 0xffff;
+            T x0v[9], x1v[9];
 #pragma unroll
-          for (int dy = 0; dy < 3; ++dy)
+            for (int dy = 0; dy < 3; ++dy)
 #pragma unroll
-            for (int dx = 0; dx < 3; ++dx) x0v[dy * 3 + dx] = Xs[(dy * kSlab + lane + dx) * Pp + b0];
-          pairs_of(e0.x, e0.y, x0v);
+              for (int dx = 0; dx < 3; ++dx) {
+                const int base = (dy * kSlab + lane + dx) * Pp;
+                x0v[dy * 3 + dx] = Xs[base + b0];
+                x1v[dy * 3 + dx] = Xs[base + b1];
+              }
+            pairs_of(e0.x, e0.y, x0v);
+            pairs_of(e1.x, e1.y, x1v);
+          }
+          if (u < piece.z) {
+            const int2 e0 = gl[u];
+            const int b0 = e0.x & 0xffff;
+            T x0v[9];
+#pragma unroll
+            for (int dy = 0; dy < 3; ++dy)
+#pragma unroll
+              for (int dx = 0; dx < 3; ++dx) x0v[dy * 3 + dx] = Xs[(dy * kSlab + lane + dx) * Pp + b0];
+            pairs_of(e0.x, e0.y, x0v);
+          }
         }
       }
       __syncthreads();
-      // ---- stage 2: Y[row, a] += sum G T over this chunk's entries of the warp's outputs
+      // ---- stage 2: this warp's runs: Y[a, row] += sum over the run's entries of G T[slot]
       {
-        const int4 cx = chunkx[c];
-        const int* ep = reinterpret_cast<const int*>(Sb + cx.z);
-        const TEnt<T>* ent = reinterpret_cast<const TEnt<T>*>(Sb + cx.w);
-#pragma unroll
-        for (int j = 0; j < APW; ++j) {
-          const int a = w + kWarps * j;
-          if (a < P) {
-            T s0 = T(0), s1 = T(0);
-            int q = ep[a];
-            const int q1 = ep[a + 1];
-            for (; q + 1 < q1; q += 2) {
-              const TEnt<T> f0 = ent[q], f1 = ent[q + 1];
-              s0 = fma(f0.g, Ts[(size_t)f0.slot * kTW + lane], s0);
-              s1 = fma(f1.g, Ts[(size_t)f1.slot * kTW + lane], s1);
-            }
-            if (q < q1) {
-              const TEnt<T> f0 = ent[q];
-              s0 = fma(f0.g, Ts[(size_t)f0.slot * kTW + lane], s0);
-            }
-            acc[j] += s0 + s1;
+        const int* s2ptr = reinterpret_cast<const int*>(Sb + hdr[3]);
+        const int4* s2 = reinterpret_cast<const int4*>(Sb + hdr[4]);
+        const TEnt<T>* ent = reinterpret_cast<const TEnt<T>*>(Sb + hdr[5]);
+        for (int rn = s2ptr[w]; rn < s2ptr[w + 1]; ++rn) {
+          const int4 run = s2[rn];
+          T s0 = T(0), s1v = T(0);
+          int q = run.y;
+          for (; q + 1 < run.z; q += 2) {
+            const TEnt<T> f0 = ent[q], f1 = ent[q + 1];
+            s0 = fma(f0.g, Ts[(size_t)f0.slot * kTW + lane], s0);
+            s1v = fma(f1.g, Ts[(size_t)f1.slot * kTW + lane], s1v);
           }
+          if (q < run.z) {
+            const TEnt<T> f0 = ent[q];
+            s0 = fma(f0.g, Ts[(size_t)f0.slot * kTW + lane], s0);
+          }
+          Ys[(size_t)run.x * kTW + lane] += s0 + s1v;
         }
       }
       __syncthreads();
     }
     if (failed) break;
-    // ---- epilogue: Y rows of the tile through shared memory (coalesced)
-#pragma unroll
-    for (int j = 0; j < APW; ++j) {
-      const int a = w + kWarps * j;
-      if (a < P) Ts[(size_t)a * kTW + lane] = acc[j];
-    }
-    __syncthreads();
+    // ---- epilogue: Y rows of the tile (coalesced)
     const size_t row0 = (size_t)y * m + x0;
     for (int r = w; r < nrows; r += kWarps) {
       const size_t o = (row0 + r) * P;
       for (int a = lane; a < P; a += 32) {
-        T v = alpha * Ts[(size_t)a * kTW + r];
+        T v = alpha * Ys[(size_t)a * kTW + r];
         if (B != nullptr) v = fma(beta, B[o + a], v);
         Y[o + a] = v;
       }
@@ -327,24 +331,18 @@ __global__ void __launch_bounds__(kWarps * 32, MINB) sg_apply_tile_kernel(
   }
 }
 
-// Kernel variants that are instantiated (the others would spill registers or are not needed):
-// FP64 with kappa 1 or 2, two CTAs per SM only without spills; FP32 with kappa 1, 2 or 4.
-inline int tile_apw_bucket(int apw) { return apw <= 8 ? 8 : apw <= 16 ? 16 : 32; }
-inline bool tile_variant_ok(int elem, int kappa, int apw, int ctas) {
-  const int b = tile_apw_bucket(apw);
-  if (elem == 8) {
-    if (kappa != 1 && kappa != 2) return false;
-    if (ctas == 2) return (kappa == 1 && b <= 16) || (kappa == 2 && b == 8);
-    return true;
-  }
-  if (kappa != 1 && kappa != 2 && kappa != 4) return false;
-  return ctas == 1 || b <= 16;
+// Kernel variants that are instantiated: FP64 with kappa 1 or 2, FP32 with kappa 1, 2 or 4,
+// each for one or two CTAs per SM.
+inline bool tile_variant_ok(int elem, int kappa, int ctas) {
+  if (ctas != 1 && ctas != 2) return false;
+  if (elem == 8) return kappa == 1 || kappa == 2;
+  return kappa == 1 || kappa == 2 || kappa == 4;
 }
 
-template <typename T, int KAPPA, int APW, int MINB>
+template <typename T, int KAPPA, int MINB>
 int launch_tile_k(const System& s, const TileOp& op, const T* X, T* Y, T alpha, const T* B,
                   T beta, cudaStream_t st, const int* done) {
-  auto kern = sg_apply_tile_kernel<T, KAPPA, APW, MINB>;
+  auto kern = sg_apply_tile_kernel<T, KAPPA, MINB>;
   SG_TRY(ensure_smem((const void*)kern, op.smem));
   TileArgs d{s.pat.m, op.tiles_per_line, op.ntiles, s.P, op.Pp, op.nchunks,
              (long long)op.Lu * 9 * kTW, op.abytes_slot, op.sbytes_slot, op.tbuf_elems};

@@ -6,32 +6,16 @@
 
 namespace sg {
 
-namespace {
-
-template <int KAPPA, int MINB>
-int by_apw(const System& s, const TileOp& op, const double* X, double* Y, double alpha, const double* B,
-           double beta, cudaStream_t st, const int* done) {
-  const int b = tile_apw_bucket(op.apw);
-  if (b == 8) return launch_tile_k<double, KAPPA, 8, MINB>(s, op, X, Y, alpha, B, beta, st, done);
-  if constexpr (MINB == 1 || KAPPA == 1) {
-    if (b == 16) return launch_tile_k<double, KAPPA, 16, MINB>(s, op, X, Y, alpha, B, beta, st, done);
-  }
-  if constexpr (MINB == 1) return launch_tile_k<double, KAPPA, 32, MINB>(s, op, X, Y, alpha, B, beta, st, done);
-  return fail(SG_ERR_ARG, "tile operator: kernel variant not built");
-}
-
-}  // namespace
-
 int launch_tile_op_f64(const System& s, const TileOp& op, const double* X, double* Y, double alpha,
                       const double* B, double beta, cudaStream_t st, const int* done) {
-  if (!tile_variant_ok(sizeof(double), op.kappa, op.apw, op.ctas))
+  if (!tile_variant_ok(sizeof(double), op.kappa, op.ctas))
     return fail(SG_ERR_ARG, "tile operator: kernel variant not built");
   const bool two = op.ctas == 2;
   switch (op.kappa) {
-    case 1: return two ? by_apw<1, 2>(s, op, X, Y, alpha, B, beta, st, done)
-                       : by_apw<1, 1>(s, op, X, Y, alpha, B, beta, st, done);
-    default: return two ? by_apw<2, 2>(s, op, X, Y, alpha, B, beta, st, done)
-                        : by_apw<2, 1>(s, op, X, Y, alpha, B, beta, st, done);
+    case 1: return two ? launch_tile_k<double, 1, 2>(s, op, X, Y, alpha, B, beta, st, done)
+                       : launch_tile_k<double, 1, 1>(s, op, X, Y, alpha, B, beta, st, done);
+    default: return two ? launch_tile_k<double, 2, 2>(s, op, X, Y, alpha, B, beta, st, done)
+                        : launch_tile_k<double, 2, 1>(s, op, X, Y, alpha, B, beta, st, done);
   }
 }
 
