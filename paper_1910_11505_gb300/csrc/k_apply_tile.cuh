@@ -218,17 +218,25 @@ __global__ void __launch_bounds__(kWarps * 32, MINB) sg_apply_tile_kernel(
             }
           }
           const int2* gl = ul + gd.x + piece.y;
+          // T for the k of the group that need this b.  Each 9-term sum runs as three partial
+          // sums over the stencil lines (a short dependency chain).  In FP32 every k of the group
+          // is computed and only the needed ones stored, so the products of several k and b are
+          // independent and overlap; in FP64 only the needed ones are computed (the FP64 pipe,
+          // not latency, bounds that kernel on this GPU).
           auto pairs_of = [&](int bm, int sl, const T* xv) {
             const int mask = bm >> 16;
 #pragma unroll
             for (int j = 0; j < KAPPA; ++j) {
-              if (mask & (1 << j)) {
-                T s = a[j][0] * xv[0];
-#pragma unroll
-                for (int e = 1; e < 9; ++e) s = fma(a[j][e], xv[e], s);
-                Ts[(size_t)sl * kTW + lane] = s;
-                ++sl;
-              }
+              const bool need = mask & (1 << j);
+              if (sizeof(T) == 8 && !need) continue;
+              T s0 = a[j][0] * xv[0], s1 = a[j][3] * xv[3], s2 = a[j][6] * xv[6];
+              s0 = fma(a[j][1], xv[1], s0);
+              s1 = fma(a[j][4], xv[4], s1);
+              s2 = fma(a[j][7], xv[7], s2);
+              s0 = fma(a[j][2], xv[2], s0);
+              s1 = fma(a[j][5], xv[5], s1);
+              s2 = fma(a[j][8], xv[8], s2);
+              if (need) Ts[(size_t)(sl + __popc(mask & ((1 << j) - 1))) * kTW + lane] = (s0 + s1) + s2;
             }
           };
           int u = 0;

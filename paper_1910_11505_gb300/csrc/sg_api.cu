@@ -9,6 +9,7 @@
 #include <cstring>
 #include <map>
 #include <mutex>
+#include <thread>
 
 #include "sg_internal.h"
 
@@ -474,6 +475,8 @@ static void free_system(System* s) {
   s->graphs.clear();
   if (s->hpin) cudaFreeHost(s->hpin);
   if (s->ev) cudaEventDestroy(s->ev);
+  for (cudaEvent_t e : {s->seg_ev[0], s->seg_ev[1]})
+    if (e) cudaEventDestroy(e);
   if (s->stream2) cudaStreamDestroy(s->stream2);
   for (cudaEvent_t e : {s->ev_z, s->ev_r[0], s->ev_r[1]})
     if (e) cudaEventDestroy(e);
@@ -514,6 +517,8 @@ static int setup_system(System& s, cudaStream_t st, bool krylov = true) {
   SG_CUDA(cudaDeviceGetStreamPriorityRange(&prio_low, &prio_high));
   SG_CUDA(cudaStreamCreateWithPriority(&s.stream, cudaStreamNonBlocking, prio_high));
   SG_CUDA(cudaEventCreateWithFlags(&s.ev, cudaEventDisableTiming));
+  SG_CUDA(cudaEventCreateWithFlags(&s.seg_ev[0], cudaEventDisableTiming));
+  SG_CUDA(cudaEventCreateWithFlags(&s.seg_ev[1], cudaEventDisableTiming));
   SG_CUDA(cudaMallocHost((void**)&s.hpin, 16 * sizeof(double)));
 
   SG_TRY(upload_i(s.rowptr, s.pat.rowptr, st));
@@ -660,6 +665,10 @@ struct SolveState {
   int iters = 0, restarts = 0, status = SG_OK;
   bool active = true, graphed = false;
   int jmax = 0;
+  int seg_next = 0;     // first step of the next segment to queue
+  int seg_queued = 0;   // segments queued in this cycle
+  int seg_seen = 0;     // segments whose flags the host has read
+  bool seg_more = false;  // more segments may be needed
 };
 
 static int iteration(System& s, int j, int last_col) {
@@ -693,30 +702,32 @@ static int residual(SolveState& ss) {
   return SG_OK;
 }
 
-// One whole cycle of a system on its stream: cycle target upload (from the pinned mirror),
-// V0 = r / beta, jmax Arnoldi steps, back-substitution and update, new residual and read-back.
-static int enqueue_cycle(SolveState& q) {
-  System& s = *q.s;
-  SG_CUDA(cudaMemcpyAsync(s.scal.p, s.hpin, sizeof(double), cudaMemcpyHostToDevice, s.stream));
-  SG_TRY(k_init_cycle(s, (size_t)s.N * s.P, s.rvec.p, s.stream));
-  for (int j = 0; j < q.jmax; ++j) SG_TRY(iteration(s, j, q.jmax - 1));
-  SG_TRY(k_finish_cycle(s, (size_t)s.N * s.P, q.X, s.prm.precision != SG_FP64, s.stream));
-  return residual(q);
-}
+// A cycle is queued in segments of kSegSteps Arnoldi steps.  After each segment the cycle's flags
+// are copied to pinned host memory behind an event; the host queues the next segment only while
+// the segment before the last one queued has not reported convergence, so at most two segments
+// of steps that return at once (the device's done flag) follow the converged step, instead of
+// the rest of the cycle.
+constexpr int kSegSteps = 6;
 
-// Replay the captured graph of this cycle shape, capturing it on first use.  Kernel timing is
-// suspended during capture (events recorded there would become graph nodes).
-static int launch_cycle_graph(SolveState& q) {
+// Steps [j0, j1) of the current cycle, as plain launches or as a graph captured on first use
+// (keyed by the cycle length and j0).  Kernel timing is suspended during capture (events
+// recorded there would become graph nodes).
+static int launch_segment(SolveState& q, int j0, int j1) {
   System& s = *q.s;
+  if (!q.graphed) {
+    for (int j = j0; j < j1; ++j) SG_TRY(iteration(s, j, q.jmax - 1));
+    return SG_OK;
+  }
   for (auto& g : s.graphs)
-    if (g.jmax == q.jmax && g.F == q.F && g.X == q.X) {
+    if (g.jmax == q.jmax && g.j0 == j0) {
       SG_CUDA(cudaGraphLaunch(g.exec, s.stream));
       return SG_OK;
     }
   const bool timing = s.timer && s.timer->on;
   if (timing) s.timer->on = false;
   SG_CUDA(cudaStreamBeginCapture(s.stream, cudaStreamCaptureModeThreadLocal));
-  int rc = enqueue_cycle(q);
+  int rc = SG_OK;
+  for (int j = j0; j < j1 && rc == SG_OK; ++j) rc = iteration(s, j, q.jmax - 1);
   cudaGraph_t graph = nullptr;
   cudaError_t e = cudaStreamEndCapture(s.stream, &graph);
   if (timing) s.timer->on = true;
@@ -728,8 +739,22 @@ static int launch_cycle_graph(SolveState& q) {
   e = cudaGraphInstantiate(&exec, graph, 0);
   cudaGraphDestroy(graph);
   if (e != cudaSuccess) return fail(SG_ERR_CUDA, std::string("graph instantiate: ") + cudaGetErrorString(e));
-  s.graphs.push_back({q.jmax, q.F, q.X, exec});
+  s.graphs.push_back({q.jmax, j0, exec});
   SG_CUDA(cudaGraphLaunch(exec, s.stream));
+  return SG_OK;
+}
+
+// Queue the next segment of q's cycle and the read-back of its flags (slot = segment parity).
+static int queue_segment(SolveState& q) {
+  System& s = *q.s;
+  const int j0 = q.seg_next, j1 = std::min(q.jmax, j0 + kSegSteps);
+  SG_TRY(launch_segment(q, j0, j1));
+  const int slot = q.seg_queued & 1;
+  SG_CUDA(cudaMemcpyAsync(s.hpin + 8 + 2 * slot, s.flags.p, 4 * sizeof(int), cudaMemcpyDeviceToHost,
+                          s.stream));
+  SG_CUDA(cudaEventRecord(s.seg_ev[slot], s.stream));
+  q.seg_next = j1;
+  q.seg_queued += 1;
   return SG_OK;
 }
 
@@ -765,32 +790,54 @@ int gmres_solve_all(sg_handle* h, const double* const* F, double* const* X, sg_s
     }
   }
   while (true) {
-    int maxj = 0;
+    bool any = false;
     for (auto& q : st) {
       System& s = *q.s;
       q.active = q.status == SG_OK && q.beta > q.target && q.iters < s.prm.max_iters;
       if (!q.active) continue;
+      any = true;
       double cyc = q.target;
       if (s.prm.precision != SG_FP64) cyc = std::max(q.target, s.prm.inner_rtol * q.beta);
       s.hpin[0] = cyc;
       q.jmax = std::min(s.m, s.prm.max_iters - q.iters);
       q.graphed = s.prm.graphs != 0;
-      if (q.graphed) {
-        SG_TRY(launch_cycle_graph(q));
-        maxj = std::max(maxj, 1);
-        continue;
-      }
+      q.seg_next = q.seg_queued = q.seg_seen = 0;
       SG_CUDA(cudaMemcpyAsync(s.scal.p, s.hpin, sizeof(double), cudaMemcpyHostToDevice, s.stream));
       SG_TRY(k_init_cycle(s, (size_t)s.N * s.P, s.rvec.p, s.stream));
-      maxj = std::max(maxj, q.jmax);
+      // two segments in flight per system
+      SG_TRY(queue_segment(q));
+      if (q.seg_next < q.jmax) SG_TRY(queue_segment(q));
+      q.seg_more = q.seg_next < q.jmax;
     }
-    if (maxj == 0) break;
-    // plain launches: the systems' Arnoldi steps are interleaved so their streams overlap
-    for (int j = 0; j < maxj; ++j)
-      for (auto& q : st)
-        if (q.active && !q.graphed && j < q.jmax) SG_TRY(iteration(*q.s, j, q.jmax - 1));
+    if (!any) break;
+    // keep queuing segments while the device has not reported convergence
+    bool pending = true;
+    while (pending) {
+      pending = false;
+      for (auto& q : st) {
+        if (!q.active || !q.seg_more) continue;
+        System& s = *q.s;
+        const int slot = q.seg_seen & 1;
+        cudaError_t e = cudaEventQuery(s.seg_ev[slot]);
+        if (e == cudaErrorNotReady) {
+          pending = true;
+          continue;
+        }
+        if (e != cudaSuccess) return fail(SG_ERR_CUDA, std::string("segment event: ") + cudaGetErrorString(e));
+        const int* fl = reinterpret_cast<const int*>(s.hpin + 8 + 2 * slot);
+        q.seg_seen += 1;
+        if (fl[0] || q.seg_next >= q.jmax) {
+          q.seg_more = false;
+          continue;
+        }
+        SG_TRY(queue_segment(q));
+        q.seg_more = q.seg_next < q.jmax;
+        pending = pending || q.seg_more;
+      }
+      if (pending) std::this_thread::yield();
+    }
     for (auto& q : st) {
-      if (!q.active || q.graphed) continue;
+      if (!q.active) continue;
       System& s = *q.s;
       SG_TRY(k_finish_cycle(s, (size_t)s.N * s.P, q.X, s.prm.precision != SG_FP64, s.stream));
       SG_TRY(residual(q));

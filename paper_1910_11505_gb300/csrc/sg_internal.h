@@ -251,12 +251,11 @@ struct System {
   double* hpin = nullptr;      // pinned host mirror of state[0..3] and flags[0..2]
   Timer* timer = nullptr;      // the handle's timer
   struct CycleGraph {
-    int jmax;
-    const double* F;
-    double* X;
+    int jmax, j0;
     cudaGraphExec_t exec;
   };
-  std::vector<CycleGraph> graphs;  // captured GMRES cycles (sg_params.graphs = 1)
+  std::vector<CycleGraph> graphs;  // captured segments of GMRES cycles (sg_params.graphs = 1)
+  cudaEvent_t seg_ev[2] = {nullptr, nullptr};  // flags of the last two queued cycle segments
   cudaStream_t stream = nullptr;
   cudaEvent_t ev = nullptr;
   // Gauss-Seidel sweep: second stream for the later-column scatters, which overlap the next
