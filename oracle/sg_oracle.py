@@ -21,6 +21,9 @@ Readings where the paper is silent (numbered as in the design notes):
   R7  right-preconditioned GMRES(restart), classical Gram-Schmidt applied twice (CGS2), Givens
       rotations, stop on the true relative residual ||F - K x|| / ||F||.
   R8  mean-based preconditioner = I (x) ILU0(A_0), A_0 the stiffness of E[a].
+  R18 ILU(0) ordering (the paper names none): natural order by default; a four-colour ordering
+      (colour (x mod 2) + 2 (y mod 2)) is the alternative, whose triangular solves run one colour
+      at a time with every node of a colour independent.
 
 Layout conventions: a nodal field over the chaos basis is an N x P float64 array X with
 X[j, b] = u_b(node j); node id = i + m*j for grid point (i/n, j/n), m = n + 1.
@@ -42,7 +45,7 @@ __all__ = [
     "chaos_coefficients", "gauss_legendre_3", "q1_local_stiffness_stack",
     "SGProblem", "build_problem", "stack_rows_dense", "sg_matvec", "sg_matvec_rows",
     "ilu0", "ilu0_solve", "mean_precond", "fs_blocks", "fs_precond", "gmres", "boundary_mask",
-    "prolongation", "mg_levels", "mg_setup", "mg_vcycle",
+    "prolongation", "mg_levels", "mg_setup", "mg_vcycle", "color4_order",
 ]
 
 
@@ -406,10 +409,27 @@ def sg_matvec_rows(n, rows, kl, Jq, G, a_min, mu, X):
 # ILU(0) (reading R5) and the preconditioners.
 # ----------------------------------------------------------------------------------------------
 
-def ilu0(A: scipy.sparse.csr_matrix):
-    """Incomplete LU with zero fill on the pattern of A, natural order, no pivoting (the IKJ
-    form: for each row i, for each k < i in its pattern, l_ik = a_ik / u_kk and
-    a_ij -= l_ik u_kj for j > k present in both rows).  Returns (unit lower L, upper U) as CSR."""
+def color4_order(n: int) -> np.ndarray:
+    """Four-colour ordering of the nodes of the n x n mesh (reading R18): colour (x mod 2) +
+    2 (y mod 2), colours in turn, natural order inside a colour.  No two nodes of one colour are
+    neighbours in the 9-point stencil."""
+    m = n + 1
+    x = np.arange(m * m) % m
+    y = np.arange(m * m) // m
+    return np.lexsort((np.arange(m * m), (x % 2) + 2 * (y % 2)))
+
+
+def ilu0(A: scipy.sparse.csr_matrix, order=None):
+    """Incomplete LU with zero fill on the pattern of A, no pivoting (the IKJ form: for each
+    row i, for each k < i in its pattern, l_ik = a_ik / u_kk and a_ij -= l_ik u_kj for j > k
+    present in both rows), in natural order (reading R5) or, with ``order`` (a permutation of the
+    rows), of A permuted symmetrically into that order.  Returns (unit lower L, upper U) as CSR,
+    with the permutation appended when one was given."""
+    if order is not None:
+        order = np.asarray(order)
+        Ap = A.tocsr()[order][:, order].tocsr()
+        Lo, Up = ilu0(Ap)
+        return Lo, Up, order
     A = A.tocsr().copy()
     A.sort_indices()
     indptr, indices, data = A.indptr, A.indices, A.data.astype(np.float64).copy()
@@ -437,7 +457,15 @@ def ilu0(A: scipy.sparse.csr_matrix):
 
 
 def ilu0_solve(LU, R):
-    """(L U)^{-1} R for a vector or a column block R."""
+    """(L U)^{-1} R for a vector or a column block R (in the factorisation's ordering)."""
+    if len(LU) == 3:
+        Lo, Up, order = LU
+        Rp = np.asarray(R)[order]
+        Y = scipy.sparse.linalg.spsolve_triangular(Lo, Rp, lower=True, unit_diagonal=True)
+        Zp = scipy.sparse.linalg.spsolve_triangular(Up, Y, lower=False)
+        Z = np.empty_like(Zp)
+        Z[order] = Zp
+        return Z
     Lo, Up = LU
     Y = scipy.sparse.linalg.spsolve_triangular(Lo, R, lower=True, unit_diagonal=True)
     return scipy.sparse.linalg.spsolve_triangular(Up, Y, lower=False)
@@ -451,17 +479,23 @@ def _richardson(apply_A, LU, rhs, iters):
     return z
 
 
-def mean_precond(prob: SGProblem, R: np.ndarray, inner_iters: int = 1, LU=None) -> np.ndarray:
+def _order(prob, ordering):
+    return None if ordering in (None, "natural") else color4_order(prob.n)
+
+
+def mean_precond(prob: SGProblem, R: np.ndarray, inner_iters: int = 1, LU=None,
+                 ordering=None) -> np.ndarray:
     """Mean-based block-diagonal preconditioner (reading R8): every chaos column of R is solved
-    with ILU0(A_0), ``inner_iters`` Richardson steps."""
+    with ILU0(A_0) (natural or four-colour ordering), ``inner_iters`` Richardson steps."""
     if LU is None:
-        LU = ilu0(prob.A[0])
+        LU = ilu0(prob.A[0], _order(prob, ordering))
     A0 = prob.A[0]
     return _richardson(lambda z: A0 @ z, LU, R, inner_iters)
 
 
-def fs_blocks(prob: SGProblem):
-    """Diagonal blocks K_aa = sum_q G_q[a, a] A_q (Eq. K_matrix) and their ILU(0) factors."""
+def fs_blocks(prob: SGProblem, ordering=None):
+    """Diagonal blocks K_aa = sum_q G_q[a, a] A_q (Eq. K_matrix) and their ILU(0) factors
+    (natural or four-colour ordering)."""
     blocks, facs = [], []
     for a in range(prob.P):
         Kaa = None
@@ -472,7 +506,7 @@ def fs_blocks(prob: SGProblem):
         Kaa = Kaa.tocsr()
         Kaa.sort_indices()
         blocks.append(Kaa)
-        facs.append(ilu0(Kaa))
+        facs.append(ilu0(Kaa, _order(prob, ordering)))
     return blocks, facs
 
 
@@ -628,18 +662,19 @@ def mg_levels(n, M, p, coarse=2, **kw):
     return [build_problem(s, M, p, **kw) for s in reversed(sizes)]
 
 
-def mg_setup(levels, smoother="fs_gs"):
-    """Per level: smoother data (ILU(0) factors), the prolongation from the level below, and the
-    dense coarsest-level operator for the direct solve."""
+def mg_setup(levels, smoother="fs_gs", ordering=None):
+    """Per level: smoother data (ILU(0) factors in natural or four-colour ordering), the
+    prolongation from the level below, and the dense coarsest-level operator for the direct
+    solve."""
     data = []
     for li, prob in enumerate(levels):
         d = {"P": prolongation(levels[li - 1].n) if li > 0 else None}
         if li == 0:
             d["K"] = sum(np.kron(prob.G[k], prob.A[k].toarray()) for k in range(prob.L))
         elif smoother == "mean":
-            d["LU"] = ilu0(prob.A[0])
+            d["LU"] = ilu0(prob.A[0], _order(prob, ordering))
         else:
-            d["blocks"] = fs_blocks(prob)
+            d["blocks"] = fs_blocks(prob, ordering)
         data.append(d)
     return data
 

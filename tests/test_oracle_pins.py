@@ -590,3 +590,59 @@ def test_mg_preconditioned_gmres_iterations_stay_flat_in_the_mesh():
         its.append(info["iters"])
     assert max(its) - min(its) <= 2, its
     assert max(its) <= 12, its
+
+
+# ------------------------------------------------------------------ four-colour ILU(0) (reading R18)
+
+def test_color4_order_separates_stencil_neighbours():
+    for n in (2, 3, 6, 9):
+        order = O.color4_order(n)
+        m = n + 1
+        assert sorted(order.tolist()) == list(range(m * m))
+        x, y = order % m, order // m
+        col = (x % 2) + 2 * (y % 2)
+        assert np.all(np.diff(col) >= 0)               # colours in turn
+        A = O.build_problem(n, 1, 0, sigma=0.0).A[0]
+        c_of = np.empty(m * m, int)
+        c_of[order] = col
+        rows, cols = A.nonzero()
+        off = rows != cols
+        assert np.all(c_of[rows[off]] != c_of[cols[off]])  # no coupling inside a colour
+
+
+def test_color4_ilu0_defining_property_and_solve():
+    prob = O.build_problem(7, 2, 1, sigma=0.6, ell=0.8, a_min=0.02)
+    A = prob.A[0]
+    LU = O.ilu0(A, O.color4_order(7))
+    Lo, Up, order = LU
+    Ap = A[order][:, order].toarray()
+    prod = (Lo @ Up).toarray()
+    pat = Ap != 0
+    assert np.allclose(prod[pat], Ap[pat], rtol=0, atol=1e-13)
+    # L couples a node only to earlier colours: its strictly lower part has no entry inside a
+    # colour block; the unit diagonal is implicit in the stored factor
+    m = 8
+    col = ((order % m) % 2) + 2 * ((order // m) % 2)
+    Ls = scipy.sparse.tril(Lo, k=-1).tocoo()
+    assert np.all(col[Ls.row] > col[Ls.col])
+    # the solve inverts L U in the original ordering
+    r = np.random.default_rng(2).normal(size=A.shape[0])
+    z = O.ilu0_solve(LU, r)
+    M = np.zeros_like(prod)
+    M[np.ix_(order, order)] = prod
+    assert np.allclose(M @ z, r, atol=1e-12)
+
+
+def test_mg_with_color4_smoother_is_mesh_independent():
+    its = []
+    for n in (8, 16, 32):
+        levels = O.mg_levels(n, 2, 2, sigma=0.5, ell=0.7)
+        data = O.mg_setup(levels, "fs_gs", ordering="color4")
+        prob = levels[-1]
+        _, info = O.gmres(lambda v, prob=prob: O.sg_matvec(prob, v.reshape(prob.N, prob.P)).ravel(),
+                          lambda v, prob=prob, levels=levels, data=data:
+                          O.mg_vcycle(levels, data, v.reshape(prob.N, prob.P)).ravel(),
+                          prob.F, rtol=1e-10, restart=30)
+        assert info["converged"]
+        its.append(info["iters"])
+    assert max(its) - min(its) <= 3 and max(its) <= 16, its
