@@ -84,7 +84,13 @@ typedef struct {
                      /* for the process), SG_OP_PAIRS or SG_OP_TILE                             */
   int op_kappa;      /* SG_OP_TILE: k per register group, 1, 2 or 4 (0: 2 in FP64, 4 in FP32)   */
   int op_ctas;       /* SG_OP_TILE: CTAs per SM the shared memory is planned for, 1 or 2 (0: 1) */
+  int ilu_order;     /* ILU(0) node ordering: SG_ILU_NATURAL, or SG_ILU_COLOR4 (colour           */
+                     /* (x mod 2) + 2 (y mod 2), colours in turn: every triangular sweep runs   */
+                     /* in 4 fully parallel phases; requires inner_iters = 1)                   */
 } sg_params;
+
+#define SG_ILU_NATURAL 0
+#define SG_ILU_COLOR4 1
 
 #define SG_OP_AUTO 0   /* choose by timing (see op_kernel)                                      */
 #define SG_OP_PAIRS 1  /* one CTA per 4 rows, (k, b) pairs over threads, operands in shared mem */
@@ -101,7 +107,7 @@ typedef struct {
 /* Fill ``prm`` with defaults: n=16, M=2, p=2, q=2p, sigma=0.5, ell=1, a_min=0, mu=0, f=1,
  * mean preconditioner, 1 inner / 1 outer step, restart 30, max_iters 2000, rtol 1e-10,
  * atol 0, FP64, inner_rtol 1e-4, graphs 0, mg_smoother SG_PC_FS_GS, mg_coarse 2,
- * op_kernel SG_OP_AUTO, op_kappa 0, op_ctas 0. */
+ * op_kernel SG_OP_AUTO, op_kappa 0, op_ctas 0, ilu_order SG_ILU_NATURAL. */
 void sg_default_params(sg_params* prm);
 
 /* Build ``nsys`` independent SG systems (Sec. 2: KL modes of Eq. gen_eigen in closed form,
@@ -171,9 +177,10 @@ int sg_gmres_solve(sg_handle* h, const double* const* F, double* const* X, sg_so
 /* Copy an internal array of system ``sys`` to host memory ``dst`` of ``bytes`` bytes, for
  * tests: what = 0 stack values (nnz_A x L doubles, entry e and chaos k at e*L + k),
  * 1 CSR row pointers (N+1 ints), 2 CSR columns (nnz_A ints), 3 KL eigenvalues (M doubles),
- * 4 ILU(0) factor values of the mean block (nnz_A doubles, L strictly below the diagonal with
- * unit diagonal implied, U on and above), 5 triple products as (k, a, b, value) records sorted by
- * k then a then b (nnz_G x 4 doubles).  Synchronous.  SG_ERR_ARG if ``bytes`` is too small. */
+ * 4 ILU(0) factor values of the first factor set (nnz_A doubles on the CSR pattern: the unit
+ * lower factor at entries of nodes before the row's node in the ILU ordering, the upper factor
+ * at the others), 5 triple products as (k, a, b, value) records sorted by k then a then b
+ * (nnz_G x 4 doubles).  Synchronous.  SG_ERR_ARG if ``bytes`` is too small. */
 int sg_export(const sg_handle* h, int sys, int what, void* dst, size_t bytes);
 
 /* Which SG operator kernel system ``sys`` runs: info[0..3] for the FP64 operator and info[4..7]

@@ -650,6 +650,8 @@ template <typename T>
 int launch_block_solve(System& s, int a0, int ncols, int fac_per_col, const T* Rt, T* Z,
                        cudaStream_t st, const int* done) {
   using B = PcBufs<T>;
+  if (s.prm.ilu_order == SG_ILU_COLOR4)
+    return launch_color_solve<T>(s, a0, ncols, fac_per_col, B::lu9(s), const_cast<T*>(Rt), Z, st, done);
   const int wc = s.tri_wc;
   const bool full = B::full(s);
   const int nthreads = 2 * wc + (full ? 32 : tri_staging_threads(wc));

@@ -143,6 +143,10 @@ static int validate(const sg_params& p) {
   if (p.op_kappa != 0 && p.op_kappa != 1 && p.op_kappa != 2 && p.op_kappa != 4)
     return fail(SG_ERR_ARG, "op_kappa must be 0, 1, 2 or 4");
   if (p.op_ctas < 0 || p.op_ctas > 2) return fail(SG_ERR_ARG, "op_ctas must be 0, 1 or 2");
+  if (p.ilu_order != SG_ILU_NATURAL && p.ilu_order != SG_ILU_COLOR4)
+    return fail(SG_ERR_ARG, "unknown ilu_order");
+  if (p.ilu_order == SG_ILU_COLOR4 && p.inner_iters != 1)
+    return fail(SG_ERR_ARG, "the four-colour ILU(0) ordering takes inner_iters = 1");
   if (p.precond == SG_PC_MEAN || p.precond == SG_PC_FS_GS || p.precond == SG_PC_FS_JACOBI ||
       p.precond == SG_PC_MG) {
     // the wavefront solve: 2 wc compute and some staging threads; shared memory for its level
@@ -458,6 +462,7 @@ static void free_system(System* s) {
                      &s->gsn_ea, &s->flags};
   for (auto* b : ib) b->release();
   s->lev9_off.release();
+  s->cstart.release();
   s->stack_km16.release();
   DBuf<double>* db[] = {&s->stack, &s->stack_km, &s->ent_g, &s->blk, &s->fac, &s->lu9, &s->gs_eg, &s->gsn_eg, &s->rhs_t, &s->tmp,
                         &s->tmp2, &s->tri_w, &s->V, &s->Z, &s->Hs, &s->cs, &s->sn, &s->g, &s->y,
@@ -576,8 +581,12 @@ static int setup_system(System& s, cudaStream_t st, bool krylov = true) {
     SG_TRY(s.blk.alloc((size_t)s.nfac * s.pat.nnz));
     SG_TRY(s.fac.alloc((size_t)s.nfac * s.pat.nnz));
     SG_TRY(launch_block_values(s, st));
-    SG_TRY(launch_ilu0(s, st));
-    SG_TRY(launch_lu9(s, st));
+    if (p.ilu_order == SG_ILU_COLOR4) {
+      SG_TRY(launch_color_ilu(s, st));
+    } else {
+      SG_TRY(launch_ilu0(s, st));
+      SG_TRY(launch_lu9(s, st));
+    }
     if (lowp) {
       SG_TRY(s.lu9_f32.alloc(s.lu9.n));
       SG_TRY(s.blk_f32.alloc(s.blk.n));
@@ -912,6 +921,7 @@ void sg_default_params(sg_params* p) {
   p->op_kernel = SG_OP_AUTO;
   p->op_kappa = 0;
   p->op_ctas = 0;
+  p->ilu_order = SG_ILU_NATURAL;
 }
 
 int sg_setup(const sg_params* prm, int nsys, void* stream, sg_handle** out) {

@@ -220,6 +220,7 @@ struct System {
   DBuf<double> lu9;            // nfac x 9 x N level-major slot layout of the factors
   DBuf<float> lu9_f32;
   DBuf<int> lev9_off;          // start of each wavefront level in level-major order
+  DBuf<int> cstart;            // four-colour ordering: start of each colour (5 offsets)
   int nlev9 = 0;
   int tri_wc = 0;              // threads per group of the wavefront solve (multiple of 32)
   int ldN = 0;                 // column stride of rhs_t / tri_w: N rounded up to a multiple of 4
@@ -293,6 +294,11 @@ int launch_assemble(System& s, const double* qp, cudaStream_t st);
 int launch_rhs(System& s, double* F, cudaStream_t st);
 int launch_block_values(System& s, cudaStream_t st);
 int launch_ilu0(System& s, cudaStream_t st);
+// ILU(0) in the four-colour ordering (k_ilu_color.cu): factors into lu9 (colour-major slots)
+int launch_color_ilu(System& s, cudaStream_t st);
+template <typename T>
+int launch_color_solve(System& s, int a0, int ncols, int fac_per_col, const T* lu, T* Rt, T* Z,
+                       cudaStream_t st, const int* done);
 int launch_lu9(System& s, cudaStream_t st);
 int launch_cast_f32(const double* src, float* dst, size_t n, cudaStream_t st);
 int launch_cast_bf16(const double* src, __nv_bfloat16* dst, size_t n, cudaStream_t st);

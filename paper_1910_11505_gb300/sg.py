@@ -27,6 +27,7 @@ PRECONDS = {"none": SG_PC_NONE, "mean": SG_PC_MEAN, "fs_gs": SG_PC_FS_GS,
             "fs_jacobi": SG_PC_FS_JACOBI, "mg": SG_PC_MG}
 PRECISIONS = {"fp64": SG_FP64, "fp32": SG_MIXED_FP32, "bf16": SG_MIXED_BF16}
 OP_KERNELS = {"auto": 0, "pairs": 1, "tile": 2}
+ILU_ORDERS = {"natural": 0, "color4": 1}
 
 EXPORTED = ["sg_default_params", "sg_setup", "sg_dims", "sg_nnz", "sg_matvec", "sg_matvec_lowp",
             "sg_precond_apply", "sg_precond_apply_lowp", "sg_precond_apply_noalloc", "sg_rhs",
@@ -55,7 +56,8 @@ class sg_params(ctypes.Structure):
                 ("atol", ctypes.c_double), ("precision", ctypes.c_int),
                 ("inner_rtol", ctypes.c_double), ("graphs", ctypes.c_int),
                 ("mg_smoother", ctypes.c_int), ("mg_coarse", ctypes.c_int),
-                ("op_kernel", ctypes.c_int), ("op_kappa", ctypes.c_int), ("op_ctas", ctypes.c_int)]
+                ("op_kernel", ctypes.c_int), ("op_kappa", ctypes.c_int), ("op_ctas", ctypes.c_int),
+                ("ilu_order", ctypes.c_int)]
 
 
 class sg_solve_info(ctypes.Structure):
@@ -172,6 +174,8 @@ def sg_default_params(**overrides) -> sg_params:
             v = PRECONDS[v]
         if k == "op_kernel" and isinstance(v, str):
             v = OP_KERNELS[v]
+        if k == "ilu_order" and isinstance(v, str):
+            v = ILU_ORDERS[v]
         if k == "precision" and isinstance(v, str):
             v = PRECISIONS[v]
         setattr(p, k, v)

@@ -1,0 +1,105 @@
+"""The four-colour ILU(0) ordering (reading R18) through the C ABI against the oracle: the factors
+themselves, every block preconditioner at small and large meshes (one CTA per column with the
+column in shared memory, and the one-launch-per-colour-phase path of large meshes), and the
+multigrid V-cycle with these smoothers.  Tolerances as in test_gpu_parity (1e-12 FP64)."""
+
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_1910_11505_gb300 import sg, workloads as W
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    from paper_1910_11505_gb300 import build as B
+    B.build()
+    assert torch.cuda.is_available()
+
+
+def _relerr(a, b):
+    return float(np.abs(a - b).max() / np.abs(b).max())
+
+
+def test_color4_factors_match_oracle():
+    d = dict(n=9, M=2, p=1, sigma=0.7, ell=0.6, a_min=0.02)
+    h = sg.sg_setup(sg.sg_default_params(**d, precond="mean", ilu_order="color4"))
+    prob = O.build_problem(9, 2, 1, sigma=0.7, ell=0.6, a_min=0.02)
+    Lo, Up, order = O.ilu0(prob.A[0], O.color4_order(9))
+    LUp = Lo.toarray() - np.eye(prob.N) + Up.toarray()
+    inv = np.empty_like(order)
+    inv[order] = np.arange(len(order))
+    LU = LUp[np.ix_(inv, inv)]               # back to natural node numbering
+    rowptr, col = sg.sg_export(h, 0, 1), sg.sg_export(h, 0, 2)
+    vals = sg.sg_export(h, 0, 4)
+    for r in range(prob.N):
+        for e in range(rowptr[r], rowptr[r + 1]):
+            assert abs(vals[e] - LU[r, col[e]]) <= 1e-13 * np.abs(LU).max(), (r, col[e])
+    h.close()
+
+
+@pytest.mark.parametrize("d,pc", [
+    (dict(n=6, M=3, p=2, sigma=0.5, ell=1.0, a_min=0.01), "mean"),
+    (dict(n=6, M=3, p=2, sigma=0.5, ell=1.0, a_min=0.01), "fs_gs"),
+    (dict(n=7, M=2, p=2, sigma=0.8, ell=0.6), "fs_jacobi"),
+    (dict(n=200, M=2, p=1, sigma=0.8, ell=0.5), "fs_gs"),      # FP64 column beyond 200 KB
+    (dict(n=200, M=2, p=1, sigma=0.8, ell=0.5), "mean"),
+])
+def test_color4_preconditioners_match_oracle(d, pc):
+    h = sg.sg_setup(sg.sg_default_params(**d, precond=pc, ilu_order="color4"))
+    N, P, _ = sg.sg_dims(h)
+    kw = {k: d[k] for k in ("sigma", "ell", "a_min") if k in d}
+    prob = O.build_problem(d["n"], d["M"], d["p"], **kw)
+    R = W.random_field(N, P, seed=51)
+    Z = torch.empty(N, P, dtype=torch.float64, device="cuda")
+    sg.sg_precond_apply(h, 0, torch.from_numpy(R).cuda(), Z)
+    if pc == "mean":
+        ref = O.mean_precond(prob, R, ordering="color4")
+    else:
+        ref = O.fs_precond(prob, R, mode="gs" if pc == "fs_gs" else "jacobi",
+                           blocks=O.fs_blocks(prob, ordering="color4"))
+    assert _relerr(Z.cpu().numpy(), ref) <= 1e-12
+    h.close()
+
+
+def test_color4_fp32_large_mesh():
+    d = dict(n=256, M=2, p=1, sigma=0.8, ell=0.5)              # FP32 column beyond 200 KB
+    h = sg.sg_setup(sg.sg_default_params(**d, precond="fs_gs", ilu_order="color4",
+                                         precision="fp32"))
+    N, P, _ = sg.sg_dims(h)
+    prob = O.build_problem(256, 2, 1, sigma=0.8, ell=0.5)
+    R = W.random_field(N, P, seed=52)
+    Z = torch.empty(N, P, dtype=torch.float32, device="cuda")
+    sg.sg_precond_apply_lowp(h, 0, torch.from_numpy(R).float().cuda(), Z)
+    ref = O.fs_precond(prob, R.astype(np.float32).astype(np.float64),
+                       blocks=O.fs_blocks(prob, ordering="color4"))
+    assert _relerr(Z.double().cpu().numpy(), ref) <= 1e-6
+    h.close()
+
+
+@pytest.mark.parametrize("smoother", ["fs_gs", "fs_jacobi"])
+def test_color4_vcycle_matches_oracle(smoother):
+    case = dict(n=16, M=3, p=2, sigma=0.7, ell=0.6)
+    h = sg.sg_setup(sg.sg_default_params(**case, precond="mg", mg_smoother=smoother,
+                                         ilu_order="color4"))
+    N, P, _ = sg.sg_dims(h)
+    levels = O.mg_levels(16, 3, 2, sigma=0.7, ell=0.6)
+    data = O.mg_setup(levels, smoother, ordering="color4")
+    R = W.random_field(N, P, seed=53)
+    R[levels[-1].boundary] = 0.0
+    Z = torch.empty(N, P, dtype=torch.float64, device="cuda")
+    sg.sg_precond_apply(h, 0, torch.from_numpy(R).cuda(), Z)
+    ref = O.mg_vcycle(levels, data, R, smoother)
+    assert _relerr(Z.cpu().numpy(), ref) <= 1e-12
+    h.close()
+
+
+def test_color4_refuses_inner_iterations():
+    with pytest.raises(sg.SGError) as ei:
+        sg.sg_setup(sg.sg_default_params(n=8, M=2, p=1, precond="mean", ilu_order="color4",
+                                         inner_iters=2))
+    assert ei.value.code == sg.SG_ERR_ARG
