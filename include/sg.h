@@ -134,8 +134,10 @@ int sg_matvec_lowp(sg_handle* h, int sys, const float* X, float* Y, void* stream
 
 /* Z = P^{-1} R for the system's preconditioner, with ``outer_sweeps`` steps of Eq. level_solver
  * from zero and ``inner_iters`` ILU(0)-Richardson steps per diagonal block; mean-based
- * (I (x) ILU0(A_0)), field-split Gauss-Seidel (Eq. P_preconditioner) or block Jacobi.
- * R, Z device N x P FP64, must not overlap.  Asynchronous on ``stream``. */
+ * (I (x) ILU0(A_0)), field-split Gauss-Seidel (Eq. P_preconditioner), block Jacobi or the
+ * multigrid V-cycle.  R, Z device N x P FP64, must not overlap.  Asynchronous on ``stream``.
+ * SG_ERR_ARG for a field-split Gauss-Seidel sweep (alone or as a smoother) of a mixed-precision
+ * system, whose FP64 coupling copy is not kept (use sg_precond_apply_lowp). */
 int sg_precond_apply(sg_handle* h, int sys, const double* R, double* Z, void* stream);
 
 /* The same preconditioner application in FP32 arithmetic with the FP32 ILU(0) factors and the

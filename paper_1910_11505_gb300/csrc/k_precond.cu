@@ -711,6 +711,9 @@ int launch_scatter(System& s, int b, bool next, const T* Z, T* Rt, cudaStream_t 
 template <>
 int launch_scatter<double>(System& s, int b, bool next, const double* Z, double* Rt,
                            cudaStream_t st, const int* done) {
+  if (s.stack_km.p == nullptr)
+    return fail(SG_ERR_ARG, "the FP64 field-split Gauss-Seidel sweep is not kept for a "
+                            "mixed-precision system (its sweeps run in FP32)");
   return launch_scatter_t<double, double>(s, b, next, s.stack_km.p, s.gsn_eg.p, s.gs_eg.p, Z, Rt,
                                           st, done);
 }

@@ -571,8 +571,14 @@ static int setup_system(System& s, cudaStream_t st, bool krylov = true) {
     SG_TRY(launch_cast_bf16(s.stack.p, s.stack_bf16.p, nnzL, st));
   }
   // the SG operator kernels, chosen by op_kernel (timed per system shape when automatic)
-  SG_TRY(choose_operator(s, 8, st));
-  if (p.precision == SG_MIXED_FP32) SG_TRY(choose_operator(s, 4, st));
+  // In the mixed forms the FP64 operator serves only the outer residual (once per refinement):
+  // it keeps the pair kernel on the FP64 stack unless the row-tiled one is asked for, and the
+  // FP32 stack copy of the pair kernel is dropped once the row-tiled FP32 operator serves.
+  if (p.precision == SG_FP64 || p.op_kernel == SG_OP_TILE) SG_TRY(choose_operator(s, 8, st));
+  if (p.precision == SG_MIXED_FP32) {
+    SG_TRY(choose_operator(s, 4, st));
+    if (s.tile32.ready) s.stack_f32.release();
+  }
 
   // preconditioner blocks and factors
   const size_t NP = (size_t)s.N * s.P;
@@ -603,6 +609,11 @@ static int setup_system(System& s, cudaStream_t st, bool krylov = true) {
       } else if (p.precision == SG_MIXED_BF16) {
         SG_TRY(s.stack_km16.alloc(nnzL));
         SG_TRY(launch_cast_bf16(s.stack_km.p, s.stack_km16.p, nnzL, st));
+      }
+      // the mixed forms sweep in FP32 only: their FP64 k-major copy is not kept
+      if (lowp) {
+        SG_CUDA(cudaStreamSynchronize(st));
+        s.stack_km.release();
       }
     }
     const size_t PL = (size_t)s.P * s.ldN;
