@@ -4,8 +4,9 @@ Workload (c3): the stochastic Galerkin system of -div(a grad u) = 1 on the unit 
 Q1 mesh, M = 6 KL terms of the exponential covariance (sigma = 1, ell = 0.5), chaos degree p = 3
 (P = 84 solution terms, L = 924 coefficient terms; 5.5 M unknowns), relative residual 1e-8 from a
 zero initial guess, GMRES(50) preconditioned by the multigrid V-cycle of the paper's G-M-F-I
-(field-split Gauss-Seidel with ILU(0) blocks as the level solver, one pre- and one post-smoothing
-step, 2 x 2 coarsest mesh solved directly).  One step = one solve in the mixed-precision form
+(field-split Gauss-Seidel with ILU(0) blocks as the level solver, the blocks' ILU(0) in the
+four-colour node ordering, one pre- and one post-smoothing step, 2 x 2 coarsest mesh solved
+directly).  One step = one solve in the mixed-precision form
 (FP32 operator, preconditioner and inner basis inside FP64 flexible GMRES with FP64 iterative
 refinement).  value = solves per second over all ranks (each rank solves its own copy: weak
 scaling, no collective on the data path).
@@ -37,8 +38,9 @@ sys.path.insert(0, ROOT)
 
 METRIC = "SG solves/sec & matvec HBM GB/s, mixed/learned vs FP64 GMRES at 1e-8 residual"
 WORKLOAD = ("c3: 256x256 Q1 mesh, M=6, p=3 (P=84, L=924, 5.5M unknowns), sigma=1, ell=0.5, "
-            "GMRES(50) + multigrid V-cycle (field-split Gauss-Seidel + ILU(0) smoother, 1/1, "
-            "2x2 coarsest), rel. residual 1e-8, x0 = 0; mixed FP32/FP64 FGMRES + refinement")
+            "GMRES(50) + multigrid V-cycle (field-split Gauss-Seidel + ILU(0) smoother in the "
+            "four-colour ordering, 1/1, 2x2 coarsest), rel. residual 1e-8, x0 = 0; mixed "
+            "FP32/FP64 FGMRES + refinement")
 PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "traffic.json")
 

@@ -61,11 +61,13 @@ def c2_params(sigma=None):
                  max_iters=4000) for s in sig]
 
 
-def c3_mg_params(precision="fp64"):
+def c3_mg_params(precision="fp64", ilu_order="color4"):
     """c3 with the multigrid V-cycle preconditioner of the paper's G-M-F-I (field-split
-    Gauss-Seidel + ILU(0) smoothing, one pre- and one post-step, 2 x 2 coarsest mesh)."""
+    Gauss-Seidel + ILU(0) smoothing, one pre- and one post-step, 2 x 2 coarsest mesh), the
+    ILU(0) blocks in the four-colour ordering by default."""
     return dict(n=256, M=6, p=3, sigma=1.0, ell=0.5, precond="mg", mg_smoother="fs_gs",
-                rtol=1e-8, restart=50, max_iters=400, precision=precision, graphs=1)
+                rtol=1e-8, restart=50, max_iters=400, precision=precision, graphs=1,
+                ilu_order=ilu_order)
 
 
 def c3_params(precision="fp64"):
