@@ -133,23 +133,6 @@ __device__ __forceinline__ void color_phase_node(int pos, int i, int m, int N, c
   w[i] = v;
 }
 
-template <typename T, bool UPPER>
-__global__ void color_phase_kernel(int m, int N, int ldN, int P, int a0, int fac_per_col, int c,
-                                   const int* __restrict__ cstart, const T* __restrict__ cfs,
-                                   T* __restrict__ Rt, T* __restrict__ Z, const int* __restrict__ done) {
-  if (done != nullptr && *done) return;
-  const int a = a0 + blockIdx.y;
-  const T* cf = cfs + (size_t)(fac_per_col ? a : 0) * 9 * N;
-  T* w = Rt + (size_t)a * ldN;
-  const int p0 = cstart[c], n = cstart[c + 1] - p0;
-  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < n; t += gridDim.x * blockDim.x) {
-    const int pos = p0 + t;
-    const int i = colour_node(c, pos, m, cstart);
-    color_phase_node<T, UPPER>(pos, i, m, N, cf, w);
-    if (UPPER) Z[(size_t)i * P + a] = w[i];
-  }
-}
-
 // All eight phases of one column in one CTA, the column in shared memory (meshes whose column
 // fits): CTA b solves column a0 + b.
 template <typename T>
@@ -179,6 +162,69 @@ __global__ void __launch_bounds__(1024) color_cta_kernel(int m, int N, int ldN, 
     __syncthreads();
   }
   for (int i = threadIdx.x; i < N; i += blockDim.x) Z[(size_t)i * P + a] = w[i];
+}
+
+// All eight phases of one column on a thread-block cluster of CL CTAs (grid = columns x CL): the
+// column stays in global memory (L2), every CTA takes a share of each colour's nodes, and a
+// cluster barrier (release / acquire at cluster scope) separates the phases.  Neighbour values
+// are read at L2 (ld.global.cg) so no SM reads a stale L1 line written by another.
+template <typename T, int CL>
+__global__ void __launch_bounds__(1024) color_cluster_kernel(
+    int m, int N, int ldN, int P, int a0, int fac_per_col, const int* __restrict__ cstart_g,
+    const T* __restrict__ cfs, T* __restrict__ Rt, T* __restrict__ Z, const int* __restrict__ done) {
+  if (done != nullptr && *done) return;  // uniform over the cluster: no barrier is skipped by some
+  __shared__ int cstart[5];
+  const int a = a0 + blockIdx.x / CL;
+  const int rank = blockIdx.x % CL;
+  const T* cf = cfs + (size_t)(fac_per_col ? a : 0) * 9 * N;
+  T* w = Rt + (size_t)a * ldN;
+  if (threadIdx.x < 5) cstart[threadIdx.x] = cstart_g[threadIdx.x];
+  __syncthreads();
+  const int stride = CL * blockDim.x;
+  auto phase = [&](int c, bool upper) {
+    for (int pos = cstart[c] + rank * blockDim.x + threadIdx.x; pos < cstart[c + 1]; pos += stride) {
+      const int i = colour_node(c, pos, m, cstart);
+      const int x = i % m, y = i / m;
+      T v = __ldcg(w + i);
+      if (upper) v *= cf[(size_t)4 * N + pos];
+#pragma unroll
+      for (int sl = 0; sl < 9; ++sl) {
+        if (sl == 4) continue;
+        const int jx = x + sl % 3 - 1, jy = y + sl / 3 - 1;
+        if (jx < 0 || jy < 0 || jx >= m || jy >= m) continue;
+        const int cj = node_colour(jx, jy);
+        if (upper ? cj <= c : cj >= c) continue;
+        v -= cf[(size_t)sl * N + pos] * __ldcg(w + jx + m * jy);
+      }
+      w[i] = v;
+      if (upper) Z[(size_t)i * P + a] = v;
+    }
+    asm volatile("barrier.cluster.arrive.release.aligned;\n"
+                 "barrier.cluster.wait.acquire.aligned;\n" ::: "memory");
+  };
+  for (int c = 0; c < 4; ++c) phase(c, false);
+  for (int c = 3; c >= 0; --c) phase(c, true);
+}
+
+template <typename T, int CL>
+int launch_cluster(System& s, int a0, int ncols, int fac_per_col, const T* lu, T* Rt, T* Z,
+                   cudaStream_t st, const int* done) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)(ncols * CL), 1, 1);
+  cfg.blockDim = dim3(1024, 1, 1);
+  cfg.dynamicSmemBytes = 0;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = CL;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  TimeScope ts(s.timer, K_ILU_SOLVE, st);
+  SG_CUDA(cudaLaunchKernelEx(&cfg, color_cluster_kernel<T, CL>, s.pat.m, s.N, s.ldN, s.P, a0,
+                             fac_per_col, (const int*)s.cstart.p, lu, Rt, Z, done));
+  return check_launch("color_cluster");
 }
 
 }  // namespace
@@ -216,29 +262,22 @@ int launch_color_solve(System& s, int a0, int ncols, int fac_per_col, const T* l
                        cudaStream_t st, const int* done) {
   const int m = s.pat.m;
   const size_t smem = sizeof(T) * (size_t)s.ldN;
-  if (smem <= 200 * 1024) {
+  // a cluster of CTAs once one CTA would hold more than ~1024 nodes per colour; one CTA with the
+  // column in shared memory below that
+  const int per_colour = (s.N + 3) / 4;
+  if (per_colour > 2048) {
+    if (per_colour > 4 * 2048) return launch_cluster<T, 8>(s, a0, ncols, fac_per_col, lu, Rt, Z, st, done);
+    if (per_colour > 2 * 2048) return launch_cluster<T, 4>(s, a0, ncols, fac_per_col, lu, Rt, Z, st, done);
+    return launch_cluster<T, 2>(s, a0, ncols, fac_per_col, lu, Rt, Z, st, done);
+  }
+  {
     auto kern = color_cta_kernel<T>;
     SG_TRY(ensure_smem((const void*)kern, smem));
     TimeScope ts(s.timer, K_ILU_SOLVE, st);
     kern<<<ncols, 1024, smem, st>>>(m, s.N, s.ldN, s.P, a0, fac_per_col, s.cstart.p, lu, Rt, Z, done);
     return check_launch("color_cta");
   }
-  // large meshes: one launch per phase, every node of the colour in parallel
-  const int per_colour = (s.N + 3) / 4;
-  const int gx = std::max(1, std::min((per_colour + 255) / 256, 152 * 8 / std::max(1, ncols) + 1));
-  dim3 grid(gx, ncols);
-  TimeScope ts(s.timer, K_ILU_SOLVE, st);
-  for (int c = 0; c < 4; ++c) {
-    color_phase_kernel<T, false><<<grid, 256, 0, st>>>(m, s.N, s.ldN, s.P, a0, fac_per_col, c,
-                                                       s.cstart.p, lu, Rt, Z, done);
-    SG_TRY(check_launch("color_lower"));
-  }
-  for (int c = 3; c >= 0; --c) {
-    color_phase_kernel<T, true><<<grid, 256, 0, st>>>(m, s.N, s.ldN, s.P, a0, fac_per_col, c,
-                                                      s.cstart.p, lu, Rt, Z, done);
-    SG_TRY(check_launch("color_upper"));
-  }
-  return SG_OK;
+  return fail(SG_ERR_ARG, "four-colour block solve: column larger than shared memory");
 }
 
 template int launch_color_solve<double>(System&, int, int, int, const double*, double*, double*,

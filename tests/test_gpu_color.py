@@ -1,7 +1,8 @@
 """The four-colour ILU(0) ordering (reading R18) through the C ABI against the oracle: the factors
-themselves, every block preconditioner at small and large meshes (one CTA per column with the
-column in shared memory, and the one-launch-per-colour-phase path of large meshes), and the
-multigrid V-cycle with these smoothers.  Tolerances as in test_gpu_parity (1e-12 FP64)."""
+themselves, every block preconditioner at small and large meshes, and the multigrid V-cycle with
+these smoothers.  Block solves run on one CTA with the column in shared memory up to ~8 k nodes,
+on a thread-block cluster of 2, 4 or 8 CTAs beyond.  Tolerances as in test_gpu_parity (1e-12
+FP64)."""
 
 import numpy as np
 import pytest
@@ -46,8 +47,10 @@ def test_color4_factors_match_oracle():
     (dict(n=6, M=3, p=2, sigma=0.5, ell=1.0, a_min=0.01), "mean"),
     (dict(n=6, M=3, p=2, sigma=0.5, ell=1.0, a_min=0.01), "fs_gs"),
     (dict(n=7, M=2, p=2, sigma=0.8, ell=0.6), "fs_jacobi"),
-    (dict(n=200, M=2, p=1, sigma=0.8, ell=0.5), "fs_gs"),      # FP64 column beyond 200 KB
+    (dict(n=200, M=2, p=1, sigma=0.8, ell=0.5), "fs_gs"),      # cluster of 8 CTAs per column
     (dict(n=200, M=2, p=1, sigma=0.8, ell=0.5), "mean"),
+    (dict(n=128, M=2, p=1, sigma=0.6, ell=0.5), "fs_gs"),      # cluster of 4
+    (dict(n=100, M=2, p=1, sigma=0.6, ell=0.5), "fs_jacobi"),  # cluster of 2
 ])
 def test_color4_preconditioners_match_oracle(d, pc):
     h = sg.sg_setup(sg.sg_default_params(**d, precond=pc, ilu_order="color4"))
@@ -67,7 +70,7 @@ def test_color4_preconditioners_match_oracle(d, pc):
 
 
 def test_color4_fp32_large_mesh():
-    d = dict(n=256, M=2, p=1, sigma=0.8, ell=0.5)              # FP32 column beyond 200 KB
+    d = dict(n=256, M=2, p=1, sigma=0.8, ell=0.5)              # cluster of 8, FP32
     h = sg.sg_setup(sg.sg_default_params(**d, precond="fs_gs", ilu_order="color4",
                                          precision="fp32"))
     N, P, _ = sg.sg_dims(h)
