@@ -87,6 +87,10 @@ typedef struct {
   int ilu_order;     /* ILU(0) node ordering: SG_ILU_NATURAL, or SG_ILU_COLOR4 (colour           */
                      /* (x mod 2) + 2 (y mod 2), colours in turn: every triangular sweep runs   */
                      /* in 4 fully parallel phases; requires inner_iters = 1)                   */
+  int coupling_bf16; /* SG_MIXED_FP32 with a field-split Gauss-Seidel sweep (alone or as the    */
+                     /* smoother): 1 = the sweep's coupling sum_{b<a} K_ab z_b reads a BF16     */
+                     /* copy of the stiffness values (FP32 arithmetic), half the bytes of the   */
+                     /* sweep's dominant traffic; the operator keeps its FP32 copy              */
 } sg_params;
 
 #define SG_ILU_NATURAL 0
@@ -107,7 +111,7 @@ typedef struct {
 /* Fill ``prm`` with defaults: n=16, M=2, p=2, q=2p, sigma=0.5, ell=1, a_min=0, mu=0, f=1,
  * mean preconditioner, 1 inner / 1 outer step, restart 30, max_iters 2000, rtol 1e-10,
  * atol 0, FP64, inner_rtol 1e-4, graphs 0, mg_smoother SG_PC_FS_GS, mg_coarse 2,
- * op_kernel SG_OP_AUTO, op_kappa 0, op_ctas 0, ilu_order SG_ILU_NATURAL. */
+ * op_kernel SG_OP_AUTO, op_kappa 0, op_ctas 0, ilu_order SG_ILU_NATURAL, coupling_bf16 0. */
 void sg_default_params(sg_params* prm);
 
 /* Build ``nsys`` independent SG systems (Sec. 2: KL modes of Eq. gen_eigen in closed form,

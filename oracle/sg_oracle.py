@@ -510,19 +510,21 @@ def fs_blocks(prob: SGProblem, ordering=None):
     return blocks, facs
 
 
-def _offdiag_apply(prob: SGProblem, a: int, Z: np.ndarray, bs) -> np.ndarray:
-    """sum over b in bs of K_ab z_b, K_ab = sum_q G_q[a, b] A_q."""
+def _offdiag_apply(prob: SGProblem, a: int, Z: np.ndarray, bs, coupling=None) -> np.ndarray:
+    """sum over b in bs of K_ab z_b, K_ab = sum_q G_q[a, b] A_q (``coupling`` replaces the A_q,
+    e.g. by copies rounded to a storage precision)."""
+    A = prob.A if coupling is None else coupling
     out = np.zeros(Z.shape[0])
     for b in bs:
         for k in range(prob.L):
             c = prob.G[k, a, b]
             if c != 0.0:
-                out += c * (prob.A[k] @ Z[:, b])
+                out += c * (A[k] @ Z[:, b])
     return out
 
 
 def fs_precond(prob: SGProblem, R: np.ndarray, mode: str = "gs", inner_iters: int = 1,
-               outer_sweeps: int = 1, blocks=None) -> np.ndarray:
+               outer_sweeps: int = 1, blocks=None, coupling=None) -> np.ndarray:
     """Field-split preconditioner: ``outer_sweeps`` steps of Eq. level_solver from zero with P the
     block lower triangle of K (Eq. P_preconditioner, mode 'gs') or its block diagonal
     (mode 'jacobi'); each diagonal block solved by ``inner_iters`` ILU(0)-Richardson steps."""
@@ -537,7 +539,7 @@ def fs_precond(prob: SGProblem, R: np.ndarray, mode: str = "gs", inner_iters: in
         for a in range(P):
             rhs = res[:, a].copy()
             if mode == "gs" and a > 0:
-                rhs -= _offdiag_apply(prob, a, D, range(a))
+                rhs -= _offdiag_apply(prob, a, D, range(a), coupling)
             D[:, a] = _richardson(lambda z, A=Kd[a]: A @ z, facs[a], rhs, inner_iters)
         Z = Z + D
     return Z

@@ -720,7 +720,7 @@ int launch_scatter<double>(System& s, int b, bool next, const double* Z, double*
 template <>
 int launch_scatter<float>(System& s, int b, bool next, const float* Z, float* Rt, cudaStream_t st,
                           const int* done) {
-  if (s.prm.precision == SG_MIXED_BF16)
+  if (s.prm.precision == SG_MIXED_BF16 || s.prm.coupling_bf16)
     return launch_scatter_t<float, __nv_bfloat16>(s, b, next, s.stack_km16.p, s.gsn_eg_f32.p,
                                                   s.gs_eg_f32.p, Z, Rt, st, done);
   return launch_scatter_t<float, float>(s, b, next, s.stack_km32.p, s.gsn_eg_f32.p,

@@ -147,6 +147,9 @@ static int validate(const sg_params& p) {
     return fail(SG_ERR_ARG, "unknown ilu_order");
   if (p.ilu_order == SG_ILU_COLOR4 && p.inner_iters != 1)
     return fail(SG_ERR_ARG, "the four-colour ILU(0) ordering takes inner_iters = 1");
+  if (p.coupling_bf16 != 0 && p.coupling_bf16 != 1) return fail(SG_ERR_ARG, "coupling_bf16 must be 0 or 1");
+  if (p.coupling_bf16 && p.precision != SG_MIXED_FP32)
+    return fail(SG_ERR_ARG, "coupling_bf16 applies to SG_MIXED_FP32 systems");
   if (p.precond == SG_PC_MEAN || p.precond == SG_PC_FS_GS || p.precond == SG_PC_FS_JACOBI ||
       p.precond == SG_PC_MG) {
     // the wavefront solve: 2 wc compute and some staging threads; shared memory for its level
@@ -603,10 +606,10 @@ static int setup_system(System& s, cudaStream_t st, bool krylov = true) {
       SG_TRY(build_gs_tables(s, st));
       SG_TRY(s.stack_km.alloc(nnzL));
       SG_TRY(launch_transpose(s.stack.p, s.stack_km.p, (size_t)s.pat.nnz, s.L, st));
-      if (p.precision == SG_MIXED_FP32) {
+      if (p.precision == SG_MIXED_FP32 && !p.coupling_bf16) {
         SG_TRY(s.stack_km32.alloc(nnzL));
         SG_TRY(launch_cast_f32(s.stack_km.p, s.stack_km32.p, nnzL, st));
-      } else if (p.precision == SG_MIXED_BF16) {
+      } else if (p.precision == SG_MIXED_BF16 || p.coupling_bf16) {
         SG_TRY(s.stack_km16.alloc(nnzL));
         SG_TRY(launch_cast_bf16(s.stack_km.p, s.stack_km16.p, nnzL, st));
       }
@@ -933,6 +936,7 @@ void sg_default_params(sg_params* p) {
   p->op_kappa = 0;
   p->op_ctas = 0;
   p->ilu_order = SG_ILU_NATURAL;
+  p->coupling_bf16 = 0;
 }
 
 int sg_setup(const sg_params* prm, int nsys, void* stream, sg_handle** out) {

@@ -64,10 +64,14 @@ def c2_params(sigma=None):
 def c3_mg_params(precision="fp64", ilu_order="color4"):
     """c3 with the multigrid V-cycle preconditioner of the paper's G-M-F-I (field-split
     Gauss-Seidel + ILU(0) smoothing, one pre- and one post-step, 2 x 2 coarsest mesh), the
-    ILU(0) blocks in the four-colour ordering by default."""
-    return dict(n=256, M=6, p=3, sigma=1.0, ell=0.5, precond="mg", mg_smoother="fs_gs",
-                rtol=1e-8, restart=50, max_iters=400, precision=precision, graphs=1,
-                ilu_order=ilu_order)
+    ILU(0) blocks in the four-colour ordering by default; in the mixed form the smoother's
+    Gauss-Seidel coupling reads a BF16 copy of the stiffness values."""
+    d = dict(n=256, M=6, p=3, sigma=1.0, ell=0.5, precond="mg", mg_smoother="fs_gs",
+             rtol=1e-8, restart=50, max_iters=400, precision=precision, graphs=1,
+             ilu_order=ilu_order)
+    if precision == "fp32":
+        d["coupling_bf16"] = 1  # the smoother's Gauss-Seidel coupling from a BF16 copy
+    return d
 
 
 def c3_params(precision="fp64"):

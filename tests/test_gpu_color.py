@@ -106,3 +106,37 @@ def test_color4_refuses_inner_iterations():
         sg.sg_setup(sg.sg_default_params(n=8, M=2, p=1, precond="mean", ilu_order="color4",
                                          inner_iters=2))
     assert ei.value.code == sg.SG_ERR_ARG
+
+
+def _bf16_round(x):
+    """Round-to-nearest-even of FP64 values to BF16 (8 significant bits), written out."""
+    m, e = np.frexp(x)
+    return np.ldexp(np.rint(m * 256.0) / 256.0, e)
+
+
+def test_bf16_coupling_sweep_matches_oracle_with_rounded_coupling():
+    # the FP32 Gauss-Seidel sweep whose coupling reads BF16 stiffness values, against the oracle
+    # sweep with the coupling matrices rounded the same way (FP32 arithmetic bound 1e-6 as for the
+    # other FP32 sweeps, plus ties that FP32 rounding of the products may resolve differently)
+    import scipy.sparse
+    d = dict(n=40, M=3, p=2, sigma=0.9, ell=0.5)
+    h = sg.sg_setup(sg.sg_default_params(**d, precond="fs_gs", precision="fp32", coupling_bf16=1))
+    N, P, _ = sg.sg_dims(h)
+    prob = O.build_problem(40, 3, 2, sigma=0.9, ell=0.5)
+    coupling = []
+    for A in prob.A:
+        Ar = A.copy()
+        Ar.data = _bf16_round(Ar.data)
+        coupling.append(Ar)
+    R = W.random_field(N, P, seed=54)
+    Z = torch.empty(N, P, dtype=torch.float32, device="cuda")
+    sg.sg_precond_apply_lowp(h, 0, torch.from_numpy(R).float().cuda(), Z)
+    Rr = R.astype(np.float32).astype(np.float64)
+    ref = O.fs_precond(prob, Rr, coupling=coupling)
+    ref_exact = O.fs_precond(prob, Rr)
+    err = _relerr(Z.double().cpu().numpy(), ref)
+    assert err <= 1e-5, err
+    assert _relerr(ref, ref_exact) > 10 * err  # the rounding is visible: the test sees the copy
+    h.close()
+    with pytest.raises(sg.SGError):
+        sg.sg_setup(sg.sg_default_params(**d, precond="fs_gs", precision="fp64", coupling_bf16=1))
