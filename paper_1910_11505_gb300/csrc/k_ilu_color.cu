@@ -111,119 +111,249 @@ __global__ void color_slots_kernel(int m, int N, int nnz, int nfac, const int* _
   }
 }
 
-// One phase of the triangular sweeps for ncols columns: lower (w_i -= sum l_ij w_j over lower
-// colours) or upper (w_i = (w_i - sum over higher colours) / u_ii, i.e. w_i / u_ii minus the scaled
-// couplings), colour c, in place on the column; the upper phases also store the result into Z.
-template <typename T, bool UPPER>
-__device__ __forceinline__ void color_phase_node(int pos, int i, int m, int N, const T* __restrict__ cf,
-                                                 T* __restrict__ w) {
-  const int x = i % m, y = i / m, c = node_colour(x, y);
-  T v = w[i];
-  if (UPPER) v *= cf[(size_t)4 * N + pos];
+// Next-column coupling stencils: for every column a >= 1 and node i, slot sl of K_{a,a-1} =
+// sum_k G_k[a,a-1] A_k (the G-weighted sum in the order of the next-column tables, in FP64, each
+// A_k value first rounded to BF16 when the sweep couples in BF16), at the node's colour-major
+// position; absent neighbours 0.
+template <typename D>
+__global__ void color_coupling_kernel(int m, int N, int nnz, int P, int round_bf16,
+                                      const int* __restrict__ rowptr, const int* __restrict__ col,
+                                      const int* __restrict__ cstart, const double* __restrict__ km,
+                                      const int* __restrict__ kptr, const int* __restrict__ klist,
+                                      const int* __restrict__ eptr, const int* __restrict__ ek,
+                                      const double* __restrict__ eg, D* __restrict__ out) {
+  const long long total = (long long)(P - 1) * N;
+  for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < total;
+       t += (long long)gridDim.x * blockDim.x) {
+    const int a = 1 + (int)(t / N), i = (int)(t % N), b = a - 1;
+    const int x = i % m, y = i / m;
+    const int pos = colour_pos(x, y, m, cstart);
+    D* o = out + (size_t)(a - 1) * 9 * N;
+    for (int sl = 0; sl < 9; ++sl) o[(size_t)sl * N + pos] = D(0);
+    const int q0 = eptr[(size_t)b * (P + 1) + a], q1 = eptr[(size_t)b * (P + 1) + a + 1];
+    const int k0 = kptr[b];
+    for (int e = rowptr[i]; e < rowptr[i + 1]; ++e) {
+      const int j = col[e];
+      const int sl = (j / m - y + 1) * 3 + (j % m - x + 1);
+      double v = 0.0;
+      for (int q = q0; q < q1; ++q) {
+        double av = km[(size_t)klist[k0 + ek[q]] * nnz + e];
+        if (round_bf16) av = (double)__bfloat162float(__double2bfloat16(av));
+        v += eg[q] * av;
+      }
+      o[(size_t)sl * N + pos] = (D)v;
+    }
+  }
+}
+
+// Node (x, y) of position p of colour C: q = p - cstart[C] splits into y = cy + 2 (q / nx),
+// x = cx + 2 (q mod nx), the quotient taken in FP32 and corrected by one step (exact for
+// q < 2^24, nx < 2^12).
+template <int C>
+__device__ __forceinline__ void colour_xy(int p, int m, const int* __restrict__ cstart, int& x, int& y) {
+  constexpr int cx = C & 1, cy = C >> 1;
+  const int nx = (m - cx + 1) >> 1;
+  const int q = p - cstart[C];
+  int r = (int)((float)q * __frcp_rn((float)nx));
+  int rem = q - r * nx;
+  if (rem < 0) {
+    --r;
+    rem += nx;
+  } else if (rem >= nx) {
+    ++r;
+    rem -= nx;
+  }
+  y = cy + 2 * r;
+  x = cx + 2 * rem;
+}
+
+// Colour of the neighbour (dx, dy) of a node of colour C.
+__host__ __device__ constexpr int nb_colour(int C, int dx, int dy) {
+  return ((C & 1) ^ (dx & 1)) + 2 * (((C >> 1) & 1) ^ (dy & 1));
+}
+
+// New value of node (x, y) (colour C, position pos) in one phase of the triangular sweeps: lower
+// (w_i minus sum l_ij w_j over the lower colours; first, with ``csa``, minus the coupling
+// sum_j K_{a,a-1}[i, j] z_{a-1}[j] of the previous column) or upper (w_i / u_ii minus the scaled
+// couplings of the higher colours).  Slots in increasing order; which slots a colour uses is fixed
+// at compile time.  Neighbour indices are clamped into the mesh: an absent neighbour's slot holds
+// 0, so it subtracts 0 * (a finite value).  CG reads the column at L2 (ld.global.cg: other SMs of
+// the cluster wrote it).
+template <typename T, int C, bool UPPER, bool CG>
+__device__ __forceinline__ T color_node_value(int x, int y, int pos, int m, int N,
+                                              const T* __restrict__ cf, const T* w,
+                                              const T* __restrict__ csa, const T* __restrict__ zprev) {
+  const int i = x + m * y;
+  const int xl = max(x - 1, 0), xr = min(x + 1, m - 1);
+  const int yd = max(y - 1, 0) * m, yu = min(y + 1, m - 1) * m, yc = y * m;
+  auto nb = [&](int dx, int dy) {
+    return (dx < 0 ? xl : dx > 0 ? xr : x) + (dy < 0 ? yd : dy > 0 ? yu : yc);
+  };
+  T v = CG ? __ldcg(w + i) : w[i];
+  if (UPPER) {
+    v *= cf[(size_t)4 * N + pos];
+  } else if (csa != nullptr) {
+    T s = T(0);
+#pragma unroll
+    for (int sl = 0; sl < 9; ++sl) s += csa[(size_t)sl * N + pos] * __ldg(zprev + nb(sl % 3 - 1, sl / 3 - 1));
+    v -= s;
+  }
 #pragma unroll
   for (int sl = 0; sl < 9; ++sl) {
     if (sl == 4) continue;
     const int dx = sl % 3 - 1, dy = sl / 3 - 1;
-    const int jx = x + dx, jy = y + dy;
-    if (jx < 0 || jy < 0 || jx >= m || jy >= m) continue;
-    const int cj = node_colour(jx, jy);
-    if (UPPER ? cj <= c : cj >= c) continue;
-    v -= cf[(size_t)sl * N + pos] * w[jx + m * jy];
+    const int cj = nb_colour(C, dx, dy);
+    if (UPPER ? cj <= C : cj >= C) continue;
+    const int j = nb(dx, dy);
+    v -= cf[(size_t)sl * N + pos] * (CG ? __ldcg(w + j) : w[j]);
   }
-  w[i] = v;
+  return v;
+}
+
+// One phase over the positions beg, beg + stride, ... < end of colour C, two nodes at a time:
+// both nodes' loads are issued before either result is stored, so a thread waits for memory once
+// per pair.  Nodes of one colour are independent, so the order of the stores does not matter.
+// Z (optional, upper phases) receives the solution at column a of an N x P row-major array.
+template <typename T, int C, bool UPPER, bool CG>
+__device__ __forceinline__ void color_phase(int beg, int end, int stride, int m, int N, int P,
+                                            int a, const int* __restrict__ cstart,
+                                            const T* __restrict__ cf, T* w,
+                                            const T* __restrict__ csa, const T* __restrict__ zprev,
+                                            T* __restrict__ Z) {
+  for (int p0 = beg; p0 < end; p0 += 2 * stride) {
+    const int p1 = p0 + stride;
+    const bool two = p1 < end;
+    int x0, y0, x1, y1;
+    colour_xy<C>(p0, m, cstart, x0, y0);
+    colour_xy<C>(two ? p1 : p0, m, cstart, x1, y1);
+    const T v0 = color_node_value<T, C, UPPER, CG>(x0, y0, p0, m, N, cf, w, csa, zprev);
+    const T v1 = two ? color_node_value<T, C, UPPER, CG>(x1, y1, p1, m, N, cf, w, csa, zprev) : T(0);
+    const int i0 = x0 + m * y0, i1 = x1 + m * y1;
+    w[i0] = v0;
+    if (two) w[i1] = v1;
+    if (UPPER && Z != nullptr) {
+      Z[(size_t)i0 * P + a] = v0;
+      if (two) Z[(size_t)i1 * P + a] = v1;
+    }
+  }
+}
+
+// The four lower phases (colours 0..3) then the four upper phases (3..0) of one column, with
+// ``sync`` between phases.
+template <typename T, bool CG, typename Sync>
+__device__ __forceinline__ void color_sweeps(int off, int stride, int m, int N, int P, int a,
+                                             const int* __restrict__ cstart, const T* __restrict__ cf,
+                                             T* w, const T* __restrict__ csa,
+                                             const T* __restrict__ zprev, T* __restrict__ Z, Sync sync) {
+  color_phase<T, 0, false, CG>(cstart[0] + off, cstart[1], stride, m, N, P, a, cstart, cf, w, csa, zprev, nullptr);
+  sync();
+  color_phase<T, 1, false, CG>(cstart[1] + off, cstart[2], stride, m, N, P, a, cstart, cf, w, csa, zprev, nullptr);
+  sync();
+  color_phase<T, 2, false, CG>(cstart[2] + off, cstart[3], stride, m, N, P, a, cstart, cf, w, csa, zprev, nullptr);
+  sync();
+  color_phase<T, 3, false, CG>(cstart[3] + off, cstart[4], stride, m, N, P, a, cstart, cf, w, csa, zprev, nullptr);
+  sync();
+  color_phase<T, 3, true, CG>(cstart[3] + off, cstart[4], stride, m, N, P, a, cstart, cf, w, nullptr, nullptr, Z);
+  sync();
+  color_phase<T, 2, true, CG>(cstart[2] + off, cstart[3], stride, m, N, P, a, cstart, cf, w, nullptr, nullptr, Z);
+  sync();
+  color_phase<T, 1, true, CG>(cstart[1] + off, cstart[2], stride, m, N, P, a, cstart, cf, w, nullptr, nullptr, Z);
+  sync();
+  color_phase<T, 0, true, CG>(cstart[0] + off, cstart[1], stride, m, N, P, a, cstart, cf, w, nullptr, nullptr, Z);
+  sync();
 }
 
 // All eight phases of one column in one CTA, the column in shared memory (meshes whose column
-// fits): CTA b solves column a0 + b.
+// fits): CTA b solves column a0 + b.  The solution goes to column a of Z and, contiguous, back
+// over column a of Rt (as the cluster kernel leaves it), where the coupling scatter reads it.
+// A single-column launch first prefetches the column's factors (and coupling stencil) into L2, so
+// only the first phase waits for HBM.
 template <typename T>
 __global__ void __launch_bounds__(1024) color_cta_kernel(int m, int N, int ldN, int P, int a0,
                                                         int fac_per_col, const int* __restrict__ cstart_g,
                                                         const T* __restrict__ cfs,
-                                                        const T* __restrict__ Rt, T* __restrict__ Z,
-                                                        const int* __restrict__ done) {
+                                                        T* __restrict__ Rt, T* __restrict__ Z,
+                                                        const int* __restrict__ done,
+                                                        const T* __restrict__ cs) {
   if (done != nullptr && *done) return;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T* w = reinterpret_cast<T*>(smem_raw);
   __shared__ int cstart[5];
   const int a = a0 + blockIdx.x;
   const T* cf = cfs + (size_t)(fac_per_col ? a : 0) * 9 * N;
-  const T* rhs = Rt + (size_t)a * ldN;
+  T* rhs = Rt + (size_t)a * ldN;
+  const T* csa = (cs != nullptr && a > 0) ? cs + (size_t)(a - 1) * 9 * N : nullptr;
+  const T* zprev = Rt + (size_t)(a > 0 ? a - 1 : 0) * ldN;
+  if (gridDim.x == 1) {
+    l2_prefetch(cf, sizeof(T) * 9 * (size_t)N, 0, 1);
+    if (csa != nullptr) l2_prefetch(csa, sizeof(T) * 9 * (size_t)N, 0, 1);
+  }
   if (threadIdx.x < 5) cstart[threadIdx.x] = cstart_g[threadIdx.x];
   for (int i = threadIdx.x; i < N; i += blockDim.x) w[i] = rhs[i];
   __syncthreads();
-  for (int c = 0; c < 4; ++c) {
-    for (int pos = cstart[c] + threadIdx.x; pos < cstart[c + 1]; pos += blockDim.x)
-      color_phase_node<T, false>(pos, colour_node(c, pos, m, cstart), m, N, cf, w);
-    __syncthreads();
+  color_sweeps<T, false>(threadIdx.x, blockDim.x, m, N, P, a, cstart, cf, w, csa, zprev,
+                         (T*)nullptr, []() { __syncthreads(); });
+  for (int i = threadIdx.x; i < N; i += blockDim.x) {
+    if (Z != nullptr) Z[(size_t)i * P + a] = w[i];
+    rhs[i] = w[i];
   }
-  for (int c = 3; c >= 0; --c) {
-    for (int pos = cstart[c] + threadIdx.x; pos < cstart[c + 1]; pos += blockDim.x)
-      color_phase_node<T, true>(pos, colour_node(c, pos, m, cstart), m, N, cf, w);
-    __syncthreads();
-  }
-  for (int i = threadIdx.x; i < N; i += blockDim.x) Z[(size_t)i * P + a] = w[i];
 }
 
 // All eight phases of one column on a thread-block cluster of CL CTAs (grid = columns x CL): the
 // column stays in global memory (L2), every CTA takes a share of each colour's nodes, and a
 // cluster barrier (release / acquire at cluster scope) separates the phases.  Neighbour values
-// are read at L2 (ld.global.cg) so no SM reads a stale L1 line written by another.
+// are read at L2 (ld.global.cg) so no SM reads a stale L1 line written by another.  Each CTA of a
+// single-column launch first prefetches its share of the column's factors (and coupling stencil)
+// into L2.  The coupling of column a - 1 is subtracted from each node's right-hand side in the
+// lower phase of its colour, before the node's own update: its lower-colour neighbours are final
+// by then.
 template <typename T, int CL>
 __global__ void __launch_bounds__(1024) color_cluster_kernel(
     int m, int N, int ldN, int P, int a0, int fac_per_col, const int* __restrict__ cstart_g,
-    const T* __restrict__ cfs, T* __restrict__ Rt, T* __restrict__ Z, const int* __restrict__ done) {
+    const T* __restrict__ cfs, T* __restrict__ Rt, T* __restrict__ Z, const int* __restrict__ done,
+    const T* __restrict__ cs) {
   if (done != nullptr && *done) return;  // uniform over the cluster: no barrier is skipped by some
   __shared__ int cstart[5];
   const int a = a0 + blockIdx.x / CL;
   const int rank = blockIdx.x % CL;
   const T* cf = cfs + (size_t)(fac_per_col ? a : 0) * 9 * N;
   T* w = Rt + (size_t)a * ldN;
+  const T* csa = (cs != nullptr && a > 0) ? cs + (size_t)(a - 1) * 9 * N : nullptr;
+  const T* zprev = Rt + (size_t)(a > 0 ? a - 1 : 0) * ldN;
+  if (gridDim.x == CL) {
+    l2_prefetch(cf, sizeof(T) * 9 * (size_t)N, rank, CL);
+    if (csa != nullptr) l2_prefetch(csa, sizeof(T) * 9 * (size_t)N, rank, CL);
+  }
   if (threadIdx.x < 5) cstart[threadIdx.x] = cstart_g[threadIdx.x];
   __syncthreads();
   const int stride = CL * blockDim.x;
-  auto phase = [&](int c, bool upper) {
-    for (int pos = cstart[c] + rank * blockDim.x + threadIdx.x; pos < cstart[c + 1]; pos += stride) {
-      const int i = colour_node(c, pos, m, cstart);
-      const int x = i % m, y = i / m;
-      T v = __ldcg(w + i);
-      if (upper) v *= cf[(size_t)4 * N + pos];
-#pragma unroll
-      for (int sl = 0; sl < 9; ++sl) {
-        if (sl == 4) continue;
-        const int jx = x + sl % 3 - 1, jy = y + sl / 3 - 1;
-        if (jx < 0 || jy < 0 || jx >= m || jy >= m) continue;
-        const int cj = node_colour(jx, jy);
-        if (upper ? cj <= c : cj >= c) continue;
-        v -= cf[(size_t)sl * N + pos] * __ldcg(w + jx + m * jy);
-      }
-      w[i] = v;
-      if (upper) Z[(size_t)i * P + a] = v;
-    }
+  const int off = rank * blockDim.x + threadIdx.x;
+  color_sweeps<T, true>(off, stride, m, N, P, a, cstart, cf, w, csa, zprev, Z, []() {
     asm volatile("barrier.cluster.arrive.release.aligned;\n"
                  "barrier.cluster.wait.acquire.aligned;\n" ::: "memory");
-  };
-  for (int c = 0; c < 4; ++c) phase(c, false);
-  for (int c = 3; c >= 0; --c) phase(c, true);
+  });
 }
 
 template <typename T, int CL>
 int launch_cluster(System& s, int a0, int ncols, int fac_per_col, const T* lu, T* Rt, T* Z,
-                   cudaStream_t st, const int* done) {
+                   cudaStream_t st, const int* done, const T* cs) {
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3((unsigned)(ncols * CL), 1, 1);
   cfg.blockDim = dim3(1024, 1, 1);
   cfg.dynamicSmemBytes = 0;
   cfg.stream = st;
-  cudaLaunchAttribute attr[1];
+  cudaLaunchAttribute attr[2];
   attr[0].id = cudaLaunchAttributeClusterDimension;
   attr[0].val.clusterDim.x = CL;
   attr[0].val.clusterDim.y = 1;
   attr[0].val.clusterDim.z = 1;
+  attr[1].id = cudaLaunchAttributePriority;
+  attr[1].val.priority = s.prio_hi;
   cfg.attrs = attr;
-  cfg.numAttrs = 1;
+  cfg.numAttrs = 2;
   TimeScope ts(s.timer, K_ILU_SOLVE, st);
   SG_CUDA(cudaLaunchKernelEx(&cfg, color_cluster_kernel<T, CL>, s.pat.m, s.N, s.ldN, s.P, a0,
-                             fac_per_col, (const int*)s.cstart.p, lu, Rt, Z, done));
+                             fac_per_col, (const int*)s.cstart.p, lu, Rt, Z, done, cs));
   return check_launch("color_cluster");
 }
 
@@ -259,30 +389,65 @@ int launch_color_ilu(System& s, cudaStream_t st) {
 // Block solves of columns a0 .. a0 + ncols - 1 from Rt into Z (colour-ordered factors).
 template <typename T>
 int launch_color_solve(System& s, int a0, int ncols, int fac_per_col, const T* lu, T* Rt, T* Z,
-                       cudaStream_t st, const int* done) {
+                       cudaStream_t st, const int* done, const T* cs) {
   const int m = s.pat.m;
   const size_t smem = sizeof(T) * (size_t)s.ldN;
   // a cluster of CTAs once one CTA would hold more than ~1024 nodes per colour; one CTA with the
   // column in shared memory below that
   const int per_colour = (s.N + 3) / 4;
   if (per_colour > 2048) {
-    if (per_colour > 4 * 2048) return launch_cluster<T, 8>(s, a0, ncols, fac_per_col, lu, Rt, Z, st, done);
-    if (per_colour > 2 * 2048) return launch_cluster<T, 4>(s, a0, ncols, fac_per_col, lu, Rt, Z, st, done);
-    return launch_cluster<T, 2>(s, a0, ncols, fac_per_col, lu, Rt, Z, st, done);
+    if (per_colour > 4 * 2048)
+      return launch_cluster<T, 8>(s, a0, ncols, fac_per_col, lu, Rt, Z, st, done, cs);
+    if (per_colour > 2 * 2048)
+      return launch_cluster<T, 4>(s, a0, ncols, fac_per_col, lu, Rt, Z, st, done, cs);
+    return launch_cluster<T, 2>(s, a0, ncols, fac_per_col, lu, Rt, Z, st, done, cs);
   }
   {
     auto kern = color_cta_kernel<T>;
     SG_TRY(ensure_smem((const void*)kern, smem));
     TimeScope ts(s.timer, K_ILU_SOLVE, st);
-    kern<<<ncols, 1024, smem, st>>>(m, s.N, s.ldN, s.P, a0, fac_per_col, s.cstart.p, lu, Rt, Z, done);
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)ncols, 1, 1);
+    cfg.blockDim = dim3(1024, 1, 1);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributePriority;
+    attr[0].val.priority = s.prio_hi;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    SG_CUDA(cudaLaunchKernelEx(&cfg, kern, m, s.N, s.ldN, s.P, a0, fac_per_col,
+                               (const int*)s.cstart.p, lu, Rt, Z, done, cs));
     return check_launch("color_cta");
   }
   return fail(SG_ERR_ARG, "four-colour block solve: column larger than shared memory");
 }
 
 template int launch_color_solve<double>(System&, int, int, int, const double*, double*, double*,
-                                        cudaStream_t, const int*);
+                                        cudaStream_t, const int*, const double*);
 template int launch_color_solve<float>(System&, int, int, int, const float*, float*, float*,
-                                       cudaStream_t, const int*);
+                                       cudaStream_t, const int*, const float*);
+
+int launch_color_coupling(System& s, cudaStream_t st) {
+  if (s.P < 2) return SG_OK;
+  if (s.stack_km.p == nullptr) return fail(SG_ERR_ARG, "coupling stencils: no FP64 k-major stack");
+  const size_t n = (size_t)(s.P - 1) * 9 * s.N;
+  const long long total = (long long)(s.P - 1) * s.N;
+  const int grid = (int)std::max(1LL, std::min((total + 255) / 256, 152LL * 32));
+  const bool lowp = s.prm.precision != SG_FP64;
+  const int round_bf16 = lowp && (s.prm.precision == SG_MIXED_BF16 || s.prm.coupling_bf16) ? 1 : 0;
+  if (lowp) {
+    SG_TRY(s.gsn_cs32.alloc(n));
+    color_coupling_kernel<float><<<grid, 256, 0, st>>>(
+        s.pat.m, s.N, s.pat.nnz, s.P, round_bf16, s.rowptr.p, s.col.p, s.cstart.p, s.stack_km.p,
+        s.gsn_kptr.p, s.gsn_k.p, s.gsn_eptr.p, s.gsn_ea.p, s.gsn_eg.p, s.gsn_cs32.p);
+  } else {
+    SG_TRY(s.gsn_cs.alloc(n));
+    color_coupling_kernel<double><<<grid, 256, 0, st>>>(
+        s.pat.m, s.N, s.pat.nnz, s.P, 0, s.rowptr.p, s.col.p, s.cstart.p, s.stack_km.p,
+        s.gsn_kptr.p, s.gsn_k.p, s.gsn_eptr.p, s.gsn_ea.p, s.gsn_eg.p, s.gsn_cs.p);
+  }
+  return check_launch("color_coupling");
+}
 
 }  // namespace sg

@@ -529,58 +529,119 @@ __global__ void columns_kernel(const T* __restrict__ R, T* __restrict__ Rt, int 
   }
 }
 
-constexpr int kScatterRows = 8;
+// Z[r * P + c] = Rt[c * ld + r]: the P columns back into the N x P row-major layout.
+template <typename T>
+__global__ void rows_kernel(const T* __restrict__ Rt, T* __restrict__ Z, int N, int P, int ld,
+                            const int* __restrict__ done) {
+  if (done != nullptr && *done) return;
+  __shared__ T tile[32][33];
+  const int r0 = blockIdx.x * 32, c0 = blockIdx.y * 32;
+  for (int dy = threadIdx.y; dy < 32; dy += blockDim.y) {
+    const int c = c0 + dy, r = r0 + threadIdx.x;
+    tile[dy][threadIdx.x] = (r < N && c < P) ? Rt[(size_t)c * ld + r] : T(0);
+  }
+  __syncthreads();
+  for (int dy = threadIdx.y; dy < 32; dy += blockDim.y) {
+    const int r = r0 + dy, c = c0 + threadIdx.x;
+    if (r < N && c < P) Z[(size_t)r * P + c] = tile[threadIdx.x][dy];
+  }
+}
+
+constexpr int kScatterRows = 32;   // rows per tile of the later-column scatter (one per lane)
+constexpr int kScatterWarps = 8;
+// k of one warp whose stiffness loads are in flight together (fewer for 8-byte values, so the
+// kernel stays within 85 registers a thread)
+template <typename TV>
+__host__ __device__ constexpr int scatter_ku() { return sizeof(TV) >= 8 ? 2 : 4; }
+constexpr int kScatterTW = 12;     // target columns of one warp whose Rt values are prefetched
 
 // After block b of the Gauss-Seidel sweep, for the target columns a_lo <= a <= a_hi (all > b):
 // Rt[a, i] -= sum_k G_k[a,b] (A_k z_b)[i] for every row i.  kptr / klist / eptr / ek / eg are the
-// tables of those targets.  The stiffness values are read from the k-major copy of the stack
-// (stack_km[k*nnz + e]): the block needs only the k of its list, and consecutive threads take
-// consecutive rows of one k, so each k reads one contiguous run of entries.
+// tables of those targets.  A tile of 32 rows per step, one row per lane: each warp forms
+// T[k, row] = sum_e A_k[e] z_b[col_e] for its share of the k list (the stiffness values from the
+// k-major copy, stack_km[k * nnz + e], consecutive rows reading consecutive entries; z_b read
+// once per lane from the column zc with stride zs), then each warp subtracts the G-weighted sums
+// of its share of the target columns.  The loads are issued in batches (kScatterKU k at a time,
+// the Rt values of a warp's targets before the stiffness loads) so that a warp waits for memory
+// once per batch rather than once per k or target.  A CTA holds at most a third of an SM's
+// registers.
 template <typename T, typename TV>
-__global__ void __launch_bounds__(128) fs_scatter_kernel(
+__global__ void __launch_bounds__(kScatterWarps * 32, 3) fs_scatter_kernel(
     int N, int P, int ldN, int nnz, int b, int a_lo, int a_hi, const int* __restrict__ rowptr,
     const int* __restrict__ col, const TV* __restrict__ stack_km, const int* __restrict__ kptr,
     const int* __restrict__ klist, const int* __restrict__ eptr, const int* __restrict__ ek,
-    const T* __restrict__ eg, const T* __restrict__ Z, T* __restrict__ Rt,
+    const T* __restrict__ eg, const T* __restrict__ zc, int zs, T* __restrict__ Rt,
     const int* __restrict__ done) {
   if (done != nullptr && *done) return;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  T* Ts = reinterpret_cast<T*>(smem_raw);
+  T* Ts = reinterpret_cast<T*>(smem_raw);  // klen x 32
   const int k0 = kptr[b], klen = kptr[b + 1] - k0;
-  const int r0 = blockIdx.x * kScatterRows;
-  const int nr = min(kScatterRows, N - r0);
-  for (int t = threadIdx.x; t < kScatterRows * klen; t += blockDim.x) {
-    const int rr = t % kScatterRows, kk = t / kScatterRows;
-    T s = T(0);
-    if (rr < nr) {
-      const int i = r0 + rr;
-      const TV* ak = stack_km + (size_t)klist[k0 + kk] * nnz;
-      for (int e = rowptr[i]; e < rowptr[i + 1]; ++e)
-        s += (T)ak[e] * Z[(size_t)col[e] * P + b];
-    }
-    Ts[rr * klen + kk] = s;
-  }
-  __syncthreads();
-  const int na = a_hi - a_lo + 1;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   const int* ep = eptr + (size_t)b * (P + 1);
-  for (int t = threadIdx.x; t < nr * na; t += blockDim.x) {  // rows fastest: runs of nr entries
-    const int a = a_lo + t / nr, rr = t - (a - a_lo) * nr;
-    T s = T(0);
-    for (int q = ep[a]; q < ep[a + 1]; ++q) s += eg[q] * Ts[rr * klen + ek[q]];
-    Rt[(size_t)a * ldN + r0 + rr] -= s;
+  const int ntiles = (N + kScatterRows - 1) / kScatterRows;
+  constexpr int kChunk = kScatterWarps * kScatterTW;  // target columns per prefetch round
+  for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    const int i = tile * kScatterRows + lane;
+    const bool live = i < N;
+    T r[kScatterTW];
+    auto prefetch = [&](int cb) {
+#pragma unroll
+      for (int j = 0; j < kScatterTW; ++j) {
+        const int a = cb + w + kScatterWarps * j;
+        r[j] = (live && a <= a_hi) ? Rt[(size_t)a * ldN + i] : T(0);
+      }
+    };
+    prefetch(a_lo);
+    const int e0 = live ? rowptr[i] : 0;
+    const int ne = live ? rowptr[i + 1] - e0 : 0;
+    T z[9];
+#pragma unroll
+    for (int e = 0; e < 9; ++e) z[e] = e < ne ? zc[(size_t)col[e0 + e] * zs] : T(0);
+    constexpr int kScatterKU = scatter_ku<TV>();
+    for (int kb = w * kScatterKU; kb < klen; kb += kScatterWarps * kScatterKU) {
+      TV av[kScatterKU][9];
+#pragma unroll
+      for (int u = 0; u < kScatterKU; ++u) {
+        const TV* ak = stack_km + (size_t)klist[k0 + min(kb + u, klen - 1)] * nnz + e0;
+#pragma unroll
+        for (int e = 0; e < 9; ++e) av[u][e] = e < ne ? ak[e] : TV(0);
+      }
+#pragma unroll
+      for (int u = 0; u < kScatterKU; ++u) {
+        T t = T(0);
+#pragma unroll
+        for (int e = 0; e < 9; ++e)
+          if (e < ne) t += (T)av[u][e] * z[e];
+        if (kb + u < klen) Ts[(size_t)(kb + u) * kScatterRows + lane] = t;
+      }
+    }
+    __syncthreads();
+    for (int cb = a_lo; cb <= a_hi; cb += kChunk) {
+      if (cb != a_lo) prefetch(cb);
+#pragma unroll
+      for (int j = 0; j < kScatterTW; ++j) {
+        const int a = cb + w + kScatterWarps * j;
+        if (a > a_hi) break;
+        T s = T(0);
+        for (int q = ep[a]; q < ep[a + 1]; ++q) s += eg[q] * Ts[(size_t)ek[q] * kScatterRows + lane];
+        if (live) Rt[(size_t)a * ldN + i] = r[j] - s;
+      }
+    }
+    __syncthreads();
   }
 }
 
 // After block b, for the next column only: Rt[b+1, i] -= sum_k G_k[b+1,b] (A_k z_b)[i], one
 // thread per row (the row's stencil values of z_b loaded once, then the short k list of the
 // next-column tables).  Same arithmetic order as fs_scatter_kernel: per k the stencil sum in
-// entry order, then the G-weighted sum in table order.
+// entry order, then the G-weighted sum in table order.  z_b comes from the column zcol with
+// stride zs (the contiguous column the four-colour solve leaves, or column b of Z).
 template <typename T, typename TV>
 __global__ void __launch_bounds__(256) fs_next_kernel(
     int N, int P, int ldN, int nnz, int b, const int* __restrict__ rowptr,
     const int* __restrict__ col, const TV* __restrict__ stack_km, const int* __restrict__ kptr,
     const int* __restrict__ klist, const int* __restrict__ eptr, const int* __restrict__ ek,
-    const T* __restrict__ eg, const T* __restrict__ Z, T* __restrict__ Rt,
+    const T* __restrict__ eg, const T* __restrict__ zcol, int zs, T* __restrict__ Rt,
     const int* __restrict__ done) {
   if (done != nullptr && *done) return;
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -589,7 +650,7 @@ __global__ void __launch_bounds__(256) fs_next_kernel(
   const int e0 = rowptr[i], ne = rowptr[i + 1] - e0;  // at most 9
   T zc[9];
 #pragma unroll
-  for (int e = 0; e < 9; ++e) zc[e] = e < ne ? Z[(size_t)col[e0 + e] * P + b] : T(0);
+  for (int e = 0; e < 9; ++e) zc[e] = e < ne ? zcol[(size_t)col[e0 + e] * zs] : T(0);
   const int k0 = kptr[b];
   const int* ep = eptr + (size_t)b * (P + 1);
   T s = T(0);
@@ -625,6 +686,7 @@ struct PcBufs<double> {
   static double* triw(System& s) { return s.tri_w.p; }
   static bool full(const System& s) { return s.tri_full; }
   static const double* eg(const System& s) { return s.gs_eg.p; }
+  static const double* cs(const System& s) { return s.gsn_cs.p; }
 };
 template <>
 struct PcBufs<float> {
@@ -636,6 +698,7 @@ struct PcBufs<float> {
   static float* triw(System& s) { return s.tri_w32.p; }
   static bool full(const System& s) { return s.tri_full32; }
   static const float* eg(const System& s) { return s.gs_eg_f32.p; }
+  static const float* cs(const System& s) { return s.gsn_cs32.p; }
 };
 
 template <typename T>
@@ -644,6 +707,14 @@ int launch_columns(System& s, const T* R, T* Rt, cudaStream_t st, const int* don
   TimeScope ts(s.timer, K_OTHER, st);
   columns_kernel<T><<<grid, block, 0, st>>>(R, Rt, s.N, s.P, s.ldN, done);
   return check_launch("columns");
+}
+
+template <typename T>
+int launch_rows(System& s, const T* Rt, T* Z, cudaStream_t st, const int* done) {
+  dim3 block(32, 8), grid((unsigned)((s.N + 31) / 32), (unsigned)((s.P + 31) / 32));
+  TimeScope ts(s.timer, K_OTHER, st);
+  rows_kernel<T><<<grid, block, 0, st>>>(Rt, Z, s.N, s.P, s.ldN, done);
+  return check_launch("rows");
 }
 
 template <typename T>
@@ -688,20 +759,37 @@ int launch_block_solve(System& s, int a0, int ncols, int fac_per_col, const T* R
 template <typename T, typename TV>
 int launch_scatter_t(System& s, int b, bool next, const TV* stack_km, const T* eg_next,
                      const T* eg_later, const T* Z, T* Rt, cudaStream_t st, const int* done) {
-  size_t smem = sizeof(T) * kScatterRows * std::max(1, s.gs_max_klen);
-  auto kern = fs_scatter_kernel<T, TV>;
-  SG_TRY(ensure_smem((const void*)kern, smem));
-  const int grid = (s.N + kScatterRows - 1) / kScatterRows;
-  const int a_lo = next ? b + 1 : b + 2, a_hi = next ? b + 1 : s.P - 1;
+  // z_b: the four-colour solve leaves it contiguous in column b of Rt; else column b of Z
+  const bool col_z = s.prm.ilu_order == SG_ILU_COLOR4;
+  const T* zc = col_z ? Rt + (size_t)b * s.ldN : Z + b;
+  const int zs = col_z ? 1 : s.P;
   TimeScope ts(s.timer, K_GS_SCATTER, st);
-  if (next)
+  if (next) {
     fs_next_kernel<T, TV><<<(s.N + 255) / 256, 256, 0, st>>>(
         s.N, s.P, s.ldN, s.pat.nnz, b, s.rowptr.p, s.col.p, stack_km, s.gsn_kptr.p, s.gsn_k.p,
-        s.gsn_eptr.p, s.gsn_ea.p, eg_next, Z, Rt, done);
-  else
-    kern<<<grid, 128, smem, st>>>(s.N, s.P, s.ldN, s.pat.nnz, b, a_lo, a_hi, s.rowptr.p, s.col.p,
-                                  stack_km, s.gs_kptr.p, s.gs_k.p, s.gs_eptr.p, s.gs_ea.p,
-                                  eg_later, Z, Rt, done);
+        s.gsn_eptr.p, s.gsn_ea.p, eg_next, zc, zs, Rt, done);
+  } else {
+    const size_t smem = sizeof(T) * kScatterRows * std::max(1, s.gs_max_klen);
+    auto kern = fs_scatter_kernel<T, TV>;
+    SG_TRY(ensure_smem((const void*)kern, smem));
+    // one CTA per 32-row tile at the lowest launch priority: SMs that its CTAs free go to a
+    // pending block solve first
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)std::max(1, (s.N + kScatterRows - 1) / kScatterRows), 1, 1);
+    cfg.blockDim = dim3(kScatterWarps * 32, 1, 1);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributePriority;
+    attr[0].val.priority = s.prio_lo;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    SG_CUDA(cudaLaunchKernelEx(&cfg, kern, s.N, s.P, s.ldN, s.pat.nnz, b, b + 2, s.P - 1,
+                               (const int*)s.rowptr.p, (const int*)s.col.p, stack_km,
+                               (const int*)s.gs_kptr.p, (const int*)s.gs_k.p,
+                               (const int*)s.gs_eptr.p, (const int*)s.gs_ea.p, eg_later, zc, zs,
+                               Rt, done));
+  }
   return check_launch("fs_scatter");
 }
 
@@ -732,11 +820,32 @@ int launch_scatter<float>(System& s, int b, bool next, const float* Z, float* Rt
 // the scatter into columns a + 2 .. runs on the system's second stream, overlapping the solve of
 // block a + 1.  Ordering: that scatter waits for z_a; the next-column scatter of block a waits for
 // the later-column scatter of block a - 1, which also subtracts into column a + 1; the sweep ends
-// by joining the second stream.
+// by joining the second stream.  In the four-colour ordering the next-column coupling is part of
+// the block solve (its stencil K_{a+1,a} assembled at setup): the solve of block a + 1 subtracts
+// K_{a+1,a} z_a itself and waits for the later-column scatter of block a - 1 instead; the solves
+// leave z_a in column a of Rt, and one transpose at the end writes D.
 template <typename T>
 int fs_gs_sweep(System& s, const T* R, T* D, T* Rt, cudaStream_t st, const int* done, bool fork) {
   SG_TRY(launch_columns<T>(s, R, Rt, st, done));
   cudaStream_t s2 = fork ? s.stream2 : st;
+  const T* cs = PcBufs<T>::cs(s);
+  if (s.prm.ilu_order == SG_ILU_COLOR4 && cs != nullptr) {
+    for (int a = 0; a < s.P; ++a) {
+      if (fork && a >= 2) SG_CUDA(cudaStreamWaitEvent(st, s.ev_r[(a - 2) & 1], 0));
+      SG_TRY(launch_color_solve<T>(s, a, 1, 1, PcBufs<T>::lu9(s), Rt, (T*)nullptr, st, done, cs));
+      if (a + 2 < s.P) {
+        if (fork) {
+          SG_CUDA(cudaEventRecord(s.ev_z, st));
+          SG_CUDA(cudaStreamWaitEvent(s2, s.ev_z, 0));
+        }
+        SG_TRY(launch_scatter<T>(s, a, false, D, Rt, s2, done));
+        if (fork) SG_CUDA(cudaEventRecord(s.ev_r[a & 1], s2));
+      }
+    }
+    if (fork && s.P >= 3) SG_CUDA(cudaStreamWaitEvent(st, s.ev_r[(s.P - 3) & 1], 0));
+    // every column of Rt now holds its block's solution
+    return launch_rows<T>(s, Rt, D, st, done);
+  }
   for (int a = 0; a < s.P; ++a) {
     SG_TRY(launch_block_solve<T>(s, a, 1, 1, Rt, D, st, done));
     if (a + 1 >= s.P) break;

@@ -441,6 +441,8 @@ static int build_gs_tables(System& s, cudaStream_t st) {
                               s.gsn_eg_f32, st));
   int prio_low = 0, prio_high = 0;
   SG_CUDA(cudaDeviceGetStreamPriorityRange(&prio_low, &prio_high));
+  s.prio_lo = prio_low;
+  s.prio_hi = prio_high;
   SG_CUDA(cudaStreamCreateWithPriority(&s.stream2, cudaStreamNonBlocking, prio_low));
   SG_CUDA(cudaEventCreateWithFlags(&s.ev_z, cudaEventDisableTiming));
   SG_CUDA(cudaEventCreateWithFlags(&s.ev_r[0], cudaEventDisableTiming));
@@ -467,11 +469,11 @@ static void free_system(System* s) {
   s->lev9_off.release();
   s->cstart.release();
   s->stack_km16.release();
-  DBuf<double>* db[] = {&s->stack, &s->stack_km, &s->ent_g, &s->blk, &s->fac, &s->lu9, &s->gs_eg, &s->gsn_eg, &s->rhs_t, &s->tmp,
+  DBuf<double>* db[] = {&s->stack, &s->stack_km, &s->ent_g, &s->blk, &s->fac, &s->lu9, &s->gs_eg, &s->gsn_eg, &s->gsn_cs, &s->rhs_t, &s->tmp,
                         &s->tmp2, &s->tri_w, &s->V, &s->Z, &s->Hs, &s->cs, &s->sn, &s->g, &s->y,
                         &s->scal, &s->red, &s->rvec};
   for (auto* b : db) b->release();
-  DBuf<float>* fb[] = {&s->stack_f32, &s->stack_km32, &s->ent_g_f32, &s->lu9_f32, &s->blk_f32, &s->gs_eg_f32, &s->gsn_eg_f32,
+  DBuf<float>* fb[] = {&s->stack_f32, &s->stack_km32, &s->ent_g_f32, &s->lu9_f32, &s->blk_f32, &s->gs_eg_f32, &s->gsn_eg_f32, &s->gsn_cs32,
                        &s->rhs_t32, &s->tmp32, &s->tmp232, &s->tri_w32, &s->V32, &s->Z32,
                        &s->mv32a, &s->mv32b};
   for (auto* b : fb) b->release();
@@ -523,6 +525,8 @@ static int setup_system(System& s, cudaStream_t st, bool krylov = true) {
   // the Gauss-Seidel sweep (later-column scatters) fills idle SMs at the lowest priority
   int prio_low = 0, prio_high = 0;
   SG_CUDA(cudaDeviceGetStreamPriorityRange(&prio_low, &prio_high));
+  s.prio_lo = prio_low;
+  s.prio_hi = prio_high;
   SG_CUDA(cudaStreamCreateWithPriority(&s.stream, cudaStreamNonBlocking, prio_high));
   SG_CUDA(cudaEventCreateWithFlags(&s.ev, cudaEventDisableTiming));
   SG_CUDA(cudaEventCreateWithFlags(&s.seg_ev[0], cudaEventDisableTiming));
@@ -613,6 +617,7 @@ static int setup_system(System& s, cudaStream_t st, bool krylov = true) {
         SG_TRY(s.stack_km16.alloc(nnzL));
         SG_TRY(launch_cast_bf16(s.stack_km.p, s.stack_km16.p, nnzL, st));
       }
+      if (p.ilu_order == SG_ILU_COLOR4) SG_TRY(launch_color_coupling(s, st));
       // the mixed forms sweep in FP32 only: their FP64 k-major copy is not kept
       if (lowp) {
         SG_CUDA(cudaStreamSynchronize(st));
@@ -759,7 +764,7 @@ static int launch_segment(SolveState& q, int j0, int j1) {
     return rc != SG_OK ? rc : fail(SG_ERR_CUDA, std::string("stream capture: ") + cudaGetErrorString(e));
   }
   cudaGraphExec_t exec = nullptr;
-  e = cudaGraphInstantiate(&exec, graph, 0);
+  e = cudaGraphInstantiate(&exec, graph, cudaGraphInstantiateFlagUseNodePriority);
   cudaGraphDestroy(graph);
   if (e != cudaSuccess) return fail(SG_ERR_CUDA, std::string("graph instantiate: ") + cudaGetErrorString(e));
   s.graphs.push_back({q.jmax, j0, exec});

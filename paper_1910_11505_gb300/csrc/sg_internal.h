@@ -70,6 +70,26 @@ struct TimeScope {
   ~TimeScope();
 };
 
+// ------------------------------------------------------------------ device helpers
+
+#ifdef __CUDACC__
+// Bulk prefetch of [base, base + bytes) into L2 (cp.async.bulk.prefetch.L2), in 16 KB pieces
+// spread over the threads of ``nparts`` CTAs of which this is CTA ``part``.  The range is trimmed
+// inward to 16-byte boundaries (the instruction's alignment rule), so nothing outside it is touched.
+__device__ __forceinline__ void l2_prefetch(const void* base, size_t bytes, int part, int nparts) {
+  const unsigned long long b0 = reinterpret_cast<unsigned long long>(base);
+  const unsigned long long lo = (b0 + 15ull) & ~15ull, hi = (b0 + bytes) & ~15ull;
+  constexpr unsigned long long kPiece = 16384ull;
+  for (unsigned long long off = lo + (unsigned long long)(part * blockDim.x + threadIdx.x) * kPiece;
+       off < hi; off += (unsigned long long)nparts * blockDim.x * kPiece) {
+    const unsigned sz = (unsigned)(hi - off < kPiece ? hi - off : kPiece);
+    unsigned long long g;
+    asm volatile("cvta.to.global.u64 %0, %1;" : "=l"(g) : "l"(off));
+    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(g), "r"(sz) : "memory");
+  }
+}
+#endif
+
 // ------------------------------------------------------------------ device buffers
 
 template <typename T>
@@ -234,6 +254,11 @@ struct System {
   DBuf<int> gsn_kptr, gsn_k, gsn_eptr, gsn_ea;
   DBuf<double> gsn_eg;
   DBuf<float> gsn_eg_f32;
+  // four-colour sweeps: the next-column coupling K_{a,a-1} = sum_k G_k[a,a-1] A_k of every column
+  // a >= 1 as a 9-slot stencil in the colour-major layout of the factors, (P - 1) x 9 x N; the
+  // block solve of column a subtracts K_{a,a-1} z_{a-1} from its right-hand side itself
+  DBuf<double> gsn_cs;
+  DBuf<float> gsn_cs32;
   int gs_max_klen = 0;
   // device scratch
   DBuf<double> rhs_t;          // P columns of stride ldN: right-hand sides of the block solves
@@ -263,6 +288,10 @@ struct System {
   // block solve, and the events ordering the two streams
   cudaStream_t stream2 = nullptr;
   cudaEvent_t ev_z = nullptr, ev_r[2] = {nullptr, nullptr};
+  // launch priorities (cudaDeviceGetStreamPriorityRange): the block solves of the sweep launch at
+  // the highest, the later-column scatters at the lowest, so that the block scheduler gives SMs
+  // freed by scatter CTAs to a pending block solve first (graphs keep the per-node priorities)
+  int prio_lo = 0, prio_hi = 0;
   // multigrid (SG_PC_MG): the coarser levels, coarsest first, each a System on its own mesh with
   // the same stochastic data; per level the V-cycle's right-hand side b, iterate u, residual r and
   // smoother correction d (the finest level uses the caller's R and Z as b and u)
@@ -296,9 +325,14 @@ int launch_block_values(System& s, cudaStream_t st);
 int launch_ilu0(System& s, cudaStream_t st);
 // ILU(0) in the four-colour ordering (k_ilu_color.cu): factors into lu9 (colour-major slots)
 int launch_color_ilu(System& s, cudaStream_t st);
+// Block solves of columns a0 .. a0 + ncols - 1 from Rt into Z; with ``cs`` (a coupling stencil
+// set laid out as gsn_cs) column a first subtracts the coupling of column a - 1 of Rt.
 template <typename T>
 int launch_color_solve(System& s, int a0, int ncols, int fac_per_col, const T* lu, T* Rt, T* Z,
-                       cudaStream_t st, const int* done);
+                       cudaStream_t st, const int* done, const T* cs = nullptr);
+// The next-column coupling stencils gsn_cs (FP64 systems) or gsn_cs32 (mixed systems, from the
+// BF16-rounded stiffness values when the sweep couples in BF16), from the FP64 k-major stack.
+int launch_color_coupling(System& s, cudaStream_t st);
 int launch_lu9(System& s, cudaStream_t st);
 int launch_cast_f32(const double* src, float* dst, size_t n, cudaStream_t st);
 int launch_cast_bf16(const double* src, __nv_bfloat16* dst, size_t n, cudaStream_t st);
