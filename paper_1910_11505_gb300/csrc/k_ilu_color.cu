@@ -173,16 +173,16 @@ __host__ __device__ constexpr int nb_colour(int C, int dx, int dy) {
 }
 
 // New value of node (x, y) (colour C, position pos) in one phase of the triangular sweeps: lower
-// (w_i minus sum l_ij w_j over the lower colours; first, with ``csa``, minus the coupling
-// sum_j K_{a,a-1}[i, j] z_{a-1}[j] of the previous column) or upper (w_i / u_ii minus the scaled
-// couplings of the higher colours).  Slots in increasing order; which slots a colour uses is fixed
+// (w_i minus sum l_ij w_j over the lower colours; first, with ``corr``, minus the coupling
+// corr[pos] = sum_j K_{a,a-1}[i, j] z_{a-1}[j] of the previous column) or upper (w_i / u_ii minus
+// the scaled couplings of the higher colours).  Slots in increasing order; which slots a colour uses is fixed
 // at compile time.  Neighbour indices are clamped into the mesh: an absent neighbour's slot holds
 // 0, so it subtracts 0 * (a finite value).  CG reads the column at L2 (ld.global.cg: other SMs of
 // the cluster wrote it).
 template <typename T, int C, bool UPPER, bool CG>
 __device__ __forceinline__ T color_node_value(int x, int y, int pos, int m, int N,
                                               const T* __restrict__ cf, const T* w,
-                                              const T* __restrict__ csa, const T* __restrict__ zprev) {
+                                              const T* __restrict__ corr) {
   const int i = x + m * y;
   const int xl = max(x - 1, 0), xr = min(x + 1, m - 1);
   const int yd = max(y - 1, 0) * m, yu = min(y + 1, m - 1) * m, yc = y * m;
@@ -192,11 +192,8 @@ __device__ __forceinline__ T color_node_value(int x, int y, int pos, int m, int 
   T v = CG ? __ldcg(w + i) : w[i];
   if (UPPER) {
     v *= cf[(size_t)4 * N + pos];
-  } else if (csa != nullptr) {
-    T s = T(0);
-#pragma unroll
-    for (int sl = 0; sl < 9; ++sl) s += csa[(size_t)sl * N + pos] * __ldg(zprev + nb(sl % 3 - 1, sl / 3 - 1));
-    v -= s;
+  } else if (corr != nullptr) {
+    v -= corr[pos];
   }
 #pragma unroll
   for (int sl = 0; sl < 9; ++sl) {
@@ -218,16 +215,15 @@ template <typename T, int C, bool UPPER, bool CG>
 __device__ __forceinline__ void color_phase(int beg, int end, int stride, int m, int N, int P,
                                             int a, const int* __restrict__ cstart,
                                             const T* __restrict__ cf, T* w,
-                                            const T* __restrict__ csa, const T* __restrict__ zprev,
-                                            T* __restrict__ Z) {
+                                            const T* __restrict__ corr, T* __restrict__ Z) {
   for (int p0 = beg; p0 < end; p0 += 2 * stride) {
     const int p1 = p0 + stride;
     const bool two = p1 < end;
     int x0, y0, x1, y1;
     colour_xy<C>(p0, m, cstart, x0, y0);
     colour_xy<C>(two ? p1 : p0, m, cstart, x1, y1);
-    const T v0 = color_node_value<T, C, UPPER, CG>(x0, y0, p0, m, N, cf, w, csa, zprev);
-    const T v1 = two ? color_node_value<T, C, UPPER, CG>(x1, y1, p1, m, N, cf, w, csa, zprev) : T(0);
+    const T v0 = color_node_value<T, C, UPPER, CG>(x0, y0, p0, m, N, cf, w, corr);
+    const T v1 = two ? color_node_value<T, C, UPPER, CG>(x1, y1, p1, m, N, cf, w, corr) : T(0);
     const int i0 = x0 + m * y0, i1 = x1 + m * y1;
     w[i0] = v0;
     if (two) w[i1] = v1;
@@ -238,29 +234,69 @@ __device__ __forceinline__ void color_phase(int beg, int end, int stride, int m,
   }
 }
 
+// Coupling of the next column for the positions beg, beg + stride, ... < end of colour C:
+// corr[pos] = sum over slots of K_{a+1,a}[i, j] z_a[j] (slots in increasing order), z_a the
+// completed column w; two nodes at a time as in color_phase.
+template <typename T, int C, bool CG>
+__device__ __forceinline__ void coupling_phase(int beg, int end, int stride, int m, int N,
+                                               const int* __restrict__ cstart,
+                                               const T* __restrict__ csn, const T* w,
+                                               T* __restrict__ corr) {
+  auto value = [&](int p) {
+    int x, y;
+    colour_xy<C>(p, m, cstart, x, y);
+    const int xl = max(x - 1, 0), xr = min(x + 1, m - 1);
+    const int yd = max(y - 1, 0) * m, yu = min(y + 1, m - 1) * m, yc = y * m;
+    T s = T(0);
+#pragma unroll
+    for (int sl = 0; sl < 9; ++sl) {
+      const int dx = sl % 3 - 1, dy = sl / 3 - 1;
+      const int j = (dx < 0 ? xl : dx > 0 ? xr : x) + (dy < 0 ? yd : dy > 0 ? yu : yc);
+      s += csn[(size_t)sl * N + p] * (CG ? __ldcg(w + j) : w[j]);
+    }
+    return s;
+  };
+  for (int p0 = beg; p0 < end; p0 += 2 * stride) {
+    const int p1 = p0 + stride;
+    const bool two = p1 < end;
+    const T s0 = value(p0);
+    const T s1 = two ? value(p1) : T(0);
+    corr[p0] = s0;
+    if (two) corr[p1] = s1;
+  }
+}
+
 // The four lower phases (colours 0..3) then the four upper phases (3..0) of one column, with
-// ``sync`` between phases.
+// ``sync`` between phases; with ``csn``, then the next column's coupling into ``corr`` (no phase
+// of this column reads corr after the last sync).
 template <typename T, bool CG, typename Sync>
 __device__ __forceinline__ void color_sweeps(int off, int stride, int m, int N, int P, int a,
                                              const int* __restrict__ cstart, const T* __restrict__ cf,
-                                             T* w, const T* __restrict__ csa,
-                                             const T* __restrict__ zprev, T* __restrict__ Z, Sync sync) {
-  color_phase<T, 0, false, CG>(cstart[0] + off, cstart[1], stride, m, N, P, a, cstart, cf, w, csa, zprev, nullptr);
+                                             T* w, const T* __restrict__ corr_in,
+                                             const T* __restrict__ csn, T* __restrict__ corr,
+                                             T* __restrict__ Z, Sync sync) {
+  color_phase<T, 0, false, CG>(cstart[0] + off, cstart[1], stride, m, N, P, a, cstart, cf, w, corr_in, nullptr);
   sync();
-  color_phase<T, 1, false, CG>(cstart[1] + off, cstart[2], stride, m, N, P, a, cstart, cf, w, csa, zprev, nullptr);
+  color_phase<T, 1, false, CG>(cstart[1] + off, cstart[2], stride, m, N, P, a, cstart, cf, w, corr_in, nullptr);
   sync();
-  color_phase<T, 2, false, CG>(cstart[2] + off, cstart[3], stride, m, N, P, a, cstart, cf, w, csa, zprev, nullptr);
+  color_phase<T, 2, false, CG>(cstart[2] + off, cstart[3], stride, m, N, P, a, cstart, cf, w, corr_in, nullptr);
   sync();
-  color_phase<T, 3, false, CG>(cstart[3] + off, cstart[4], stride, m, N, P, a, cstart, cf, w, csa, zprev, nullptr);
+  color_phase<T, 3, false, CG>(cstart[3] + off, cstart[4], stride, m, N, P, a, cstart, cf, w, corr_in, nullptr);
   sync();
-  color_phase<T, 3, true, CG>(cstart[3] + off, cstart[4], stride, m, N, P, a, cstart, cf, w, nullptr, nullptr, Z);
+  color_phase<T, 3, true, CG>(cstart[3] + off, cstart[4], stride, m, N, P, a, cstart, cf, w, nullptr, Z);
   sync();
-  color_phase<T, 2, true, CG>(cstart[2] + off, cstart[3], stride, m, N, P, a, cstart, cf, w, nullptr, nullptr, Z);
+  color_phase<T, 2, true, CG>(cstart[2] + off, cstart[3], stride, m, N, P, a, cstart, cf, w, nullptr, Z);
   sync();
-  color_phase<T, 1, true, CG>(cstart[1] + off, cstart[2], stride, m, N, P, a, cstart, cf, w, nullptr, nullptr, Z);
+  color_phase<T, 1, true, CG>(cstart[1] + off, cstart[2], stride, m, N, P, a, cstart, cf, w, nullptr, Z);
   sync();
-  color_phase<T, 0, true, CG>(cstart[0] + off, cstart[1], stride, m, N, P, a, cstart, cf, w, nullptr, nullptr, Z);
+  color_phase<T, 0, true, CG>(cstart[0] + off, cstart[1], stride, m, N, P, a, cstart, cf, w, nullptr, Z);
   sync();
+  if (csn != nullptr) {
+    coupling_phase<T, 0, CG>(cstart[0] + off, cstart[1], stride, m, N, cstart, csn, w, corr);
+    coupling_phase<T, 1, CG>(cstart[1] + off, cstart[2], stride, m, N, cstart, csn, w, corr);
+    coupling_phase<T, 2, CG>(cstart[2] + off, cstart[3], stride, m, N, cstart, csn, w, corr);
+    coupling_phase<T, 3, CG>(cstart[3] + off, cstart[4], stride, m, N, cstart, csn, w, corr);
+  }
 }
 
 // All eight phases of one column in one CTA, the column in shared memory (meshes whose column
@@ -274,7 +310,7 @@ __global__ void __launch_bounds__(1024) color_cta_kernel(int m, int N, int ldN, 
                                                         const T* __restrict__ cfs,
                                                         T* __restrict__ Rt, T* __restrict__ Z,
                                                         const int* __restrict__ done,
-                                                        const T* __restrict__ cs) {
+                                                        const T* __restrict__ cs, T* __restrict__ corr) {
   if (done != nullptr && *done) return;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T* w = reinterpret_cast<T*>(smem_raw);
@@ -282,16 +318,16 @@ __global__ void __launch_bounds__(1024) color_cta_kernel(int m, int N, int ldN, 
   const int a = a0 + blockIdx.x;
   const T* cf = cfs + (size_t)(fac_per_col ? a : 0) * 9 * N;
   T* rhs = Rt + (size_t)a * ldN;
-  const T* csa = (cs != nullptr && a > 0) ? cs + (size_t)(a - 1) * 9 * N : nullptr;
-  const T* zprev = Rt + (size_t)(a > 0 ? a - 1 : 0) * ldN;
+  const T* corr_in = (cs != nullptr && a > 0) ? corr : nullptr;
+  const T* csn = (cs != nullptr && a + 1 < P) ? cs + (size_t)a * 9 * N : nullptr;
   if (gridDim.x == 1) {
     l2_prefetch(cf, sizeof(T) * 9 * (size_t)N, 0, 1);
-    if (csa != nullptr) l2_prefetch(csa, sizeof(T) * 9 * (size_t)N, 0, 1);
+    if (csn != nullptr) l2_prefetch(csn, sizeof(T) * 9 * (size_t)N, 0, 1);
   }
   if (threadIdx.x < 5) cstart[threadIdx.x] = cstart_g[threadIdx.x];
   for (int i = threadIdx.x; i < N; i += blockDim.x) w[i] = rhs[i];
   __syncthreads();
-  color_sweeps<T, false>(threadIdx.x, blockDim.x, m, N, P, a, cstart, cf, w, csa, zprev,
+  color_sweeps<T, false>(threadIdx.x, blockDim.x, m, N, P, a, cstart, cf, w, corr_in, csn, corr,
                          (T*)nullptr, []() { __syncthreads(); });
   for (int i = threadIdx.x; i < N; i += blockDim.x) {
     if (Z != nullptr) Z[(size_t)i * P + a] = w[i];
@@ -304,39 +340,67 @@ __global__ void __launch_bounds__(1024) color_cta_kernel(int m, int N, int ldN, 
 // cluster barrier (release / acquire at cluster scope) separates the phases.  Neighbour values
 // are read at L2 (ld.global.cg) so no SM reads a stale L1 line written by another.  Each CTA of a
 // single-column launch first prefetches its share of the column's factors (and coupling stencil)
-// into L2.  The coupling of column a - 1 is subtracted from each node's right-hand side in the
-// lower phase of its colour, before the node's own update: its lower-colour neighbours are final
-// by then.
+// into L2.  The coupling of column a - 1, left in ``corr`` by the previous solve, is subtracted
+// from each node's right-hand side in the lower phase of its colour, before the node's own
+// update; after the last phase the cluster computes the coupling of column a + 1 into ``corr``.
 template <typename T, int CL>
 __global__ void __launch_bounds__(1024) color_cluster_kernel(
     int m, int N, int ldN, int P, int a0, int fac_per_col, const int* __restrict__ cstart_g,
     const T* __restrict__ cfs, T* __restrict__ Rt, T* __restrict__ Z, const int* __restrict__ done,
-    const T* __restrict__ cs) {
+    const T* __restrict__ cs, T* __restrict__ corr) {
   if (done != nullptr && *done) return;  // uniform over the cluster: no barrier is skipped by some
   __shared__ int cstart[5];
   const int a = a0 + blockIdx.x / CL;
   const int rank = blockIdx.x % CL;
   const T* cf = cfs + (size_t)(fac_per_col ? a : 0) * 9 * N;
   T* w = Rt + (size_t)a * ldN;
-  const T* csa = (cs != nullptr && a > 0) ? cs + (size_t)(a - 1) * 9 * N : nullptr;
-  const T* zprev = Rt + (size_t)(a > 0 ? a - 1 : 0) * ldN;
+  const T* corr_in = (cs != nullptr && a > 0) ? corr : nullptr;
+  const T* csn = (cs != nullptr && a + 1 < P) ? cs + (size_t)a * 9 * N : nullptr;
   if (gridDim.x == CL) {
     l2_prefetch(cf, sizeof(T) * 9 * (size_t)N, rank, CL);
-    if (csa != nullptr) l2_prefetch(csa, sizeof(T) * 9 * (size_t)N, rank, CL);
+    if (csn != nullptr) l2_prefetch(csn, sizeof(T) * 9 * (size_t)N, rank, CL);
   }
   if (threadIdx.x < 5) cstart[threadIdx.x] = cstart_g[threadIdx.x];
   __syncthreads();
   const int stride = CL * blockDim.x;
   const int off = rank * blockDim.x + threadIdx.x;
-  color_sweeps<T, true>(off, stride, m, N, P, a, cstart, cf, w, csa, zprev, Z, []() {
+  color_sweeps<T, true>(off, stride, m, N, P, a, cstart, cf, w, corr_in, csn, corr, Z, []() {
     asm volatile("barrier.cluster.arrive.release.aligned;\n"
                  "barrier.cluster.wait.acquire.aligned;\n" ::: "memory");
   });
 }
 
+// Whether clusters of 16 CTAs of 1024 threads (a non-portable size) can be scheduled on this
+// device: asked once per process and kernel; on any failure the answer is no.
+template <typename T>
+bool cluster16_ok() {
+  static int ok = -1;
+  if (ok < 0) {
+    ok = 0;
+    auto kern = color_cluster_kernel<T, 16>;
+    if (cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) == cudaSuccess) {
+      cudaLaunchConfig_t cfg = {};
+      cfg.gridDim = dim3(16, 1, 1);
+      cfg.blockDim = dim3(1024, 1, 1);
+      cudaLaunchAttribute attr[1];
+      attr[0].id = cudaLaunchAttributeClusterDimension;
+      attr[0].val.clusterDim.x = 16;
+      attr[0].val.clusterDim.y = 1;
+      attr[0].val.clusterDim.z = 1;
+      cfg.attrs = attr;
+      cfg.numAttrs = 1;
+      int nclusters = 0;
+      if (cudaOccupancyMaxActiveClusters(&nclusters, kern, &cfg) == cudaSuccess && nclusters >= 2)
+        ok = 1;
+    }
+    cudaGetLastError();
+  }
+  return ok == 1;
+}
+
 template <typename T, int CL>
 int launch_cluster(System& s, int a0, int ncols, int fac_per_col, const T* lu, T* Rt, T* Z,
-                   cudaStream_t st, const int* done, const T* cs) {
+                   cudaStream_t st, const int* done, const T* cs, T* corr) {
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3((unsigned)(ncols * CL), 1, 1);
   cfg.blockDim = dim3(1024, 1, 1);
@@ -353,7 +417,7 @@ int launch_cluster(System& s, int a0, int ncols, int fac_per_col, const T* lu, T
   cfg.numAttrs = 2;
   TimeScope ts(s.timer, K_ILU_SOLVE, st);
   SG_CUDA(cudaLaunchKernelEx(&cfg, color_cluster_kernel<T, CL>, s.pat.m, s.N, s.ldN, s.P, a0,
-                             fac_per_col, (const int*)s.cstart.p, lu, Rt, Z, done, cs));
+                             fac_per_col, (const int*)s.cstart.p, lu, Rt, Z, done, cs, corr));
   return check_launch("color_cluster");
 }
 
@@ -389,18 +453,23 @@ int launch_color_ilu(System& s, cudaStream_t st) {
 // Block solves of columns a0 .. a0 + ncols - 1 from Rt into Z (colour-ordered factors).
 template <typename T>
 int launch_color_solve(System& s, int a0, int ncols, int fac_per_col, const T* lu, T* Rt, T* Z,
-                       cudaStream_t st, const int* done, const T* cs) {
+                       cudaStream_t st, const int* done, const T* cs, T* corr) {
+  if (cs != nullptr && (ncols != 1 || corr == nullptr))
+    return fail(SG_ERR_ARG, "four-colour solve: the coupled form takes one column and a buffer");
   const int m = s.pat.m;
   const size_t smem = sizeof(T) * (size_t)s.ldN;
-  // a cluster of CTAs once one CTA would hold more than ~1024 nodes per colour; one CTA with the
-  // column in shared memory below that
+  // a cluster of CTAs once one CTA would hold more than ~2048 nodes per colour (two per thread);
+  // one CTA with the column in shared memory below that.  A single-column solve with more than
+  // 16384 nodes per colour takes a cluster of 16 where the device schedules one.
   const int per_colour = (s.N + 3) / 4;
   if (per_colour > 2048) {
+    if (per_colour > 8 * 2048 && ncols == 1 && cluster16_ok<T>())
+      return launch_cluster<T, 16>(s, a0, ncols, fac_per_col, lu, Rt, Z, st, done, cs, corr);
     if (per_colour > 4 * 2048)
-      return launch_cluster<T, 8>(s, a0, ncols, fac_per_col, lu, Rt, Z, st, done, cs);
+      return launch_cluster<T, 8>(s, a0, ncols, fac_per_col, lu, Rt, Z, st, done, cs, corr);
     if (per_colour > 2 * 2048)
-      return launch_cluster<T, 4>(s, a0, ncols, fac_per_col, lu, Rt, Z, st, done, cs);
-    return launch_cluster<T, 2>(s, a0, ncols, fac_per_col, lu, Rt, Z, st, done, cs);
+      return launch_cluster<T, 4>(s, a0, ncols, fac_per_col, lu, Rt, Z, st, done, cs, corr);
+    return launch_cluster<T, 2>(s, a0, ncols, fac_per_col, lu, Rt, Z, st, done, cs, corr);
   }
   {
     auto kern = color_cta_kernel<T>;
@@ -417,16 +486,16 @@ int launch_color_solve(System& s, int a0, int ncols, int fac_per_col, const T* l
     cfg.attrs = attr;
     cfg.numAttrs = 1;
     SG_CUDA(cudaLaunchKernelEx(&cfg, kern, m, s.N, s.ldN, s.P, a0, fac_per_col,
-                               (const int*)s.cstart.p, lu, Rt, Z, done, cs));
+                               (const int*)s.cstart.p, lu, Rt, Z, done, cs, corr));
     return check_launch("color_cta");
   }
   return fail(SG_ERR_ARG, "four-colour block solve: column larger than shared memory");
 }
 
 template int launch_color_solve<double>(System&, int, int, int, const double*, double*, double*,
-                                        cudaStream_t, const int*, const double*);
+                                        cudaStream_t, const int*, const double*, double*);
 template int launch_color_solve<float>(System&, int, int, int, const float*, float*, float*,
-                                       cudaStream_t, const int*, const float*);
+                                       cudaStream_t, const int*, const float*, float*);
 
 int launch_color_coupling(System& s, cudaStream_t st) {
   if (s.P < 2) return SG_OK;
@@ -437,11 +506,13 @@ int launch_color_coupling(System& s, cudaStream_t st) {
   const bool lowp = s.prm.precision != SG_FP64;
   const int round_bf16 = lowp && (s.prm.precision == SG_MIXED_BF16 || s.prm.coupling_bf16) ? 1 : 0;
   if (lowp) {
+    SG_TRY(s.gsn_corr32.alloc((size_t)s.N));
     SG_TRY(s.gsn_cs32.alloc(n));
     color_coupling_kernel<float><<<grid, 256, 0, st>>>(
         s.pat.m, s.N, s.pat.nnz, s.P, round_bf16, s.rowptr.p, s.col.p, s.cstart.p, s.stack_km.p,
         s.gsn_kptr.p, s.gsn_k.p, s.gsn_eptr.p, s.gsn_ea.p, s.gsn_eg.p, s.gsn_cs32.p);
   } else {
+    SG_TRY(s.gsn_corr.alloc((size_t)s.N));
     SG_TRY(s.gsn_cs.alloc(n));
     color_coupling_kernel<double><<<grid, 256, 0, st>>>(
         s.pat.m, s.N, s.pat.nnz, s.P, 0, s.rowptr.p, s.col.p, s.cstart.p, s.stack_km.p,

@@ -687,6 +687,7 @@ struct PcBufs<double> {
   static bool full(const System& s) { return s.tri_full; }
   static const double* eg(const System& s) { return s.gs_eg.p; }
   static const double* cs(const System& s) { return s.gsn_cs.p; }
+  static double* corr(System& s) { return s.gsn_corr.p; }
 };
 template <>
 struct PcBufs<float> {
@@ -699,6 +700,7 @@ struct PcBufs<float> {
   static bool full(const System& s) { return s.tri_full32; }
   static const float* eg(const System& s) { return s.gs_eg_f32.p; }
   static const float* cs(const System& s) { return s.gsn_cs32.p; }
+  static float* corr(System& s) { return s.gsn_corr32.p; }
 };
 
 template <typename T>
@@ -821,9 +823,10 @@ int launch_scatter<float>(System& s, int b, bool next, const float* Z, float* Rt
 // block a + 1.  Ordering: that scatter waits for z_a; the next-column scatter of block a waits for
 // the later-column scatter of block a - 1, which also subtracts into column a + 1; the sweep ends
 // by joining the second stream.  In the four-colour ordering the next-column coupling is part of
-// the block solve (its stencil K_{a+1,a} assembled at setup): the solve of block a + 1 subtracts
-// K_{a+1,a} z_a itself and waits for the later-column scatter of block a - 1 instead; the solves
-// leave z_a in column a of Rt, and one transpose at the end writes D.
+// the block solves (its stencil K_{a+1,a} assembled at setup): the solve of block a leaves
+// K_{a+1,a} z_a in a buffer that the solve of block a + 1 subtracts, and the solve of block a + 1
+// waits for the later-column scatter of block a - 1 instead; the solves leave z_a in column a of
+// Rt, and one transpose at the end writes D.
 template <typename T>
 int fs_gs_sweep(System& s, const T* R, T* D, T* Rt, cudaStream_t st, const int* done, bool fork) {
   SG_TRY(launch_columns<T>(s, R, Rt, st, done));
@@ -832,7 +835,8 @@ int fs_gs_sweep(System& s, const T* R, T* D, T* Rt, cudaStream_t st, const int* 
   if (s.prm.ilu_order == SG_ILU_COLOR4 && cs != nullptr) {
     for (int a = 0; a < s.P; ++a) {
       if (fork && a >= 2) SG_CUDA(cudaStreamWaitEvent(st, s.ev_r[(a - 2) & 1], 0));
-      SG_TRY(launch_color_solve<T>(s, a, 1, 1, PcBufs<T>::lu9(s), Rt, (T*)nullptr, st, done, cs));
+      SG_TRY(launch_color_solve<T>(s, a, 1, 1, PcBufs<T>::lu9(s), Rt, (T*)nullptr, st, done, cs,
+                                   PcBufs<T>::corr(s)));
       if (a + 2 < s.P) {
         if (fork) {
           SG_CUDA(cudaEventRecord(s.ev_z, st));

@@ -259,6 +259,10 @@ struct System {
   // block solve of column a subtracts K_{a,a-1} z_{a-1} from its right-hand side itself
   DBuf<double> gsn_cs;
   DBuf<float> gsn_cs32;
+  // the coupling term K_{a,a-1} z_{a-1} per colour-major position, left by the solve of column
+  // a - 1 for the solve of column a
+  DBuf<double> gsn_corr;
+  DBuf<float> gsn_corr32;
   int gs_max_klen = 0;
   // device scratch
   DBuf<double> rhs_t;          // P columns of stride ldN: right-hand sides of the block solves
@@ -325,11 +329,13 @@ int launch_block_values(System& s, cudaStream_t st);
 int launch_ilu0(System& s, cudaStream_t st);
 // ILU(0) in the four-colour ordering (k_ilu_color.cu): factors into lu9 (colour-major slots)
 int launch_color_ilu(System& s, cudaStream_t st);
-// Block solves of columns a0 .. a0 + ncols - 1 from Rt into Z; with ``cs`` (a coupling stencil
-// set laid out as gsn_cs) column a first subtracts the coupling of column a - 1 of Rt.
+// Block solves of columns a0 .. a0 + ncols - 1 from Rt into Z (Z may be null: the solutions stay
+// in the columns of Rt).  With ``cs`` (a coupling stencil set laid out as gsn_cs; one column):
+// the solve of column a first subtracts the coupling of column a - 1 left in ``corr`` (a > 0),
+// and leaves the coupling of column a + 1 in ``corr`` (a + 1 < P).
 template <typename T>
 int launch_color_solve(System& s, int a0, int ncols, int fac_per_col, const T* lu, T* Rt, T* Z,
-                       cudaStream_t st, const int* done, const T* cs = nullptr);
+                       cudaStream_t st, const int* done, const T* cs = nullptr, T* corr = nullptr);
 // The next-column coupling stencils gsn_cs (FP64 systems) or gsn_cs32 (mixed systems, from the
 // BF16-rounded stiffness values when the sweep couples in BF16), from the FP64 k-major stack.
 int launch_color_coupling(System& s, cudaStream_t st);

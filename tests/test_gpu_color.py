@@ -47,6 +47,7 @@ def test_color4_factors_match_oracle():
     (dict(n=6, M=3, p=2, sigma=0.5, ell=1.0, a_min=0.01), "mean"),
     (dict(n=6, M=3, p=2, sigma=0.5, ell=1.0, a_min=0.01), "fs_gs"),
     (dict(n=7, M=2, p=2, sigma=0.8, ell=0.6), "fs_jacobi"),
+    (dict(n=256, M=2, p=2, sigma=0.8, ell=0.5), "fs_gs"),      # cluster of 16 (where offered)
     (dict(n=200, M=2, p=1, sigma=0.8, ell=0.5), "fs_gs"),      # cluster of 8 CTAs per column
     (dict(n=200, M=2, p=1, sigma=0.8, ell=0.5), "mean"),
     (dict(n=128, M=2, p=1, sigma=0.6, ell=0.5), "fs_gs"),      # cluster of 4
@@ -70,7 +71,7 @@ def test_color4_preconditioners_match_oracle(d, pc):
 
 
 def test_color4_fp32_large_mesh():
-    d = dict(n=256, M=2, p=1, sigma=0.8, ell=0.5)              # cluster of 8, FP32
+    d = dict(n=256, M=2, p=1, sigma=0.8, ell=0.5)              # cluster of 16 or 8, FP32
     h = sg.sg_setup(sg.sg_default_params(**d, precond="fs_gs", ilu_order="color4",
                                          precision="fp32"))
     N, P, _ = sg.sg_dims(h)
