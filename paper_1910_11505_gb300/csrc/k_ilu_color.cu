@@ -32,6 +32,17 @@ __device__ __forceinline__ int colour_node(int c, int p, int m, const int* __res
   return x + m * y;
 }
 
+// Elements of padding after the slot arrays (lu9, gsn_cs): a bulk copy of the last column's
+// array may run up to 16 bytes past its end.
+constexpr size_t kColorPad = 8;
+constexpr size_t kColorSmemMax = 200 * 1024;  // shared memory the one-CTA solve may take
+
+// Shared-memory bytes that hold one 9-slot array of n nodes copied from any 16-byte-aligned
+// start at or below it: the array plus up to 16 bytes either side, a multiple of 16.
+__host__ __device__ constexpr size_t kColorSlotBuf(long long n, size_t elem) {
+  return ((size_t)(9 * n) * elem + 32 + 15) & ~(size_t)15;
+}
+
 // One colour of the IKJ factorisation for every factor set: row i (colour c) takes, in increasing
 // colour-major position, each neighbour k of a lower colour: l_ik = a_ik / u_kk, then
 // a_ij -= l_ik u_kj for every j after k in that order present in both rows.  Rows of lower
@@ -310,7 +321,8 @@ __global__ void __launch_bounds__(1024) color_cta_kernel(int m, int N, int ldN, 
                                                         const T* __restrict__ cfs,
                                                         T* __restrict__ Rt, T* __restrict__ Z,
                                                         const int* __restrict__ done,
-                                                        const T* __restrict__ cs, T* __restrict__ corr) {
+                                                        const T* __restrict__ cs, T* __restrict__ corr,
+                                                        int stage) {
   if (done != nullptr && *done) return;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T* w = reinterpret_cast<T*>(smem_raw);
@@ -320,19 +332,60 @@ __global__ void __launch_bounds__(1024) color_cta_kernel(int m, int N, int ldN, 
   T* rhs = Rt + (size_t)a * ldN;
   const T* corr_in = (cs != nullptr && a > 0) ? corr : nullptr;
   const T* csn = (cs != nullptr && a + 1 < P) ? cs + (size_t)a * 9 * N : nullptr;
-  if (gridDim.x == 1) {
+  // stage >= 1: the factors (stage 2: also the coupling stencil) are copied into shared memory
+  // after the column by one bulk copy each, issued before the column load so the two overlap; a
+  // copy takes the 16-byte-aligned range around its array (the arrays are padded for that) and
+  // the phases index from the offset.  Should the bounded wait give up, the phases read the
+  // arrays in global memory instead (same values).
+  __shared__ unsigned long long bar;
+  unsigned char* buf = smem_raw + sizeof(T) * (size_t)ldN;
+  const T* cf_s = nullptr;
+  const T* cs_s = nullptr;
+  if (stage >= 1) {
+    if (threadIdx.x == 0) {
+      mbar_init(&bar, 1);
+      asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+      asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+      const unsigned long long slot_bytes = sizeof(T) * 9ull * (unsigned long long)N;
+      auto span = [&](const T* p, unsigned long long& lo) {
+        const unsigned long long b0 = reinterpret_cast<unsigned long long>(p);
+        lo = b0 & ~15ull;
+        return (unsigned)(((b0 + slot_bytes + 15ull) & ~15ull) - lo);
+      };
+      unsigned long long lo_cf = 0, lo_cs = 0;
+      const unsigned n_cf = span(cf, lo_cf);
+      const unsigned n_cs = (stage >= 2 && csn != nullptr) ? span(csn, lo_cs) : 0u;
+      mbar_expect_tx(&bar, n_cf + n_cs);
+      bulk_g2s(buf, reinterpret_cast<const void*>(lo_cf), n_cf, &bar);
+      if (n_cs) bulk_g2s(buf + kColorSlotBuf(N, sizeof(T)), reinterpret_cast<const void*>(lo_cs), n_cs, &bar);
+    }
+  } else if (gridDim.x == 1) {
     l2_prefetch(cf, sizeof(T) * 9 * (size_t)N, 0, 1);
     if (csn != nullptr) l2_prefetch(csn, sizeof(T) * 9 * (size_t)N, 0, 1);
   }
   if (threadIdx.x < 5) cstart[threadIdx.x] = cstart_g[threadIdx.x];
   for (int i = threadIdx.x; i < N; i += blockDim.x) w[i] = rhs[i];
   __syncthreads();
+  bool staged = false;
+  if (stage >= 1) {
+    staged = mbar_wait_bounded(&bar, 0);
+    if (staged) {
+      cf_s = reinterpret_cast<const T*>(buf + (reinterpret_cast<unsigned long long>(cf) & 15ull));
+      cf = cf_s;
+      if (stage >= 2 && csn != nullptr) {
+        cs_s = reinterpret_cast<const T*>(buf + kColorSlotBuf(N, sizeof(T)) +
+                                          (reinterpret_cast<unsigned long long>(csn) & 15ull));
+        csn = cs_s;
+      }
+    }
+  }
   color_sweeps<T, false>(threadIdx.x, blockDim.x, m, N, P, a, cstart, cf, w, corr_in, csn, corr,
                          (T*)nullptr, []() { __syncthreads(); });
   for (int i = threadIdx.x; i < N; i += blockDim.x) {
     if (Z != nullptr) Z[(size_t)i * P + a] = w[i];
     rhs[i] = w[i];
   }
+  if (stage >= 1 && !staged) mbar_wait_bounded(&bar, 0);  // no copy may land after the exit
 }
 
 // All eight phases of one column on a thread-block cluster of CL CTAs (grid = columns x CL): the
@@ -369,6 +422,8 @@ __global__ void __launch_bounds__(1024) color_cluster_kernel(
                  "barrier.cluster.wait.acquire.aligned;\n" ::: "memory");
   });
 }
+
+
 
 // Whether clusters of 16 CTAs of 1024 threads (a non-portable size) can be scheduled on this
 // device: asked once per process and kernel; on any failure the answer is no.
@@ -442,7 +497,7 @@ int launch_color_ilu(System& s, cudaStream_t st) {
                                             s.cstart.p, s.fac.p);
     SG_TRY(check_launch("color_ilu0"));
   }
-  SG_TRY(s.lu9.alloc((size_t)s.nfac * 9 * s.N));
+  SG_TRY(s.lu9.alloc((size_t)s.nfac * 9 * s.N + kColorPad));
   const long long total = (long long)s.N * s.nfac;
   const int grid = (int)std::max(1LL, std::min((total + 255) / 256, 152LL * 32));
   color_slots_kernel<<<grid, 256, 0, st>>>(m, s.N, s.pat.nnz, s.nfac, s.rowptr.p, s.col.p,
@@ -457,7 +512,6 @@ int launch_color_solve(System& s, int a0, int ncols, int fac_per_col, const T* l
   if (cs != nullptr && (ncols != 1 || corr == nullptr))
     return fail(SG_ERR_ARG, "four-colour solve: the coupled form takes one column and a buffer");
   const int m = s.pat.m;
-  const size_t smem = sizeof(T) * (size_t)s.ldN;
   // a cluster of CTAs once one CTA would hold more than ~2048 nodes per colour (two per thread);
   // one CTA with the column in shared memory below that.  A single-column solve with more than
   // 16384 nodes per colour takes a cluster of 16 where the device schedules one.
@@ -472,6 +526,18 @@ int launch_color_solve(System& s, int a0, int ncols, int fac_per_col, const T* l
     return launch_cluster<T, 2>(s, a0, ncols, fac_per_col, lu, Rt, Z, st, done, cs, corr);
   }
   {
+    // shared memory: the column, then the factors and the coupling stencil where they fit
+    int stage = 0;
+    size_t smem = sizeof(T) * (size_t)s.ldN;
+    const size_t slots = kColorSlotBuf(s.N, sizeof(T));
+    if (smem + slots <= kColorSmemMax) {
+      stage = 1;
+      smem += slots;
+      if (cs != nullptr && smem + slots <= kColorSmemMax) {
+        stage = 2;
+        smem += slots;
+      }
+    }
     auto kern = color_cta_kernel<T>;
     SG_TRY(ensure_smem((const void*)kern, smem));
     TimeScope ts(s.timer, K_ILU_SOLVE, st);
@@ -486,7 +552,7 @@ int launch_color_solve(System& s, int a0, int ncols, int fac_per_col, const T* l
     cfg.attrs = attr;
     cfg.numAttrs = 1;
     SG_CUDA(cudaLaunchKernelEx(&cfg, kern, m, s.N, s.ldN, s.P, a0, fac_per_col,
-                               (const int*)s.cstart.p, lu, Rt, Z, done, cs, corr));
+                               (const int*)s.cstart.p, lu, Rt, Z, done, cs, corr, stage));
     return check_launch("color_cta");
   }
   return fail(SG_ERR_ARG, "four-colour block solve: column larger than shared memory");
@@ -507,13 +573,13 @@ int launch_color_coupling(System& s, cudaStream_t st) {
   const int round_bf16 = lowp && (s.prm.precision == SG_MIXED_BF16 || s.prm.coupling_bf16) ? 1 : 0;
   if (lowp) {
     SG_TRY(s.gsn_corr32.alloc((size_t)s.N));
-    SG_TRY(s.gsn_cs32.alloc(n));
+    SG_TRY(s.gsn_cs32.alloc(n + kColorPad));
     color_coupling_kernel<float><<<grid, 256, 0, st>>>(
         s.pat.m, s.N, s.pat.nnz, s.P, round_bf16, s.rowptr.p, s.col.p, s.cstart.p, s.stack_km.p,
         s.gsn_kptr.p, s.gsn_k.p, s.gsn_eptr.p, s.gsn_ea.p, s.gsn_eg.p, s.gsn_cs32.p);
   } else {
     SG_TRY(s.gsn_corr.alloc((size_t)s.N));
-    SG_TRY(s.gsn_cs.alloc(n));
+    SG_TRY(s.gsn_cs.alloc(n + kColorPad));
     color_coupling_kernel<double><<<grid, 256, 0, st>>>(
         s.pat.m, s.N, s.pat.nnz, s.P, 0, s.rowptr.p, s.col.p, s.cstart.p, s.stack_km.p,
         s.gsn_kptr.p, s.gsn_k.p, s.gsn_eptr.p, s.gsn_ea.p, s.gsn_eg.p, s.gsn_cs.p);

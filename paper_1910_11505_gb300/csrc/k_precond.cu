@@ -554,6 +554,7 @@ constexpr int kScatterWarps = 8;
 template <typename TV>
 __host__ __device__ constexpr int scatter_ku() { return sizeof(TV) >= 8 ? 2 : 4; }
 constexpr int kScatterTW = 12;     // target columns of one warp whose Rt values are prefetched
+constexpr int kScatterDirectTiles = 256;  // meshes with fewer 32-row tiles scatter per entry
 
 // After block b of the Gauss-Seidel sweep, for the target columns a_lo <= a <= a_hi (all > b):
 // Rt[a, i] -= sum_k G_k[a,b] (A_k z_b)[i] for every row i.  kptr / klist / eptr / ek / eg are the
@@ -628,6 +629,50 @@ __global__ void __launch_bounds__(kScatterWarps * 32, 3) fs_scatter_kernel(
       }
     }
     __syncthreads();
+  }
+}
+
+// The same update for small meshes, one warp per (32-row tile, target column) with the rows on
+// the lanes: the warp forms sum_q G_q[a,b] (A_{k_q} z_b)[i] over the target's entries directly
+// (the product A_k z_b once per entry rather than once per k: the entries of a source block name
+// each k about once), so the many short work items spread over the whole GPU and no item waits
+// on a long chain of dependent loads.  Same arithmetic, in the same order, as fs_scatter_kernel.
+template <typename T, typename TV>
+__global__ void __launch_bounds__(256) fs_scatter_direct_kernel(
+    int N, int P, int ldN, int nnz, int b, int a_lo, int a_hi, const int* __restrict__ rowptr,
+    const int* __restrict__ col, const TV* __restrict__ stack_km, const int* __restrict__ kptr,
+    const int* __restrict__ klist, const int* __restrict__ eptr, const int* __restrict__ ek,
+    const T* __restrict__ eg, const T* __restrict__ zc, int zs, T* __restrict__ Rt,
+    const int* __restrict__ done) {
+  if (done != nullptr && *done) return;
+  const int lane = threadIdx.x & 31;
+  const int gw = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+  const int nw = (int)((gridDim.x * blockDim.x) >> 5);
+  const int ntiles = (N + 31) / 32, na = a_hi - a_lo + 1;
+  const int k0 = kptr[b];
+  const int* ep = eptr + (size_t)b * (P + 1);
+  for (int item = gw; item < ntiles * na; item += nw) {
+    const int tile = item / na, a = a_lo + item % na;
+    const int q0 = ep[a], q1 = ep[a + 1];
+    if (q0 == q1) continue;
+    const int i = tile * 32 + lane;
+    const bool live = i < N;
+    const T r = live ? Rt[(size_t)a * ldN + i] : T(0);
+    const int e0 = live ? rowptr[i] : 0;
+    const int ne = live ? rowptr[i + 1] - e0 : 0;
+    T z[9];
+#pragma unroll
+    for (int e = 0; e < 9; ++e) z[e] = e < ne ? zc[(size_t)col[e0 + e] * zs] : T(0);
+    T s = T(0);
+    for (int q = q0; q < q1; ++q) {
+      const TV* ak = stack_km + (size_t)klist[k0 + ek[q]] * nnz + e0;
+      T t = T(0);
+#pragma unroll
+      for (int e = 0; e < 9; ++e)
+        if (e < ne) t += (T)ak[e] * z[e];
+      s += eg[q] * t;
+    }
+    if (live) Rt[(size_t)a * ldN + i] = r - s;
   }
 }
 
@@ -771,13 +816,16 @@ int launch_scatter_t(System& s, int b, bool next, const TV* stack_km, const T* e
         s.N, s.P, s.ldN, s.pat.nnz, b, s.rowptr.p, s.col.p, stack_km, s.gsn_kptr.p, s.gsn_k.p,
         s.gsn_eptr.p, s.gsn_ea.p, eg_next, zc, zs, Rt, done);
   } else {
-    const size_t smem = sizeof(T) * kScatterRows * std::max(1, s.gs_max_klen);
-    auto kern = fs_scatter_kernel<T, TV>;
-    SG_TRY(ensure_smem((const void*)kern, smem));
-    // one CTA per 32-row tile at the lowest launch priority: SMs that its CTAs free go to a
-    // pending block solve first
+    // at the lowest launch priority: SMs that its CTAs free go to a pending block solve first
+    const int ntiles = (s.N + kScatterRows - 1) / kScatterRows;
+    const bool direct = ntiles < kScatterDirectTiles;
+    const size_t smem = direct ? 0 : sizeof(T) * kScatterRows * std::max(1, s.gs_max_klen);
+    auto kern = direct ? fs_scatter_direct_kernel<T, TV> : fs_scatter_kernel<T, TV>;
+    if (!direct) SG_TRY(ensure_smem((const void*)kern, smem));
+    const long long items = (long long)ntiles * std::max(1, s.P - 1 - (b + 2) + 1);
     cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3((unsigned)std::max(1, (s.N + kScatterRows - 1) / kScatterRows), 1, 1);
+    // the tiled kernel: one CTA per 32-row tile; the direct one: one warp per (tile, target)
+    cfg.gridDim = dim3((unsigned)(direct ? std::max(1LL, (items + 7) / 8) : std::max(1, ntiles)), 1, 1);
     cfg.blockDim = dim3(kScatterWarps * 32, 1, 1);
     cfg.dynamicSmemBytes = smem;
     cfg.stream = st;
