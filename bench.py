@@ -46,8 +46,9 @@ TRAFFIC_FILE = os.path.join(ROOT, "profiles", "traffic.json")
 
 
 def measured_traffic(kernel):
-    """DRAM bytes per launch of ``kernel`` from the committed ncu summary, or None when the
-    kernel's source has changed since the counters were taken."""
+    """Measured DRAM bytes per algorithmic byte of kernel class ``kernel`` from the committed ncu
+    capture (profiles/traffic.json), or None when a source file of the kernel has changed since
+    the counters were taken."""
     import hashlib
     try:
         with open(TRAFFIC_FILE) as f:
@@ -56,7 +57,7 @@ def measured_traffic(kernel):
         for src in rec["sources"]:
             with open(os.path.join(ROOT, src), "rb") as f:
                 h.update(f.read())
-        return rec["bytes_per_launch"] if h.hexdigest() == rec["sha256"] else None
+        return rec["dram_per_algorithmic_byte"] if h.hexdigest() == rec["sha256"] else None
     except Exception:
         return None
 
@@ -300,6 +301,47 @@ def algorithmic_bytes_apply(nnzA, N, P, L, s):
     return nnzA * L * s + 4 * nnzA + 4 * (N + 1) + 2 * N * P * s
 
 
+def smoothing_levels(n=256, coarse=2):
+    """(N, nnz_A) of each smoothing level of the V-cycle: meshes n, n/2, ... above the coarsest."""
+    out = []
+    while n > coarse:
+        m = n + 1
+        out.append((m * m, (3 * m - 2) ** 2))
+        n //= 2
+    return out
+
+
+def coupling_blocks(trip, P):
+    """Per source block b of the later-column scatter (targets a >= b + 2): the number of distinct
+    stiffness matrices k it reads and of target columns it updates."""
+    ks = [set() for _ in range(P)]
+    ts = [set() for _ in range(P)]
+    for k, a, b, _ in trip:
+        k, a, b = int(k), int(a), int(b)
+        if a >= b + 2:
+            ks[b].add(k)
+            ts[b].add(a)
+    return [(len(ks[b]), len(ts[b])) for b in range(P - 2)]
+
+
+def later_scatter_bytes(levels, blocks, s, sv):
+    """Algorithmic bytes of one later-column scatter launch, averaged over blocks and levels: the
+    k-major stiffness values of the block's k list (sv bytes each), the read and write of every
+    target column it updates and the read of z_b (s bytes each)."""
+    tot = sum(kl * nnz * sv + 2 * s * N * nt + s * N for N, nnz in levels for kl, nt in blocks)
+    return tot / (len(levels) * len(blocks))
+
+
+def colour_solve_bytes(levels, P, s):
+    """Algorithmic bytes of one coupled four-colour block solve, averaged over columns and levels:
+    the 9 factor slots, the next column's 9 coupling slots (all but the last column), the column's
+    read and write, the coupling term's read (all but the first) and write (all but the last)."""
+    tot = 0.0
+    for N, _ in levels:
+        tot += s * N * (P * (9 + 2) + (P - 1) * (9 + 1 + 1))
+    return tot / (len(levels) * P)
+
+
 def time_matvec(sg, torch, h, X, Y, fn, stream, reps=20):
     for _ in range(3):
         fn(h, 0, X, Y, stream)
@@ -374,10 +416,12 @@ def main():
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(stream)
     infos = []
+    torch.cuda.nvtx.range_push("timed")  # lets a profiler select the timed region
     for _ in range(args.steps):
         rc, info = step()
         assert rc == sg.SG_OK, info
         infos.append(info[0])
+    torch.cuda.nvtx.range_pop()
     e1.record(stream)
     torch.cuda.synchronize()
     ms = e0.elapsed_time(e1)
@@ -401,9 +445,6 @@ def main():
     del Xt
     est = {c: (v[0] / v[1] * v[2] if v[1] else 0.0) for c, v in ktimes.items()}
     tot = sum(est.values())
-    dom = max(est, key=est.get)
-    d_ms, d_timed, _ = ktimes[dom]
-    d_avg_s = d_ms / max(1, d_timed) / 1000.0
     hbm, peak_kind = _peaks()
     dfma = sg.sg_probe_fma("fp64")
     ffma = sg.sg_probe_fma("fp32")
@@ -431,28 +472,55 @@ def main():
         "tuner": opk["msg"]}
     del Xr, Yr, X32, Y32
 
-    if dom in ("apply_lowp", "apply_f64"):
-        s = 4 if dom == "apply_lowp" else 8
-        alg = algorithmic_bytes_apply(nnzA, N, P, L, s)
-        roof = {"kernel": "sg_apply (SG operator, %s)" % ("FP32" if s == 4 else "FP64"),
-                "bound": "hbm", "achieved": alg / d_avg_s / 1e9, "peak": hbm, "unit": "GB/s",
-                "frac": alg / d_avg_s / 1e9 / hbm, "traffic": measured_traffic(dom)}
+    # The roofline: the kernel class with the largest share of the step's GPU time (timing pass
+    # above) among those with a byte model, timed again on the finest level where its bytes
+    # and time concentrate.  The smoother classes: one FS-GS sweep of the n = 256 level alone
+    # (the c3 system with the four-colour ILU(0) and BF16 coupling, as the V-cycle runs it),
+    # every launch bracketed by CUDA events on its stream; the operator classes: the timed
+    # operator applications above.
+    rated = {c: est[c] for c in ("apply_lowp", "apply_f64", "ilu_solve", "gs_scatter") if c in est}
+    dom = max(rated, key=rated.get)
+    fine = [(N, nnzA)]
+    if dom in ("ilu_solve", "gs_scatter"):
+        hf = sg.sg_setup(sg.sg_default_params(**W.c3_smoother_params()), stream)
+        Rf = torch.from_numpy(W.random_field(N, P, seed=11)).float().cuda()
+        Zf = torch.empty_like(Rf)
+        for _ in range(2):
+            sg.sg_precond_apply_lowp(hf, 0, Rf, Zf, stream)
+        sg.sg_timing_start(hf, 1)
+        for _ in range(3):
+            sg.sg_precond_apply_lowp(hf, 0, Rf, Zf, stream)
+        ft = sg.sg_timing_stop(hf)
+        hf.close()
+        del Rf, Zf
+        d_ms, d_timed, _ = ft[dom]
+        d_avg_s = d_ms / max(1, d_timed) / 1000.0
+        if dom == "ilu_solve":
+            alg = colour_solve_bytes(fine, P, 4)
+        else:
+            alg = later_scatter_bytes(fine, coupling_blocks(trip, P), 4, 2)
     else:
-        # ILU(0) block solves (FP32) of the seven smoothing levels n = 256 .. 4, the same number
-        # of launches on each: per launch the 9 factor values per row, the right-hand side and
-        # the result, averaged over the levels
-        s = 4
-        lev_n = [256 >> k for k in range(7)]
-        alg = sum(11 * s * (nl + 1) ** 2 for nl in lev_n) / len(lev_n)
-        # the floor of the dependency chain: 2 (3m - 8) + 4 barrier steps per solve
-        steps = sum(2 * (3 * (nl + 1) - 8) + 4 for nl in lev_n) / len(lev_n)
-        roof = {"kernel": "ilu block solve (FP32, levels n=256..4)", "bound": "hbm",
-                "achieved": alg / d_avg_s / 1e9, "peak": hbm, "unit": "GB/s",
-                "frac": alg / d_avg_s / 1e9 / hbm, "traffic": measured_traffic(dom),
-                "latency_bound": True, "barrier_steps_per_launch": steps,
-                "ns_per_barrier_step": d_avg_s * 1e9 / steps}
+        d_timed = args.steps
+        d_avg_s = mv32_s if dom == "apply_lowp" else mv64_s
+        alg = algorithmic_bytes_apply(nnzA, N, P, L, 4 if dom == "apply_lowp" else 8)
+    names = {"apply_lowp": "sg_apply (SG operator, FP32)", "apply_f64": "sg_apply (SG operator, FP64)",
+             "ilu_solve": "color_cluster_kernel (four-colour ILU(0) block solve with the "
+                          "next-column coupling pass, FP32, n=256 level)",
+             "gs_scatter": "fs_scatter_kernel (later-column Gauss-Seidel coupling, FP32 from the "
+                           "BF16 stiffness copy, n=256 level)"}
+    traffic = measured_traffic(dom)
+    roof = {"kernel": names[dom], "bound": "hbm", "achieved": alg / d_avg_s / 1e9, "peak": hbm,
+            "unit": "GB/s", "frac": alg / d_avg_s / 1e9 / hbm,
+            "traffic": None if traffic is None else traffic * alg,
+            "algorithmic_bytes_per_launch": alg}
+    if dom == "ilu_solve":
+        # eight colour phases and the coupling pass per solve, each a dependent round trip
+        roof.update({"latency_bound": True, "phases_per_launch": 9,
+                     "us_per_phase": d_avg_s * 1e6 / 9})
     roof.update({"peak_kind": peak_kind, "class": dom, "avg_launch_us": d_avg_s * 1e6,
                  "launches_timed": d_timed, "share_of_gpu_time": est[dom] / max(1e-30, tot)})
+    if dom in ("ilu_solve", "gs_scatter"):
+        roof["fine_level_sweep_ms"] = {c: v[0] / 3 * (v[2] / max(1, v[1])) for c, v in ft.items() if v[2]}
 
     # FP64 GPU GMRES on the same system (the comparison of the metric)
     h64 = sg.sg_setup(sg.sg_default_params(**W.c3_mg_params("fp64")), stream)

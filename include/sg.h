@@ -209,7 +209,8 @@ int sg_tune_plan(int n, int M, int p, int q, int precision, long long smem_max, 
  * stream of the current device; synchronous.  The ALU roofline of the FP64 operator divides by it. */
 int sg_probe_fma(int precision, double* gflops);
 
-/* Count of kernel launches this library has queued since load (all handles, all threads). */
+/* Count of kernel launches this library has queued since load (all handles, all threads); each
+ * replay of a captured GMRES segment counts the kernel nodes of its graph. */
 long long sg_launch_count(void);
 
 /* Live kernel timing.  Kernel classes: */

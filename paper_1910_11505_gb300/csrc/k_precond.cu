@@ -589,7 +589,7 @@ __global__ void __launch_bounds__(kScatterWarps * 32, 3) fs_scatter_kernel(
 #pragma unroll
       for (int j = 0; j < kScatterTW; ++j) {
         const int a = cb + w + kScatterWarps * j;
-        r[j] = (live && a <= a_hi) ? Rt[(size_t)a * ldN + i] : T(0);
+        r[j] = (live && a <= a_hi && ep[a] < ep[a + 1]) ? Rt[(size_t)a * ldN + i] : T(0);
       }
     };
     prefetch(a_lo);
@@ -623,8 +623,10 @@ __global__ void __launch_bounds__(kScatterWarps * 32, 3) fs_scatter_kernel(
       for (int j = 0; j < kScatterTW; ++j) {
         const int a = cb + w + kScatterWarps * j;
         if (a > a_hi) break;
+        const int q0 = ep[a], q1 = ep[a + 1];
+        if (q0 == q1) continue;  // no coupling into this column: nothing read or written
         T s = T(0);
-        for (int q = ep[a]; q < ep[a + 1]; ++q) s += eg[q] * Ts[(size_t)ek[q] * kScatterRows + lane];
+        for (int q = q0; q < q1; ++q) s += eg[q] * Ts[(size_t)ek[q] * kScatterRows + lane];
         if (live) Rt[(size_t)a * ldN + i] = r[j] - s;
       }
     }

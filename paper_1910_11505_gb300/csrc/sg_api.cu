@@ -749,10 +749,13 @@ static int launch_segment(SolveState& q, int j0, int j1) {
   for (auto& g : s.graphs)
     if (g.jmax == q.jmax && g.j0 == j0) {
       SG_CUDA(cudaGraphLaunch(g.exec, s.stream));
+      count_launch((int)g.kernels);
       return SG_OK;
     }
   const bool timing = s.timer && s.timer->on;
   if (timing) s.timer->on = false;
+  // launches queued during capture run only as the graph's kernel nodes: counted per replay
+  const long long counted = sg_launch_count();
   SG_CUDA(cudaStreamBeginCapture(s.stream, cudaStreamCaptureModeThreadLocal));
   int rc = SG_OK;
   for (int j = j0; j < j1 && rc == SG_OK; ++j) rc = iteration(s, j, q.jmax - 1);
@@ -763,12 +766,24 @@ static int launch_segment(SolveState& q, int j0, int j1) {
     if (graph) cudaGraphDestroy(graph);
     return rc != SG_OK ? rc : fail(SG_ERR_CUDA, std::string("stream capture: ") + cudaGetErrorString(e));
   }
+  count_launch((int)(counted - sg_launch_count()));
+  size_t nnodes = 0;
+  long long kernels = 0;
+  if (cudaGraphGetNodes(graph, nullptr, &nnodes) == cudaSuccess && nnodes > 0) {
+    std::vector<cudaGraphNode_t> nodes(nnodes);
+    if (cudaGraphGetNodes(graph, nodes.data(), &nnodes) == cudaSuccess)
+      for (auto nd : nodes) {
+        cudaGraphNodeType t;
+        if (cudaGraphNodeGetType(nd, &t) == cudaSuccess && t == cudaGraphNodeTypeKernel) ++kernels;
+      }
+  }
   cudaGraphExec_t exec = nullptr;
   e = cudaGraphInstantiate(&exec, graph, cudaGraphInstantiateFlagUseNodePriority);
   cudaGraphDestroy(graph);
   if (e != cudaSuccess) return fail(SG_ERR_CUDA, std::string("graph instantiate: ") + cudaGetErrorString(e));
-  s.graphs.push_back({q.jmax, j0, exec});
+  s.graphs.push_back({q.jmax, j0, exec, kernels});
   SG_CUDA(cudaGraphLaunch(exec, s.stream));
+  count_launch((int)kernels);
   return SG_OK;
 }
 

@@ -331,6 +331,7 @@ struct System {
   struct CycleGraph {
     int jmax, j0;
     cudaGraphExec_t exec;
+    long long kernels;  // kernel nodes: the launches one replay makes
   };
   std::vector<CycleGraph> graphs;  // captured segments of GMRES cycles (sg_params.graphs = 1)
   cudaEvent_t seg_ev[2] = {nullptr, nullptr};  // flags of the last two queued cycle segments

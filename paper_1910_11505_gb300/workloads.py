@@ -74,6 +74,13 @@ def c3_mg_params(precision="fp64", ilu_order="color4"):
     return d
 
 
+def c3_smoother_params():
+    """The finest level's smoother of c3_mg_params("fp32") on its own: one field-split
+    Gauss-Seidel sweep (four-colour ILU(0) blocks, BF16 coupling copy) per application."""
+    return dict(n=256, M=6, p=3, sigma=1.0, ell=0.5, precond="fs_gs", precision="fp32",
+                ilu_order="color4", coupling_bf16=1)
+
+
 def c3_params(precision="fp64"):
     return dict(n=256, M=6, p=3, sigma=1.0, ell=0.5, precond="mean", rtol=1e-8, restart=100,
                 max_iters=6000, precision=precision)

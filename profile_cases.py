@@ -1,9 +1,16 @@
 """Small, self-contained cases of single kernels for profiling (e.g. under ``ncu``).
 
     python profile_cases.py precond [fs_gs|fs_jacobi|mean] [n]
+    python profile_cases.py sweep [n] [M] [p] [fp32|fp64]   # four-colour FS-GS sweep as in c3
+    python profile_cases.py vcycle [reps]          # the c3 mixed solve's V-cycle preconditioner
     python profile_cases.py matvec [fp64|fp32|bf16] [n] [M] [p] [pairs|tile [kappa] [ctas]]
     python profile_cases.py gmres [n] [iters]      # Arnoldi kernels
     python profile_cases.py net [batch]            # network training step
+    python profile_cases.py stamp CLASS RATIO SUMMARY SRC...   # record a capture's DRAM ratio
+
+``stamp`` writes profiles/traffic.json's entry for a kernel class: the measured DRAM bytes per
+algorithmic byte of a captured launch, the summary that documents the capture and the SHA-256
+of the kernel's source files (bench.py reports the traffic only while they are unchanged).
 
 Each case builds one SG system, runs three applications of the chosen operation on seeded
 inputs and exits 0.  Sizes stay at a few GB of device memory.
@@ -19,7 +26,30 @@ if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
 
+def stamp(argv):
+    import hashlib
+    import json
+    cls, ratio, summary, srcs = argv[2], float(argv[3]), argv[4], argv[5:]
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        with open(path) as f:
+            rec = json.load(f)
+    except (OSError, ValueError):
+        rec = {}
+    h = hashlib.sha256()
+    for src in srcs:
+        with open(os.path.join(ROOT, src), "rb") as f:
+            h.update(f.read())
+    rec[cls] = {"dram_per_algorithmic_byte": ratio, "capture": summary, "sources": srcs,
+                "sha256": h.hexdigest()}
+    with open(path, "w") as f:
+        json.dump(rec, f, indent=1, sort_keys=True)
+        f.write("\n")
+
+
 def main(argv):
+    if len(argv) > 1 and argv[1] == "stamp":
+        return stamp(argv)
     import torch
 
     from paper_1910_11505_gb300 import build as B
@@ -36,6 +66,39 @@ def main(argv):
         Z = torch.empty_like(R)
         for _ in range(3):
             sg.sg_precond_apply(h, 0, R, Z)
+    elif what == "sweep":
+        # the field-split Gauss-Seidel sweep of the c3 smoother (four-colour ILU(0); the FP32
+        # form couples from the BF16 stiffness copy)
+        n = int(argv[2]) if len(argv) > 2 else 128
+        M = int(argv[3]) if len(argv) > 3 else 6
+        p = int(argv[4]) if len(argv) > 4 else 3
+        prec = argv[5] if len(argv) > 5 else "fp32"
+        h = sg.sg_setup(sg.sg_default_params(n=n, M=M, p=p, sigma=1.0, ell=0.5, precond="fs_gs",
+                                             precision=prec, ilu_order="color4",
+                                             coupling_bf16=1 if prec == "fp32" else 0))
+        N, P, _ = sg.sg_dims(h)
+        R = torch.from_numpy(W.random_field(N, P, seed=1)).cuda()
+        if prec == "fp32":
+            R = R.float()
+        Z = torch.empty_like(R)
+        apply = sg.sg_precond_apply_lowp if prec == "fp32" else sg.sg_precond_apply
+        for _ in range(3):
+            apply(h, 0, R, Z)
+    elif what == "vcycle":
+        # applications of the c3 multigrid preconditioner as the mixed solver's inner FGMRES
+        # runs it (FP32, G-M-F-I with four-colour ILU(0) and BF16 coupling); prints the library's
+        # launch count after setup and after each application (for a profiler's -s / -c)
+        reps = int(argv[2]) if len(argv) > 2 else 2
+        h = sg.sg_setup(sg.sg_default_params(**W.c3_mg_params("fp32")))
+        N, P, _ = sg.sg_dims(h)
+        R = torch.from_numpy(W.random_field(N, P, seed=1)).float().cuda()
+        Z = torch.empty_like(R)
+        torch.cuda.synchronize()
+        print("launches after setup", sg.sg_launch_count(), flush=True)
+        for _ in range(reps):
+            sg.sg_precond_apply_lowp(h, 0, R, Z)
+            torch.cuda.synchronize()
+            print("launches", sg.sg_launch_count(), flush=True)
     elif what == "matvec":
         prec = argv[2] if len(argv) > 2 else "fp64"
         n = int(argv[3]) if len(argv) > 3 else 128
