@@ -24,6 +24,14 @@ Readings where the paper is silent (numbered as in the design notes):
   R18 ILU(0) ordering (the paper names none): natural order by default; a four-colour ordering
       (colour (x mod 2) + 2 (y mod 2)) is the alternative, whose triangular solves run one colour
       at a time with every node of a colour independent.
+  R20 ILU(0) of a block of K with several fields (the whole K of G-I / G-M-I, a split of
+      G-M-Fg-I): unknowns node-major (a node's fields together), nodes in the four-colour order,
+      the pattern every field of a node coupled to every field of its 9-point neighbours.  With
+      q = 2p that is K's own pattern; scalar ILU(0) on it equals block ILU(0) with exact dense
+      LU of the diagonal blocks.
+  R21 G-M-Fg-I splits (Sec. 3, Eq. P_group): fields grouped by the first index of their
+      multi-index; in order, a group that holds a multi-index with all indices equal opens a
+      new split, any other group joins the preceding split.
 
 Layout conventions: a nodal field over the chaos basis is an N x P float64 array X with
 X[j, b] = u_b(node j); node id = i + m*j for grid point (i/n, j/n), m = n + 1.
@@ -46,6 +54,7 @@ __all__ = [
     "SGProblem", "build_problem", "stack_rows_dense", "sg_matvec", "sg_matvec_rows",
     "ilu0", "ilu0_solve", "mean_precond", "fs_blocks", "fs_precond", "gmres", "boundary_mask",
     "prolongation", "mg_levels", "mg_setup", "mg_vcycle", "color4_order",
+    "fg_splits", "block_pattern_matrix", "bilu0", "bilu0_solve", "fg_blocks", "fg_precond",
 ]
 
 
@@ -546,6 +555,111 @@ def fs_precond(prob: SGProblem, R: np.ndarray, mode: str = "gs", inner_iters: in
 
 
 # ----------------------------------------------------------------------------------------------
+# ILU(0) of multi-field blocks of K and the grouped field split (G-I, G-M-I, G-M-Fg-I; Sec. 3).
+# ----------------------------------------------------------------------------------------------
+
+def fg_splits(Jp: np.ndarray, rule: str = "paper"):
+    """Field ranges [start, end) of the splits (Sec. 3, Eq. P_group; reading R21).  Fields are
+    grouped by the first index of their multi-index (the groups are consecutive ranges in the
+    R3 order).  rule 'paper': a group opens a new split when one of its multi-indices has all
+    indices equal, else it joins the preceding split; 'groups': every group is a split; 'whole':
+    one split of all fields (G-I / G-M-I); 'fields': one split per field (G-F-I / G-M-F-I)."""
+    Jp = np.asarray(Jp)
+    P = Jp.shape[0]
+    if rule == "whole":
+        return [(0, P)]
+    if rule == "fields":
+        return [(a, a + 1) for a in range(P)]
+    groups = []
+    for a in range(P):
+        if not groups or Jp[a, 0] != Jp[groups[-1][0], 0]:
+            groups.append([a, a + 1])
+        else:
+            groups[-1][1] = a + 1
+    if rule == "groups":
+        return [tuple(g) for g in groups]
+    if rule != "paper":
+        raise ValueError("unknown split rule")
+    splits = []
+    for g0, g1 in groups:
+        all_equal = any(np.all(Jp[a] == Jp[a, 0]) for a in range(g0, g1))
+        if all_equal or not splits:
+            splits.append([g0, g1])
+        else:
+            splits[-1][1] = g1
+    return [tuple(sp) for sp in splits]
+
+
+def block_pattern_matrix(prob: SGProblem, f0: int, f1: int) -> scipy.sparse.csr_matrix:
+    """K restricted to the fields f0..f1-1, unknowns node-major (index node * Q + field - f0), on
+    the pattern of reading R20: every field of a node coupled to every field of each 9-point
+    neighbour, explicit zeros kept."""
+    n, Q = prob.n, f1 - f0
+    m = n + 1
+    Knm = sum(scipy.sparse.kron(prob.A[k], prob.G[k][f0:f1, f0:f1], format="csr")
+              for k in range(prob.L)).tocsr()
+    Knm.sort_indices()
+    indptr, indices, data = [0], [], []
+    for node in range(m * m):
+        x, y = node % m, node // m
+        nbs = [xx + m * yy for yy in range(y - 1, y + 2) for xx in range(x - 1, x + 2)
+               if 0 <= xx < m and 0 <= yy < m]
+        for a in range(Q):
+            r = node * Q + a
+            row = dict(zip(Knm.indices[Knm.indptr[r]:Knm.indptr[r + 1]].tolist(),
+                           Knm.data[Knm.indptr[r]:Knm.indptr[r + 1]].tolist()))
+            for j in nbs:
+                for b in range(Q):
+                    c = j * Q + b
+                    indices.append(c)
+                    data.append(row.get(c, 0.0))
+            indptr.append(len(indices))
+    return scipy.sparse.csr_matrix((np.array(data), np.array(indices), np.array(indptr)),
+                                   shape=(m * m * Q, m * m * Q))
+
+
+def bilu0(prob: SGProblem, f0: int, f1: int, ordering="color4"):
+    """ILU(0) of the block of K on fields f0..f1-1 (reading R20): the scalar IKJ ILU(0) of
+    ``ilu0`` on the node-major block pattern, nodes in the four-colour (or natural) order, each
+    node's fields in order."""
+    Q = f1 - f0
+    A = block_pattern_matrix(prob, f0, f1)
+    nodes = color4_order(prob.n) if ordering == "color4" else np.arange(prob.N)
+    order = (nodes[:, None] * Q + np.arange(Q)[None, :]).ravel()
+    return ilu0(A, order)
+
+
+def bilu0_solve(LU, R: np.ndarray) -> np.ndarray:
+    """(L U)^{-1} R for R of shape N x Q (node-major flattening)."""
+    N, Q = R.shape
+    return ilu0_solve(LU, R.reshape(N * Q)).reshape(N, Q)
+
+
+def fg_blocks(prob: SGProblem, splits, ordering="color4"):
+    """The ILU(0) factors of every split's diagonal block (reading R20)."""
+    return [bilu0(prob, f0, f1, ordering) for f0, f1 in splits]
+
+
+def fg_precond(prob: SGProblem, R: np.ndarray, splits, facs=None, mode: str = "gs",
+               coupling=None) -> np.ndarray:
+    """Grouped field split (Sec. 3, Eq. P_group): block Gauss-Seidel over the splits (or block
+    Jacobi, mode 'jacobi'), split s solved with the ILU(0) of its diagonal block K_ss after
+    subtracting sum_{t<s} K_st z_t.  Singleton splits give the field split of Eq.
+    P_preconditioner; one split of all fields gives ILU(0) of K (G-I)."""
+    if facs is None:
+        facs = fg_blocks(prob, splits)
+    Z = np.zeros_like(R)
+    for s, (f0, f1) in enumerate(splits):
+        rhs = R[:, f0:f1].copy()
+        if mode == "gs" and s > 0:
+            prev = range(0, f0)
+            for a in range(f0, f1):
+                rhs[:, a - f0] -= _offdiag_apply(prob, a, Z, prev, coupling)
+        Z[:, f0:f1] = bilu0_solve(facs[s], rhs)
+    return Z
+
+
+# ----------------------------------------------------------------------------------------------
 # Restarted, right-preconditioned GMRES with CGS2 Arnoldi and Givens rotations (reading R7).
 # ----------------------------------------------------------------------------------------------
 
@@ -667,7 +781,8 @@ def mg_levels(n, M, p, coarse=2, **kw):
 def mg_setup(levels, smoother="fs_gs", ordering=None):
     """Per level: smoother data (ILU(0) factors in natural or four-colour ordering), the
     prolongation from the level below, and the dense coarsest-level operator for the direct
-    solve."""
+    solve.  Smoothers: 'fs_gs', 'fs_jacobi', 'mean', and 'fg' / 'fg:<rule>' (the grouped field
+    split with the split rule of ``fg_splits``; 'fg:whole' is G-M-I)."""
     data = []
     for li, prob in enumerate(levels):
         d = {"P": prolongation(levels[li - 1].n) if li > 0 else None}
@@ -675,6 +790,10 @@ def mg_setup(levels, smoother="fs_gs", ordering=None):
             d["K"] = sum(np.kron(prob.G[k], prob.A[k].toarray()) for k in range(prob.L))
         elif smoother == "mean":
             d["LU"] = ilu0(prob.A[0], _order(prob, ordering))
+        elif smoother.startswith("fg"):
+            rule = smoother.split(":")[1] if ":" in smoother else "paper"
+            d["splits"] = fg_splits(prob.Jp, rule)
+            d["fg"] = fg_blocks(prob, d["splits"], ordering or "color4")
         else:
             d["blocks"] = fs_blocks(prob, ordering)
         data.append(d)
@@ -684,6 +803,8 @@ def mg_setup(levels, smoother="fs_gs", ordering=None):
 def _smooth(prob, d, smoother, r):
     if smoother == "mean":
         return mean_precond(prob, r, LU=d["LU"])
+    if smoother.startswith("fg"):
+        return fg_precond(prob, r, d["splits"], d["fg"])
     return fs_precond(prob, r, mode="gs" if smoother == "fs_gs" else "jacobi", blocks=d["blocks"])
 
 
