@@ -44,6 +44,12 @@ extern "C" {
 #define SG_PC_MG 4         /* geometric multigrid V-cycle (Sec. 3): on every level one pre- and */
                            /* one post-smoothing step of Eq. level_solver with the block        */
                            /* preconditioner mg_smoother, a direct solve on the coarsest mesh   */
+#define SG_PC_FG 5         /* grouped field split (Sec. 3, Eq. P_group): block Gauss-Seidel over */
+                           /* the splits that fg_rule forms, the diagonal block of each split   */
+                           /* approximated by its ILU(0) on the node-major block pattern (every */
+                           /* field of a node coupled to every field of its 9-point neighbours; */
+                           /* nodes in the four-colour order).  fg_rule SG_FG_WHOLE (one split) */
+                           /* is the ILU(0) of K: G-I alone, G-M-I as the multigrid smoother     */
 
 #define SG_FP64 0          /* every step in FP64                                                */
 #define SG_MIXED_FP32 1    /* FP32 operator / preconditioner inside FP64 flexible GMRES + IR    */
@@ -75,7 +81,8 @@ typedef struct {
   int graphs;        /* 1: capture each GMRES cycle of this system once as a CUDA graph (keyed  */
                      /* by cycle length and the F, X pointers) and replay it; 0: plain launches */
   int mg_smoother;   /* SG_PC_MG: smoother of every level, SG_PC_MEAN | SG_PC_FS_GS |           */
-                     /* SG_PC_FS_JACOBI (G-M-F-I of the paper is SG_PC_FS_GS)                   */
+                     /* SG_PC_FS_JACOBI | SG_PC_FG (G-M-F-I of the paper is SG_PC_FS_GS,        */
+                     /* G-M-Fg-I SG_PC_FG with SG_FG_PAPER, G-M-I SG_PC_FG with SG_FG_WHOLE)    */
   int mg_coarse;     /* SG_PC_MG: cells per side of the coarsest mesh (the paper: 2); n must be  */
                      /* mg_coarse times a power of two, and the coarsest interior system of     */
                      /* (mg_coarse - 1)^2 P unknowns is solved with its dense inverse (<= 4096)  */
@@ -91,7 +98,17 @@ typedef struct {
                      /* smoother): 1 = the sweep's coupling sum_{b<a} K_ab z_b reads a BF16     */
                      /* copy of the stiffness values (FP32 arithmetic), half the bytes of the   */
                      /* sweep's dominant traffic; the operator keeps its FP32 copy              */
+  int fg_rule;       /* SG_PC_FG (alone or as mg_smoother): how fields form splits, one of      */
+                     /* SG_FG_PAPER, SG_FG_GROUPS, SG_FG_WHOLE; a split holds at most 96 fields */
+                     /* in FP64 systems, 128 in mixed ones; requires ilu_order SG_ILU_COLOR4    */
 } sg_params;
+
+/* Splits of SG_PC_FG.  Fields are grouped by the first index of their multi-index (the groups
+ * are consecutive ranges of the chaos basis, lexicographic with the last index fastest). */
+#define SG_FG_PAPER 0   /* in order, a group holding a multi-index with all indices equal opens */
+                        /* a new split, any other group joins the preceding split (Sec. 3)      */
+#define SG_FG_GROUPS 1  /* every group is a split                                               */
+#define SG_FG_WHOLE 2   /* one split of all fields: the ILU(0) of K (G-I, G-M-I)                */
 
 #define SG_ILU_NATURAL 0
 #define SG_ILU_COLOR4 1
@@ -111,7 +128,8 @@ typedef struct {
 /* Fill ``prm`` with defaults: n=16, M=2, p=2, q=2p, sigma=0.5, ell=1, a_min=0, mu=0, f=1,
  * mean preconditioner, 1 inner / 1 outer step, restart 30, max_iters 2000, rtol 1e-10,
  * atol 0, FP64, inner_rtol 1e-4, graphs 0, mg_smoother SG_PC_FS_GS, mg_coarse 2,
- * op_kernel SG_OP_AUTO, op_kappa 0, op_ctas 0, ilu_order SG_ILU_NATURAL, coupling_bf16 0. */
+ * op_kernel SG_OP_AUTO, op_kappa 0, op_ctas 0, ilu_order SG_ILU_NATURAL, coupling_bf16 0,
+ * fg_rule SG_FG_PAPER. */
 void sg_default_params(sg_params* prm);
 
 /* Build ``nsys`` independent SG systems (Sec. 2: KL modes of Eq. gen_eigen in closed form,

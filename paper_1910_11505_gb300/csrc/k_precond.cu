@@ -930,6 +930,8 @@ int apply_block(System& s, const T* R, T* D, cudaStream_t st, const int* done) {
                                    B::rhs_t(s), D, st, done);
     case SG_PC_FS_GS:
       return fs_gs_sweep<T>(s, R, D, B::rhs_t(s), st, done, true);
+    case SG_PC_FG:
+      return fg_apply<T>(s, R, D, st, done);
     default: {
       SG_CUDA(cudaMemcpyAsync(D, R, sizeof(T) * (size_t)s.N * s.P, cudaMemcpyDeviceToDevice, st));
       return SG_OK;

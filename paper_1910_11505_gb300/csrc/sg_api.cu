@@ -121,10 +121,11 @@ static int validate(const sg_params& p) {
   if (!(p.sigma >= 0.0) || !(p.ell > 0.0) || !(p.a_min >= 0.0))
     return fail(SG_ERR_ARG, "need sigma >= 0, ell > 0, a_min >= 0");
   if (!std::isfinite(p.mu) || !std::isfinite(p.f)) return fail(SG_ERR_ARG, "mu and f must be finite");
-  if (p.precond < SG_PC_NONE || p.precond > SG_PC_MG) return fail(SG_ERR_ARG, "unknown preconditioner");
+  if (p.precond < SG_PC_NONE || p.precond > SG_PC_FG) return fail(SG_ERR_ARG, "unknown preconditioner");
   if (p.precond == SG_PC_MG) {
-    if (p.mg_smoother != SG_PC_MEAN && p.mg_smoother != SG_PC_FS_GS && p.mg_smoother != SG_PC_FS_JACOBI)
-      return fail(SG_ERR_ARG, "mg_smoother must be SG_PC_MEAN, SG_PC_FS_GS or SG_PC_FS_JACOBI");
+    if (p.mg_smoother != SG_PC_MEAN && p.mg_smoother != SG_PC_FS_GS &&
+        p.mg_smoother != SG_PC_FS_JACOBI && p.mg_smoother != SG_PC_FG)
+      return fail(SG_ERR_ARG, "mg_smoother must be SG_PC_MEAN, SG_PC_FS_GS, SG_PC_FS_JACOBI or SG_PC_FG");
     if (p.mg_coarse < 2) return fail(SG_ERR_ARG, "mg_coarse must be >= 2");
     int nn = p.n;
     while (nn > p.mg_coarse && nn % 2 == 0) nn /= 2;
@@ -148,6 +149,11 @@ static int validate(const sg_params& p) {
   if (p.ilu_order == SG_ILU_COLOR4 && p.inner_iters != 1)
     return fail(SG_ERR_ARG, "the four-colour ILU(0) ordering takes inner_iters = 1");
   if (p.coupling_bf16 != 0 && p.coupling_bf16 != 1) return fail(SG_ERR_ARG, "coupling_bf16 must be 0 or 1");
+  if (p.precond == SG_PC_FG || (p.precond == SG_PC_MG && p.mg_smoother == SG_PC_FG)) {
+    if (p.fg_rule < SG_FG_PAPER || p.fg_rule > SG_FG_WHOLE) return fail(SG_ERR_ARG, "unknown fg_rule");
+    if (p.ilu_order != SG_ILU_COLOR4)
+      return fail(SG_ERR_ARG, "the grouped field split runs in the four-colour ILU(0) ordering");
+  }
   if (p.coupling_bf16 && p.precision != SG_MIXED_FP32)
     return fail(SG_ERR_ARG, "coupling_bf16 applies to SG_MIXED_FP32 systems");
   if (p.precond == SG_PC_MEAN || p.precond == SG_PC_FS_GS || p.precond == SG_PC_FS_JACOBI ||
@@ -469,6 +475,13 @@ static void free_system(System* s) {
   s->lev9_off.release();
   s->cstart.release();
   s->stack_km16.release();
+  for (auto& sp : s->fg) {
+    sp.fac.release();
+    sp.fac32.release();
+  }
+  s->fg.clear();
+  for (auto* b : {&s->fg_tmp, &s->fg_tmp2}) b->release();
+  for (auto* b : {&s->fg_tmp32, &s->fg_tmp232}) b->release();
   DBuf<double>* db[] = {&s->stack, &s->stack_km, &s->ent_g, &s->blk, &s->fac, &s->lu9, &s->gs_eg, &s->gsn_eg, &s->gsn_cs, &s->gsn_corr, &s->rhs_t, &s->tmp,
                         &s->tmp2, &s->tri_w, &s->V, &s->Z, &s->Hs, &s->cs, &s->sn, &s->g, &s->y,
                         &s->scal, &s->red, &s->rvec};
@@ -589,6 +602,7 @@ static int setup_system(System& s, cudaStream_t st, bool krylov = true) {
 
   // preconditioner blocks and factors
   const size_t NP = (size_t)s.N * s.P;
+  if (s.pc_fac == SG_PC_FG) SG_TRY(fg_setup(s, st));
   if (s.pc_fac == SG_PC_MEAN || s.pc_fac == SG_PC_FS_GS || s.pc_fac == SG_PC_FS_JACOBI) {
     s.nfac = s.pc_fac == SG_PC_MEAN ? 1 : s.P;
     SG_TRY(s.blk.alloc((size_t)s.nfac * s.pat.nnz));
@@ -951,6 +965,7 @@ void sg_default_params(sg_params* p) {
   p->inner_rtol = 1e-4;
   p->graphs = 0;
   p->mg_smoother = SG_PC_FS_GS;
+  p->fg_rule = SG_FG_PAPER;
   p->mg_coarse = 2;
   p->op_kernel = SG_OP_AUTO;
   p->op_kappa = 0;

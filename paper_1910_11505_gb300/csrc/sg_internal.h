@@ -311,6 +311,19 @@ struct System {
   // a - 1 for the solve of column a
   DBuf<double> gsn_corr;
   DBuf<float> gsn_corr32;
+  // grouped field split (SG_PC_FG): per split its fields [f0, f1) and the ILU(0) of its diagonal
+  // block, N x 9 blocks of Q x Q (Q = f1 - f0) in the colour-major node order, block slot
+  // (dy+1)*3 + (dx+1); lower-colour slots hold L_ij D_j^-1, slot 4 D_i^-1, higher-colour slots
+  // D_i^-1 U_ij; each block column-major.  FP64 systems keep fac, mixed ones fac32.
+  struct FgSplit {
+    int f0 = 0, f1 = 0;
+    DBuf<double> fac;
+    DBuf<float> fac32;
+  };
+  std::vector<FgSplit> fg;
+  std::vector<int> cstart_h;     // host copy of the four-colour offsets (grouped field split)
+  DBuf<double> fg_tmp, fg_tmp2;  // splits after the first: the earlier splits' solution (other
+  DBuf<float> fg_tmp32, fg_tmp232;  // fields zero) and K times it
   int gs_max_klen = 0;
   // device scratch
   DBuf<double> rhs_t;          // P columns of stride ldN: right-hand sides of the block solves
@@ -413,6 +426,12 @@ int fs_gs_apply_f64_with(System& s, const double* R, double* Z, double* rhs_t, c
 // transfers: restriction (transpose of bilinear interpolation, zero on coarse boundary nodes)
 // and prolongation added into the fine iterate.
 int mg_setup_levels(System& s, cudaStream_t st);
+// Grouped field split (k_bilu.cu): the splits of fg_rule as field ranges; the assembly and ILU(0)
+// of every split's diagonal block; one application D = P^{-1} R of Eq. P_group.
+std::vector<std::pair<int, int>> fg_split_ranges(int M, int p, int rule);
+int fg_setup(System& s, cudaStream_t st);
+template <typename T>
+int fg_apply(System& s, const T* R, T* D, cudaStream_t st, const int* done);
 template <typename T>
 int launch_restrict(const T* rf, T* bc, int nc, int P, cudaStream_t st, const int* done,
                     Timer* timer);

@@ -20,11 +20,12 @@ SG_ERR_OOM = -3
 SG_ERR_NAN = -4
 SG_ERR_NOT_CONVERGED = -5
 
-SG_PC_NONE, SG_PC_MEAN, SG_PC_FS_GS, SG_PC_FS_JACOBI, SG_PC_MG = 0, 1, 2, 3, 4
+SG_PC_NONE, SG_PC_MEAN, SG_PC_FS_GS, SG_PC_FS_JACOBI, SG_PC_MG, SG_PC_FG = 0, 1, 2, 3, 4, 5
 SG_FP64, SG_MIXED_FP32, SG_MIXED_BF16 = 0, 1, 2
 
 PRECONDS = {"none": SG_PC_NONE, "mean": SG_PC_MEAN, "fs_gs": SG_PC_FS_GS,
-            "fs_jacobi": SG_PC_FS_JACOBI, "mg": SG_PC_MG}
+            "fs_jacobi": SG_PC_FS_JACOBI, "mg": SG_PC_MG, "fg": SG_PC_FG}
+FG_RULES = {"paper": 0, "groups": 1, "whole": 2}
 PRECISIONS = {"fp64": SG_FP64, "fp32": SG_MIXED_FP32, "bf16": SG_MIXED_BF16}
 OP_KERNELS = {"auto": 0, "pairs": 1, "tile": 2}
 ILU_ORDERS = {"natural": 0, "color4": 1}
@@ -57,7 +58,8 @@ class sg_params(ctypes.Structure):
                 ("inner_rtol", ctypes.c_double), ("graphs", ctypes.c_int),
                 ("mg_smoother", ctypes.c_int), ("mg_coarse", ctypes.c_int),
                 ("op_kernel", ctypes.c_int), ("op_kappa", ctypes.c_int), ("op_ctas", ctypes.c_int),
-                ("ilu_order", ctypes.c_int), ("coupling_bf16", ctypes.c_int)]
+                ("ilu_order", ctypes.c_int), ("coupling_bf16", ctypes.c_int),
+                ("fg_rule", ctypes.c_int)]
 
 
 class sg_solve_info(ctypes.Structure):
@@ -176,6 +178,8 @@ def sg_default_params(**overrides) -> sg_params:
             v = OP_KERNELS[v]
         if k == "ilu_order" and isinstance(v, str):
             v = ILU_ORDERS[v]
+        if k == "fg_rule" and isinstance(v, str):
+            v = FG_RULES[v]
         if k == "precision" and isinstance(v, str):
             v = PRECISIONS[v]
         setattr(p, k, v)
