@@ -61,24 +61,32 @@ def c2_params(sigma=None):
                  max_iters=4000) for s in sig]
 
 
-def c3_mg_params(precision="fp64", ilu_order="color4"):
-    """c3 with the multigrid V-cycle preconditioner of the paper's G-M-F-I (field-split
-    Gauss-Seidel + ILU(0) smoothing, one pre- and one post-step, 2 x 2 coarsest mesh), the
-    ILU(0) blocks in the four-colour ordering by default; in the mixed form the smoother's
-    Gauss-Seidel coupling reads a BF16 copy of the stiffness values."""
-    d = dict(n=256, M=6, p=3, sigma=1.0, ell=0.5, precond="mg", mg_smoother="fs_gs",
+def c3_mg_params(precision="fp64", smoother="fg"):
+    """c3 with the paper's multigrid preconditioners (one pre- and one post-smoothing step, 2 x 2
+    coarsest mesh, ILU(0) in the four-colour node order): by default G-M-Fg-I — the grouped
+    field split with the paper's split rule, which at M = 6, p = 3 forms one split of all 84
+    fields, so the smoother is the ILU(0) of each level's whole K; smoother="fs_gs" gives
+    G-M-F-I (one split per field), whose mixed form couples from a BF16 stiffness copy."""
+    d = dict(n=256, M=6, p=3, sigma=1.0, ell=0.5, precond="mg", mg_smoother=smoother,
              rtol=1e-8, restart=50, max_iters=400, precision=precision, graphs=1,
-             ilu_order=ilu_order)
-    if precision == "fp32":
+             ilu_order="color4")
+    if smoother == "fg":
+        d["fg_rule"] = "paper"
+    if smoother == "fs_gs" and precision == "fp32":
         d["coupling_bf16"] = 1  # the smoother's Gauss-Seidel coupling from a BF16 copy
     return d
 
 
-def c3_smoother_params():
-    """The finest level's smoother of c3_mg_params("fp32") on its own: one field-split
-    Gauss-Seidel sweep (four-colour ILU(0) blocks, BF16 coupling copy) per application."""
-    return dict(n=256, M=6, p=3, sigma=1.0, ell=0.5, precond="fs_gs", precision="fp32",
-                ilu_order="color4", coupling_bf16=1)
+def c3_smoother_params(smoother="fg"):
+    """The finest level's smoother of c3_mg_params("fp32", smoother) on its own: one application
+    of the grouped field split (or of the field-split Gauss-Seidel sweep)."""
+    d = dict(n=256, M=6, p=3, sigma=1.0, ell=0.5, precond=smoother, precision="fp32",
+             ilu_order="color4")
+    if smoother == "fg":
+        d["fg_rule"] = "paper"
+    else:
+        d["coupling_bf16"] = 1
+    return d
 
 
 def c3_params(precision="fp64"):

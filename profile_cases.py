@@ -2,7 +2,8 @@
 
     python profile_cases.py precond [fs_gs|fs_jacobi|mean] [n]
     python profile_cases.py sweep [n] [M] [p] [fp32|fp64]   # four-colour FS-GS sweep as in c3
-    python profile_cases.py vcycle [reps]          # the c3 mixed solve's V-cycle preconditioner
+    python profile_cases.py vcycle [reps] [fg|fs_gs]   # the c3 mixed solve's V-cycle preconditioner
+    python profile_cases.py smoother [fg|fs_gs] [n]     # the c3 smoother alone on an n x n mesh
     python profile_cases.py matvec [fp64|fp32|bf16] [n] [M] [p] [pairs|tile [kappa] [ctas]]
     python profile_cases.py gmres [n] [iters]      # Arnoldi kernels
     python profile_cases.py net [batch]            # network training step
@@ -89,7 +90,8 @@ def main(argv):
         # runs it (FP32, G-M-F-I with four-colour ILU(0) and BF16 coupling); prints the library's
         # launch count after setup and after each application (for a profiler's -s / -c)
         reps = int(argv[2]) if len(argv) > 2 else 2
-        h = sg.sg_setup(sg.sg_default_params(**W.c3_mg_params("fp32")))
+        smoother = argv[3] if len(argv) > 3 else "fg"
+        h = sg.sg_setup(sg.sg_default_params(**W.c3_mg_params("fp32", smoother)))
         N, P, _ = sg.sg_dims(h)
         R = torch.from_numpy(W.random_field(N, P, seed=1)).float().cuda()
         Z = torch.empty_like(R)
@@ -99,6 +101,16 @@ def main(argv):
             sg.sg_precond_apply_lowp(h, 0, R, Z)
             torch.cuda.synchronize()
             print("launches", sg.sg_launch_count(), flush=True)
+    elif what == "smoother":
+        # three applications of the c3 smoother (FP32) alone on an n x n mesh
+        smoother = argv[2] if len(argv) > 2 else "fg"
+        n = int(argv[3]) if len(argv) > 3 else 128
+        h = sg.sg_setup(sg.sg_default_params(**dict(W.c3_smoother_params(smoother), n=n)))
+        N, P, _ = sg.sg_dims(h)
+        R = torch.from_numpy(W.random_field(N, P, seed=1)).float().cuda()
+        Z = torch.empty_like(R)
+        for _ in range(3):
+            sg.sg_precond_apply_lowp(h, 0, R, Z)
     elif what == "matvec":
         prec = argv[2] if len(argv) > 2 else "fp64"
         n = int(argv[3]) if len(argv) > 3 else 128
