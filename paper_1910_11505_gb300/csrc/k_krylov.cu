@@ -270,9 +270,25 @@ __global__ void to_f64_kernel(size_t n, const float* __restrict__ src, double* _
     dst[i] = (double)src[i];
 }
 
+// *flag = 0 if any of x[0..n) is nonzero (the caller sets it nonzero beforehand).
+__global__ void any_nonzero_kernel(size_t n, const double* __restrict__ x, int* __restrict__ flag) {
+  bool nz = false;
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n && !nz;
+       i += (size_t)gridDim.x * blockDim.x)
+    nz = x[i] != 0.0;
+  if (__syncthreads_or(nz) && threadIdx.x == 0) *flag = 0;
+}
+
 }  // namespace
 
 // ------------------------------------------------------------------ launchers used by the driver
+
+int k_zero_flag(System& s, size_t n, const double* x, int* flag, cudaStream_t st) {
+  TimeScope ts(s.timer, K_OTHER, st);
+  SG_CUDA(cudaMemsetAsync(flag, 1, sizeof(int), st));
+  any_nonzero_kernel<<<kRedBlocks, kRedThreads, 0, st>>>(n, x, flag);
+  return check_launch("any_nonzero");
+}
 
 int k_norm(System& s, size_t n, const double* r, double* out, cudaStream_t st) {
   TimeScope ts(s.timer, K_OTHER, st);

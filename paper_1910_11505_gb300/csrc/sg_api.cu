@@ -470,7 +470,7 @@ static void free_system(System* s) {
   DBuf<int>* ib[] = {&s->rowptr, &s->col, &s->diag, &s->lev_f_ptr, &s->lev_f_rows, &s->lev_b_ptr,
                      &s->lev_b_rows, &s->pair_kb, &s->ent_ptr, &s->ent_u, &s->gs_kptr, &s->gs_k,
                      &s->gs_eptr, &s->gs_ea, &s->gsn_kptr, &s->gsn_k, &s->gsn_eptr,
-                     &s->gsn_ea, &s->flags};
+                     &s->gsn_ea, &s->flags, &s->xzero};
   for (auto* b : ib) b->release();
   s->lev9_off.release();
   s->cstart.release();
@@ -592,9 +592,10 @@ static int setup_system(System& s, cudaStream_t st, bool krylov = true) {
   }
   // the SG operator kernels, chosen by op_kernel (timed per system shape when automatic)
   // In the mixed forms the FP64 operator serves only the outer residual (once per refinement):
-  // it keeps the pair kernel on the FP64 stack unless the row-tiled one is asked for, and the
-  // FP32 stack copy of the pair kernel is dropped once the row-tiled FP32 operator serves.
-  if (p.precision == SG_FP64 || p.op_kernel == SG_OP_TILE) SG_TRY(choose_operator(s, 8, st));
+  // the multigrid levels below the top keep the pair kernel on the FP64 stack unless the
+  // row-tiled one is asked for, and the FP32 stack copy of the pair kernel is dropped once the
+  // row-tiled FP32 operator serves.
+  if (p.precision == SG_FP64 || p.op_kernel == SG_OP_TILE || krylov) SG_TRY(choose_operator(s, 8, st));
   if (p.precision == SG_MIXED_FP32) {
     SG_TRY(choose_operator(s, 4, st));
     if (s.tile32.ready) s.stack_f32.release();
@@ -681,6 +682,7 @@ static int setup_system(System& s, cudaStream_t st, bool krylov = true) {
   SG_TRY(s.scal.alloc(8));
   SG_TRY(s.red.alloc((size_t)krylov_red_blocks() * mb));
   SG_TRY(s.flags.alloc(4));
+  SG_TRY(s.xzero.alloc(1));
   SG_TRY(s.ticket.alloc(4));
   SG_CUDA(cudaMemsetAsync(s.ticket.p, 0, 4 * sizeof(unsigned int), st));
   SG_CUDA(cudaMemsetAsync(s.flags.p, 0, 4 * sizeof(int), st));
@@ -733,11 +735,19 @@ static int iteration(System& s, int j, int last_col) {
   return k_arnoldi(s, n, j, last_col, st);
 }
 
-// r = F - K x, beta = ||r||, mirrored to host with the cycle flags.
-static int residual(SolveState& ss) {
+// r = F - K x, beta = ||r||, mirrored to host with the cycle flags.  For the initial iterate
+// (``first``) r starts as a copy of F and the operator product is skipped on the device when x
+// is all zero (the common cold start).
+static int residual(SolveState& ss, bool first = false) {
   System& s = *ss.s;
   const size_t n = (size_t)s.N * s.P;
-  SG_TRY(launch_matvec_f64(s, ss.X, s.rvec.p, -1.0, ss.F, 1.0, s.stream));
+  if (first) {
+    SG_TRY(k_zero_flag(s, n, ss.X, s.xzero.p, s.stream));
+    SG_CUDA(cudaMemcpyAsync(s.rvec.p, ss.F, sizeof(double) * n, cudaMemcpyDeviceToDevice, s.stream));
+    SG_TRY(launch_matvec_f64(s, ss.X, s.rvec.p, -1.0, ss.F, 1.0, s.stream, s.xzero.p));
+  } else {
+    SG_TRY(launch_matvec_f64(s, ss.X, s.rvec.p, -1.0, ss.F, 1.0, s.stream));
+  }
   SG_TRY(k_norm(s, n, s.rvec.p, s.scal.p + 1, s.stream));
   SG_CUDA(cudaMemcpyAsync(s.hpin, s.scal.p, 4 * sizeof(double), cudaMemcpyDeviceToHost, s.stream));
   SG_CUDA(cudaMemcpyAsync(s.hpin + 4, s.flags.p, 4 * sizeof(int), cudaMemcpyDeviceToHost, s.stream));
@@ -830,7 +840,7 @@ int gmres_solve_all(sg_handle* h, const double* const* F, double* const* X, sg_s
     st[i].X = X[i];
     SG_CUDA(cudaStreamWaitEvent(s.stream, start, 0));
     SG_TRY(k_norm(s, (size_t)s.N * s.P, F[i], s.scal.p + 2, s.stream));
-    SG_TRY(residual(st[i]));
+    SG_TRY(residual(st[i], true));
   }
   cudaEventDestroy(start);
   for (int i = 0; i < ns; ++i) {

@@ -335,6 +335,7 @@ struct System {
   int m = 0;
   DBuf<double> V, Z, Hs, cs, sn, g, y, scal, red;  // see krylov.cu
   DBuf<int> flags;
+  DBuf<int> xzero;             // the initial iterate is all zero (its operator product is skipped)
   DBuf<unsigned int> ticket;
   DBuf<float> V32, Z32;        // inner FGMRES basis for mixed precision (FP32 vectors)
   DBuf<double> rvec;           // FP64 residual r = F - K x
@@ -458,6 +459,8 @@ int launch_tile_op(const System& s, const TileOp& op, const T* X, T* Y, T alpha,
 
 // Krylov launchers (k_krylov.cu)
 int k_norm(System& s, size_t n, const double* r, double* out, cudaStream_t st);
+// *flag != 0 afterwards iff x[0..n) is all zero (the flag then skips kernels given it as done).
+int k_zero_flag(System& s, size_t n, const double* x, int* flag, cudaStream_t st);
 int k_init_cycle(System& s, size_t n, const double* r, cudaStream_t st);
 int k_arnoldi(System& s, size_t n, int j, int last_col, cudaStream_t st);
 int k_finish_cycle(System& s, size_t n, double* x, bool z32, cudaStream_t st);
