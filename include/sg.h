@@ -222,6 +222,12 @@ int sg_op_info(const sg_handle* h, int sys, long long* info, char* msg, int msg_
  * budget}; ``out`` holds 72 values.  SG_ERR_ARG for invalid sizes. */
 int sg_tune_plan(int n, int M, int p, int q, int precision, long long smem_max, long long* out);
 
+/* Host only, no device use: the splits of SG_PC_FG for the chaos basis of total degree p in M
+ * variables under fg_rule ``rule`` (Sec. 3, the rule before Eq. P_group), as field ranges
+ * [out[2s], out[2s+1]) in basis order; ``out`` holds room for 2 (M+p)!/(M! p!) ints (host),
+ * *count receives the number of splits.  SG_ERR_ARG for M, p or rule out of range. */
+int sg_fg_splits(int M, int p, int rule, int* out, int* count);
+
 /* Measure the device's FMA throughput (independent FMA chains on every SM, CUDA events) in FP64
  * (precision SG_FP64) or FP32 (any other), in GFLOP/s (2 flops per FMA), on the legacy default
  * stream of the current device; synchronous.  The ALU roofline of the FP64 operator divides by it. */

@@ -1127,6 +1127,19 @@ int sg_op_info(const sg_handle* h, int sys, long long* info, char* msg, int msg_
   return SG_OK;
 }
 
+int sg_fg_splits(int M, int p, int rule, int* out, int* count) {
+  if (M < 1 || M > 8 || p < 0 || p > 6 || rule < SG_FG_PAPER || rule > SG_FG_WHOLE ||
+      out == nullptr || count == nullptr)
+    return fail(SG_ERR_ARG, "sg_fg_splits: M, p or rule out of range");
+  auto r = fg_split_ranges(M, p, rule);
+  for (size_t i = 0; i < r.size(); ++i) {
+    out[2 * i] = r[i].first;
+    out[2 * i + 1] = r[i].second;
+  }
+  *count = (int)r.size();
+  return SG_OK;
+}
+
 int sg_tune_plan(int n, int M, int p, int q, int precision, long long smem_max, long long* out) {
   if (!out) return fail(SG_ERR_ARG, "out is NULL");
   sg_params prm;

@@ -8,6 +8,7 @@ CUDA device is present, the calls raise.
 from __future__ import annotations
 
 import ctypes
+import math
 import os
 
 HERE = os.path.dirname(os.path.abspath(__file__))
@@ -34,6 +35,7 @@ EXPORTED = ["sg_default_params", "sg_setup", "sg_dims", "sg_nnz", "sg_matvec", "
             "sg_precond_apply", "sg_precond_apply_lowp", "sg_precond_apply_noalloc", "sg_rhs",
             "sg_gmres_solve",
             "sg_export", "sg_launch_count", "sg_tune_plan", "sg_op_info", "sg_probe_fma",
+            "sg_fg_splits",
             "sg_timing_start", "sg_timing_stop", "sg_free", "sg_last_error",
             "sgnet_create", "sgnet_set_stats", "sgnet_set_basis", "sgnet_forward", "sgnet_predict", "sgnet_loss_grad",
             "sgnet_adam_step", "sgnet_train_step", "sgnet_num_params", "sgnet_get", "sgnet_set",
@@ -100,6 +102,8 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.sg_tune_plan.argtypes = [c_int, c_int, c_int, c_int, c_int, ctypes.c_longlong,
                                  ctypes.POINTER(ctypes.c_longlong)]
     lib.sg_tune_plan.restype = c_int
+    lib.sg_fg_splits.argtypes = [c_int, c_int, c_int, ctypes.POINTER(c_int), ctypes.POINTER(c_int)]
+    lib.sg_fg_splits.restype = c_int
     lib.sg_op_info.argtypes = [vp, c_int, ctypes.POINTER(ctypes.c_longlong), ctypes.c_char_p, c_int]
     lib.sg_op_info.restype = c_int
     lib.sg_probe_fma.argtypes = [c_int, ctypes.POINTER(ctypes.c_double)]
@@ -277,6 +281,17 @@ def sg_tune_plan(n, M, p, q=0, precision="fp64", smem_max=232448):
     keys = ["kappa", "ctas", "fits", "smem", "chunks", "max_slots", "pairs", "entries", "k_kept",
             "groups", "verified", "budget"]
     return [dict(zip(keys, out[12 * i:12 * i + 12])) for i in range(6)]
+
+
+def sg_fg_splits(M, p, rule="paper"):
+    """Host-only split ranges of the grouped field split (see include/sg.h): [(f0, f1), ...]."""
+    if isinstance(rule, str):
+        rule = FG_RULES[rule]
+    P = math.comb(M + p, p)
+    out = (ctypes.c_int * (2 * P))()
+    cnt = ctypes.c_int()
+    _check(load_library().sg_fg_splits(M, p, rule, out, ctypes.byref(cnt)))
+    return [(out[2 * i], out[2 * i + 1]) for i in range(cnt.value)]
 
 
 def sg_precond_apply_lowp(h: SGHandle, sys: int, R, Z, stream=None):
