@@ -468,11 +468,11 @@ def main():
     x_mixed = X.clone()
 
     # per-kernel timing, in a pass of its own: one more solve on a handle without graph replay
-    # (events inside a captured graph would become graph nodes), every 4th launch of each kernel
-    # class bracketed by events on its own stream
+    # (events inside a captured graph would become graph nodes), every launch bracketed by
+    # events on its own stream
     ht = sg.sg_setup(sg.sg_default_params(**dict(W.c3_mg_params("fp32"), graphs=0)), stream)
     Xt = torch.zeros_like(F)
-    sg.sg_timing_start(ht, 4)
+    sg.sg_timing_start(ht, 1)
     sg.sg_gmres_solve(ht, [F], [Xt], stream)
     ktimes = sg.sg_timing_stop(ht)
     ht.close()
