@@ -90,7 +90,7 @@ __global__ void __launch_bounds__(kWarps * 32, MINB) sg_apply_tile_kernel(
   T* Ys = Ts + d.tbuf_elems;              // P x 32 accumulators of the tile
   T* Xs = Ys + (size_t)d.P * kTW;
   const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
-  const int P = d.P, Pp = d.Pp, m = d.m;
+  const int P = d.P, m = d.m;
 
   if (tid == 0) {
     mbar_init(&bar[0], 1);
@@ -120,13 +120,14 @@ __global__ void __launch_bounds__(kWarps * 32, MINB) sg_apply_tile_kernel(
     const int y = 1 + t / d.tiles_per_line;
     const int x0 = 1 + (t % d.tiles_per_line) * kTW;
     const int nrows = min(kTW, m - 1 - x0);
-    // X on lines y-1, y, y+1 for nodes x0-1 .. x0+32 (zero beyond the mesh): one warp per node
+    // X on lines y-1, y, y+1 for nodes x0-1 .. x0+32 (zero beyond the mesh), chaos-major:
+    // Xs[(b * 3 + dy) * kSlab + xi], so a lane's 9 stencil neighbours of one b sit at fixed
+    // offsets from one address; one warp per node reads the node's P values (coalesced)
     for (int nd = w; nd < 3 * kSlab; nd += kWarps) {
       const int dy = nd / kSlab, xi = nd - dy * kSlab;
       const int x = x0 - 1 + xi;
       const T* src = X + ((size_t)(y - 1 + dy) * m + x) * P;
-      T* dst = Xs + (size_t)nd * Pp;
-      for (int b = lane; b < P; b += 32) dst[b] = x < m ? src[b] : T(0);
+      for (int b = lane; b < P; b += 32) Xs[(b * 3 + dy) * kSlab + xi] = x < m ? src[b] : T(0);
     }
     for (int i = tid; i < P * kTW; i += blockDim.x) Ys[i] = T(0);
 
@@ -199,13 +200,14 @@ __global__ void __launch_bounds__(kWarps * 32, MINB) sg_apply_tile_kernel(
             const int2 e0 = gl[u], e1 = gl[u + 1];
             const int b0 = e0.x & 0xffff, b1 = e1.x & 0xffff;
             T x0v[9], x1v[9];
+            const T* xp0 = Xs + b0 * (3 * kSlab) + lane;
+            const T* xp1 = Xs + b1 * (3 * kSlab) + lane;
 #pragma unroll
             for (int dy = 0; dy < 3; ++dy)
 #pragma unroll
               for (int dx = 0; dx < 3; ++dx) {
-                const int base = (dy * kSlab + lane + dx) * Pp;
-                x0v[dy * 3 + dx] = Xs[base + b0];
-                x1v[dy * 3 + dx] = Xs[base + b1];
+                x0v[dy * 3 + dx] = xp0[dy * kSlab + dx];
+                x1v[dy * 3 + dx] = xp1[dy * kSlab + dx];
               }
             pairs_of(e0.x, e0.y, x0v);
             pairs_of(e1.x, e1.y, x1v);
@@ -214,10 +216,11 @@ __global__ void __launch_bounds__(kWarps * 32, MINB) sg_apply_tile_kernel(
             const int2 e0 = gl[u];
             const int b0 = e0.x & 0xffff;
             T x0v[9];
+            const T* xp0 = Xs + b0 * (3 * kSlab) + lane;
 #pragma unroll
             for (int dy = 0; dy < 3; ++dy)
 #pragma unroll
-              for (int dx = 0; dx < 3; ++dx) x0v[dy * 3 + dx] = Xs[(dy * kSlab + lane + dx) * Pp + b0];
+              for (int dx = 0; dx < 3; ++dx) x0v[dy * 3 + dx] = xp0[dy * kSlab + dx];
             pairs_of(e0.x, e0.y, x0v);
           }
         }
