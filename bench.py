@@ -40,8 +40,8 @@ METRIC = "SG solves/sec & matvec HBM GB/s, mixed/learned vs FP64 GMRES at 1e-8 r
 WORKLOAD = ("c3: 256x256 Q1 mesh, M=6, p=3 (P=84, L=924, 5.5M unknowns), sigma=1, ell=0.5, "
             "GMRES(50) + multigrid V-cycle G-M-Fg-I (grouped field split, the paper's split rule "
             "giving one split of all 84 fields: block ILU(0) of each level's K in the four-colour "
-            "node order; 1/1 smoothing, 2x2 coarsest), rel. residual 1e-8, x0 = 0; mixed "
-            "FP32/FP64 FGMRES + refinement")
+            "node order, factors stored in BF16; 1/1 smoothing, 2x2 coarsest), rel. residual "
+            "1e-8, x0 = 0; mixed FP32/FP64 FGMRES + refinement")
 PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "traffic.json")
 
@@ -357,12 +357,12 @@ def later_scatter_bytes(levels, blocks, s, sv):
     return tot / (len(levels) * len(blocks))
 
 
-def fg_solve_bytes(levels, P, s):
+def fg_solve_bytes(levels, P, s, sf):
     """Algorithmic bytes of one colour-phase launch of the grouped field split with one split of
     all P fields, averaged over the 8 launches of an application and the levels: every node's 9
-    blocks of P x P values once per application, the right-hand side read and the result
-    written once."""
-    tot = sum(s * N * (9 * P * P + 2 * P) for N, _ in levels)
+    blocks of P x P factor values (sf bytes each) once per application, the right-hand side read
+    and the result written once (s bytes each)."""
+    tot = sum(N * (9 * P * P * sf + 2 * P * s) for N, _ in levels)
     return tot / (len(levels) * 8)
 
 
@@ -530,7 +530,7 @@ def main():
         d_ms, d_timed, _ = ft[dom]
         d_avg_s = d_ms / max(1, d_timed) / 1000.0
         if dom == "ilu_solve":
-            alg = fg_solve_bytes(fine, P, 4)
+            alg = fg_solve_bytes(fine, P, 4, 2)
         else:
             alg = later_scatter_bytes(fine, coupling_blocks(trip, P), 4, 2)
     else:
@@ -539,7 +539,7 @@ def main():
         alg = algorithmic_bytes_apply(nnzA, N, P, L, 4 if dom == "apply_lowp" else 8)
     names = {"apply_lowp": "sg_apply (SG operator, FP32)", "apply_f64": "sg_apply (SG operator, FP64)",
              "ilu_solve": "fg_lower_kernel / fg_upper_kernel (colour phases of the block ILU(0) "
-                          "of K, 84 x 84 blocks, FP32, n=256 level)",
+                          "of K, 84 x 84 blocks stored in BF16, FP32 arithmetic, n=256 level)",
              "gs_scatter": "fs_scatter_kernel (later-column Gauss-Seidel coupling, FP32 from the "
                            "BF16 stiffness copy, n=256 level)"}
     traffic = measured_traffic(dom)

@@ -99,8 +99,11 @@ typedef struct {
                      /* copy of the stiffness values (FP32 arithmetic), half the bytes of the   */
                      /* sweep's dominant traffic; the operator keeps its FP32 copy              */
   int fg_rule;       /* SG_PC_FG (alone or as mg_smoother): how fields form splits, one of      */
-                     /* SG_FG_PAPER, SG_FG_GROUPS, SG_FG_WHOLE; a split holds at most 96 fields */
-                     /* in FP64 systems, 128 in mixed ones; requires ilu_order SG_ILU_COLOR4    */
+                     /* SG_FG_PAPER, SG_FG_GROUPS, SG_FG_WHOLE; a split holds at most 96 fields; */
+                     /* requires ilu_order SG_ILU_COLOR4                                        */
+  int fg_bf16;       /* SG_MIXED_FP32 with SG_PC_FG: 1 = the block ILU(0) factors (computed in   */
+                     /* FP32) are stored in BF16 and applied in FP32 arithmetic: half the bytes  */
+                     /* of the smoother's traffic; the preconditioner changes, the solution not  */
 } sg_params;
 
 /* Splits of SG_PC_FG.  Fields are grouped by the first index of their multi-index (the groups
@@ -129,7 +132,7 @@ typedef struct {
  * mean preconditioner, 1 inner / 1 outer step, restart 30, max_iters 2000, rtol 1e-10,
  * atol 0, FP64, inner_rtol 1e-4, graphs 0, mg_smoother SG_PC_FS_GS, mg_coarse 2,
  * op_kernel SG_OP_AUTO, op_kappa 0, op_ctas 0, ilu_order SG_ILU_NATURAL, coupling_bf16 0,
- * fg_rule SG_FG_PAPER. */
+ * fg_rule SG_FG_PAPER, fg_bf16 0. */
 void sg_default_params(sg_params* prm);
 
 /* Build ``nsys`` independent SG systems (Sec. 2: KL modes of Eq. gen_eigen in closed form,

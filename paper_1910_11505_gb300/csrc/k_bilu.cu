@@ -310,10 +310,10 @@ __host__ __device__ constexpr int fg_lanes(int Q) { return Q > 64 ? 128 : Q > 32
 // y_i = r_i - sub_i - sum over the lower-colour slots of (L D^-1)_{i,slot} y_nb.  Each node is
 // a group of lanes (lane r: row r of every block, the neighbour's Q values staged in shared
 // memory); neighbours outside the mesh are clamped onto it, their blocks are zero.
-template <typename T>
+template <typename T, typename TV>
 __global__ void __launch_bounds__(128) fg_lower_kernel(int m, int P, int Q, int f0, int c,
                                                        const int* __restrict__ cstart_g,
-                                                       const T* __restrict__ fac,
+                                                       const TV* __restrict__ fac,
                                                        const T* __restrict__ R,
                                                        const T* __restrict__ sub, T* Y,
                                                        const int* __restrict__ done) {
@@ -334,7 +334,7 @@ __global__ void __launch_bounds__(128) fg_lower_kernel(int m, int P, int Q, int 
   }
   const int i = x + m * y;
   const size_t QQ = (size_t)Q * Q;
-  const T* blocks = fac + (size_t)pos * 9 * QQ;
+  const TV* blocks = fac + (size_t)pos * 9 * QQ;
   T* v = vec + g * Q;
   T acc = T(0);
   if (r < Q) acc = R[(size_t)i * P + f0 + r] - (sub != nullptr ? sub[(size_t)i * P + f0 + r] : T(0));
@@ -346,17 +346,17 @@ __global__ void __launch_bounds__(128) fg_lower_kernel(int m, int P, int Q, int 
     for (int t = r; t < Q; t += G) v[t] = Y[j * P + f0 + t];
     __syncthreads();
     if (r < Q) {
-      const T* blk = blocks + sl * QQ + r;
+      const TV* blk = blocks + sl * QQ + r;
       int cc = 0;
       for (; cc + 4 <= Q; cc += 4) {
-        const T b0 = blk[(size_t)cc * Q], b1 = blk[(size_t)(cc + 1) * Q];
-        const T b2 = blk[(size_t)(cc + 2) * Q], b3 = blk[(size_t)(cc + 3) * Q];
+        const T b0 = (T)blk[(size_t)cc * Q], b1 = (T)blk[(size_t)(cc + 1) * Q];
+        const T b2 = (T)blk[(size_t)(cc + 2) * Q], b3 = (T)blk[(size_t)(cc + 3) * Q];
         acc -= b0 * v[cc];
         acc -= b1 * v[cc + 1];
         acc -= b2 * v[cc + 2];
         acc -= b3 * v[cc + 3];
       }
-      for (; cc < Q; ++cc) acc -= blk[(size_t)cc * Q] * v[cc];
+      for (; cc < Q; ++cc) acc -= (T)blk[(size_t)cc * Q] * v[cc];
     }
     __syncthreads();
   }
@@ -366,10 +366,10 @@ __global__ void __launch_bounds__(128) fg_lower_kernel(int m, int P, int Q, int 
 // One colour of the backward sweep, in place: z_i = D_i^-1 y_i - sum over the higher-colour
 // slots of (D^-1 U)_{i,slot} z_nb.  The node's own y_i is staged before any lane writes z_i; no
 // other node of the colour reads it.
-template <typename T>
+template <typename T, typename TV>
 __global__ void __launch_bounds__(128) fg_upper_kernel(int m, int P, int Q, int f0, int c,
                                                        const int* __restrict__ cstart_g,
-                                                       const T* __restrict__ fac, T* Y,
+                                                       const TV* __restrict__ fac, T* Y,
                                                        const int* __restrict__ done) {
   if (done != nullptr && *done) return;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -388,7 +388,7 @@ __global__ void __launch_bounds__(128) fg_upper_kernel(int m, int P, int Q, int 
   }
   const int i = x + m * y;
   const size_t QQ = (size_t)Q * Q;
-  const T* blocks = fac + (size_t)pos * 9 * QQ;
+  const TV* blocks = fac + (size_t)pos * 9 * QQ;
   T* v = vec + g * Q;
   T acc = T(0);
   for (int sl = 4; sl < 13; ++sl) {  // the diagonal first, then slots 0..8 but 4
@@ -401,18 +401,18 @@ __global__ void __launch_bounds__(128) fg_upper_kernel(int m, int P, int Q, int 
     for (int t = r; t < Q; t += G) v[t] = Y[j * P + f0 + t];
     __syncthreads();
     if (r < Q) {
-      const T* blk = blocks + s2 * QQ + r;
+      const TV* blk = blocks + s2 * QQ + r;
       T part = T(0);
       int cc = 0;
       for (; cc + 4 <= Q; cc += 4) {
-        const T b0 = blk[(size_t)cc * Q], b1 = blk[(size_t)(cc + 1) * Q];
-        const T b2 = blk[(size_t)(cc + 2) * Q], b3 = blk[(size_t)(cc + 3) * Q];
+        const T b0 = (T)blk[(size_t)cc * Q], b1 = (T)blk[(size_t)(cc + 1) * Q];
+        const T b2 = (T)blk[(size_t)(cc + 2) * Q], b3 = (T)blk[(size_t)(cc + 3) * Q];
         part += b0 * v[cc];
         part += b1 * v[cc + 1];
         part += b2 * v[cc + 2];
         part += b3 * v[cc + 3];
       }
-      for (; cc < Q; ++cc) part += blk[(size_t)cc * Q] * v[cc];
+      for (; cc < Q; ++cc) part += (T)blk[(size_t)cc * Q] * v[cc];
       acc = s2 == 4 ? part : acc - part;
     }
     __syncthreads();
@@ -428,6 +428,13 @@ __global__ void fg_mask_kernel(size_t N, int P, int f0, const T* __restrict__ D,
   for (size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x; t < N * P;
        t += (size_t)gridDim.x * blockDim.x)
     tmp[t] = (int)(t % P) < f0 ? D[t] : T(0);
+}
+
+__global__ void fg_round_bf16_kernel(size_t n, const float* __restrict__ src,
+                                     __nv_bfloat16* __restrict__ dst) {
+  for (size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x; t < n;
+       t += (size_t)gridDim.x * blockDim.x)
+    dst[t] = __float2bfloat16_rn(src[t]);
 }
 
 template <typename T>
@@ -531,6 +538,13 @@ int fg_setup(System& s, cudaStream_t st) {
                                                       sp.fac32.p);
       SG_TRY(check_launch("fg_assemble"));
       SG_TRY(fg_factor<float>(s, sp, sp.fac32.p, st));
+      if (p.fg_bf16) {  // the factors in BF16 for the applications, the FP32 copy dropped
+        SG_TRY(sp.fac16.alloc(nblk));
+        fg_round_bf16_kernel<<<1216, 256, 0, st>>>(nblk, sp.fac32.p, sp.fac16.p);
+        SG_TRY(check_launch("fg_round_bf16"));
+        SG_CUDA(cudaStreamSynchronize(st));
+        sp.fac32.release();
+      }
     } else {
       SG_TRY(sp.fac.alloc(nblk));
       SG_CUDA(cudaMemsetAsync(sp.fac.p, 0, sizeof(double) * nblk, st));
@@ -560,7 +574,9 @@ int fg_apply(System& s, const T* R, T* D, cudaStream_t st, const int* done) {
   for (size_t si = 0; si < s.fg.size(); ++si) {
     System::FgSplit& sp = s.fg[si];
     const T* fac = B::fac(sp);
-    if (fac == nullptr) return fail(SG_ERR_ARG, "grouped field split: no factors in this precision");
+    const __nv_bfloat16* fac16 = sizeof(T) == 4 ? sp.fac16.p : nullptr;
+    if (fac == nullptr && fac16 == nullptr)
+      return fail(SG_ERR_ARG, "grouped field split: no factors in this precision");
     const int Q = sp.f1 - sp.f0;
     const T* sub = nullptr;
     if (si > 0) {  // Eq. P_group: subtract sum_{t < s} K_st z_t, from K applied to z masked
@@ -581,16 +597,26 @@ int fg_apply(System& s, const T* R, T* D, cudaStream_t st, const int* done) {
       const int cnt = s.cstart_h[c + 1] - s.cstart_h[c];
       if (cnt <= 0) continue;
       TimeScope ts(s.timer, K_ILU_SOLVE, st);
-      fg_lower_kernel<T><<<(cnt + npc - 1) / npc, 128, smem, st>>>(s.pat.m, s.P, Q, sp.f0, c,
-                                                                  s.cstart.p, fac, R, sub, D, done);
+      const int grid = (cnt + npc - 1) / npc;
+      if (fac16 != nullptr)
+        fg_lower_kernel<T, __nv_bfloat16><<<grid, 128, smem, st>>>(s.pat.m, s.P, Q, sp.f0, c,
+                                                                   s.cstart.p, fac16, R, sub, D, done);
+      else
+        fg_lower_kernel<T, T><<<grid, 128, smem, st>>>(s.pat.m, s.P, Q, sp.f0, c, s.cstart.p,
+                                                       fac, R, sub, D, done);
       SG_TRY(check_launch("fg_lower"));
     }
     for (int c = 3; c >= 0; --c) {
       const int cnt = s.cstart_h[c + 1] - s.cstart_h[c];
       if (cnt <= 0) continue;
       TimeScope ts(s.timer, K_ILU_SOLVE, st);
-      fg_upper_kernel<T><<<(cnt + npc - 1) / npc, 128, smem, st>>>(s.pat.m, s.P, Q, sp.f0, c,
-                                                                  s.cstart.p, fac, D, done);
+      const int grid = (cnt + npc - 1) / npc;
+      if (fac16 != nullptr)
+        fg_upper_kernel<T, __nv_bfloat16><<<grid, 128, smem, st>>>(s.pat.m, s.P, Q, sp.f0, c,
+                                                                   s.cstart.p, fac16, D, done);
+      else
+        fg_upper_kernel<T, T><<<grid, 128, smem, st>>>(s.pat.m, s.P, Q, sp.f0, c, s.cstart.p, fac,
+                                                       D, done);
       SG_TRY(check_launch("fg_upper"));
     }
   }

@@ -154,6 +154,9 @@ static int validate(const sg_params& p) {
     if (p.ilu_order != SG_ILU_COLOR4)
       return fail(SG_ERR_ARG, "the grouped field split runs in the four-colour ILU(0) ordering");
   }
+  if (p.fg_bf16 != 0 && p.fg_bf16 != 1) return fail(SG_ERR_ARG, "fg_bf16 must be 0 or 1");
+  if (p.fg_bf16 && p.precision != SG_MIXED_FP32)
+    return fail(SG_ERR_ARG, "fg_bf16 applies to SG_MIXED_FP32 systems");
   if (p.coupling_bf16 && p.precision != SG_MIXED_FP32)
     return fail(SG_ERR_ARG, "coupling_bf16 applies to SG_MIXED_FP32 systems");
   if (p.precond == SG_PC_MEAN || p.precond == SG_PC_FS_GS || p.precond == SG_PC_FS_JACOBI ||
@@ -478,6 +481,7 @@ static void free_system(System* s) {
   for (auto& sp : s->fg) {
     sp.fac.release();
     sp.fac32.release();
+    sp.fac16.release();
   }
   s->fg.clear();
   for (auto* b : {&s->fg_tmp, &s->fg_tmp2}) b->release();
@@ -976,6 +980,7 @@ void sg_default_params(sg_params* p) {
   p->graphs = 0;
   p->mg_smoother = SG_PC_FS_GS;
   p->fg_rule = SG_FG_PAPER;
+  p->fg_bf16 = 0;
   p->mg_coarse = 2;
   p->op_kernel = SG_OP_AUTO;
   p->op_kappa = 0;

@@ -314,11 +314,12 @@ struct System {
   // grouped field split (SG_PC_FG): per split its fields [f0, f1) and the ILU(0) of its diagonal
   // block, N x 9 blocks of Q x Q (Q = f1 - f0) in the colour-major node order, block slot
   // (dy+1)*3 + (dx+1); lower-colour slots hold L_ij D_j^-1, slot 4 D_i^-1, higher-colour slots
-  // D_i^-1 U_ij; each block column-major.  FP64 systems keep fac, mixed ones fac32.
+  // D_i^-1 U_ij; each block column-major.  FP64 systems keep fac, mixed ones fac32 (or fac16).
   struct FgSplit {
     int f0 = 0, f1 = 0;
     DBuf<double> fac;
     DBuf<float> fac32;
+    DBuf<__nv_bfloat16> fac16;  // fg_bf16: the FP32 factors rounded to BF16 (fac32 released)
   };
   std::vector<FgSplit> fg;
   std::vector<int> cstart_h;     // host copy of the four-colour offsets (grouped field split)

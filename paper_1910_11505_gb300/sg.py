@@ -61,7 +61,7 @@ class sg_params(ctypes.Structure):
                 ("mg_smoother", ctypes.c_int), ("mg_coarse", ctypes.c_int),
                 ("op_kernel", ctypes.c_int), ("op_kappa", ctypes.c_int), ("op_ctas", ctypes.c_int),
                 ("ilu_order", ctypes.c_int), ("coupling_bf16", ctypes.c_int),
-                ("fg_rule", ctypes.c_int)]
+                ("fg_rule", ctypes.c_int), ("fg_bf16", ctypes.c_int)]
 
 
 class sg_solve_info(ctypes.Structure):

@@ -65,13 +65,16 @@ def c3_mg_params(precision="fp64", smoother="fg"):
     """c3 with the paper's multigrid preconditioners (one pre- and one post-smoothing step, 2 x 2
     coarsest mesh, ILU(0) in the four-colour node order): by default G-M-Fg-I — the grouped
     field split with the paper's split rule, which at M = 6, p = 3 forms one split of all 84
-    fields, so the smoother is the ILU(0) of each level's whole K; smoother="fs_gs" gives
-    G-M-F-I (one split per field), whose mixed form couples from a BF16 stiffness copy."""
+    fields, so the smoother is the ILU(0) of each level's whole K (in the mixed form its factors
+    are stored in BF16); smoother="fs_gs" gives G-M-F-I (one split per field), whose mixed form
+    couples from a BF16 stiffness copy."""
     d = dict(n=256, M=6, p=3, sigma=1.0, ell=0.5, precond="mg", mg_smoother=smoother,
              rtol=1e-8, restart=50, max_iters=400, precision=precision, graphs=1,
              ilu_order="color4")
     if smoother == "fg":
         d["fg_rule"] = "paper"
+        if precision == "fp32":
+            d["fg_bf16"] = 1  # the block ILU(0) factors stored in BF16, applied in FP32
     if smoother == "fs_gs" and precision == "fp32":
         d["coupling_bf16"] = 1  # the smoother's Gauss-Seidel coupling from a BF16 copy
     return d
@@ -84,6 +87,7 @@ def c3_smoother_params(smoother="fg"):
              ilu_order="color4")
     if smoother == "fg":
         d["fg_rule"] = "paper"
+        d["fg_bf16"] = 1
     else:
         d["coupling_bf16"] = 1
     return d

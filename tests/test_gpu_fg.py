@@ -121,3 +121,36 @@ def test_grouped_split_refusals():
     with pytest.raises(RuntimeError):  # a split of 210 fields
         sg.sg_setup(sg.sg_default_params(n=4, M=6, p=4, precond="fg", fg_rule="whole",
                                          ilu_order="color4"))
+
+
+def test_bf16_factor_storage():
+    # rounding the stored factors to BF16 changes the preconditioner by about the BF16 unit
+    # round-off (2^-8) amplified by the sweeps; the solution of the mixed solve does not change
+    case = dict(n=16, M=2, p=2, sigma=0.8, ell=0.5)
+    hs = [sg.sg_setup(sg.sg_default_params(**case, precond="fg", fg_rule="paper",
+                                           ilu_order="color4", precision="fp32", fg_bf16=b))
+          for b in (0, 1)]
+    N, P, _ = sg.sg_dims(hs[0])
+    R = torch.from_numpy(W.random_field(N, P, seed=64)).float().cuda()
+    Z = [torch.empty_like(R) for _ in hs]
+    for h, z in zip(hs, Z):
+        sg.sg_precond_apply_lowp(h, 0, R, z)
+    d = float((Z[1] - Z[0]).abs().max() / Z[0].abs().max())
+    assert 1e-5 < d < 5e-2, d
+    for h in hs:
+        h.close()
+    h = sg.sg_setup(sg.sg_default_params(**case, precond="mg", mg_smoother="fg", fg_rule="paper",
+                                         ilu_order="color4", precision="fp32", fg_bf16=1,
+                                         rtol=1e-10, restart=40, max_iters=200))
+    F = torch.empty(N, P, dtype=torch.float64, device="cuda")
+    sg.sg_rhs(h, 0, F)
+    X = torch.zeros_like(F)
+    rc, info = sg.sg_gmres_solve(h, [F], [X])
+    assert rc == sg.SG_OK, info
+    prob = O.build_problem(16, 2, 2, **_kw(case))
+    K = sum(np.kron(prob.G[k], prob.A[k].toarray()) for k in range(prob.L))
+    ref = np.linalg.solve(K, prob.F.T.ravel()).reshape(prob.P, prob.N).T
+    assert np.linalg.norm(X.cpu().numpy() - ref) <= 1e-8 * np.linalg.norm(ref)
+    h.close()
+    with pytest.raises(RuntimeError):  # BF16 factors only in the mixed form
+        sg.sg_setup(sg.sg_default_params(**case, precond="fg", ilu_order="color4", fg_bf16=1))
