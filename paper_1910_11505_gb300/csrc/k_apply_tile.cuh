@@ -231,20 +231,42 @@ __global__ void __launch_bounds__(kWarps * 32, MINB) sg_apply_tile_kernel(
         const int* s2ptr = reinterpret_cast<const int*>(Sb + hdr[3]);
         const int4* s2 = reinterpret_cast<const int4*>(Sb + hdr[4]);
         const TEnt<T>* ent = reinterpret_cast<const TEnt<T>*>(Sb + hdr[5]);
-        for (int rn = s2ptr[w]; rn < s2ptr[w + 1]; ++rn) {
-          const int4 run = s2[rn];
-          T s0 = T(0), s1v = T(0);
-          int q = run.y;
-          for (; q + 1 < run.z; q += 2) {
-            const TEnt<T> f0 = ent[q], f1 = ent[q + 1];
-            s0 = fma(f0.g, Ts[(size_t)f0.slot * kTW + lane], s0);
-            s1v = fma(f1.g, Ts[(size_t)f1.slot * kTW + lane], s1v);
+        // runs are short (about two entries), so four of them go at a time: their chains of
+        // dependent shared-memory loads overlap; the runs of a warp have distinct outputs a
+        const int r_end = s2ptr[w + 1];
+        int rn = s2ptr[w];
+        for (; rn + 4 <= r_end; rn += 4) {
+          int4 run[4];
+          T acc[4];
+#pragma unroll
+          for (int v = 0; v < 4; ++v) {
+            run[v] = s2[rn + v];
+            acc[v] = T(0);
           }
-          if (q < run.z) {
+          int len = 0;
+#pragma unroll
+          for (int v = 0; v < 4; ++v) len = max(len, run[v].z - run[v].y);
+          for (int t = 0; t < len; ++t) {
+#pragma unroll
+            for (int v = 0; v < 4; ++v) {
+              const int q = run[v].y + t;
+              if (q < run[v].z) {
+                const TEnt<T> f = ent[q];
+                acc[v] = fma(f.g, Ts[(size_t)f.slot * kTW + lane], acc[v]);
+              }
+            }
+          }
+#pragma unroll
+          for (int v = 0; v < 4; ++v) Ys[(size_t)run[v].x * kTW + lane] += acc[v];
+        }
+        for (; rn < r_end; ++rn) {
+          const int4 run = s2[rn];
+          T s0 = T(0);
+          for (int q = run.y; q < run.z; ++q) {
             const TEnt<T> f0 = ent[q];
             s0 = fma(f0.g, Ts[(size_t)f0.slot * kTW + lane], s0);
           }
-          Ys[(size_t)run.x * kTW + lane] += s0 + s1v;
+          Ys[(size_t)run.x * kTW + lane] += s0;
         }
       }
       __syncthreads();
