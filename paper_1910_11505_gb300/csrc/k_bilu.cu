@@ -306,6 +306,50 @@ __global__ void __launch_bounds__(256) fg_factor_kernel(int m, int Q, int c,
 // Lanes per node in the solve kernels (the rows of a block) and nodes per 128-thread CTA.
 __host__ __device__ constexpr int fg_lanes(int Q) { return Q > 64 ? 128 : Q > 32 ? 64 : 32; }
 
+// Block storage of the solve kernels.  FP32 / FP64 factors: each Q x Q block column-major.
+// BF16 factors: columns in pairs, (r, c) at ((c / 2) * Q + r) * 2 + (c & 1), the column count
+// rounded up to even (Qc) with a zero column, so a lane reads the two values of its row in one
+// 4-byte load.
+template <typename TV>
+__host__ __device__ constexpr bool fg_paired() { return sizeof(TV) == 2; }
+__host__ __device__ inline int fg_qc(int Q) { return (Q + 1) & ~1; }
+
+// Row r of block blk times the vector v (Qc values, zero-padded): four partial sums.
+template <typename T, typename TV>
+__device__ __forceinline__ T fg_block_row_dot(const TV* __restrict__ blk, int Q, int r,
+                                              const T* v) {
+  T s0 = T(0), s1 = T(0), s2 = T(0), s3 = T(0);
+  if constexpr (fg_paired<TV>()) {
+    const __nv_bfloat162* b2 = reinterpret_cast<const __nv_bfloat162*>(blk) + r;
+    const int npair = fg_qc(Q) >> 1;
+    int cp = 0;
+    for (; cp + 2 <= npair; cp += 2) {
+      const float2 u0 = __bfloat1622float2(b2[(size_t)cp * Q]);
+      const float2 u1 = __bfloat1622float2(b2[(size_t)(cp + 1) * Q]);
+      s0 += (T)u0.x * v[2 * cp];
+      s1 += (T)u0.y * v[2 * cp + 1];
+      s2 += (T)u1.x * v[2 * cp + 2];
+      s3 += (T)u1.y * v[2 * cp + 3];
+    }
+    if (cp < npair) {
+      const float2 u0 = __bfloat1622float2(b2[(size_t)cp * Q]);
+      s0 += (T)u0.x * v[2 * cp];
+      s1 += (T)u0.y * v[2 * cp + 1];
+    }
+  } else {
+    const TV* b = blk + r;
+    int cc = 0;
+    for (; cc + 4 <= Q; cc += 4) {
+      s0 += (T)b[(size_t)cc * Q] * v[cc];
+      s1 += (T)b[(size_t)(cc + 1) * Q] * v[cc + 1];
+      s2 += (T)b[(size_t)(cc + 2) * Q] * v[cc + 2];
+      s3 += (T)b[(size_t)(cc + 3) * Q] * v[cc + 3];
+    }
+    for (; cc < Q; ++cc) s0 += (T)b[(size_t)cc * Q] * v[cc];
+  }
+  return (s0 + s1) + (s2 + s3);
+}
+
 // One colour of the forward sweep of a split (fields [f0, f0 + Q) of the N x P arrays):
 // y_i = r_i - sub_i - sum over the lower-colour slots of (L D^-1)_{i,slot} y_nb.  Each node is
 // a group of lanes (lane r: row r of every block, the neighbour's Q values staged in shared
@@ -333,9 +377,11 @@ __global__ void __launch_bounds__(128) fg_lower_kernel(int m, int P, int Q, int 
     x = cx + 2 * (q % nx);
   }
   const int i = x + m * y;
-  const size_t QQ = (size_t)Q * Q;
+  const int Qc = fg_qc(Q);
+  const size_t QQ = (size_t)Q * (fg_paired<TV>() ? Qc : Q);
   const TV* blocks = fac + (size_t)pos * 9 * QQ;
-  T* v = vec + g * Q;
+  T* v = vec + g * Qc;
+  if (r == 0 && Qc > Q) v[Q] = T(0);
   T acc = T(0);
   if (r < Q) acc = R[(size_t)i * P + f0 + r] - (sub != nullptr ? sub[(size_t)i * P + f0 + r] : T(0));
   for (int sl = 0; sl < 9; ++sl) {
@@ -345,19 +391,7 @@ __global__ void __launch_bounds__(128) fg_lower_kernel(int m, int P, int Q, int 
     const size_t j = (size_t)jx + (size_t)m * jy;
     for (int t = r; t < Q; t += G) v[t] = Y[j * P + f0 + t];
     __syncthreads();
-    if (r < Q) {
-      const TV* blk = blocks + sl * QQ + r;
-      int cc = 0;
-      for (; cc + 4 <= Q; cc += 4) {
-        const T b0 = (T)blk[(size_t)cc * Q], b1 = (T)blk[(size_t)(cc + 1) * Q];
-        const T b2 = (T)blk[(size_t)(cc + 2) * Q], b3 = (T)blk[(size_t)(cc + 3) * Q];
-        acc -= b0 * v[cc];
-        acc -= b1 * v[cc + 1];
-        acc -= b2 * v[cc + 2];
-        acc -= b3 * v[cc + 3];
-      }
-      for (; cc < Q; ++cc) acc -= (T)blk[(size_t)cc * Q] * v[cc];
-    }
+    if (r < Q) acc -= fg_block_row_dot<T, TV>(blocks + sl * QQ, Q, r, v);
     __syncthreads();
   }
   if (live && r < Q) Y[(size_t)i * P + f0 + r] = acc;
@@ -387,9 +421,11 @@ __global__ void __launch_bounds__(128) fg_upper_kernel(int m, int P, int Q, int 
     x = cx + 2 * (q % nx);
   }
   const int i = x + m * y;
-  const size_t QQ = (size_t)Q * Q;
+  const int Qc = fg_qc(Q);
+  const size_t QQ = (size_t)Q * (fg_paired<TV>() ? Qc : Q);
   const TV* blocks = fac + (size_t)pos * 9 * QQ;
-  T* v = vec + g * Q;
+  T* v = vec + g * Qc;
+  if (r == 0 && Qc > Q) v[Q] = T(0);
   T acc = T(0);
   for (int sl = 4; sl < 13; ++sl) {  // the diagonal first, then slots 0..8 but 4
     const int s2 = sl % 9;
@@ -401,18 +437,7 @@ __global__ void __launch_bounds__(128) fg_upper_kernel(int m, int P, int Q, int 
     for (int t = r; t < Q; t += G) v[t] = Y[j * P + f0 + t];
     __syncthreads();
     if (r < Q) {
-      const TV* blk = blocks + s2 * QQ + r;
-      T part = T(0);
-      int cc = 0;
-      for (; cc + 4 <= Q; cc += 4) {
-        const T b0 = (T)blk[(size_t)cc * Q], b1 = (T)blk[(size_t)(cc + 1) * Q];
-        const T b2 = (T)blk[(size_t)(cc + 2) * Q], b3 = (T)blk[(size_t)(cc + 3) * Q];
-        part += b0 * v[cc];
-        part += b1 * v[cc + 1];
-        part += b2 * v[cc + 2];
-        part += b3 * v[cc + 3];
-      }
-      for (; cc < Q; ++cc) part += (T)blk[(size_t)cc * Q] * v[cc];
+      const T part = fg_block_row_dot<T, TV>(blocks + s2 * QQ, Q, r, v);
       acc = s2 == 4 ? part : acc - part;
     }
     __syncthreads();
@@ -430,11 +455,20 @@ __global__ void fg_mask_kernel(size_t N, int P, int f0, const T* __restrict__ D,
     tmp[t] = (int)(t % P) < f0 ? D[t] : T(0);
 }
 
-__global__ void fg_round_bf16_kernel(size_t n, const float* __restrict__ src,
+// FP32 blocks (column-major, Q x Q) -> BF16 blocks in the paired layout (Q x Qc, zero column
+// when Q is odd); one thread per destination element.
+__global__ void fg_round_bf16_kernel(size_t nblocks, int Q, const float* __restrict__ src,
                                      __nv_bfloat16* __restrict__ dst) {
-  for (size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x; t < n;
-       t += (size_t)gridDim.x * blockDim.x)
-    dst[t] = __float2bfloat16_rn(src[t]);
+  const int Qc = fg_qc(Q);
+  const size_t per = (size_t)Q * Qc, total = nblocks * per;
+  for (size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x; t < total;
+       t += (size_t)gridDim.x * blockDim.x) {
+    const size_t blk = t / per;
+    const int o = (int)(t - blk * per);
+    const int cc = 2 * (o / (2 * Q)) + (o & 1), r = (o >> 1) % Q;
+    dst[t] = cc < Q ? __float2bfloat16_rn(src[blk * Q * Q + (size_t)cc * Q + r])
+                    : __float2bfloat16_rn(0.0f);
+  }
 }
 
 template <typename T>
@@ -539,8 +573,9 @@ int fg_setup(System& s, cudaStream_t st) {
       SG_TRY(check_launch("fg_assemble"));
       SG_TRY(fg_factor<float>(s, sp, sp.fac32.p, st));
       if (p.fg_bf16) {  // the factors in BF16 for the applications, the FP32 copy dropped
-        SG_TRY(sp.fac16.alloc(nblk));
-        fg_round_bf16_kernel<<<1216, 256, 0, st>>>(nblk, sp.fac32.p, sp.fac16.p);
+        const size_t nb = (size_t)s.N * 9;
+        SG_TRY(sp.fac16.alloc(nb * Q * fg_qc(Q)));
+        fg_round_bf16_kernel<<<1216, 256, 0, st>>>(nb, Q, sp.fac32.p, sp.fac16.p);
         SG_TRY(check_launch("fg_round_bf16"));
         SG_CUDA(cudaStreamSynchronize(st));
         sp.fac32.release();
@@ -592,7 +627,7 @@ int fg_apply(System& s, const T* R, T* D, cudaStream_t st, const int* done) {
       sub = B::tmp2(s);
     }
     const int G = fg_lanes(Q), npc = 128 / G;
-    const size_t smem = sizeof(T) * (size_t)npc * Q;
+    const size_t smem = sizeof(T) * (size_t)npc * fg_qc(Q);
     for (int c = 0; c < 4; ++c) {
       const int cnt = s.cstart_h[c + 1] - s.cstart_h[c];
       if (cnt <= 0) continue;
