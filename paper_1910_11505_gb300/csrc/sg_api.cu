@@ -758,12 +758,20 @@ static int residual(SolveState& ss, bool first = false) {
   return SG_OK;
 }
 
-// A cycle is queued in segments of kSegSteps Arnoldi steps.  After each segment the cycle's flags
-// are copied to pinned host memory behind an event; the host queues the next segment only while
-// the segment before the last one queued has not reported convergence, so at most two segments
-// of steps that return at once (the device's done flag) follow the converged step, instead of
-// the rest of the cycle.
+// A cycle is queued in segments of Arnoldi steps.  After each segment the cycle's flags are copied
+// to pinned host memory behind an event; the host queues the next segment only while the segment
+// before the last one queued has not reported convergence, so at most two segments of steps that
+// return at once (the device's done flag) follow the converged step, instead of the rest of the
+// cycle.  A step of a large system takes milliseconds, ample time for the host to read a
+// segment's flags and queue the next, so large systems queue two steps per segment (each step
+// that runs empty still launches every kernel of a V-cycle); small ones six.
 constexpr int kSegSteps = 6;
+constexpr int kSegStepsLarge = 2;
+constexpr long long kSegLargeUnknowns = 1LL << 18;
+
+static int seg_steps(const System& s) {
+  return (long long)s.N * s.P >= kSegLargeUnknowns ? kSegStepsLarge : kSegSteps;
+}
 
 // Steps [j0, j1) of the current cycle, as plain launches or as a graph captured on first use
 // (keyed by the cycle length and j0).  Kernel timing is suspended during capture (events
@@ -818,7 +826,7 @@ static int launch_segment(SolveState& q, int j0, int j1) {
 // Queue the next segment of q's cycle and the read-back of its flags (slot = segment parity).
 static int queue_segment(SolveState& q) {
   System& s = *q.s;
-  const int j0 = q.seg_next, j1 = std::min(q.jmax, j0 + kSegSteps);
+  const int j0 = q.seg_next, j1 = std::min(q.jmax, j0 + seg_steps(s));
   SG_TRY(launch_segment(q, j0, j1));
   const int slot = q.seg_queued & 1;
   SG_CUDA(cudaMemcpyAsync(s.hpin + 8 + 2 * slot, s.flags.p, 4 * sizeof(int), cudaMemcpyDeviceToHost,
