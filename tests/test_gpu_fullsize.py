@@ -145,6 +145,23 @@ def test_fullsize_c2_solution_true_residual_on_sampled_rows():
     h.close()
 
 
+def test_fullsize_c3_bench_solve_true_residual_on_sampled_rows():
+    # the bench workload: mixed G-M-Fg-I (one split: block ILU(0) of K per level, BF16 factors)
+    d = W.c3_mg_params("fp32")
+    h = sg.sg_setup(sg.sg_default_params(**d))
+    N, P, _ = sg.sg_dims(h)
+    F = torch.empty(N, P, dtype=torch.float64, device="cuda")
+    sg.sg_rhs(h, 0, F)
+    X = torch.zeros_like(F)
+    rc, info = sg.sg_gmres_solve(h, [F], [X])
+    assert rc == sg.SG_OK and info[0]["rel_resid"] <= 1e-8
+    x, f = X.cpu().numpy(), F.cpu().numpy()
+    rows = _sample_rows(d["n"], seed=11)
+    r = f[rows] - _oracle_rows(d, rows, x)
+    assert np.linalg.norm(r) <= 1.5e-8 * np.linalg.norm(f)
+    h.close()
+
+
 def test_smallest_mesh_and_single_mode():
     # n = 2: one interior node; p = 0: P = 1 (the deterministic mean problem)
     for d in (dict(n=2, M=1, p=1, sigma=0.3, ell=1.0), dict(n=4, M=2, p=0, sigma=0.5, ell=1.0)):
