@@ -278,7 +278,7 @@ def reference_arm(args):
     if rank != 0:
         return 0
     info = cpu_info()
-    iters = 8  # the mixed form's inner iterations on this workload (same algorithm on the GPU)
+    iters = 7  # the mixed form's inner iterations on this workload (same algorithm on the GPU)
     per_step = []
     for k in range(args.warmup + args.steps):
         smp = oracle_sample(nrows=16, reps=3)
