@@ -37,7 +37,9 @@ namespace sg {
 namespace {
 
 // Tiled stack from the nnz x L stack: for tile t, permuted k position kp, entry e, row r:
-// value of A_{kperm[kp]} at entry e of node (x0 + r, y), 0 for rows beyond the line.
+// value of A_{kperm[kp]} at entry e of node (x0 + r, y), 0 for rows beyond the line.  In FP32 the
+// centre entry (e = 4) holds the row sum of the nine instead (summed in FP64), for the difference
+// form of the stencil product (see k_apply_tile.cuh).
 template <typename TS>
 __global__ void tile_stack_kernel(int m, int tiles_per_line, int ntiles, int Lu, int L,
                                   const int* __restrict__ rowptr, const int* __restrict__ kperm,
@@ -56,7 +58,10 @@ __global__ void tile_stack_kernel(int m, int tiles_per_line, int ntiles, int Lu,
     double v = 0.0;
     if (x <= m - 2) {
       const int node = y * m + x;
-      v = stack[((size_t)rowptr[node] + e) * L + kperm[kp]];
+      if (sizeof(TS) == 4 && e == 4)
+        for (int q = 0; q < 9; ++q) v += stack[((size_t)rowptr[node] + q) * L + kperm[kp]];
+      else
+        v = stack[((size_t)rowptr[node] + e) * L + kperm[kp]];
     }
     out[idx] = (TS)v;
   }

@@ -195,6 +195,18 @@ __global__ void __launch_bounds__(kWarps * 32, MINB) sg_apply_tile_kernel(
               if (need) Ts[(size_t)(sl + __popc(mask & ((1 << j) - 1))) * kTW + lane] = (s0 + s1) + s2;
             }
           };
+          // FP32: the stencil product in difference form, sum_e A_e x_e =
+          // (sum_e A_e) x_c + sum_{e != c} A_e (x_e - x_c), the row sum stored in the centre slot:
+          // a stiffness row sums to about zero, so the direct form cancels ~1/h^2-sized terms in
+          // FP32, while the differences of a smooth x are small and their products carry no such
+          // cancellation (the mixed solver's refinement then gains more digits per cycle)
+          auto diff_form = [&](T* xv) {
+            if (sizeof(T) == 4) {
+#pragma unroll
+              for (int e = 0; e < 9; ++e)
+                if (e != 4) xv[e] -= xv[4];
+            }
+          };
           int u = 0;
           for (; u + 1 < piece.z; u += 2) {
             const int2 e0 = gl[u], e1 = gl[u + 1];
@@ -209,6 +221,8 @@ __global__ void __launch_bounds__(kWarps * 32, MINB) sg_apply_tile_kernel(
                 x0v[dy * 3 + dx] = xp0[dy * kSlab + dx];
                 x1v[dy * 3 + dx] = xp1[dy * kSlab + dx];
               }
+            diff_form(x0v);
+            diff_form(x1v);
             pairs_of(e0.x, e0.y, x0v);
             pairs_of(e1.x, e1.y, x1v);
           }
@@ -221,6 +235,7 @@ __global__ void __launch_bounds__(kWarps * 32, MINB) sg_apply_tile_kernel(
             for (int dy = 0; dy < 3; ++dy)
 #pragma unroll
               for (int dx = 0; dx < 3; ++dx) x0v[dy * 3 + dx] = xp0[dy * kSlab + dx];
+            diff_form(x0v);
             pairs_of(e0.x, e0.y, x0v);
           }
         }

@@ -75,10 +75,6 @@ def c3_mg_params(precision="fp64", smoother="fg"):
         d["fg_rule"] = "paper"
         if precision == "fp32":
             d["fg_bf16"] = 1  # the block ILU(0) factors stored in BF16, applied in FP32
-            # each inner cycle gains about three orders in the true FP64 residual whatever it
-            # aims at (the FP32 operator's rounding relative to ||K|| ||dx||), so it stops at
-            # 1e-3: three refinement cycles of 7 iterations in all where 1e-4 takes 8
-            d["inner_rtol"] = 1e-3
     if smoother == "fs_gs" and precision == "fp32":
         d["coupling_bf16"] = 1  # the smoother's Gauss-Seidel coupling from a BF16 copy
     return d
