@@ -219,10 +219,11 @@ int sg_op_info(const sg_handle* h, int sys, long long* info, char* msg, int msg_
 /* For tests, host only (no device work): plan the row-tiled operator of a system with these sizes
  * in FP64 (precision SG_FP64) or FP32 (any other precision) for the six variants kappa in {1, 2, 4}
  * k per register group x 1 or 2 CTAs per SM (rows 0..5, CTAs outer), under a shared-memory budget
- * of smem_max bytes per SM (halved per CTA for two CTAs).  Row r is out[12 r .. 12 r + 11] =
+ * of smem_max bytes per SM (halved per CTA for two CTAs).  Row r is out[16 r .. 16 r + 15] =
  * {kappa, CTAs, fits, shared-memory bytes, chunks, largest chunk's T slots, (k, b) pairs placed,
  * stage-2 entries placed, k kept, k groups, tables verified by decoding them as the kernel does,
- * budget}; ``out`` holds 72 values.  SG_ERR_ARG for invalid sizes. */
+ * budget, union entries, stage-1 steps and stage-2 steps of the slowest warp summed over the
+ * chunks, 0}; ``out`` holds 96 values.  SG_ERR_ARG for invalid sizes. */
 int sg_tune_plan(int n, int M, int p, int q, int precision, long long smem_max, long long* out);
 
 /* Host only, no device use: the splits of SG_PC_FG for the chaos basis of total degree p in M

@@ -161,6 +161,7 @@ int plan_tile_op(const System& s, int kappa, int elem, size_t smem_max, TilePlan
     op.max_chunk_k = op.max_slots = 0;
     op.max_side = 0;
     op.pairs = op.entries = 0;
+    op.visits = op.s1_steps = op.s2_steps = 0;
     bool ok = true;
     size_t gi = 0;
     while (gi < groups.size() && ok) {
@@ -201,10 +202,31 @@ int plan_tile_op(const System& s, int kappa, int elem, size_t smem_max, TilePlan
       // side table of the chunk (layout in k_apply_tile.cuh): union lists, the stage-1 pieces
       // and stage-2 runs of each warp, the entries sorted by a
       const int ng = (int)op.gdesc.size() - g0;
-      // stage 1: split the groups' union lists into pieces of about equal cost per warp (cost of
-      // a union entry: its 9 X loads plus 10 per pair it forms)
+      // stage 1: split the groups' union lists into pieces of about equal cost per warp
       std::vector<std::vector<int4>> pw(kWarps);
-      {
+      if (elem == 4) {
+        // FP32 forms every k of a group for each union entry, so every entry costs the same: the
+        // union entries in group order, cut into eight contiguous ranges of at most
+        // ceil(entries / 8) each (a range that spans groups is one piece per group)
+        const int total = (int)ul.size();
+        const int per = std::max(1, (total + kWarps - 1) / kWarps);
+        int wk = 0, filled = 0;
+        for (int g = 0; g < ng; ++g) {
+          const int4 gd = op.gdesc[g0 + g];
+          int u = 0;
+          while (u < gd.y) {
+            if (filled >= per && wk < kWarps - 1) {
+              ++wk;
+              filled = 0;
+            }
+            const int take = wk == kWarps - 1 ? gd.y - u : std::min(gd.y - u, per - filled);
+            pw[wk].push_back(make_int4(g, u, take, 0));
+            u += take;
+            filled += take;
+          }
+        }
+      } else {
+        // FP64 forms only the needed pairs: cost of a union entry = its 9 X loads plus 10 per pair
         double total = 0.0;
         std::vector<double> cost(ul.size());
         for (size_t u = 0; u < ul.size(); ++u) {
@@ -240,8 +262,30 @@ int plan_tile_op(const System& s, int kappa, int elem, size_t smem_max, TilePlan
           nent += perA[a].size();
         }
       }
-      std::vector<int> s2ptr(kWarps + 1, (int)runs.size());
-      {
+      // FP32: sixteen workers (the half-warps) take contiguous ranges of whole runs with about
+      // equal entry counts; s2ptr holds their entry offsets.  FP64: the warps take ranges of runs
+      // with about equal cost; s2ptr holds their run offsets.
+      const int nworkers = elem == 4 ? 2 * kWarps : kWarps;
+      std::vector<int> s2ptr(nworkers + 1, elem == 4 ? (int)nent : (int)runs.size());
+      if (elem == 4) {
+        const double per = (double)nent / nworkers;
+        int wk = 0;
+        s2ptr[0] = 0;
+        // cut at the run boundary nearest to each target
+        for (size_t r = 0; r < runs.size(); ++r) {
+          while (wk < nworkers - 1 && runs[r].z > per * (wk + 1)) {
+            const double before = per * (wk + 1) - runs[r].y, after = runs[r].z - per * (wk + 1);
+            if (before <= after) {
+              s2ptr[++wk] = runs[r].y;
+            } else {
+              s2ptr[++wk] = runs[r].z;
+              break;
+            }
+          }
+        }
+        while (wk < nworkers - 1) s2ptr[++wk] = (int)nent;
+        s2ptr[nworkers] = (int)nent;
+      } else {
         const double per = (double)(nent + runs.size()) / kWarps;
         double acc = 0.0;
         int wk = 0;
@@ -252,6 +296,11 @@ int plan_tile_op(const System& s, int kappa, int elem, size_t smem_max, TilePlan
         }
         while (wk < kWarps - 1) s2ptr[++wk] = (int)runs.size();
         s2ptr[kWarps] = (int)runs.size();
+        // a warp takes its runs four at a time for as many steps as the longest of the four:
+        // runs of equal length side by side waste no steps
+        for (int wk2 = 0; wk2 < kWarps; ++wk2)
+          std::stable_sort(runs.begin() + s2ptr[wk2], runs.begin() + s2ptr[wk2 + 1],
+                           [](const int4& a, const int4& b) { return a.z - a.y > b.z - b.y; });
       }
       std::vector<int> s1ptr(kWarps + 1, 0);
       std::vector<int4> s1;
@@ -264,20 +313,22 @@ int plan_tile_op(const System& s, int kappa, int elem, size_t smem_max, TilePlan
       const size_t off_s1ptr = round16(off_ul + 8 * ul.size());
       const size_t off_s1 = round16(off_s1ptr + 4 * (kWarps + 1));
       const size_t off_s2ptr = round16(off_s1 + 16 * s1.size());
-      const size_t off_s2 = round16(off_s2ptr + 4 * (kWarps + 1));
+      const size_t off_s2 = round16(off_s2ptr + 4 * (size_t)(nworkers + 1));
       const size_t off_ent = round16(off_s2 + 16 * runs.size());
-      const size_t bytes = round16(off_ent + esize * nent);
+      const size_t off_gd = round16(off_ent + esize * nent);
+      const size_t bytes = round16(off_gd + 16 * (size_t)ng);
       const size_t base = op.side.size();
       op.side.resize(base + bytes, 0);
       unsigned char* sb = op.side.data() + base;
       const int hdr[8] = {(int)off_ul, (int)off_s1ptr, (int)off_s1, (int)off_s2ptr, (int)off_s2,
-                          (int)off_ent, 0, 0};
+                          (int)off_ent, (int)off_gd, 0};
       std::memcpy(sb, hdr, sizeof(hdr));
       std::memcpy(sb + off_ul, ul.data(), 8 * ul.size());
       std::memcpy(sb + off_s1ptr, s1ptr.data(), 4 * s1ptr.size());
       std::memcpy(sb + off_s1, s1.data(), 16 * s1.size());
       std::memcpy(sb + off_s2ptr, s2ptr.data(), 4 * s2ptr.size());
       std::memcpy(sb + off_s2, runs.data(), 16 * runs.size());
+      std::memcpy(sb + off_gd, op.gdesc.data() + g0, 16 * (size_t)ng);
       size_t q = 0;
       for (int a = 0; a < P; ++a)
         for (auto& e : perA[a]) {
@@ -286,13 +337,42 @@ int plan_tile_op(const System& s, int kappa, int elem, size_t smem_max, TilePlan
             std::memcpy(dst, &e.first, 4);
             std::memcpy(dst + 8, &e.second, 8);
           } else {
+            // slot | a << 16 | (last entry of the run) << 24
             const float gf = (float)e.second;
-            std::memcpy(dst, &e.first, 4);
+            const int packed = e.first | a << 16 | (&e == &perA[a].back() ? 1 << 24 : 0);
+            std::memcpy(dst, &packed, 4);
             std::memcpy(dst + 4, &gf, 4);
           }
           ++q;
         }
       op.entries += (long long)nent;
+      op.visits += (long long)ul.size();
+      {
+        const int st1 = 2;
+        long long w1 = 0, w2 = 0;
+        for (int wk2 = 0; wk2 < kWarps; ++wk2) {
+          long long a1 = 0, a2 = 0;
+          for (const int4& pc : pw[wk2]) a1 += (pc.z + st1 - 1) / st1 + 1;
+          if (elem == 4) {
+            // the half-warps step through their entries side by side
+            a2 = std::max(s2ptr[2 * wk2 + 1] - s2ptr[2 * wk2], s2ptr[2 * wk2 + 2] - s2ptr[2 * wk2 + 1]);
+          } else {
+            auto blk = [&](int b0, int b1) {  // longest run of runs [b0, b1)
+              int l = 0;
+              for (int r = b0; r < b1 && r < s2ptr[wk2 + 1]; ++r) l = std::max(l, runs[r].z - runs[r].y);
+              return l;
+            };
+            const int r0 = s2ptr[wk2], r1 = s2ptr[wk2 + 1];
+            int rb = r0;
+            for (; rb + 4 <= r1; rb += 4) a2 += blk(rb, rb + 4) + 1;
+            for (; rb < r1; ++rb) a2 += blk(rb, rb + 1) + 1;
+          }
+          w1 = std::max(w1, a1);
+          w2 = std::max(w2, a2);
+        }
+        op.s1_steps += w1;
+        op.s2_steps += w2;
+      }
       const int nk = (int)op.kperm.size() - k0;
       op.cdesc.push_back(make_int4(k0, nk, g0, (int)op.gdesc.size() - g0));
       op.cxdesc.push_back(make_int4((int)(base / 16), (int)bytes, (int)off_s2, (int)off_ent));
@@ -338,8 +418,16 @@ int verify_tile_plan(const System& s, const TilePlan& pl) {
     const unsigned char* sb = pl.side.data() + (size_t)cx.x * 16;
     int hdr[8];
     rd(sb, 0, hdr, sizeof(hdr));
-    for (int i = 0; i < 6; ++i)
+    for (int i = 0; i < 7; ++i)
       if (hdr[i] % 16 || hdr[i] > cx.y) return fail(SG_ERR_ARG, "plan: header");
+    if ((size_t)hdr[6] + 16 * (size_t)cd.w > (size_t)cx.y) return fail(SG_ERR_ARG, "plan: groups");
+    for (int g = 0; g < cd.w; ++g) {
+      int4 gd;
+      rd(sb, hdr[6] + 16 * (size_t)g, &gd, 16);
+      const int4 want_gd = pl.gdesc[cd.z + g];
+      if (gd.x != want_gd.x || gd.y != want_gd.y || gd.z != want_gd.z || gd.w != want_gd.w)
+        return fail(SG_ERR_ARG, "plan: group descriptor");
+    }
     // union lists: every entry of every group exactly once in the warps' pieces
     std::vector<std::vector<char>> covered(cd.w);
     for (int g = 0; g < cd.w; ++g) covered[g].assign(pl.gdesc[cd.z + g].y, 0);
@@ -384,10 +472,48 @@ int verify_tile_plan(const System& s, const TilePlan& pl) {
     }
     if ((int)slot_kb.size() > pl.max_slots || (size_t)pl.max_slots * 32 > (size_t)pl.tbuf_elems)
       return fail(SG_ERR_ARG, "plan: T buffer");
-    // stage-2 runs: one per a at most, covering the entries once
+    std::vector<char> a_seen(P, 0);
+    if (pl.elem == 4) {
+      // FP32 stage 2: sixteen entry ranges of whole runs; a run is the consecutive entries of one
+      // a (one run per a at most), the last flagged
+      int s2p[17];
+      rd(sb, hdr[3], s2p, sizeof(s2p));
+      if (s2p[0] != 0) return fail(SG_ERR_ARG, "plan: stage-2 ranges");
+      for (int w = 0; w < 16; ++w)
+        if (s2p[w + 1] < s2p[w]) return fail(SG_ERR_ARG, "plan: stage-2 ranges");
+      const int nent = s2p[16];
+      if ((size_t)hdr[5] + 8 * (size_t)nent > (size_t)cx.y) return fail(SG_ERR_ARG, "plan: entry out of range");
+      std::vector<char> starts(nent + 1, 0);
+      for (int w = 0; w <= 16; ++w) starts[s2p[w]] = 1;
+      bool open = false;
+      int cur_a = -1;
+      for (int q = 0; q < nent; ++q) {
+        int packed;
+        float gf;
+        rd(sb, hdr[5] + 8 * (size_t)q, &packed, 4);
+        rd(sb, hdr[5] + 8 * (size_t)q + 4, &gf, 4);
+        const int slot = packed & 0xffff, a = packed >> 16 & 0xff, last = packed >> 24;
+        if (last > 1 || a >= P) return fail(SG_ERR_ARG, "plan: entry fields");
+        if (starts[q] && open) return fail(SG_ERR_ARG, "plan: range cuts a run");
+        if (!open) {
+          if (a_seen[a]++) return fail(SG_ERR_ARG, "plan: run output");
+          open = true;
+          cur_a = a;
+        } else if (a != cur_a) {
+          return fail(SG_ERR_ARG, "plan: run not flagged");
+        }
+        if (last) open = false;
+        if (slot >= (int)slot_kb.size()) return fail(SG_ERR_ARG, "plan: entry slot");
+        auto key = std::array<int, 3>{slot_kb[slot][0], a, slot_kb[slot][1]};
+        if (got.count(key)) return fail(SG_ERR_ARG, "plan: entry placed twice");
+        got[key] = gf;
+      }
+      if (open) return fail(SG_ERR_ARG, "plan: last run not flagged");
+      continue;
+    }
+    // FP64 stage-2 runs: one per a at most, covering the entries once
     int s2ptr[9];
     rd(sb, hdr[3], s2ptr, sizeof(s2ptr));
-    std::vector<char> a_seen(P, 0);
     if (s2ptr[0] != 0) return fail(SG_ERR_ARG, "plan: stage-2 lists");
     for (int w = 0; w < 8; ++w) {
       if (s2ptr[w + 1] < s2ptr[w]) return fail(SG_ERR_ARG, "plan: stage-2 lists");
@@ -456,8 +582,6 @@ int build_tile_op(System& s, TileOp& op, int kappa, int elem, size_t smem_max, c
   SG_TRY(op.chunk.upload(pl.cdesc, st));
   SG_TRY(op.chunkx.alloc(pl.cxdesc.size()));
   SG_TRY(op.chunkx.upload(pl.cxdesc, st));
-  SG_TRY(op.group.alloc(pl.gdesc.size()));
-  SG_TRY(op.group.upload(pl.gdesc, st));
   SG_TRY(op.side.alloc(pl.side.size()));
   SG_TRY(op.side.upload(pl.side, st));
   // the tiled stack
@@ -488,7 +612,6 @@ int build_tile_op(System& s, TileOp& op, int kappa, int elem, size_t smem_max, c
 void free_tile_op(TileOp& op) {
   op.chunk.release();
   op.chunkx.release();
-  op.group.release();
   op.side.release();
   op.stack.release();
   op.stack32.release();

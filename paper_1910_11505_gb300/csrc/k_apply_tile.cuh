@@ -22,6 +22,12 @@
 // entries of those a, in registers across chunks.  The tile's Y rows are written at the end
 // through shared memory, coalesced.  Boundary rows (identity rows of K) are Y = alpha X + beta B.
 //
+// FP32 runs both stages in packed FP32x2 arithmetic: a lane owns two adjacent rows and the two
+// half-warps take different union entries (stage 1) or entry ranges (stage 2), which halves the
+// load and multiply-add instructions per row; the stencil product is taken in difference form
+// (the row sum in the centre slot, see stencil_diffs_f32).  Its work is split at setup into equal
+// contiguous shares (eight per chunk in stage 1, sixteen in stage 2).  FP64 keeps one row per lane.
+//
 // Every wait on an mbarrier is bounded: after kWaitLimit polls the kernel raises the error word,
 // waits (bounded again) for its own copies in flight and returns with NaN in the rows it owns.
 #pragma once
@@ -65,27 +71,149 @@ struct TileArgs {
   int abytes_slot, sbytes_slot, tbuf_elems;
 };
 
+// ---- FP32 stages in packed FP32x2 arithmetic (fma.rn.f32x2: one instruction for two rows)
+//
+// In FP32 a lane owns the row pair (2 lp, 2 lp + 1) of the tile, lp = lane mod 16, and the two
+// half-warps work on different items (union entries in stage 1, runs in stage 2), so one warp
+// instruction still serves 32 row-items but the loads of a row pair are single 8-byte accesses
+// and the multiply-adds are packed.  Row 2 lp reads its stencil columns at slab offsets 2 lp ..
+// 2 lp + 2 and row 2 lp + 1 at 2 lp + 1 .. 2 lp + 3, so two aligned 8-byte loads per grid line
+// give both rows' three values.
+
+__device__ __forceinline__ float2 ld2(const float* p) { return *reinterpret_cast<const float2*>(p); }
+__device__ __forceinline__ void st2(float* p, float2 v) { *reinterpret_cast<float2*>(p) = v; }
+
+// The stencil values of both rows for chaos index b (xp = the b slab + 2 lp) in difference form:
+// d[4] = x_c, d[e] = x_e - x_c otherwise (each difference rounded once), so that
+// sum_e A_e x_e = (sum_e A_e) x_c + sum_{e != c} A_e (x_e - x_c) with the row sum stored in the
+// centre slot.  A stiffness row sums to about zero, so the direct form cancels ~1/h^2-sized
+// terms in FP32, while the differences of a smooth x are small and their products carry no such
+// cancellation (the mixed solver's refinement then gains more digits per cycle).
+__device__ __forceinline__ void stencil_diffs_f32(const float* xp, float2 (&d)[9]) {
+  float2 p0[3], p1[3];
+#pragma unroll
+  for (int dy = 0; dy < 3; ++dy) {
+    p0[dy] = ld2(xp + dy * kSlab);
+    p1[dy] = ld2(xp + dy * kSlab + 2);
+  }
+  const float2 xc = make_float2(p0[1].y, p1[1].x);
+  const float2 m1 = make_float2(-1.0f, -1.0f);
+#pragma unroll
+  for (int dy = 0; dy < 3; ++dy) {
+    d[dy * 3 + 0] = __ffma2_rn(xc, m1, p0[dy]);
+    d[dy * 3 + 2] = __ffma2_rn(xc, m1, p1[dy]);
+    if (dy != 1) d[dy * 3 + 1] = make_float2(p0[dy].y - xc.x, p1[dy].x - xc.y);
+  }
+  d[4] = xc;
+}
+
+// T for the k of a group that need this b (mask bit j for the group's j-th k): the row sum times
+// x_c plus the eight stiffness values times the differences, as two dependent chains per k (the
+// lines above and below the centre) joined at the end.
+template <int KAPPA>
+__device__ __forceinline__ void pair_products_f32(const float2 (&a)[KAPPA][9],
+                                                  const float2 (&d)[9], int mask, int sl,
+                                                  float* Tp) {
+#pragma unroll
+  for (int j = 0; j < KAPPA; ++j) {
+    float2 t0 = __fmul2_rn(a[j][4], d[4]);
+    float2 t1 = __fmul2_rn(a[j][6], d[6]);
+#pragma unroll
+    for (int e = 0; e < 4; ++e) t0 = __ffma2_rn(a[j][e], d[e], t0);
+    t1 = __ffma2_rn(a[j][5], d[5], t1);
+    t1 = __ffma2_rn(a[j][7], d[7], t1);
+    t1 = __ffma2_rn(a[j][8], d[8], t1);
+    if (mask >> j & 1)
+      st2(Tp + (size_t)(sl + __popc(mask & ((1 << j) - 1))) * kTW, __fadd2_rn(t0, t1));
+  }
+}
+
+// Stage 1 of one piece (count entries of the union list gl of group gd): half-warp h takes the
+// entries u + h, u = 0, 2, 4, ...  An idle half (odd count) reads entry 0 and stores nothing.
+template <int KAPPA>
+__device__ __forceinline__ void stage1_piece_f32(int count, int4 gd, const float* Ab,
+                                                 const int2* gl, const float* Xs, float* Ts,
+                                                 int lane) {
+  const int half = lane >> 4, lp = lane & 15;
+  float2 a[KAPPA][9];
+#pragma unroll
+  for (int j = 0; j < KAPPA; ++j)
+#pragma unroll
+    for (int e = 0; e < 9; ++e)
+      a[j][e] = j < gd.w ? ld2(Ab + ((size_t)(gd.z + j) * 9 + e) * kTW + 2 * lp)
+                         : make_float2(0.0f, 0.0f);
+  const float* xl = Xs + 2 * lp;
+  float* Tp = Ts + 2 * lp;
+#pragma unroll 2
+  for (int u = 0; u < count; u += 2) {
+    const int q = u + half;
+    const int2 e = gl[q < count ? q : 0];
+    float2 d[9];
+    stencil_diffs_f32(xl + (e.x & 0xffff) * (3 * kSlab), d);
+    pair_products_f32<KAPPA>(a, d, q < count ? (e.x >> 16) : 0, e.y, Tp);
+  }
+}
+
+// Stage 2 of one half-warp: its entries [q0, q1) (whole runs, in order of a; packed slot | a << 16
+// | last << 24) accumulated per row pair and added to Y[a] at the last entry of each run.  The
+// two halves of a warp step side by side for as many steps as the longer range.
+__device__ __forceinline__ void stage2_range_f32(int q0, int q1, const TEnt<float>* ent,
+                                                 const float* Ts, float* Ys, int lane) {
+  const int lp = lane & 15;
+  const float* Tp = Ts + 2 * lp;
+  float* Yp = Ys + 2 * lp;
+  const int n = q1 - q0;
+  const int steps = max(n, __shfl_xor_sync(0xffffffffu, n, 16));
+  float2 acc = make_float2(0.0f, 0.0f);
+  for (int t = 0; t < steps; t += 2) {
+    // two entries per step: their loads go before either product
+    const bool ok0 = t < n, ok1 = t + 1 < n;
+    // (an idle half reads entry 0 of the chunk and T slot 0, both in range, and uses neither)
+    const TEnt<float> f0 = ent[ok0 ? q0 + t : 0];
+    const TEnt<float> f1 = ent[ok1 ? q0 + t + 1 : 0];
+    const float2 t0 = ld2(Tp + (size_t)(ok0 ? f0.slot & 0xffff : 0) * kTW);
+    const float2 t1 = ld2(Tp + (size_t)(ok1 ? f1.slot & 0xffff : 0) * kTW);
+    if (ok0) {
+      acc = __ffma2_rn(make_float2(f0.g, f0.g), t0, acc);
+      if (f0.slot >> 24) {
+        float* yp = Yp + (size_t)(f0.slot >> 16 & 0xff) * kTW;
+        st2(yp, __fadd2_rn(ld2(yp), acc));
+        acc = make_float2(0.0f, 0.0f);
+      }
+    }
+    if (ok1) {
+      acc = __ffma2_rn(make_float2(f1.g, f1.g), t1, acc);
+      if (f1.slot >> 24) {
+        float* yp = Yp + (size_t)(f1.slot >> 16 & 0xff) * kTW;
+        st2(yp, __fadd2_rn(ld2(yp), acc));
+        acc = make_float2(0.0f, 0.0f);
+      }
+    }
+  }
+}
+
 // Side table of one chunk (16-byte aligned sections, offsets in the header, bytes):
-//   int hdr[8]   = {off_ul, off_s1ptr, off_s1, off_s2ptr, off_s2, off_ent, 0, 0}
+//   int hdr[8]   = {off_ul, off_s1ptr, off_s1, off_s2ptr, off_s2, off_ent, off_gd, 0}
 //   int2 ul[]    union lists of the chunk's groups: (b | mask << 16, first T slot)
 //   int s1ptr[9] per-warp ranges of stage-1 pieces; int4 s1[] = {group, first entry, count, 0}
 //   int s2ptr[9] per-warp ranges of stage-2 runs;   int4 s2[] = {a, first entry, end entry, 0}
 //   TEnt ent[]   stage-2 entries (T slot, G_k[a,b]) sorted by a
+//   int4 gd[]    the chunk's groups: {union list start, length, first k position, k count}
 // The pieces and runs are split over the warps at setup so every warp gets about the same work,
 // and each output a of a chunk belongs to one warp's run, so Y accumulates without conflicts.
 template <typename T, int KAPPA, int MINB>
 __global__ void __launch_bounds__(kWarps * 32, MINB) sg_apply_tile_kernel(
     TileArgs d, const int4* __restrict__ chunk, const int4* __restrict__ chunkx,
-    const int4* __restrict__ group, const unsigned char* __restrict__ side,
+    const unsigned char* __restrict__ side,
     const T* __restrict__ stack, const T* __restrict__ X, T* __restrict__ Y, T alpha,
     const T* __restrict__ B, T beta, const int* __restrict__ done, int* __restrict__ err) {
   if (done != nullptr && *done) return;
   extern __shared__ __align__(128) unsigned char smem_raw[];
   unsigned long long* bar = reinterpret_cast<unsigned long long*>(smem_raw);  // 2 barriers
   int* s_fail = reinterpret_cast<int*>(smem_raw + 16);
-  unsigned char* Aslot[2] = {smem_raw + 128, smem_raw + 128 + d.abytes_slot};
-  unsigned char* Sslot[2] = {smem_raw + 128 + 2 * (size_t)d.abytes_slot,
-                             smem_raw + 128 + 2 * (size_t)d.abytes_slot + d.sbytes_slot};
+  // the ring slots are addressed as smem_raw + offset (not through an array of pointers), so
+  // that every access to them compiles to a shared-memory access
+  const unsigned a_base = 128, s_base = 128 + 2 * (unsigned)d.abytes_slot;
   T* Ts = reinterpret_cast<T*>(smem_raw + 128 + 2 * (size_t)d.abytes_slot + 2 * (size_t)d.sbytes_slot);
   T* Ys = Ts + d.tbuf_elems;              // P x 32 accumulators of the tile
   T* Xs = Ys + (size_t)d.P * kTW;
@@ -107,8 +235,10 @@ __global__ void __launch_bounds__(kWarps * 32, MINB) sg_apply_tile_kernel(
     const int4 cd = chunk[c], cx = chunkx[c];
     const unsigned abytes = (unsigned)((size_t)cd.y * 9 * kTW * sizeof(T));
     mbar_expect_tx(&bar[slot], abytes + (unsigned)cx.y);
-    bulk_g2s(Aslot[slot], stack + (size_t)t * d.kstride + (size_t)cd.x * 9 * kTW, abytes, &bar[slot]);
-    bulk_g2s(Sslot[slot], side + (size_t)cx.x * 16, (unsigned)cx.y, &bar[slot]);
+    bulk_g2s(smem_raw + a_base + slot * d.abytes_slot,
+             stack + (size_t)t * d.kstride + (size_t)cd.x * 9 * kTW, abytes, &bar[slot]);
+    bulk_g2s(smem_raw + s_base + slot * d.sbytes_slot, side + (size_t)cx.x * 16, (unsigned)cx.y,
+             &bar[slot]);
   };
 
   long long it = 0;          // work items of this CTA so far
@@ -150,18 +280,29 @@ __global__ void __launch_bounds__(kWarps * 32, MINB) sg_apply_tile_kernel(
         failed = true;
         break;
       }
-      const T* Ab = reinterpret_cast<const T*>(Aslot[slot]);
-      const unsigned char* Sb = Sslot[slot];
+      const T* Ab = reinterpret_cast<const T*>(smem_raw + a_base + slot * d.abytes_slot);
+      const unsigned char* Sb = smem_raw + s_base + slot * d.sbytes_slot;
       const int* hdr = reinterpret_cast<const int*>(Sb);
+      const int4* gdl = reinterpret_cast<const int4*>(Sb + hdr[6]);
       const int4 cd = chunk[c];
-      // ---- stage 1: this warp's pieces of the groups' union lists, two b per step
-      {
+      // ---- stage 1: this warp's pieces of the groups' union lists
+      if constexpr (sizeof(T) == 4) {
         const int2* ul = reinterpret_cast<const int2*>(Sb + hdr[0]);
         const int* s1ptr = reinterpret_cast<const int*>(Sb + hdr[1]);
         const int4* s1 = reinterpret_cast<const int4*>(Sb + hdr[2]);
         for (int pc = s1ptr[w]; pc < s1ptr[w + 1]; ++pc) {
           const int4 piece = s1[pc];
-          const int4 gd = group[cd.z + piece.x];  // union start, length, first k position, k count
+          const int4 gd = gdl[piece.x];
+          stage1_piece_f32<KAPPA>(piece.z, gd, Ab, ul + gd.x + piece.y, Xs, Ts, lane);
+        }
+      } else {
+        // FP64: one row per lane, two b per step
+        const int2* ul = reinterpret_cast<const int2*>(Sb + hdr[0]);
+        const int* s1ptr = reinterpret_cast<const int*>(Sb + hdr[1]);
+        const int4* s1 = reinterpret_cast<const int4*>(Sb + hdr[2]);
+        for (int pc = s1ptr[w]; pc < s1ptr[w + 1]; ++pc) {
+          const int4 piece = s1[pc];
+          const int4 gd = gdl[piece.x];  // union start, length, first k position, k count
           T a[KAPPA][9];
 #pragma unroll
           for (int j = 0; j < KAPPA; ++j) {
@@ -174,17 +315,15 @@ __global__ void __launch_bounds__(kWarps * 32, MINB) sg_apply_tile_kernel(
             }
           }
           const int2* gl = ul + gd.x + piece.y;
-          // T for the k of the group that need this b.  Each 9-term sum runs as three partial
-          // sums over the stencil lines (a short dependency chain).  In FP32 every k of the group
-          // is computed and only the needed ones stored, so the products of several k and b are
-          // independent and overlap; in FP64 only the needed ones are computed (the FP64 pipe,
-          // not latency, bounds that kernel on this GPU).
+          // T for the k of the group that need this b, each 9-term sum as three partial sums
+          // over the stencil lines (a short dependency chain); only the needed k are computed
+          // (the FP64 pipe, not latency, bounds this form on this GPU)
           auto pairs_of = [&](int bm, int sl, const T* xv) {
             const int mask = bm >> 16;
 #pragma unroll
             for (int j = 0; j < KAPPA; ++j) {
               const bool need = mask & (1 << j);
-              if (sizeof(T) == 8 && !need) continue;
+              if (!need) continue;
               T s0 = a[j][0] * xv[0], s1 = a[j][3] * xv[3], s2 = a[j][6] * xv[6];
               s0 = fma(a[j][1], xv[1], s0);
               s1 = fma(a[j][4], xv[4], s1);
@@ -193,18 +332,6 @@ __global__ void __launch_bounds__(kWarps * 32, MINB) sg_apply_tile_kernel(
               s1 = fma(a[j][5], xv[5], s1);
               s2 = fma(a[j][8], xv[8], s2);
               if (need) Ts[(size_t)(sl + __popc(mask & ((1 << j) - 1))) * kTW + lane] = (s0 + s1) + s2;
-            }
-          };
-          // FP32: the stencil product in difference form, sum_e A_e x_e =
-          // (sum_e A_e) x_c + sum_{e != c} A_e (x_e - x_c), the row sum stored in the centre slot:
-          // a stiffness row sums to about zero, so the direct form cancels ~1/h^2-sized terms in
-          // FP32, while the differences of a smooth x are small and their products carry no such
-          // cancellation (the mixed solver's refinement then gains more digits per cycle)
-          auto diff_form = [&](T* xv) {
-            if (sizeof(T) == 4) {
-#pragma unroll
-              for (int e = 0; e < 9; ++e)
-                if (e != 4) xv[e] -= xv[4];
             }
           };
           int u = 0;
@@ -221,8 +348,6 @@ __global__ void __launch_bounds__(kWarps * 32, MINB) sg_apply_tile_kernel(
                 x0v[dy * 3 + dx] = xp0[dy * kSlab + dx];
                 x1v[dy * 3 + dx] = xp1[dy * kSlab + dx];
               }
-            diff_form(x0v);
-            diff_form(x1v);
             pairs_of(e0.x, e0.y, x0v);
             pairs_of(e1.x, e1.y, x1v);
           }
@@ -235,14 +360,18 @@ __global__ void __launch_bounds__(kWarps * 32, MINB) sg_apply_tile_kernel(
             for (int dy = 0; dy < 3; ++dy)
 #pragma unroll
               for (int dx = 0; dx < 3; ++dx) x0v[dy * 3 + dx] = xp0[dy * kSlab + dx];
-            diff_form(x0v);
             pairs_of(e0.x, e0.y, x0v);
           }
         }
       }
       __syncthreads();
       // ---- stage 2: this warp's runs: Y[a, row] += sum over the run's entries of G T[slot]
-      {
+      if constexpr (sizeof(T) == 4) {
+        const int* s2ptr = reinterpret_cast<const int*>(Sb + hdr[3]);
+        const int wk = 2 * w + (lane >> 4);
+        stage2_range_f32(s2ptr[wk], s2ptr[wk + 1],
+                         reinterpret_cast<const TEnt<float>*>(Sb + hdr[5]), Ts, Ys, lane);
+      } else {
         const int* s2ptr = reinterpret_cast<const int*>(Sb + hdr[3]);
         const int4* s2 = reinterpret_cast<const int4*>(Sb + hdr[4]);
         const TEnt<T>* ent = reinterpret_cast<const TEnt<T>*>(Sb + hdr[5]);
@@ -360,7 +489,7 @@ int launch_tile_k(const System& s, const TileOp& op, const T* X, T* Y, T alpha, 
   if constexpr (sizeof(T) == 8) stack = op.stack.p;
   else stack = op.stack32.p;
   TimeScope ts(s.timer, sizeof(T) == 8 ? K_APPLY_F64 : K_APPLY_LOWP, st);
-  kern<<<grid, kWarps * 32, op.smem, st>>>(d, op.chunk.p, op.chunkx.p, op.group.p, op.side.p,
+  kern<<<grid, kWarps * 32, op.smem, st>>>(d, op.chunk.p, op.chunkx.p, op.side.p,
                                            stack, X, Y, alpha, B, beta, done, op.err.p);
   return check_launch("sg_apply_tile");
 }

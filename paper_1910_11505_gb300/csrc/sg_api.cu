@@ -1169,8 +1169,8 @@ int sg_tune_plan(int n, int M, int p, int q, int precision, long long smem_max, 
   int row = 0;
   for (int ctas = 1; ctas <= 2; ++ctas)
     for (int kappa : {1, 2, 4}) {
-      long long* o = out + 12 * row++;
-      for (int i = 0; i < 12; ++i) o[i] = 0;
+      long long* o = out + 16 * row++;
+      for (int i = 0; i < 16; ++i) o[i] = 0;
       o[0] = kappa;
       o[1] = ctas;
       TilePlan pl;
@@ -1188,6 +1188,9 @@ int sg_tune_plan(int n, int M, int p, int q, int precision, long long smem_max, 
       o[9] = pl.ngroups;
       o[10] = verify_tile_plan(s, pl) == SG_OK;
       o[11] = (long long)budget;
+      o[12] = pl.visits;
+      o[13] = pl.s1_steps;
+      o[14] = pl.s2_steps;
       set_error("");
     }
   return SG_OK;

@@ -221,15 +221,15 @@ struct Triple {
 
 // Row-tiled operator (k_apply_tile.cu): k permuted into groups of kappa with similar b lists,
 // chunks of at most 8 groups, per group the union b list (b | mask << 16, first slot), per
-// (chunk, a) the stage-2 entries (slot, G), and the stack stored per tile of 32 interior rows of
-// one grid line as [k position][entry][row].
+// (chunk, a) the stage-2 entries (slot, G), the group descriptors in each chunk's side table, and
+// the stack stored per tile of 32 interior rows of one grid line as [k position][entry][row].
 struct TileOp {
   bool ready = false;
   int kappa = 0, elem = 0, ctas = 1, tiles_per_line = 0, ntiles = 0, Pp = 0, Lu = 0;
   int nchunks = 0, ngroups = 0, max_chunk_k = 0, max_slots = 0, apw = 0;
   int abytes_slot = 0, sbytes_slot = 0, tbuf_elems = 0, xslab_elems = 0;
   size_t smem = 0;
-  DBuf<int4> chunk, chunkx, group;
+  DBuf<int4> chunk, chunkx;
   DBuf<unsigned char> side;
   DBuf<int> err;
   DBuf<double> stack;
@@ -246,6 +246,10 @@ struct TilePlan {
   int abytes_slot = 0, sbytes_slot = 0, tbuf_elems = 0, xslab_elems = 0;
   size_t smem = 0, max_side = 0;
   long long pairs = 0, entries = 0;
+  // union entries, and the steps of the slowest warp summed over the chunks (stage 1: steps of
+  // four union entries in FP32, two in FP64, plus one per piece; stage 2: steps of one entry of
+  // four runs side by side, plus one per block of runs)
+  long long visits = 0, s1_steps = 0, s2_steps = 0;
   std::vector<int4> cdesc, cxdesc, gdesc;
   std::vector<int> kperm;
   std::vector<unsigned char> side;

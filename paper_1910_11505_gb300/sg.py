@@ -273,14 +273,15 @@ def sg_op_info(h: SGHandle, sys: int = 0):
 
 def sg_tune_plan(n, M, p, q=0, precision="fp64", smem_max=232448):
     """Host-only plans of the row-tiled operator (see include/sg.h): a list of six dicts with keys
-    kappa, ctas, fits, smem, chunks, max_slots, pairs, entries, k_kept, groups, verified, budget."""
+    kappa, ctas, fits, smem, chunks, max_slots, pairs, entries, k_kept, groups, verified, budget,
+    visits, s1_steps, s2_steps."""
     if isinstance(precision, str):
         precision = PRECISIONS[precision]
-    out = (ctypes.c_longlong * 72)()
+    out = (ctypes.c_longlong * 96)()
     _check(load_library().sg_tune_plan(n, M, p, q, precision, smem_max, out))
     keys = ["kappa", "ctas", "fits", "smem", "chunks", "max_slots", "pairs", "entries", "k_kept",
-            "groups", "verified", "budget"]
-    return [dict(zip(keys, out[12 * i:12 * i + 12])) for i in range(6)]
+            "groups", "verified", "budget", "visits", "s1_steps", "s2_steps"]
+    return [dict(zip(keys, out[16 * i:16 * i + 15])) for i in range(6)]
 
 
 def sg_fg_splits(M, p, rule="paper"):
