@@ -538,7 +538,7 @@ def main():
         d_avg_s = mv32_s if dom == "apply_lowp" else mv64_s
         alg = algorithmic_bytes_apply(nnzA, N, P, L, 4 if dom == "apply_lowp" else 8)
     names = {"apply_lowp": "sg_apply (SG operator, FP32)", "apply_f64": "sg_apply (SG operator, FP64)",
-             "ilu_solve": "fg_lower_kernel / fg_upper_kernel (colour phases of the block ILU(0) "
+             "ilu_solve": "fg_phase_kernel (forward / backward colour phases of the block ILU(0) "
                           "of K, 84 x 84 blocks stored in BF16, FP32 arithmetic, n=256 level)",
              "gs_scatter": "fs_scatter_kernel (later-column Gauss-Seidel coupling, FP32 from the "
                            "BF16 stiffness copy, n=256 level)"}

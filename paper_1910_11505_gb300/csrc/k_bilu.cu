@@ -307,38 +307,35 @@ __global__ void __launch_bounds__(256) fg_factor_kernel(int m, int Q, int c,
 __host__ __device__ constexpr int fg_lanes(int Q) { return Q > 64 ? 128 : Q > 32 ? 64 : 32; }
 
 // Block storage of the solve kernels.  FP32 / FP64 factors: each Q x Q block column-major.
-// BF16 factors: columns in pairs, (r, c) at ((c / 2) * Q + r) * 2 + (c & 1), the column count
-// rounded up to even (Qc) with a zero column, so a lane reads the two values of its row in one
-// 4-byte load.
+// BF16 factors: columns in fours, (r, c) at ((c / 4) * Q + r) * 4 + (c & 3), the column count
+// rounded up to a multiple of four (Qc) with zero columns, so a lane reads four values of its
+// row in one 8-byte load and a warp's load covers 256 contiguous bytes.
 template <typename TV>
-__host__ __device__ constexpr bool fg_paired() { return sizeof(TV) == 2; }
-__host__ __device__ inline int fg_qc(int Q) { return (Q + 1) & ~1; }
+__host__ __device__ constexpr bool fg_quads() { return sizeof(TV) == 2; }
+__host__ __device__ inline int fg_qc(int Q) { return (Q + 3) & ~3; }
 
 // Row r of block blk times the vector v (Qc values, zero-padded): four partial sums.
 template <typename T, typename TV>
 __device__ __forceinline__ T fg_block_row_dot(const TV* __restrict__ blk, int Q, int r,
                                               const T* v) {
   T s0 = T(0), s1 = T(0), s2 = T(0), s3 = T(0);
-  if constexpr (fg_paired<TV>()) {
-    const __nv_bfloat162* b2 = reinterpret_cast<const __nv_bfloat162*>(blk) + r;
-    const int npair = fg_qc(Q) >> 1;
-    int cp = 0;
-    for (; cp + 2 <= npair; cp += 2) {
-      const float2 u0 = __bfloat1622float2(b2[(size_t)cp * Q]);
-      const float2 u1 = __bfloat1622float2(b2[(size_t)(cp + 1) * Q]);
-      s0 += (T)u0.x * v[2 * cp];
-      s1 += (T)u0.y * v[2 * cp + 1];
-      s2 += (T)u1.x * v[2 * cp + 2];
-      s3 += (T)u1.y * v[2 * cp + 3];
-    }
-    if (cp < npair) {
-      const float2 u0 = __bfloat1622float2(b2[(size_t)cp * Q]);
-      s0 += (T)u0.x * v[2 * cp];
-      s1 += (T)u0.y * v[2 * cp + 1];
+  if constexpr (fg_quads<TV>()) {
+    const uint2* b4 = reinterpret_cast<const uint2*>(blk) + r;
+    const int nq = fg_qc(Q) >> 2;
+#pragma unroll 7
+    for (int cq = 0; cq < nq; ++cq) {
+      const uint2 w = b4[(size_t)cq * Q];
+      const float2 u0 = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&w.x));
+      const float2 u1 = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&w.y));
+      s0 += (T)u0.x * v[4 * cq];
+      s1 += (T)u0.y * v[4 * cq + 1];
+      s2 += (T)u1.x * v[4 * cq + 2];
+      s3 += (T)u1.y * v[4 * cq + 3];
     }
   } else {
     const TV* b = blk + r;
     int cc = 0;
+#pragma unroll 2
     for (; cc + 4 <= Q; cc += 4) {
       s0 += (T)b[(size_t)cc * Q] * v[cc];
       s1 += (T)b[(size_t)(cc + 1) * Q] * v[cc + 1];
@@ -350,12 +347,28 @@ __device__ __forceinline__ T fg_block_row_dot(const TV* __restrict__ blk, int Q,
   return (s0 + s1) + (s2 + s3);
 }
 
-// One colour of the forward sweep of a split (fields [f0, f0 + Q) of the N x P arrays):
-// y_i = r_i - sub_i - sum over the lower-colour slots of (L D^-1)_{i,slot} y_nb.  Each node is
-// a group of lanes (lane r: row r of every block, the neighbour's Q values staged in shared
-// memory); neighbours outside the mesh are clamped onto it, their blocks are zero.
-template <typename T, typename TV>
-__global__ void __launch_bounds__(128) fg_lower_kernel(int m, int P, int Q, int f0, int c,
+// Whether neighbour slot sl (0..8, 4 = the node itself) takes part in a phase of colour c: the
+// forward sweep uses the slots of lower colours, the backward sweep the diagonal and the slots
+// of higher colours.  A neighbour's colour follows from the node's parities, so the set is the
+// same for every node of the launch.
+__device__ __forceinline__ bool fg_slot_used(int c, int sl, bool upper) {
+  if (sl == 4) return upper;
+  const int nc = fg_colour((c & 1) + sl % 3 - 1 + 2, (c >> 1) + sl / 3 - 1 + 2);
+  return upper ? nc > c : nc < c;
+}
+
+// One colour of a sweep of a split (fields [f0, f0 + Q) of the N x P arrays).
+//   forward (UPPER = false): y_i = r_i - sub_i - sum over the lower-colour slots of
+//     (L D^-1)_{i,slot} y_nb;
+//   backward (UPPER = true, in place): z_i = D_i^-1 y_i - sum over the higher-colour slots of
+//     (D^-1 U)_{i,slot} z_nb.
+// Each node is a group of lanes (lane r: row r of every block).  The Q values of every slot the
+// phase uses (the node's own y_i included in the backward sweep) are staged in shared memory
+// first, behind one barrier; then each lane streams its rows of those blocks.  Neighbours
+// outside the mesh are clamped onto it, their blocks are zero.  No other node of the colour
+// reads node i, so writing it in place is safe.
+template <typename T, typename TV, bool UPPER>
+__global__ void __launch_bounds__(128) fg_phase_kernel(int m, int P, int Q, int f0, int c,
                                                        const int* __restrict__ cstart_g,
                                                        const TV* __restrict__ fac,
                                                        const T* __restrict__ R,
@@ -363,7 +376,6 @@ __global__ void __launch_bounds__(128) fg_lower_kernel(int m, int P, int Q, int 
                                                        const int* __restrict__ done) {
   if (done != nullptr && *done) return;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  T* vec = reinterpret_cast<T*>(smem_raw);  // nodes per CTA x Q
   const int G = fg_lanes(Q), npc = 128 / G;
   const int g = threadIdx.x / G, r = threadIdx.x % G;
   const int c0 = cstart_g[c], cnt = cstart_g[c + 1] - c0;
@@ -378,69 +390,35 @@ __global__ void __launch_bounds__(128) fg_lower_kernel(int m, int P, int Q, int 
   }
   const int i = x + m * y;
   const int Qc = fg_qc(Q);
-  const size_t QQ = (size_t)Q * (fg_paired<TV>() ? Qc : Q);
+  const size_t QQ = (size_t)Q * (fg_quads<TV>() ? Qc : Q);
   const TV* blocks = fac + (size_t)pos * 9 * QQ;
-  T* v = vec + g * Qc;
-  if (r == 0 && Qc > Q) v[Q] = T(0);
-  T acc = T(0);
-  if (r < Q) acc = R[(size_t)i * P + f0 + r] - (sub != nullptr ? sub[(size_t)i * P + f0 + r] : T(0));
+  T* v = reinterpret_cast<T*>(smem_raw) + (size_t)g * 9 * Qc;  // one vector per used slot
+  int k = 0;
+#pragma unroll
   for (int sl = 0; sl < 9; ++sl) {
-    const int dx = sl % 3 - 1, dy = sl / 3 - 1;
-    if (sl == 4 || fg_colour(x + dx + 2, y + dy + 2) >= c) continue;  // uniform over the CTA
-    const int jx = min(max(x + dx, 0), m - 1), jy = min(max(y + dy, 0), m - 1);
-    const size_t j = (size_t)jx + (size_t)m * jy;
-    for (int t = r; t < Q; t += G) v[t] = Y[j * P + f0 + t];
-    __syncthreads();
-    if (r < Q) acc -= fg_block_row_dot<T, TV>(blocks + sl * QQ, Q, r, v);
-    __syncthreads();
+    if (!fg_slot_used(c, sl, UPPER)) continue;
+    const int jx = min(max(x + sl % 3 - 1, 0), m - 1), jy = min(max(y + sl / 3 - 1, 0), m - 1);
+    const T* src = Y + ((size_t)jx + (size_t)m * jy) * P + f0;
+    for (int t = r; t < Qc; t += G) v[k * Qc + t] = t < Q ? src[t] : T(0);
+    ++k;
   }
-  if (live && r < Q) Y[(size_t)i * P + f0 + r] = acc;
-}
-
-// One colour of the backward sweep, in place: z_i = D_i^-1 y_i - sum over the higher-colour
-// slots of (D^-1 U)_{i,slot} z_nb.  The node's own y_i is staged before any lane writes z_i; no
-// other node of the colour reads it.
-template <typename T, typename TV>
-__global__ void __launch_bounds__(128) fg_upper_kernel(int m, int P, int Q, int f0, int c,
-                                                       const int* __restrict__ cstart_g,
-                                                       const TV* __restrict__ fac, T* Y,
-                                                       const int* __restrict__ done) {
-  if (done != nullptr && *done) return;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  T* vec = reinterpret_cast<T*>(smem_raw);
-  const int G = fg_lanes(Q), npc = 128 / G;
-  const int g = threadIdx.x / G, r = threadIdx.x % G;
-  const int c0 = cstart_g[c], cnt = cstart_g[c + 1] - c0;
-  const int idx = blockIdx.x * npc + g;
-  const bool live = idx < cnt;
-  const int pos = c0 + (live ? idx : cnt - 1);
-  int x, y;
-  {
-    const int cx = c & 1, cy = c >> 1, nx = (m - cx + 1) >> 1, q = pos - c0;
-    y = cy + 2 * (q / nx);
-    x = cx + 2 * (q % nx);
-  }
-  const int i = x + m * y;
-  const int Qc = fg_qc(Q);
-  const size_t QQ = (size_t)Q * (fg_paired<TV>() ? Qc : Q);
-  const TV* blocks = fac + (size_t)pos * 9 * QQ;
-  T* v = vec + g * Qc;
-  if (r == 0 && Qc > Q) v[Q] = T(0);
   T acc = T(0);
-  for (int sl = 4; sl < 13; ++sl) {  // the diagonal first, then slots 0..8 but 4
-    const int s2 = sl % 9;
-    if (sl > 4 && s2 == 4) continue;
-    const int dx = s2 % 3 - 1, dy = s2 / 3 - 1;
-    if (s2 != 4 && fg_colour(x + dx + 2, y + dy + 2) <= c) continue;  // uniform over the CTA
-    const int jx = min(max(x + dx, 0), m - 1), jy = min(max(y + dy, 0), m - 1);
-    const size_t j = (size_t)jx + (size_t)m * jy;
-    for (int t = r; t < Q; t += G) v[t] = Y[j * P + f0 + t];
-    __syncthreads();
-    if (r < Q) {
-      const T part = fg_block_row_dot<T, TV>(blocks + s2 * QQ, Q, r, v);
-      acc = s2 == 4 ? part : acc - part;
+  if (!UPPER && r < Q)
+    acc = R[(size_t)i * P + f0 + r] - (sub != nullptr ? sub[(size_t)i * P + f0 + r] : T(0));
+  __syncthreads();
+  if (r < Q) {
+    unsigned used = 0;
+#pragma unroll
+    for (int sl = 0; sl < 9; ++sl) used |= fg_slot_used(c, sl, UPPER) ? 1u << sl : 0u;
+    // slot sl's vector is the k-th staged one, k = the used slots before it
+    if (UPPER)  // the diagonal first
+      acc = fg_block_row_dot<T, TV>(blocks + 4 * QQ, Q, r, v + (size_t)__popc(used & 15u) * Qc);
+#pragma unroll 1
+    for (int sl = 0; sl < 9; ++sl) {
+      if (sl == 4 || !(used >> sl & 1u)) continue;
+      acc -= fg_block_row_dot<T, TV>(blocks + sl * QQ, Q, r,
+                                     v + (size_t)__popc(used & ((1u << sl) - 1u)) * Qc);
     }
-    __syncthreads();
   }
   if (live && r < Q) Y[(size_t)i * P + f0 + r] = acc;
 }
@@ -455,8 +433,8 @@ __global__ void fg_mask_kernel(size_t N, int P, int f0, const T* __restrict__ D,
     tmp[t] = (int)(t % P) < f0 ? D[t] : T(0);
 }
 
-// FP32 blocks (column-major, Q x Q) -> BF16 blocks in the paired layout (Q x Qc, zero column
-// when Q is odd); one thread per destination element.
+// FP32 blocks (column-major, Q x Q) -> BF16 blocks in the layout of fours (Q x Qc, zero columns
+// up to a multiple of four); one thread per destination element.
 __global__ void fg_round_bf16_kernel(size_t nblocks, int Q, const float* __restrict__ src,
                                      __nv_bfloat16* __restrict__ dst) {
   const int Qc = fg_qc(Q);
@@ -465,7 +443,7 @@ __global__ void fg_round_bf16_kernel(size_t nblocks, int Q, const float* __restr
        t += (size_t)gridDim.x * blockDim.x) {
     const size_t blk = t / per;
     const int o = (int)(t - blk * per);
-    const int cc = 2 * (o / (2 * Q)) + (o & 1), r = (o >> 1) % Q;
+    const int cc = 4 * (o / (4 * Q)) + (o & 3), r = (o >> 2) % Q;
     dst[t] = cc < Q ? __float2bfloat16_rn(src[blk * Q * Q + (size_t)cc * Q + r])
                     : __float2bfloat16_rn(0.0f);
   }
@@ -627,19 +605,19 @@ int fg_apply(System& s, const T* R, T* D, cudaStream_t st, const int* done) {
       sub = B::tmp2(s);
     }
     const int G = fg_lanes(Q), npc = 128 / G;
-    const size_t smem = sizeof(T) * (size_t)npc * fg_qc(Q);
+    const size_t smem = sizeof(T) * (size_t)npc * 9 * fg_qc(Q);
     for (int c = 0; c < 4; ++c) {
       const int cnt = s.cstart_h[c + 1] - s.cstart_h[c];
       if (cnt <= 0) continue;
       TimeScope ts(s.timer, K_ILU_SOLVE, st);
       const int grid = (cnt + npc - 1) / npc;
       if (fac16 != nullptr)
-        fg_lower_kernel<T, __nv_bfloat16><<<grid, 128, smem, st>>>(s.pat.m, s.P, Q, sp.f0, c,
-                                                                   s.cstart.p, fac16, R, sub, D, done);
+        fg_phase_kernel<T, __nv_bfloat16, false><<<grid, 128, smem, st>>>(
+            s.pat.m, s.P, Q, sp.f0, c, s.cstart.p, fac16, R, sub, D, done);
       else
-        fg_lower_kernel<T, T><<<grid, 128, smem, st>>>(s.pat.m, s.P, Q, sp.f0, c, s.cstart.p,
-                                                       fac, R, sub, D, done);
-      SG_TRY(check_launch("fg_lower"));
+        fg_phase_kernel<T, T, false><<<grid, 128, smem, st>>>(s.pat.m, s.P, Q, sp.f0, c,
+                                                              s.cstart.p, fac, R, sub, D, done);
+      SG_TRY(check_launch("fg_phase (forward)"));
     }
     for (int c = 3; c >= 0; --c) {
       const int cnt = s.cstart_h[c + 1] - s.cstart_h[c];
@@ -647,12 +625,13 @@ int fg_apply(System& s, const T* R, T* D, cudaStream_t st, const int* done) {
       TimeScope ts(s.timer, K_ILU_SOLVE, st);
       const int grid = (cnt + npc - 1) / npc;
       if (fac16 != nullptr)
-        fg_upper_kernel<T, __nv_bfloat16><<<grid, 128, smem, st>>>(s.pat.m, s.P, Q, sp.f0, c,
-                                                                   s.cstart.p, fac16, D, done);
+        fg_phase_kernel<T, __nv_bfloat16, true><<<grid, 128, smem, st>>>(
+            s.pat.m, s.P, Q, sp.f0, c, s.cstart.p, fac16, nullptr, nullptr, D, done);
       else
-        fg_upper_kernel<T, T><<<grid, 128, smem, st>>>(s.pat.m, s.P, Q, sp.f0, c, s.cstart.p, fac,
-                                                       D, done);
-      SG_TRY(check_launch("fg_upper"));
+        fg_phase_kernel<T, T, true><<<grid, 128, smem, st>>>(s.pat.m, s.P, Q, sp.f0, c,
+                                                             s.cstart.p, fac, nullptr, nullptr, D,
+                                                             done);
+      SG_TRY(check_launch("fg_phase (backward)"));
     }
   }
   return SG_OK;
