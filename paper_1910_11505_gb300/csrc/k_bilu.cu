@@ -303,8 +303,12 @@ __global__ void __launch_bounds__(256) fg_factor_kernel(int m, int Q, int c,
   }
 }
 
-// Lanes per node in the solve kernels (the rows of a block) and nodes per 128-thread CTA.
-__host__ __device__ constexpr int fg_lanes(int Q) { return Q > 64 ? 128 : Q > 32 ? 64 : 32; }
+// Lanes per node in the solve kernels (the rows of a block, in whole warps) and threads per CTA:
+// one node of 3 or 4 warps, else 128 threads holding 2 or 4 nodes.
+__host__ __device__ constexpr int fg_lanes(int Q) {
+  return Q > 96 ? 128 : Q > 64 ? 96 : Q > 32 ? 64 : 32;
+}
+__host__ __device__ constexpr int fg_cta_threads(int Q) { return fg_lanes(Q) == 96 ? 96 : 128; }
 
 // Block storage of the solve kernels.  FP32 / FP64 factors: each Q x Q block column-major.
 // BF16 factors: columns in fours, (r, c) at ((c / 4) * Q + r) * 4 + (c & 3), the column count
@@ -322,7 +326,7 @@ __device__ __forceinline__ T fg_block_row_dot(const TV* __restrict__ blk, int Q,
   if constexpr (fg_quads<TV>()) {
     const uint2* b4 = reinterpret_cast<const uint2*>(blk) + r;
     const int nq = fg_qc(Q) >> 2;
-#pragma unroll 7
+#pragma unroll 21  // all of a row's loads in flight at once for up to 84 fields
     for (int cq = 0; cq < nq; ++cq) {
       const uint2 w = b4[(size_t)cq * Q];
       const float2 u0 = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&w.x));
@@ -376,7 +380,7 @@ __global__ void __launch_bounds__(128) fg_phase_kernel(int m, int P, int Q, int 
                                                        const int* __restrict__ done) {
   if (done != nullptr && *done) return;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  const int G = fg_lanes(Q), npc = 128 / G;
+  const int G = fg_lanes(Q), npc = fg_cta_threads(Q) / G;
   const int g = threadIdx.x / G, r = threadIdx.x % G;
   const int c0 = cstart_g[c], cnt = cstart_g[c + 1] - c0;
   const int idx = blockIdx.x * npc + g;
@@ -604,7 +608,7 @@ int fg_apply(System& s, const T* R, T* D, cudaStream_t st, const int* done) {
                                  0.0f, st, done));
       sub = B::tmp2(s);
     }
-    const int G = fg_lanes(Q), npc = 128 / G;
+    const int G = fg_lanes(Q), nthr = fg_cta_threads(Q), npc = nthr / G;
     const size_t smem = sizeof(T) * (size_t)npc * 9 * fg_qc(Q);
     for (int c = 0; c < 4; ++c) {
       const int cnt = s.cstart_h[c + 1] - s.cstart_h[c];
@@ -612,10 +616,10 @@ int fg_apply(System& s, const T* R, T* D, cudaStream_t st, const int* done) {
       TimeScope ts(s.timer, K_ILU_SOLVE, st);
       const int grid = (cnt + npc - 1) / npc;
       if (fac16 != nullptr)
-        fg_phase_kernel<T, __nv_bfloat16, false><<<grid, 128, smem, st>>>(
+        fg_phase_kernel<T, __nv_bfloat16, false><<<grid, nthr, smem, st>>>(
             s.pat.m, s.P, Q, sp.f0, c, s.cstart.p, fac16, R, sub, D, done);
       else
-        fg_phase_kernel<T, T, false><<<grid, 128, smem, st>>>(s.pat.m, s.P, Q, sp.f0, c,
+        fg_phase_kernel<T, T, false><<<grid, nthr, smem, st>>>(s.pat.m, s.P, Q, sp.f0, c,
                                                               s.cstart.p, fac, R, sub, D, done);
       SG_TRY(check_launch("fg_phase (forward)"));
     }
@@ -625,10 +629,10 @@ int fg_apply(System& s, const T* R, T* D, cudaStream_t st, const int* done) {
       TimeScope ts(s.timer, K_ILU_SOLVE, st);
       const int grid = (cnt + npc - 1) / npc;
       if (fac16 != nullptr)
-        fg_phase_kernel<T, __nv_bfloat16, true><<<grid, 128, smem, st>>>(
+        fg_phase_kernel<T, __nv_bfloat16, true><<<grid, nthr, smem, st>>>(
             s.pat.m, s.P, Q, sp.f0, c, s.cstart.p, fac16, nullptr, nullptr, D, done);
       else
-        fg_phase_kernel<T, T, true><<<grid, 128, smem, st>>>(s.pat.m, s.P, Q, sp.f0, c,
+        fg_phase_kernel<T, T, true><<<grid, nthr, smem, st>>>(s.pat.m, s.P, Q, sp.f0, c,
                                                              s.cstart.p, fac, nullptr, nullptr, D,
                                                              done);
       SG_TRY(check_launch("fg_phase (backward)"));

@@ -43,7 +43,7 @@ FG_CASES = [
     (dict(n=5, M=4, p=2, sigma=0.5, ell=0.8), "groups"),    # Q = 10 + 4 + 1
     (dict(n=4, M=2, p=6, sigma=0.6, ell=0.6), "whole"),     # Q = 28: three lanes' groups
     (dict(n=3, M=3, p=4, sigma=0.6, ell=0.6), "whole"),     # Q = 35: two warps per node
-    (dict(n=3, M=4, p=4, sigma=0.6, ell=0.6), "whole"),     # Q = 70: four warps per node
+    (dict(n=3, M=4, p=4, sigma=0.6, ell=0.6), "whole"),     # Q = 70: three warps per node
 ]
 
 
