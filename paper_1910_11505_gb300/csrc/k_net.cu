@@ -374,6 +374,7 @@ struct sgnet {
   int frozen_out = 0;        // 1: Adam leaves the output layer (W3, b3) as set_basis left it
   sg::DBuf<float> P, G, M, V, mu, sd, Zh, H1, H2, dY, dH2, dA2, dA1, part, lpart, loss, Ytmp;
   sg::DBuf<__nv_bfloat16> W3h;
+  sg::DBuf<int> err;         // raised by a tensor-core kernel whose MMA completion timed out
 };
 
 using namespace sg;
@@ -383,6 +384,18 @@ static int net_release(sgnet* n) {
                        &n->dY, &n->dH2, &n->dA2, &n->dA1, &n->part, &n->lpart, &n->loss, &n->Ytmp};
   for (auto* b : bs) b->release();
   n->W3h.release();
+  n->err.release();
+  return SG_OK;
+}
+
+// The output layer runs on the tensor cores (k_net_tc.cu) when its weights have a BF16 copy.
+static bool use_tc(const sgnet* n) { return n->bf16 && n->h2 <= kMaxH2; }
+
+static int check_net_err(sgnet* n, cudaStream_t st) {
+  int e = 0;
+  SG_CUDA(cudaMemcpyAsync(&e, n->err.p, sizeof(int), cudaMemcpyDeviceToHost, st));
+  SG_CUDA(cudaStreamSynchronize(st));
+  if (e) return fail(SG_ERR_CUDA, "tensor-core output layer: MMA completion wait timed out");
   return SG_OK;
 }
 
@@ -456,9 +469,14 @@ int sgnet_create(int in_dim, int h1, int h2, int out_dim, int max_batch, int bf1
   A(n->Zh, B * in_dim); A(n->H1, B * h1); A(n->H2, B * h2); A(n->dY, B * out_dim);
   A(n->dH2, B * h2); A(n->dA2, B * h2); A(n->dA1, B * h1);
   A(n->part, (size_t)kSplit * kMaxBatch * kMaxH2);
-  A(n->lpart, (size_t)(out_dim + kOutThreads - 1) / kOutThreads);
+  // loss partials: one per CTA of the SIMT output kernel, or per 128 x 128 tile of the
+  // tensor-core one
+  A(n->lpart, (size_t)(out_dim + kOutThreads - 1) / kOutThreads * ((B + 127) / 128));
   A(n->loss, 1);
   if (rc == SG_OK && n->bf16) rc = n->W3h.alloc((size_t)out_dim * h2);
+  if (rc == SG_OK) rc = n->err.alloc(1);
+  if (rc == SG_OK && cudaMemset(n->err.p, 0, sizeof(int)) != cudaSuccess)
+    rc = fail(SG_ERR_CUDA, "cudaMemset of the error word failed");
   if (rc != SG_OK) {
     net_release(n);
     delete n;
@@ -539,6 +557,9 @@ int sgnet_forward(sgnet* n, const float* Z, int B, float* Y, void* stream) {
   if (!Z || !Y) return fail(SG_ERR_ARG, "NULL pointer");
   cudaStream_t st = (cudaStream_t)stream;
   SG_TRY(forward_hidden(n, Z, B, st));
+  if (use_tc(n))
+    return launch_out_tc(0, B, n->h2, n->out, n->H2.p, n->W3h.p, n->P.p + n->ob3, Y, nullptr,
+                         nullptr, nullptr, nullptr, n->err.p, st, nullptr);
   out_kernel<0, float><<<(n->out + kOutThreads - 1) / kOutThreads, kOutThreads, 0, st>>>(
       B, n->h2, n->out, n->H2.p, n->P.p + n->oW3, w3h(n), n->P.p + n->ob3, Y, nullptr, nullptr,
       nullptr, nullptr, nullptr);
@@ -550,6 +571,9 @@ int sgnet_predict(sgnet* n, const float* Z, int B, double* X, void* stream) {
   if (!Z || !X) return fail(SG_ERR_ARG, "NULL pointer");
   cudaStream_t st = (cudaStream_t)stream;
   SG_TRY(forward_hidden(n, Z, B, st));
+  if (use_tc(n))
+    return launch_out_tc(0, B, n->h2, n->out, n->H2.p, n->W3h.p, n->P.p + n->ob3, nullptr, X,
+                         nullptr, nullptr, nullptr, n->err.p, st, nullptr);
   out_kernel<0, double><<<(n->out + kOutThreads - 1) / kOutThreads, kOutThreads, 0, st>>>(
       B, n->h2, n->out, n->H2.p, n->P.p + n->oW3, w3h(n), n->P.p + n->ob3, X, nullptr, nullptr,
       nullptr, nullptr, nullptr);
@@ -561,12 +585,18 @@ int sgnet_loss_grad(sgnet* n, const float* Z, const float* T, int B, float* loss
   if (!Z || !T) return fail(SG_ERR_ARG, "NULL pointer");
   cudaStream_t st = (cudaStream_t)stream;
   SG_TRY(forward_hidden(n, Z, B, st));
-  const int nblk = (n->out + kOutThreads - 1) / kOutThreads;
-  out_kernel<1, float><<<nblk, kOutThreads, 0, st>>>(B, n->h2, n->out, n->H2.p, n->P.p + n->oW3,
-                                                      w3h(n), n->P.p + n->ob3, nullptr, T,
-                                                      n->dY.p, n->G.p + n->oW3, n->G.p + n->ob3,
-                                                      n->lpart.p);
-  SG_TRY(check_launch("out_grad"));
+  int nblk = (n->out + kOutThreads - 1) / kOutThreads;
+  if (use_tc(n) && n->frozen_out) {
+    // the output layer is fixed: only the residual gradient dY and the loss are needed
+    SG_TRY(launch_out_tc(1, B, n->h2, n->out, n->H2.p, n->W3h.p, n->P.p + n->ob3, nullptr,
+                         nullptr, T, n->dY.p, n->lpart.p, n->err.p, st, &nblk));
+  } else {
+    out_kernel<1, float><<<nblk, kOutThreads, 0, st>>>(B, n->h2, n->out, n->H2.p,
+                                                        n->P.p + n->oW3, w3h(n), n->P.p + n->ob3,
+                                                        nullptr, T, n->dY.p, n->G.p + n->oW3,
+                                                        n->G.p + n->ob3, n->lpart.p);
+    SG_TRY(check_launch("out_grad"));
+  }
   loss_final_kernel<<<1, 32, 0, st>>>(nblk, n->lpart.p, (float)B * (float)n->out, n->loss.p);
   SG_TRY(check_launch("loss_final"));
   dim3 g(kSplit, (B + 63) / 64);
@@ -584,7 +614,7 @@ int sgnet_loss_grad(sgnet* n, const float* Z, const float* T, int B, float* loss
   SG_TRY(check_launch("small_wgrad"));
   if (loss) {
     SG_CUDA(cudaMemcpyAsync(loss, n->loss.p, sizeof(float), cudaMemcpyDeviceToHost, st));
-    SG_CUDA(cudaStreamSynchronize(st));
+    SG_TRY(check_net_err(n, st));
   }
   return SG_OK;
 }

@@ -43,6 +43,11 @@ int check_launch(const char* what);
 int ensure_smem(const void* kernel, size_t bytes);
 // Largest dynamic shared memory one CTA may opt into on the current device.
 size_t smem_optin_max();
+// Output layer of the learned warm start on the tensor cores (k_net_tc.cu): mode 0 writes
+// Y = H2 W3^T + b3 (Yf or Yd), mode 1 the residual gradient dY and per-CTA loss partials.
+int launch_out_tc(int mode, int B, int h2, int out, const float* H2, const __nv_bfloat16* W3h,
+                  const float* b3, float* Yf, double* Yd, const float* T, float* dY, float* lpart,
+                  int* err, cudaStream_t st, int* nparts);
 
 // ------------------------------------------------------------------ live kernel timing
 

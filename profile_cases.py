@@ -6,7 +6,7 @@
     python profile_cases.py smoother [fg|fs_gs] [n]     # the c3 smoother alone on an n x n mesh
     python profile_cases.py matvec [fp64|fp32|bf16] [n] [M] [p] [pairs|tile [kappa] [ctas]]
     python profile_cases.py gmres [n] [iters]      # Arnoldi kernels
-    python profile_cases.py net [batch]            # network training step
+    python profile_cases.py net [batch] [basis]    # network training step (basis 1: fixed output layer)
     python profile_cases.py stamp CLASS RATIO SUMMARY SRC...   # record a capture's DRAM ratio
 
 ``stamp`` writes profiles/traffic.json's entry for a kernel class: the measured DRAM bytes per
@@ -148,11 +148,14 @@ def main(argv):
         sg.sg_gmres_solve(h, [F], [X], raise_on_error=False)
     elif what == "net":
         B = int(argv[2]) if len(argv) > 2 else 256
+        basis = int(argv[3]) if len(argv) > 3 else 1
         D = 4225 * 35
         net = sg.SGNet(6, 64, 64, D, max_batch=B, bf16=True, seed=1)
         Z = torch.from_numpy(W.random_field(B, 6, seed=3)).float().cuda()
         T = 0.01 * torch.from_numpy(W.random_field(B, D, seed=4)).float().cuda()
         net.set_stats(Z, T)
+        if basis:  # the c5 network: fixed output layer (the tensor-core residual epilogue)
+            net.set_basis(T)
         for _ in range(3):
             net.train_step(Z, T, 1e-3)
         torch.cuda.synchronize()

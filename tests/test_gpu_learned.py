@@ -100,6 +100,50 @@ def test_predict_equals_forward():
     net.close()
 
 
+def _hidden_ref(params, Z, stats):
+    """h2 of the network in FP64 for inputs Z (the layers before the output layer)."""
+    W1, b1, W2, b2 = params[:4]
+    zh = (Z.astype(np.float64) - stats[:6]) / stats[6:]
+    return np.tanh(np.tanh(zh @ W1.T + b1) @ W2.T + b2)
+
+
+@pytest.mark.parametrize("h2,out,B", [(64, 300, 200), (40, 128, 129), (64, 1000, 7)])
+def test_tensor_core_output_layer_matches_reference(h2, out, B):
+    # with a BF16 copy of W3 the output layer runs as tcgen05 MMAs on BF16 operands (h2 and W3
+    # rounded to BF16) with FP32 accumulation; sizes cover ragged batch and unit tiles and
+    # h2 < 64 (K zero-padded)
+    dims = (6, 16, h2, out)
+    net = sg.SGNet(*dims, max_batch=256, bf16=True, seed=21)
+    rng = np.random.default_rng(5)
+    flat = rng.normal(scale=0.4, size=net.num_params).astype(np.float32)
+    net.set(0, flat)
+    stats = np.concatenate([rng.normal(size=6), 0.5 + rng.random(6)]).astype(np.float32)
+    net.set(2, stats)
+    Z = rng.normal(size=(B, 6)).astype(np.float32)
+    Y = torch.empty(B, out, device="cuda")
+    net.forward(torch.from_numpy(Z).cuda(), Y)
+    params = _unflatten(flat, dims)
+    W3b, b3 = _bf16_round(params[4]), params[5]
+    hb = _bf16_round(_hidden_ref(params, Z, stats.astype(np.float64)))
+    ref = hb @ W3b.T + b3
+    # the GPU's FP32 hidden layers may round an h2 value to the neighbouring BF16 number (one
+    # unit 2^-8 of it) where the FP64 one falls the other side; FP32 accumulation of 64 terms
+    terms = np.abs(hb)[:, None, :] * np.abs(W3b)[None, :, :]
+    bound = 2.0 ** -8 * terms.max(axis=2) + 64 * 2.0 ** -24 * terms.sum(axis=2) + 1e-7
+    got = Y.double().cpu().numpy()
+    assert np.all(np.abs(got - ref) <= bound), np.abs(got - ref).max()
+    # the fixed-output-layer training loss (residual epilogue of the same kernel) equals the
+    # mean square of the forward result against the targets
+    T = rng.normal(size=(B, out)).astype(np.float32)
+    net.set_basis(torch.from_numpy(T).cuda())
+    Y2 = torch.empty(B, out, device="cuda")
+    net.forward(torch.from_numpy(Z).cuda(), Y2)
+    loss = net.loss_grad(torch.from_numpy(Z).cuda(), torch.from_numpy(T).cuda())
+    want = float(((Y2.double().cpu().numpy() - T) ** 2).mean())
+    assert abs(loss - want) <= 1e-5 * want
+    net.close()
+
+
 def test_trained_network_reduces_gmres_iterations():
     # small mesh: n = 16, M = 2, p = 2 (D = 289 x 6); sigma ~ U[0.1, 1.5], ell ~ U[0.25, 2]
     draws = W.c5_draws(288, seed=11)
