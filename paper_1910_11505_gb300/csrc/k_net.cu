@@ -120,14 +120,20 @@ __global__ void __launch_bounds__(kOutThreads) out_kernel(
   }
 }
 
-// Sum of the per-CTA loss partials, divided by B*out.
-__global__ void loss_final_kernel(int n, const float* __restrict__ part, float denom,
-                                  float* __restrict__ loss) {
-  if (threadIdx.x == 0 && blockIdx.x == 0) {
-    double s = 0.0;
-    for (int i = 0; i < n; ++i) s += part[i];
-    *loss = (float)(s / denom);
+// Sum of the per-CTA loss partials, divided by B*out: one CTA of 256 threads, strided FP64 sums
+// and a fixed tree (the order does not depend on scheduling).
+__global__ void __launch_bounds__(256) loss_final_kernel(int n, const float* __restrict__ part,
+                                                         float denom, float* __restrict__ loss) {
+  __shared__ double red[256];
+  double s = 0.0;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) s += part[i];
+  red[threadIdx.x] = s;
+  __syncthreads();
+  for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+    if ((int)threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+    __syncthreads();
   }
+  if (threadIdx.x == 0) *loss = (float)(red[0] / denom);
 }
 
 // Split-K partial of dH2 = dY W3 over the output units of this CTA; part[cta][b][k] for the
@@ -374,6 +380,10 @@ struct sgnet {
   int frozen_out = 0;        // 1: Adam leaves the output layer (W3, b3) as set_basis left it
   sg::DBuf<float> P, G, M, V, mu, sd, Zh, H1, H2, dY, dH2, dA2, dA1, part, lpart, loss, Ytmp;
   sg::DBuf<__nv_bfloat16> W3h;
+  // tensor-core back-propagation: W3 transposed (64 x outp) and dY (max batch x outp) in BF16,
+  // outp = out rounded up to a multiple of 64
+  int outp = 0;
+  sg::DBuf<__nv_bfloat16> W3hT, dYh;
   sg::DBuf<int> err;         // raised by a tensor-core kernel whose MMA completion timed out
 };
 
@@ -384,6 +394,8 @@ static int net_release(sgnet* n) {
                        &n->dY, &n->dH2, &n->dA2, &n->dA1, &n->part, &n->lpart, &n->loss, &n->Ytmp};
   for (auto* b : bs) b->release();
   n->W3h.release();
+  n->W3hT.release();
+  n->dYh.release();
   n->err.release();
   return SG_OK;
 }
@@ -402,7 +414,9 @@ static int check_net_err(sgnet* n, cudaStream_t st) {
 static int refresh_bf16(sgnet* n, cudaStream_t st) {
   if (!n->bf16) return SG_OK;
   to_bf16_kernel<<<608, 256, 0, st>>>((size_t)n->out * n->h2, n->P.p + n->oW3, n->W3h.p);
-  return check_launch("to_bf16");
+  SG_TRY(check_launch("to_bf16"));
+  if (n->W3hT.p) SG_TRY(launch_w3t_bf16(n->out, n->outp, n->h2, n->P.p + n->oW3, n->W3hT.p, st));
+  return SG_OK;
 }
 
 static const __nv_bfloat16* w3h(const sgnet* n) { return n->bf16 ? n->W3h.p : nullptr; }
@@ -474,6 +488,11 @@ int sgnet_create(int in_dim, int h1, int h2, int out_dim, int max_batch, int bf1
   A(n->lpart, (size_t)(out_dim + kOutThreads - 1) / kOutThreads * ((B + 127) / 128));
   A(n->loss, 1);
   if (rc == SG_OK && n->bf16) rc = n->W3h.alloc((size_t)out_dim * h2);
+  if (rc == SG_OK && n->bf16 && h2 <= kMaxH2) {
+    n->outp = (out_dim + 63) / 64 * 64;
+    rc = n->W3hT.alloc((size_t)64 * n->outp);
+    if (rc == SG_OK) rc = n->dYh.alloc(B * n->outp);
+  }
   if (rc == SG_OK) rc = n->err.alloc(1);
   if (rc == SG_OK && cudaMemset(n->err.p, 0, sizeof(int)) != cudaSuccess)
     rc = fail(SG_ERR_CUDA, "cudaMemset of the error word failed");
@@ -559,7 +578,7 @@ int sgnet_forward(sgnet* n, const float* Z, int B, float* Y, void* stream) {
   SG_TRY(forward_hidden(n, Z, B, st));
   if (use_tc(n))
     return launch_out_tc(0, B, n->h2, n->out, n->H2.p, n->W3h.p, n->P.p + n->ob3, Y, nullptr,
-                         nullptr, nullptr, nullptr, n->err.p, st, nullptr);
+                         nullptr, nullptr, 0, nullptr, n->err.p, st, nullptr);
   out_kernel<0, float><<<(n->out + kOutThreads - 1) / kOutThreads, kOutThreads, 0, st>>>(
       B, n->h2, n->out, n->H2.p, n->P.p + n->oW3, w3h(n), n->P.p + n->ob3, Y, nullptr, nullptr,
       nullptr, nullptr, nullptr);
@@ -573,7 +592,7 @@ int sgnet_predict(sgnet* n, const float* Z, int B, double* X, void* stream) {
   SG_TRY(forward_hidden(n, Z, B, st));
   if (use_tc(n))
     return launch_out_tc(0, B, n->h2, n->out, n->H2.p, n->W3h.p, n->P.p + n->ob3, nullptr, X,
-                         nullptr, nullptr, nullptr, n->err.p, st, nullptr);
+                         nullptr, nullptr, 0, nullptr, n->err.p, st, nullptr);
   out_kernel<0, double><<<(n->out + kOutThreads - 1) / kOutThreads, kOutThreads, 0, st>>>(
       B, n->h2, n->out, n->H2.p, n->P.p + n->oW3, w3h(n), n->P.p + n->ob3, X, nullptr, nullptr,
       nullptr, nullptr, nullptr);
@@ -586,10 +605,11 @@ int sgnet_loss_grad(sgnet* n, const float* Z, const float* T, int B, float* loss
   cudaStream_t st = (cudaStream_t)stream;
   SG_TRY(forward_hidden(n, Z, B, st));
   int nblk = (n->out + kOutThreads - 1) / kOutThreads;
-  if (use_tc(n) && n->frozen_out) {
-    // the output layer is fixed: only the residual gradient dY and the loss are needed
+  const bool tc = use_tc(n) && n->frozen_out;
+  if (tc) {
+    // the output layer is fixed: only the residual gradient dY (BF16) and the loss are needed
     SG_TRY(launch_out_tc(1, B, n->h2, n->out, n->H2.p, n->W3h.p, n->P.p + n->ob3, nullptr,
-                         nullptr, T, n->dY.p, n->lpart.p, n->err.p, st, &nblk));
+                         nullptr, T, n->dYh.p, n->outp, n->lpart.p, n->err.p, st, &nblk));
   } else {
     out_kernel<1, float><<<nblk, kOutThreads, 0, st>>>(B, n->h2, n->out, n->H2.p,
                                                         n->P.p + n->oW3, w3h(n), n->P.p + n->ob3,
@@ -597,12 +617,19 @@ int sgnet_loss_grad(sgnet* n, const float* Z, const float* T, int B, float* loss
                                                         n->G.p + n->ob3, n->lpart.p);
     SG_TRY(check_launch("out_grad"));
   }
-  loss_final_kernel<<<1, 32, 0, st>>>(nblk, n->lpart.p, (float)B * (float)n->out, n->loss.p);
+  loss_final_kernel<<<1, 256, 0, st>>>(nblk, n->lpart.p, (float)B * (float)n->out, n->loss.p);
   SG_TRY(check_launch("loss_final"));
-  dim3 g(kSplit, (B + 63) / 64);
-  dh2_partial_kernel<<<g, 256, 0, st>>>(B, n->h2, n->out, n->dY.p, n->P.p + n->oW3, w3h(n), n->part.p);
-  SG_TRY(check_launch("dh2_partial"));
-  dh2_final_kernel<<<(B * n->h2 + 255) / 256, 256, 0, st>>>(B, n->h2, kSplit, n->part.p, n->dH2.p);
+  int nsplit = kSplit;
+  if (tc) {
+    SG_TRY(launch_dh2_tc(B, n->outp, n->dYh.p, n->W3hT.p, n->part.p, (size_t)kMaxBatch * kMaxH2,
+                         kMaxH2, kSplit, n->err.p, st, &nsplit));
+  } else {
+    dim3 g(kSplit, (B + 63) / 64);
+    dh2_partial_kernel<<<g, 256, 0, st>>>(B, n->h2, n->out, n->dY.p, n->P.p + n->oW3, w3h(n),
+                                          n->part.p);
+    SG_TRY(check_launch("dh2_partial"));
+  }
+  dh2_final_kernel<<<(B * n->h2 + 255) / 256, 256, 0, st>>>(B, n->h2, nsplit, n->part.p, n->dH2.p);
   SG_TRY(check_launch("dh2_final"));
   small_bwd_kernel<<<B, 128, 0, st>>>(n->h1, n->h2, n->P.p, n->oW2, n->dH2.p, n->H1.p, n->H2.p,
                                       n->dA2.p, n->dA1.p);

@@ -46,8 +46,15 @@ size_t smem_optin_max();
 // Output layer of the learned warm start on the tensor cores (k_net_tc.cu): mode 0 writes
 // Y = H2 W3^T + b3 (Yf or Yd), mode 1 the residual gradient dY and per-CTA loss partials.
 int launch_out_tc(int mode, int B, int h2, int out, const float* H2, const __nv_bfloat16* W3h,
-                  const float* b3, float* Yf, double* Yd, const float* T, float* dY, float* lpart,
-                  int* err, cudaStream_t st, int* nparts);
+                  const float* b3, float* Yf, double* Yd, const float* T, __nv_bfloat16* dYh,
+                  int outp, float* lpart, int* err, cudaStream_t st, int* nparts);
+// dH2 = dY W3 split over the output units on the tensor cores (k_net_tc.cu), and the transposed
+// BF16 copy of W3 it reads.
+int launch_dh2_tc(int B, int outp, const __nv_bfloat16* dYh, const __nv_bfloat16* W3hT,
+                  float* part, size_t part_stride, int ldp, int max_split, int* err,
+                  cudaStream_t st, int* nsplit);
+int launch_w3t_bf16(int out, int outp, int h2, const float* W3, __nv_bfloat16* W3hT,
+                    cudaStream_t st);
 
 // ------------------------------------------------------------------ live kernel timing
 

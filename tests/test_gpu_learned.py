@@ -144,6 +144,44 @@ def test_tensor_core_output_layer_matches_reference(h2, out, B):
     net.close()
 
 
+@pytest.mark.parametrize("B,out", [(200, 300), (129, 1000), (7, 64)])
+def test_tensor_core_backprop_matches_reference(B, out):
+    # with the output layer fixed and a BF16 copy of W3, a training step runs the output layer
+    # and dH2 = dY W3 (split over the units, K padded to a multiple of 64) as tcgen05 MMAs on
+    # BF16 dY and W3; the hidden layers' gradient then follows in FP32.  Reference: dY formed
+    # from the tensor-core forward result exactly as the kernel rounds it (FP32 residual and
+    # scale, BF16), then back-propagated in FP64.
+    dims = (6, 16, 64, out)
+    net = sg.SGNet(*dims, max_batch=256, bf16=True, seed=23)
+    rng = np.random.default_rng(6)
+    flat = rng.normal(scale=0.4, size=net.num_params).astype(np.float32)
+    net.set(0, flat)
+    stats = np.concatenate([rng.normal(size=6), 0.5 + rng.random(6)]).astype(np.float32)
+    net.set(2, stats)
+    Z = rng.normal(size=(B, 6)).astype(np.float32)
+    T = rng.normal(size=(B, out)).astype(np.float32)
+    net.set_basis(torch.from_numpy(T).cuda())
+    Y = torch.empty(B, out, device="cuda")
+    net.forward(torch.from_numpy(Z).cuda(), Y)
+    net.loss_grad(torch.from_numpy(Z).cuda(), torch.from_numpy(T).cuda())
+    grad = net.get(1).astype(np.float64)
+    params = _unflatten(net.get(0), dims)
+    W1, b1, W2, b2, W3 = params[:5]
+    scale = np.float32(2.0) / (np.float32(B) * np.float32(out))
+    dY = _bf16_round(scale * (Y.cpu().numpy() - T))
+    dH2 = dY @ _bf16_round(W3)
+    zh = (Z.astype(np.float64) - stats[:6]) / stats[6:]
+    H1 = np.tanh(zh @ W1.T + b1)
+    H2 = np.tanh(H1 @ W2.T + b2)
+    dA2 = dH2 * (1.0 - H2 * H2)
+    dA1 = (dA2 @ W2) * (1.0 - H1 * H1)
+    ref = np.concatenate([(dA1.T @ zh).ravel(), dA1.sum(0), (dA2.T @ H1).ravel(), dA2.sum(0)])
+    got = grad[:ref.size]
+    err = np.abs(got - ref).max() / np.abs(ref).max()
+    assert err <= 1e-4, err
+    net.close()
+
+
 def test_trained_network_reduces_gmres_iterations():
     # small mesh: n = 16, M = 2, p = 2 (D = 289 x 6); sigma ~ U[0.1, 1.5], ell ~ U[0.25, 2]
     draws = W.c5_draws(288, seed=11)
