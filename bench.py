@@ -3,10 +3,11 @@
 Workload (c3): the stochastic Galerkin system of -div(a grad u) = 1 on the unit square, 256 x 256
 Q1 mesh, M = 6 KL terms of the exponential covariance (sigma = 1, ell = 0.5), chaos degree p = 3
 (P = 84 solution terms, L = 924 coefficient terms; 5.5 M unknowns), relative residual 1e-8 from a
-zero initial guess, GMRES(50) preconditioned by the multigrid V-cycle of the paper's G-M-F-I
-(field-split Gauss-Seidel with ILU(0) blocks as the level solver, the blocks' ILU(0) in the
-four-colour node ordering, one pre- and one post-smoothing step, 2 x 2 coarsest mesh solved
-directly).  One step = one solve in the mixed-precision form
+zero initial guess, GMRES(50) preconditioned by the multigrid V-cycle of the paper's G-M-Fg-I
+(grouped field split as the level solver: at M = 6, p = 3 the paper's rule gives one split of all
+84 fields, i.e. the block ILU(0) of each level's K in the four-colour node ordering, its factors
+stored in BF16 for the inner solve; one pre- and one post-smoothing step, 2 x 2 coarsest mesh
+solved directly).  One step = one solve in the mixed-precision form
 (FP32 operator, preconditioner and inner basis inside FP64 flexible GMRES with FP64 iterative
 refinement).  value = solves per second over all ranks (each rank solves its own copy: weak
 scaling, no collective on the data path).
@@ -15,8 +16,10 @@ Also in the JSON line: the FP64 GPU solve of the same system (rate, iterations, 
 solution's distance from it), the SG operator alone in FP64 and FP32 (HBM GB/s and, for FP64,
 FLOP/s against the FP64 FMA peak measured here by the library's probe), the roofline of the
 dominant kernel from a separate per-kernel timing pass, the end-to-end rate through the C ABI
-with host buffers, SM clocks sampled during the timed region, and the FP64 CPU oracle on the
-host cores (``cpu_baseline``).
+with host buffers, SM clocks sampled during the timed region, the FP64 CPU oracle on the
+host cores (``cpu_baseline``), and (``learned``) the learned warm start on c5-sized systems
+reduced to a few hundred training solves: FP64 and mixed solves from zero and from the network's
+prediction.
 
 ``--impl reference`` times the oracle alone (the CPU reference of this project) on a bounded
 sample of the same workload and prints the same JSON line with "impl": "reference".
@@ -391,6 +394,48 @@ def time_matvec(sg, torch, h, X, Y, fn, stream, reps=20):
     return statistics.median(ts) / 1000.0
 
 
+def learned_c5_leg(ntrain, ntest=32, steps=1000):
+    """The learned warm start on c5-sized systems (64 x 64 mesh, M = 4, p = 3, sigma and ell
+    drawn from the seed), reduced to ``ntrain`` training solves so that it fits the bench: the
+    network is trained on the GPU by the library's kernels, then each held-out system is solved
+    to 1e-8 from zero and from the prediction, in FP64 and in the mixed form, with the paper's
+    multigrid preconditioner (G-M-Fg-I).  Solve times exclude setup."""
+    import numpy as np
+    import torch
+    from paper_1910_11505_gb300 import learned, sg, workloads as W
+    draws = W.c5_draws(ntrain + ntest)
+    base = dict(n=64, M=4, p=3, precond="mg", mg_smoother="fg", fg_rule="paper",
+                ilu_order="color4")
+    tr = [dict(base, sigma=a, ell=b) for a, b in draws[:ntrain]]
+    te = [dict(base, sigma=a, ell=b) for a, b in draws[ntrain:]]
+    Z, T, gen = learned.generate(tr, chunk=64, precision="fp32", rtol=1e-6)
+    net = sg.SGNet(Z.shape[1], 64, 64, T.shape[1], max_batch=256, bf16=True, seed=1910)
+    net.set_stats(Z, T)
+    net.set_basis(T)
+    torch.cuda.synchronize()
+    t0 = time.time()
+    learned.train(net, Z, T, steps=steps, batch=min(128, ntrain), lr=1e-3)
+    torch.cuda.synchronize()
+    train_s = time.time() - t0
+    out = {"config": f"c5 reduced: 64x64 Q1, M=4, p=3 (D=4225x35), {ntrain} training and {ntest} "
+                     "held-out draws of sigma~U[0.1,1.5], ell~U[0.25,2]; MLP 6-64-64-D, output "
+                     "layer on the tensor cores; G-M-Fg-I, rel. residual 1e-8",
+           "generation_s": gen["seconds"], "train_s": train_s, "train_steps": steps}
+    for prec in ("fp64", "fp32"):
+        ev = learned.warm_start_eval(net, te, precision=prec, rtol=1e-8)
+        key = "fp64" if prec == "fp64" else "mixed"
+        out[key] = {"zero_iters": float(np.mean(ev["zero_iters"])),
+                    "warm_iters": float(np.mean(ev["warm_iters"])),
+                    "zero_solves_per_s": len(te) / ev["zero_seconds"],
+                    "warm_solves_per_s": len(te) / ev["warm_seconds"],
+                    "max_warm_resid": max(ev["warm_resid"])}
+    out["mixed_learned_over_fp64_zero"] = (out["mixed"]["warm_solves_per_s"]
+                                           / out["fp64"]["zero_solves_per_s"])
+    net.close()
+    torch.cuda.empty_cache()
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -399,6 +444,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--fp64-solves", type=int, default=2)
+    ap.add_argument("--learned-train", type=int, default=256,
+                    help="training draws of the reduced c5 learned-warm-start leg (0: skip)")
     args = ap.parse_args()
     if args.impl == "reference":
         return reference_arm(args)
@@ -592,6 +639,10 @@ def main():
     e2e = {"value": world / (e2e_ms / 1000.0), "unit": "solves/s",
            "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes}
 
+    learned_leg = None
+    if rank == 0 and args.learned_train > 0:
+        learned_leg = learned_c5_leg(args.learned_train)
+
     last = infos[-1]
     line = {"metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
@@ -606,6 +657,8 @@ def main():
             "gpu_launches": launches, "clocks": clk,
             "kernel_ms_timing_pass": {c: {"timed_ms": v[0], "timed": v[1], "launches": v[2],
                                           "est_total_ms": est[c]} for c, v in ktimes.items()}}
+    if learned_leg is not None:
+        line["learned"] = learned_leg
     if cpu is not None:
         est1, estn = oracle_solve_estimate(cpu, last["iters"])
         info = cpu_info()
