@@ -555,10 +555,10 @@ def main():
 
     # The roofline: the kernel class with the largest share of the step's GPU time (timing pass
     # above) among those with a byte model, timed again on the finest level where its bytes
-    # and time concentrate.  The smoother classes: one FS-GS sweep of the n = 256 level alone
-    # (the c3 system with the four-colour ILU(0) and BF16 coupling, as the V-cycle runs it),
-    # every launch bracketed by CUDA events on its stream; the operator classes: the timed
-    # operator applications above.
+    # and time concentrate.  The smoother classes: one application of the n = 256 level's
+    # smoother alone (the grouped field split with BF16 factors, as the V-cycle runs it), every
+    # launch bracketed by CUDA events on its stream; the operator classes: the timed operator
+    # applications above.
     rated = {c: est[c] for c in ("apply_lowp", "apply_f64", "ilu_solve", "gs_scatter") if c in est}
     dom = max(rated, key=rated.get)
     fine = [(N, nnzA)]
