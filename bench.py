@@ -17,9 +17,9 @@ solution's distance from it), the SG operator alone in FP64 and FP32 (HBM GB/s a
 FLOP/s against the FP64 FMA peak measured here by the library's probe), the roofline of the
 dominant kernel from a separate per-kernel timing pass, the end-to-end rate through the C ABI
 with host buffers, SM clocks sampled during the timed region, the FP64 CPU oracle on the
-host cores (``cpu_baseline``), and (``learned``) the learned warm start on c5-sized systems
-reduced to a few hundred training solves: FP64 and mixed solves from zero and from the network's
-prediction.
+host cores (``cpu_baseline``), and (``learned``) the learned warm start on 64 x 64 mesh systems
+(M = 4, p = 3, sigma and ell drawn from the seed) trained on a few hundred solves: FP64 and
+mixed solves from zero and from the network's prediction.
 
 ``--impl reference`` times the oracle alone (the CPU reference of this project) on a bounded
 sample of the same workload and prints the same JSON line with "impl": "reference".
@@ -395,8 +395,8 @@ def time_matvec(sg, torch, h, X, Y, fn, stream, reps=20):
 
 
 def learned_c5_leg(ntrain, ntest=32, steps=1000):
-    """The learned warm start on c5-sized systems (64 x 64 mesh, M = 4, p = 3, sigma and ell
-    drawn from the seed), reduced to ``ntrain`` training solves so that it fits the bench: the
+    """The learned warm start on 64 x 64 mesh systems (M = 4, p = 3, sigma and ell drawn from
+    the seed), with ``ntrain`` training solves so that it fits the bench: the
     network is trained on the GPU by the library's kernels, then each held-out system is solved
     to 1e-8 from zero and from the prediction, in FP64 and in the mixed form, with the paper's
     multigrid preconditioner (G-M-Fg-I).  Solve times exclude setup."""
