@@ -108,8 +108,8 @@ __device__ __forceinline__ void stencil_diffs_f32(const float* xp, float2 (&d)[9
 }
 
 // T for the k of a group that need this b (mask bit j for the group's j-th k): the row sum times
-// x_c plus the eight stiffness values times the differences, as two dependent chains per k (the
-// lines above and below the centre) joined at the end.
+// x_c plus the eight stiffness values times the differences, one dependent chain per k (the
+// chains of the group's k and of the two half-warps' entries overlap).
 template <int KAPPA>
 __device__ __forceinline__ void pair_products_f32(const float2 (&a)[KAPPA][9],
                                                   const float2 (&d)[9], int mask, int sl,
@@ -117,14 +117,10 @@ __device__ __forceinline__ void pair_products_f32(const float2 (&a)[KAPPA][9],
 #pragma unroll
   for (int j = 0; j < KAPPA; ++j) {
     float2 t0 = __fmul2_rn(a[j][4], d[4]);
-    float2 t1 = __fmul2_rn(a[j][6], d[6]);
 #pragma unroll
-    for (int e = 0; e < 4; ++e) t0 = __ffma2_rn(a[j][e], d[e], t0);
-    t1 = __ffma2_rn(a[j][5], d[5], t1);
-    t1 = __ffma2_rn(a[j][7], d[7], t1);
-    t1 = __ffma2_rn(a[j][8], d[8], t1);
-    if (mask >> j & 1)
-      st2(Tp + (size_t)(sl + __popc(mask & ((1 << j) - 1))) * kTW, __fadd2_rn(t0, t1));
+    for (int e = 0; e < 9; ++e)
+      if (e != 4) t0 = __ffma2_rn(a[j][e], d[e], t0);
+    if (mask >> j & 1) st2(Tp + (size_t)(sl + __popc(mask & ((1 << j) - 1))) * kTW, t0);
   }
 }
 
