@@ -369,8 +369,8 @@ __device__ __forceinline__ bool fg_slot_used(int c, int sl, bool upper) {
 // Each node is a group of lanes (lane r: row r of every block).  The Q values of every slot the
 // phase uses (the node's own y_i included in the backward sweep) are staged in shared memory
 // first, behind one barrier; then each lane streams its rows of those blocks.  Neighbours
-// outside the mesh are clamped onto it, their blocks are zero.  No other node of the colour
-// reads node i, so writing it in place is safe.
+// outside the mesh have zero blocks and are staged as zero vectors.  No other node of the
+// colour reads node i, so writing it in place is safe.
 template <typename T, typename TV, bool UPPER>
 __global__ void __launch_bounds__(128) fg_phase_kernel(int m, int P, int Q, int f0, int c,
                                                        const int* __restrict__ cstart_g,
@@ -401,9 +401,13 @@ __global__ void __launch_bounds__(128) fg_phase_kernel(int m, int P, int Q, int 
 #pragma unroll
   for (int sl = 0; sl < 9; ++sl) {
     if (!fg_slot_used(c, sl, UPPER)) continue;
-    const int jx = min(max(x + sl % 3 - 1, 0), m - 1), jy = min(max(y + sl / 3 - 1, 0), m - 1);
+    // a neighbour outside the mesh has a zero block and a zero vector: its clamped stand-in may
+    // be a node this sweep has not written yet (the node itself at an even-sized mesh's edge)
+    const int nx = x + sl % 3 - 1, ny = y + sl / 3 - 1;
+    const bool inside = nx >= 0 && ny >= 0 && nx < m && ny < m;
+    const int jx = min(max(nx, 0), m - 1), jy = min(max(ny, 0), m - 1);
     const T* src = Y + ((size_t)jx + (size_t)m * jy) * P + f0;
-    for (int t = r; t < Qc; t += G) v[k * Qc + t] = t < Q ? src[t] : T(0);
+    for (int t = r; t < Qc; t += G) v[k * Qc + t] = t < Q && inside ? src[t] : T(0);
     ++k;
   }
   T acc = T(0);
