@@ -59,7 +59,7 @@ def test_color4_preconditioners_match_oracle(d, pc):
     kw = {k: d[k] for k in ("sigma", "ell", "a_min") if k in d}
     prob = O.build_problem(d["n"], d["M"], d["p"], **kw)
     R = W.random_field(N, P, seed=51)
-    Z = torch.empty(N, P, dtype=torch.float64, device="cuda")
+    Z = torch.full((N, P), float("nan"), dtype=torch.float64, device="cuda")
     sg.sg_precond_apply(h, 0, torch.from_numpy(R).cuda(), Z)
     if pc == "mean":
         ref = O.mean_precond(prob, R, ordering="color4")
@@ -77,7 +77,7 @@ def test_color4_fp32_large_mesh():
     N, P, _ = sg.sg_dims(h)
     prob = O.build_problem(256, 2, 1, sigma=0.8, ell=0.5)
     R = W.random_field(N, P, seed=52)
-    Z = torch.empty(N, P, dtype=torch.float32, device="cuda")
+    Z = torch.full((N, P), float("nan"), dtype=torch.float32, device="cuda")
     sg.sg_precond_apply_lowp(h, 0, torch.from_numpy(R).float().cuda(), Z)
     ref = O.fs_precond(prob, R.astype(np.float32).astype(np.float64),
                        blocks=O.fs_blocks(prob, ordering="color4"))
@@ -95,7 +95,7 @@ def test_color4_vcycle_matches_oracle(smoother):
     data = O.mg_setup(levels, smoother, ordering="color4")
     R = W.random_field(N, P, seed=53)
     R[levels[-1].boundary] = 0.0
-    Z = torch.empty(N, P, dtype=torch.float64, device="cuda")
+    Z = torch.full((N, P), float("nan"), dtype=torch.float64, device="cuda")
     sg.sg_precond_apply(h, 0, torch.from_numpy(R).cuda(), Z)
     ref = O.mg_vcycle(levels, data, R, smoother)
     assert _relerr(Z.cpu().numpy(), ref) <= 1e-12
@@ -130,7 +130,7 @@ def test_bf16_coupling_sweep_matches_oracle_with_rounded_coupling():
         Ar.data = _bf16_round(Ar.data)
         coupling.append(Ar)
     R = W.random_field(N, P, seed=54)
-    Z = torch.empty(N, P, dtype=torch.float32, device="cuda")
+    Z = torch.full((N, P), float("nan"), dtype=torch.float32, device="cuda")
     sg.sg_precond_apply_lowp(h, 0, torch.from_numpy(R).float().cuda(), Z)
     Rr = R.astype(np.float32).astype(np.float64)
     ref = O.fs_precond(prob, Rr, coupling=coupling)

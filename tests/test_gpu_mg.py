@@ -50,7 +50,7 @@ def test_vcycle_matches_oracle(case, smoother, coarse):
     data = O.mg_setup(levels, smoother)
     R = W.random_field(N, P, seed=41)
     R[levels[-1].boundary] = 0.0
-    Z = torch.empty(N, P, dtype=torch.float64, device="cuda")
+    Z = torch.full((N, P), float("nan"), dtype=torch.float64, device="cuda")
     for _ in range(2):  # a second application reuses every level's buffers
         sg.sg_precond_apply(h, 0, torch.from_numpy(R).cuda(), Z)
     ref = O.mg_vcycle(levels, data, R, smoother)
@@ -66,7 +66,7 @@ def test_vcycle_fp32_matches_oracle():
     data = O.mg_setup(levels, "fs_gs")
     R = W.random_field(N, P, seed=42)
     R[levels[-1].boundary] = 0.0
-    Z = torch.empty(N, P, dtype=torch.float32, device="cuda")
+    Z = torch.full((N, P), float("nan"), dtype=torch.float32, device="cuda")
     sg.sg_precond_apply_lowp(h, 0, torch.from_numpy(R).float().cuda(), Z)
     ref = O.mg_vcycle(levels, data, R.astype(np.float32).astype(np.float64), "fs_gs")
     assert _relerr(Z.double().cpu().numpy(), ref) <= 1e-5
@@ -83,7 +83,7 @@ def test_mg_gmres_solution_and_mesh_independent_iterations(smoother, sigma):
         h = sg.sg_setup(sg.sg_default_params(**case, precond="mg", mg_smoother=smoother,
                                              rtol=1e-12, restart=30, max_iters=300))
         N, P, _ = sg.sg_dims(h)
-        F = torch.empty(N, P, dtype=torch.float64, device="cuda")
+        F = torch.full((N, P), float("nan"), dtype=torch.float64, device="cuda")
         sg.sg_rhs(h, 0, F)
         X = torch.zeros_like(F)
         rc, info = sg.sg_gmres_solve(h, [F], [X])

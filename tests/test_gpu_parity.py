@@ -72,7 +72,7 @@ def test_setup_arrays_match_oracle(case):
     G = np.zeros_like(prob.G)
     G[trip[:, 0].astype(int), trip[:, 1].astype(int), trip[:, 2].astype(int)] = trip[:, 3]
     assert np.allclose(G, prob.G, rtol=1e-14, atol=1e-15)
-    F = torch.empty(N, P, dtype=torch.float64, device="cuda")
+    F = torch.full((N, P), float("nan"), dtype=torch.float64, device="cuda")
     sg.sg_rhs(h, 0, F)
     torch.cuda.synchronize()
     assert _relerr(F.cpu().numpy(), prob.F) <= 1e-14
@@ -85,7 +85,7 @@ def test_matvec_parity(case):
     prob = _oracle(case)
     X = W.random_field(prob.N, prob.P, seed=11)
     Xd = _dev(X)
-    Y = torch.empty_like(Xd)
+    Y = torch.full_like(Xd, float("nan"))
     sg.sg_matvec(h, 0, Xd, Y)
     torch.cuda.synchronize()
     ref = O.sg_matvec(prob, X)
@@ -107,7 +107,7 @@ def test_precond_parity(pc, inner, outer):
     prob = _oracle(case)
     R = W.random_field(prob.N, prob.P, seed=5)
     Rd = _dev(R)
-    Z = torch.empty_like(Rd)
+    Z = torch.full_like(Rd, float("nan"))
     sg.sg_precond_apply(h, 0, Rd, Z)
     torch.cuda.synchronize()
     if pc == "mean":
@@ -170,7 +170,7 @@ def test_batch_of_uneven_systems_equals_single_solves():
     Fs, Xs = [], []
     for i in range(len(cases)):
         N, P, _ = sg.sg_dims(h, i)
-        F = torch.empty(N, P, dtype=torch.float64, device="cuda")
+        F = torch.full((N, P), float("nan"), dtype=torch.float64, device="cuda")
         sg.sg_rhs(h, i, F)
         Fs.append(F)
         Xs.append(torch.zeros_like(F))
@@ -208,7 +208,7 @@ def test_not_converged_status():
     case = dict(n=16, M=2, p=2, sigma=0.5, ell=1.0)
     h = sg.sg_setup(_params(case, precond="none", max_iters=3, rtol=1e-12))
     N, P, _ = sg.sg_dims(h)
-    F = torch.empty(N, P, dtype=torch.float64, device="cuda")
+    F = torch.full((N, P), float("nan"), dtype=torch.float64, device="cuda")
     sg.sg_rhs(h, 0, F)
     X = torch.zeros_like(F)
     rc, info = sg.sg_gmres_solve(h, [F], [X])
@@ -237,7 +237,7 @@ def test_lowp_matvec_close_to_fp64(precision):
     prob = _oracle(case)
     X = W.random_field(prob.N, prob.P, seed=2)
     Xd = _dev(X).float()
-    Y = torch.empty_like(Xd)
+    Y = torch.full_like(Xd, float("nan"))
     sg.sg_matvec_lowp(h, 0, Xd, Y)
     torch.cuda.synchronize()
     ref = O.sg_matvec(prob, X)
@@ -273,7 +273,7 @@ def test_graph_replay_equals_plain_launches(pc, prec):
         Fs, Xs = [], []
         for i in range(2):
             N, P, _ = sg.sg_dims(h, i)
-            F = torch.empty(N, P, dtype=torch.float64, device="cuda")
+            F = torch.full((N, P), float("nan"), dtype=torch.float64, device="cuda")
             sg.sg_rhs(h, i, F)
             Fs.append(F)
             Xs.append(torch.zeros_like(F))
@@ -307,7 +307,7 @@ def test_matvec_parity_every_operator_kernel(case, variant):
     assert info["fp64"]["kernel"] == want, info
     prob = _oracle(case)
     X = W.random_field(prob.N, prob.P, seed=13)
-    Y = torch.empty(prob.N, prob.P, dtype=torch.float64, device="cuda")
+    Y = torch.full((prob.N, prob.P), float("nan"), dtype=torch.float64, device="cuda")
     sg.sg_matvec(h, 0, _dev(X), Y)
     torch.cuda.synchronize()
     ref = O.sg_matvec(prob, X)
@@ -323,7 +323,7 @@ def test_fp32_operator_every_kernel(variant):
     assert sg.sg_op_info(h)["fp32"]["kernel"] == ("pairs" if variant["op_kernel"] == "pairs" else "tile")
     prob = _oracle(case)
     X = W.random_field(prob.N, prob.P, seed=15)
-    Y = torch.empty(prob.N, prob.P, dtype=torch.float32, device="cuda")
+    Y = torch.full((prob.N, prob.P), float("nan"), dtype=torch.float32, device="cuda")
     sg.sg_matvec_lowp(h, 0, _dev(X).float(), Y)
     ref = O.sg_matvec(prob, X.astype(np.float32).astype(np.float64))
     assert _relerr(Y.double().cpu().numpy(), ref) <= 2e-5

@@ -53,7 +53,7 @@ def test_field_split_elementwise_at_solver_sizes(d, mode, inner):
     h = sg.sg_setup(sg.sg_default_params(**d, precond=pc, inner_iters=inner))
     N, P, _ = sg.sg_dims(h)
     R = W.random_field(N, P, seed=31)
-    Z = torch.empty(N, P, dtype=torch.float64, device="cuda")
+    Z = torch.full((N, P), float("nan"), dtype=torch.float64, device="cuda")
     sg.sg_precond_apply(h, 0, torch.from_numpy(R).cuda(), Z)
     ref = O.fs_precond(prob, R, mode=mode, inner_iters=inner, blocks=blocks)
     err = _relerr(Z.cpu().numpy(), ref)
@@ -76,7 +76,7 @@ def test_field_split_fp32_against_fp64_oracle(d, mode):
     h = sg.sg_setup(sg.sg_default_params(**d, precond=pc, precision="fp32"))
     N, P, _ = sg.sg_dims(h)
     R = W.random_field(N, P, seed=32)
-    Z = torch.empty(N, P, dtype=torch.float32, device="cuda")
+    Z = torch.full((N, P), float("nan"), dtype=torch.float32, device="cuda")
     sg.sg_precond_apply_lowp(h, 0, torch.from_numpy(R).float().cuda(), Z)
     ref = O.fs_precond(prob, R.astype(np.float32).astype(np.float64), mode=mode, blocks=blocks)
     err = _relerr(Z.double().cpu().numpy(), ref)
@@ -90,6 +90,6 @@ def test_lowp_preconditioner_refuses_fp64_system():
     N, P, _ = sg.sg_dims(h)
     R = torch.zeros(N, P, dtype=torch.float32, device="cuda")
     with pytest.raises(sg.SGError) as ei:
-        sg.sg_precond_apply_lowp(h, 0, R, torch.empty_like(R))
+        sg.sg_precond_apply_lowp(h, 0, R, torch.full_like(R, float("nan")))
     assert ei.value.code == sg.SG_ERR_ARG
     h.close()
