@@ -39,8 +39,19 @@ def _newest_header() -> float:
 def build(verbose: bool = False, extra_flags=None, out_dir: str = BUILD) -> str:
     """Compile every CUDA source for sm_103a and link the shared library; returns its path.
 
-    ``extra_flags`` (e.g. compile-time tuning macros) and ``out_dir`` build a variant elsewhere."""
+    ``extra_flags`` (e.g. compile-time tuning macros) and ``out_dir`` build a variant elsewhere.
+    Processes that build at the same time (one per rank) take turns on a lock file."""
     os.makedirs(out_dir, exist_ok=True)
+    import fcntl
+    with open(os.path.join(out_dir, ".build.lock"), "w") as lock:
+        fcntl.flock(lock, fcntl.LOCK_EX)
+        try:
+            return _build_locked(verbose, extra_flags, out_dir)
+        finally:
+            fcntl.flock(lock, fcntl.LOCK_UN)
+
+
+def _build_locked(verbose, extra_flags, out_dir):
     nvcc = _nvcc()
     srcs = sorted(glob.glob(os.path.join(CSRC, "*.cu")))
     hdr_time = _newest_header()
