@@ -53,7 +53,11 @@ int sgnet_forward(sgnet* net, const float* Z, int B, float* Y, void* stream);
 int sgnet_predict(sgnet* net, const float* Z, int B, double* X, void* stream);
 
 /* Loss of the batch (Z, T) and its gradient, kept inside the network (see sgnet_get).
- * If ``loss`` (host) is not NULL the call synchronises the stream and stores the loss. */
+ * If ``loss`` (host) is not NULL the call synchronises the stream and stores the loss; it returns
+ * SG_ERR_CUDA if a tensor-core kernel's bounded wait for its MMAs timed out.  With ``bf16`` = 1
+ * and the output layer fixed by sgnet_set_basis, the output layer and the back-propagation into
+ * the hidden layer run on the tensor cores (BF16 operands, FP32 accumulation; dY rounded to
+ * BF16), and the gradient's W3 and b3 parts are not formed (Adam leaves them fixed). */
 int sgnet_loss_grad(sgnet* net, const float* Z, const float* T, int B, float* loss, void* stream);
 
 /* One Adam step (beta1 0.9, beta2 0.999, eps 1e-8, bias-corrected) with the stored gradient. */
