@@ -10,7 +10,8 @@
  * Model: z_hat = (z - mu) / sd,  h1 = tanh(W1 z_hat + b1),  h2 = tanh(W2 h1 + b2),
  * y = W3 h2 + b3; loss = sum (y - t)^2 / (B D).  Parameters are FP32 (the master copy of Adam);
  * with ``bf16`` = 1 the output layer, which holds almost all parameters, computes from a BF16
- * copy of W3 with FP32 accumulation.  Flat parameter order: W1 (h1 x in, row-major), b1, W2
+ * copy of W3 with FP32 accumulation, on the tensor cores (tcgen05 MMAs, h2 rounded to BF16) when
+ * h2 <= 64.  Flat parameter order: W1 (h1 x in, row-major), b1, W2
  * (h2 x h1), b2, W3 (out x h2), b3.
  *
  * All array arguments are device pointers owned by the caller unless stated; calls are
