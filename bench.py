@@ -222,9 +222,21 @@ def main():
         O.ilu0_solve((Lo, Up, order), rb)
         ts.append(time.perf_counter() - t)
     bilu_node = sorted(ts)[reps // 2] / nodes9.shape[0]
+    # a whole small solve: the 16 x 16 mesh, M = 2, p = 2, sigma = 0.5, ell = 1, mean-based
+    # ILU(0) GMRES(30) to 1e-10 (median of 3, setup excluded)
+    p1 = O.build_problem(16, 2, 2, sigma=0.5, ell=1.0)
+    n1, q1 = p1.N, p1.P
+    ts, it1 = [], 0
+    for _ in range(3):
+        t = time.perf_counter()
+        _, inf1 = O.gmres(lambda v: O.sg_matvec(p1, v.reshape(n1, q1)).ravel(),
+                          lambda v: O.mean_precond(p1, v.reshape(n1, q1)).ravel(), p1.F.ravel(),
+                          restart=30, rtol=1e-10)
+        ts.append(time.perf_counter() - t)
+        it1 = inf1["iters"]
     print(json.dumps({"row_s_single": single, "row_s_allcores": multi, "block_solve_s": block,
                       "bilu_solve_s_per_node": bilu_node, "rows": nrows, "reps": reps,
-                      "cores": cores}))
+                      "cores": cores, "small_solve_s": sorted(ts)[1], "small_solve_iters": it1}))
 
 
 if __name__ == "__main__":
@@ -235,7 +247,9 @@ if __name__ == "__main__":
 def oracle_sample(nrows=48, reps=5, cores=None):
     """Run the FP64 oracle on a bounded sample of the c3 workload in a fresh process (started
     before any GPU work): sampled operator rows (median of ``reps``) on one core and on all
-    cores, and one c3-size ILU(0) block solve (median of ``reps``)."""
+    cores, one ILU(0) solve of the 256 x 256 mean stiffness and one application of the ILU(0) of
+    K on an 8 x 8 mesh (medians of ``reps``), and a whole small solve (16 x 16 mesh, M = 2,
+    p = 2, mean-based ILU(0) GMRES to 1e-10) on one core."""
     cores = cores or os.cpu_count() or 1
     import tempfile
     code = f"ROOT = {ROOT!r}\n" + ORACLE_SAMPLE
@@ -668,6 +682,10 @@ def main():
             "matvec_s_single_core": cpu["row_s_single"] * N,
             "matvec_s_all_cores": cpu["row_s_allcores"] * N,
             "block_solve_s": cpu["block_solve_s"],
+            "small_full_solve": {"s_single_core": cpu["small_solve_s"],
+                                 "iters": cpu["small_solve_iters"],
+                                 "config": "16x16 Q1, M=2, p=2, sigma=0.5, ell=1, mean-based "
+                                           "ILU(0) GMRES(30), rel. residual 1e-10"},
             "sample": (f"{cpu['rows']} sampled c3 operator rows (median of {cpu['reps']}) on one "
                        f"core and on all {cpu['cores']} cores, and one application of the "
                        f"ILU(0) of K on an 8 x 8 mesh at M=6, p=3 (median of {cpu['reps']}, per "
