@@ -692,7 +692,8 @@ def main():
                        f"node); a solve estimated from them for the GPU's {last['iters']} GMRES "
                        "iterations: per iteration one V-cycle (per level two applications of "
                        "the ILU(0) of K and two operator applications, levels 4x smaller each) "
-                       "and one outer operator application, in FP64")}
+                       "and one outer operator application, in FP64; beside it a whole small "
+                       "solve on one core (small_full_solve)")}
     if rank == 0:
         print(json.dumps(line), flush=True)
     h.close()
