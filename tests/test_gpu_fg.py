@@ -46,6 +46,7 @@ FG_CASES = [
     (dict(n=3, M=3, p=4, sigma=0.6, ell=0.6), "whole"),     # Q = 35: two warps per node
     (dict(n=3, M=4, p=4, sigma=0.6, ell=0.6), "whole"),     # Q = 70: three warps per node
     (dict(n=3, M=4, p=5, sigma=0.5, ell=0.8), "paper"),     # splits of 56 and 70 fields
+    (dict(n=4, M=6, p=3, sigma=1.0, ell=0.5), "paper"),     # the c3 chaos basis: one split of 84
 ]
 
 
