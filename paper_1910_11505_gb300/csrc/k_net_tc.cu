@@ -1,4 +1,5 @@
-// Output layer of the learned warm start on the 5th-generation tensor cores (tcgen05).
+// Output layer of the learned warm start, and the back-propagation through it into the hidden
+// layer, on the 5th-generation tensor cores (tcgen05).
 //
 // Y = H2 W3^T + b3 for a batch: H2 is B x h2 (h2 <= 64, FP32, rounded to BF16 here), W3 is
 // out x h2 (the network's BF16 copy), Y is B x out.  One CTA of 128 threads computes a 128 x 128
