@@ -11,6 +11,7 @@ import math
 import os
 
 import numpy as np
+import scipy.linalg
 import pytest
 import scipy.sparse
 import scipy.sparse.linalg
@@ -135,6 +136,49 @@ def test_kl_1d_against_nystrom_and_orthonormality():
                     lhs += np.sum(0.5 * (hi - lo) * w * np.exp(-np.abs(xv - ss) / ell)
                                   * O.kl_eval_1d(mode, ss))
                 assert abs(lhs - mode[2] * O.kl_eval_1d(mode, xv)) < 1e-12
+
+
+def _galerkin_kl(n, sigma, ell, M):
+    """The paper's Galerkin KL (Sec. 2.1): Q1 on an n x n mesh of the unit square, the covariance
+    integrated with 3 x 3 Gauss points per cell, C v = lam Mass v; top M eigenpairs (vectors at
+    the nodes, Mass-orthonormal)."""
+    g = np.array([-np.sqrt(0.6), 0.0, np.sqrt(0.6)])
+    w = np.array([5.0, 8.0, 5.0]) / 9.0
+    h, m = 1.0 / n, n + 1
+    pts, wts, cols, vals = [], [], [], []
+    for ey in range(n):
+        for ex in range(n):
+            for a in range(3):
+                for b in range(3):
+                    s, t = (g[a] + 1) / 2, (g[b] + 1) / 2
+                    pts.append(((ex + s) * h, (ey + t) * h))
+                    wts.append(w[a] * w[b] * h * h / 4)
+                    cols.append([ex + m * ey, ex + 1 + m * ey, ex + m * (ey + 1), ex + 1 + m * (ey + 1)])
+                    vals.append([(1 - s) * (1 - t), s * (1 - t), (1 - s) * t, s * t])
+    pts, wts = np.array(pts), np.array(wts)
+    Phi = np.zeros((len(pts), m * m))
+    for q in range(len(pts)):
+        Phi[q, cols[q]] = vals[q]
+    dx = np.abs(pts[:, None, 0] - pts[None, :, 0]) + np.abs(pts[:, None, 1] - pts[None, :, 1])
+    WP = wts[:, None] * Phi
+    lam, V = scipy.linalg.eigh(WP.T @ (sigma ** 2 * np.exp(-dx / ell)) @ WP, WP.T @ Phi)
+    return lam[::-1][:M], V[:, ::-1][:, :M]
+
+
+def test_kl_closed_form_is_the_limit_of_the_galerkin_kl():
+    # the paper computes the KL modes by a Galerkin FE eigenproblem; for the separable exponential
+    # covariance the closed form is its mesh limit: eigenvalues converge at O(h^2) and the first
+    # eigenfunction agrees at the nodes (reading R9: the closed form stands for the Galerkin KL)
+    kl = O.kl_modes_2d(1.0, 0.5, 6)
+    errs = [np.abs(_galerkin_kl(n, 1.0, 0.5, 6)[0] - kl.lam) / kl.lam for n in (4, 8, 16)]
+    assert np.all(errs[2] < 3e-3)
+    assert 3.0 < errs[0][0] / errs[1][0] < 5.0 and 3.0 < errs[1][0] / errs[2][0] < 5.0
+    _, V = _galerkin_kl(16, 1.0, 0.5, 1)
+    x = np.arange(17) / 16.0
+    X1, X2 = np.meshgrid(x, x)          # node id = x1 index + 17 * x2 index
+    b1 = O.kl_fields(kl, X1.ravel(), X2.ravel())[0] / np.sqrt(kl.lam[0])
+    v = V[:, 0] * np.sign(V[:, 0] @ b1)
+    assert np.abs(v - b1).max() <= 5e-3 * np.abs(b1).max()
 
 
 def test_kl_trace_sums_to_one():
