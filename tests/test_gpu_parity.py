@@ -22,6 +22,9 @@ CASES = [
     dict(n=5, M=1, p=4, sigma=1.0, ell=0.5),
     dict(n=9, M=4, p=1, sigma=0.3, ell=2.0, f=2.5),
     dict(n=3, M=2, p=0, sigma=0.4, ell=1.0),
+    # the paper's own data: a_min = 0.01, correlation length 0.1, coefficient degree q apart
+    # from 2p (reading R9)
+    dict(n=8, M=3, p=2, q=3, sigma=0.5, ell=0.1, a_min=0.01),
 ]
 
 
@@ -33,7 +36,7 @@ def _built():
 
 
 def _oracle(case):
-    kw = {k: case[k] for k in ("sigma", "ell", "a_min", "mu", "f") if k in case}
+    kw = {k: case[k] for k in ("q", "sigma", "ell", "a_min", "mu", "f") if k in case}
     return O.build_problem(case["n"], case["M"], case["p"], **kw)
 
 
